@@ -1,0 +1,186 @@
+/*
+ * holo.h - C ABI of the GB300 holography functional library.
+ *
+ * The library evaluates, on one GPU, the multi-distance cone-beam holography functional
+ * with simultaneous probe retrieval of Nikitin et al., "X-ray nano-holotomography
+ * reconstruction with simultaneous probe retrieval" (Sec. 2), and its gradients:
+ *
+ *   u_kj  = L_kj(psi_k) = C D_{zeta_j/m~_j^2}( D_{omega_j}(q) * M_{1/m~_j}(S_{t_kj} psi_k) )
+ *                                                   (Eq. fwd_model_cone3 with the shifts of Eq. min1)
+ *   F2    = sum_kj || |u_kj| - sqrt(d~_kj) ||^2 + w_ref || |C D_{zeta_0} q| - sqrt(d~^r) ||^2
+ *                                                   (Eq. min1)
+ *   grad_psi_k F2 = 2 sum_j L*_kj( u - sqrt(d~) u/|u| )        (Eq. gradpsi)
+ *   grad_q F2     = 2 ( sum_kj Q*_kj(...) + D*_{zeta_0}(...) ) (probe gradient after Eq. gradpsi)
+ *
+ * with m~_j = z_j/z_0, omega_j = (z_j - z_0)/m~_j, zeta_j = z_j (Z - z_j)/Z (Sec. 2;
+ * Theorem t3 of Appendix A), D_z Fresnel propagation (Appendix A, Eq. defPz/defGz), M the
+ * dilation and S the lateral shift.  Discretisation (the paper gives none):
+ *   - psi_k is n x n; q and all propagations live on a P x P grid (P = 2n by default);
+ *     the detector is the central n x n crop C of the P x P grid.
+ *   - D_z multiplies the DFT of the P x P field by exp(-i pi lambda z (fx^2 + fy^2)),
+ *     f = k/(P pixel), k in [-P/2, P/2).
+ *   - M_{1/m~} S_t psi is bilinear interpolation of psi at psi-coordinate m~ x - t
+ *     (pixels; pixel centres at i - n/2 for psi and i - P/2 for the P x P grid), with
+ *     the value `ext` outside psi's n x n domain.  Gradients use its exact transpose.
+ *   - Gradients are real gradients for <a, b> = Re sum conj(a) b: dF(x; h) = Re <grad, h>.
+ *
+ * Conventions for every entry point:
+ *   - Complex arrays are interleaved complex64 (float re, float im), row-major, densely
+ *     packed.  "dev" pointers are CUDA device pointers on the context's device; "host"
+ *     pointers are CPU memory (pinned memory makes copies faster).
+ *   - The caller owns every array it passes; the library never frees them.  Device
+ *     arrays registered with holo_set_data must stay valid until the next holo_set_data
+ *     or holo_destroy.  The context owns only its workspace (probe planes, tables,
+ *     per-plane intermediates, partial sums).
+ *   - Work is issued on the stream given to holo_create.  Calls that return a host
+ *     scalar (loss, inner product) synchronise that stream before returning; all other
+ *     calls are asynchronous with respect to the host.
+ *   - Every entry point returns a holo_status and never aborts the process.  Invalid
+ *     arguments are rejected before any device work (HOLO_ERR_ARG); CUDA failures return
+ *     HOLO_ERR_CUDA (details in holo_last_error).  Calls in the wrong order (e.g. a
+ *     gradient before holo_set_probe) return HOLO_ERR_STATE.
+ */
+#ifndef HOLO_H
+#define HOLO_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct holo_ctx holo_ctx;
+
+typedef enum {
+  HOLO_OK = 0,
+  HOLO_ERR_ARG = 1,         /* invalid argument (null pointer, bad size, bad geometry) */
+  HOLO_ERR_CUDA = 2,        /* a CUDA runtime call or kernel launch failed */
+  HOLO_ERR_OOM = 3,         /* workspace allocation failed */
+  HOLO_ERR_TIMEOUT = 4,     /* a bounded device wait gave up */
+  HOLO_ERR_STATE = 5,       /* call order: shifts / data / probe not set yet */
+  HOLO_ERR_NUMERIC = 6,     /* non-finite loss */
+  HOLO_ERR_UNSUPPORTED = 7  /* valid but unsupported size (e.g. P not a power of two) */
+} holo_status;
+
+#define HOLO_MAX_DIST 8
+
+/* Flags of holo_gradient / holo_gradient_host. */
+#define HOLO_ACCUMULATE 1u   /* add to grad_psi, grad_q and *loss instead of overwriting */
+
+/*
+ * Instrument geometry and discretisation (Table 1 lists the paper's instrument).
+ *   n           psi / detector side in pixels; even, 16 <= n <= pad.
+ *   pad         P, the side of the grid on which q lives and fields propagate; 0 means
+ *               2n.  Supported: powers of two 16 .. 4096 with P - n even.
+ *   n_angles    N_theta: number of projection angles of the whole problem (indexing of
+ *               shifts and data).
+ *   n_dist      N_z: number of sample planes, 1 .. HOLO_MAX_DIST.
+ *   chunk       maximum angles per forward / gradient call (workspace size); 0 means
+ *               n_angles.
+ *   wavelength  lambda [m]; pixel: object-plane pixel size [m] (detector pixel / m0);
+ *   Z           focus-to-detector distance [m]; z[j]: focus-to-sample distances [m],
+ *               0 < z[0] < z[1] < ... < Z.
+ *   w_ref       weight of the reference-image term of Eq. min1 (0 disables it).
+ *   ext         free-space value of the resample: 1 (transmittance of empty space) or 0
+ *               (a test mode in which the model is bilinear in (psi, q)).
+ */
+typedef struct {
+  int n;
+  int pad;
+  int n_angles;
+  int n_dist;
+  int chunk;
+  double wavelength;
+  double pixel;
+  double Z;
+  double z[HOLO_MAX_DIST];
+  double w_ref;
+  double ext;
+} holo_geometry;
+
+/* Create a context on the current CUDA device.  `stream` is a cudaStream_t (NULL: the
+ * legacy default stream).  Derives m~_j, omega_j, zeta_j (Sec. 2) and builds the FP64
+ * chirp and twiddle tables.  On failure *out is set to NULL. */
+holo_status holo_create(const holo_geometry* geo, void* stream, holo_ctx** out);
+
+/* Free the context's workspace.  NULL is accepted. */
+holo_status holo_destroy(holo_ctx* ctx);
+
+/* Sample shifts t_kj of Eq. min1 (S_{t_kj} psi_k), host float [n_angles][n_dist][2] as
+ * (t_y, t_x) in psi pixels, copied.  Sizes the per-plane workspace; must precede
+ * holo_forward / holo_gradient.  Probe shifts s_kj are zero (Sec. 2: they can be moved
+ * onto psi and the data). */
+holo_status holo_set_shifts(holo_ctx* ctx, const float* t_host);
+
+/* Register the data: sqrt_d (dev float [n_angles][n_dist][n][n]) holds sqrt(d~_kj), the
+ * amplitudes of the data rescaled to the plane-0 grid (d~ = m0^2 M_{1/m0} d, Sec. 2);
+ * sqrt_dref (dev float [n][n], may be NULL when w_ref = 0) holds sqrt(d~^r).  Not
+ * copied: both must stay valid while used.  sqrt_d may be NULL when every evaluation
+ * passes its chunk's data through holo_gradient_host (only the reference is kept). */
+holo_status holo_set_data(holo_ctx* ctx, const float* sqrt_d, const float* sqrt_dref);
+
+/* Set the probe q (dev complex64 [P][P]) and compute its propagations p_j = D_{omega_j} q
+ * (Eq. fwd_model_cone3) and the reference field C D_{zeta_0} q (copied into the
+ * workspace; q itself is not retained). */
+holo_status holo_set_probe(holo_ctx* ctx, const void* q);
+
+/* Forward model and F2 restricted to angles [k0, k0 + nk) (Eq. fwd_model_cone3,
+ * Eq. min1).  psi: dev complex64 [nk][n][n].  u_out: dev complex64 [nk][n_dist][n][n]
+ * receiving u_kj, or NULL.  loss (host, may be NULL): sum over the chunk's planes of
+ * || |u| - sqrt(d~) ||^2, plus the reference term when k0 == 0.  Requires 1 <= nk <=
+ * chunk and k0 + nk <= n_angles. */
+holo_status holo_forward(holo_ctx* ctx, int k0, int nk, const void* psi, void* u_out,
+                         double* loss);
+
+/* F2 and its gradients over angles [k0, k0 + nk) (Eq. gradpsi and the probe gradient
+ * after it).  psi: dev complex64 [nk][n][n]; grad_psi: dev complex64 [nk][n][n];
+ * grad_q: dev complex64 [P][P] (the chunk's contribution; the reference term is included
+ * when k0 == 0).  loss: host, may be NULL.  flags: HOLO_ACCUMULATE adds to grad_psi,
+ * grad_q and *loss (to sum chunks), otherwise they are overwritten. */
+holo_status holo_gradient(holo_ctx* ctx, int k0, int nk, const void* psi, double* loss,
+                          void* grad_psi, void* grad_q, unsigned flags);
+
+/* holo_gradient with host buffers: copies psi_host ([nk][n][n]) and, when not NULL,
+ * sqrt_d_host (float [nk][n_dist][n][n], the chunk's data, used instead of the data
+ * registered with holo_set_data) and q_host ([P][P], then holo_set_probe) to the
+ * device, evaluates, and copies grad_psi_host ([nk][n][n]) and grad_q_host ([P][P])
+ * back.  HOLO_ACCUMULATE applies to *loss only.  Staging buffers are allocated on the
+ * first call and kept. */
+holo_status holo_gradient_host(holo_ctx* ctx, int k0, int nk, const void* psi_host,
+                               const float* sqrt_d_host, const void* q_host, double* loss,
+                               void* grad_psi_host, void* grad_q_host, unsigned flags);
+
+/* Fresnel propagation D_z of a P x P field (Appendix A, Eq. defGz): out = D_z(in),
+ * dev complex64 [P][P] each (in == out allowed). */
+holo_status holo_propagate(holo_ctx* ctx, const void* in, void* out, double z);
+
+/* Re <a, b> = Re sum conj(a_i) b_i over n_c64 complex64 elements (dev), accumulated in
+ * FP64: the inner products of the Dai-Yuan coefficient (Eq. DaiYuan2) and the step
+ * length. */
+holo_status holo_dot(holo_ctx* ctx, const void* a, const void* b, long long n_c64,
+                     double* re_out);
+
+/* x += gamma * eta over n_c64 complex64 elements (dev): the CG update
+ * psi^(m+1) = psi^(m) + gamma eta (Sec. 2). */
+holo_status holo_step(holo_ctx* ctx, void* x, const void* eta, double gamma, long long n_c64);
+
+/* eta = -g + beta * eta over n_c64 complex64 elements (dev): the conjugate direction of
+ * Eq. DaiYuan2 (beta = 0 restarts with the steepest-descent direction). */
+holo_status holo_direction(holo_ctx* ctx, void* eta, const void* g, double beta,
+                           long long n_c64);
+
+/* Bytes of device workspace currently held by the context. */
+holo_status holo_workspace_bytes(const holo_ctx* ctx, long long* bytes);
+
+/* Kernel launches issued by the context since creation (a counter for benchmarks). */
+holo_status holo_launch_count(const holo_ctx* ctx, long long* count);
+
+/* Static text for a status code. */
+const char* holo_status_string(holo_status s);
+
+/* Text of the last error recorded in ctx (never NULL; "" when none). */
+const char* holo_last_error(const holo_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* HOLO_H */

@@ -30,6 +30,7 @@ R8  z_j are the focus-to-sample distances; m~_j = z_j/z_0, omega_j = (z_j-z_0)/m
 from dataclasses import dataclass, field
 
 import numpy as np
+import scipy.fft as sfft  # library FFT primitive (multi-threaded), as one step of D_z
 
 
 @dataclass(frozen=True)
@@ -91,7 +92,7 @@ def propagate(x, z, wavelength, dx):
     assert x.shape[-2] == P
     f = spatial_freq(P, dx)
     H = np.exp(-1j * np.pi * wavelength * z * (f[:, None] ** 2 + f[None, :] ** 2))
-    return np.fft.ifft2(np.fft.fft2(x) * H)
+    return sfft.ifft2(sfft.fft2(x, workers=-1) * H, workers=-1)
 
 
 def crop(x, n):

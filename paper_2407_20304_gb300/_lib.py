@@ -1,0 +1,81 @@
+"""ctypes loader and prototypes of libholo.so (the C ABI declared in include/holo.h).
+
+There is no fallback: if the compiled library is missing the import of an operation
+fails with an error that says how to build it.
+"""
+
+import ctypes
+import os
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "_build", "libholo.so")
+MAX_DIST = 8
+ACCUMULATE = 1
+
+STATUS = {0: "HOLO_OK", 1: "HOLO_ERR_ARG", 2: "HOLO_ERR_CUDA", 3: "HOLO_ERR_OOM",
+          4: "HOLO_ERR_TIMEOUT", 5: "HOLO_ERR_STATE", 6: "HOLO_ERR_NUMERIC",
+          7: "HOLO_ERR_UNSUPPORTED"}
+
+# Every symbol declared in include/holo.h.
+EXPORTS = ("holo_create", "holo_destroy", "holo_set_shifts", "holo_set_data", "holo_set_probe",
+           "holo_forward", "holo_gradient", "holo_gradient_host", "holo_propagate", "holo_dot",
+           "holo_step", "holo_direction", "holo_workspace_bytes", "holo_launch_count",
+           "holo_status_string", "holo_last_error")
+
+
+class HoloGeometry(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int), ("pad", ctypes.c_int), ("n_angles", ctypes.c_int),
+                ("n_dist", ctypes.c_int), ("chunk", ctypes.c_int),
+                ("wavelength", ctypes.c_double), ("pixel", ctypes.c_double),
+                ("Z", ctypes.c_double), ("z", ctypes.c_double * MAX_DIST),
+                ("w_ref", ctypes.c_double), ("ext", ctypes.c_double)]
+
+
+class HoloError(RuntimeError):
+    def __init__(self, status, where, detail=""):
+        self.status = status
+        name = STATUS.get(status, str(status))
+        super().__init__(f"{where}: {name}" + (f" ({detail})" if detail else ""))
+
+
+_lib = None
+
+
+def load():
+    """Load libholo.so once; raise if it has not been built."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise RuntimeError(f"{LIB_PATH} is missing: build it with "
+                           "`python -c 'import __graft_entry__ as g; g.build()'`")
+    lib = ctypes.CDLL(LIB_PATH)
+    P = ctypes.c_void_p
+    I, LL, D = ctypes.c_int, ctypes.c_longlong, ctypes.c_double
+    U = ctypes.c_uint
+    sigs = {
+        "holo_create": [ctypes.POINTER(HoloGeometry), P, ctypes.POINTER(P)],
+        "holo_destroy": [P],
+        "holo_set_shifts": [P, P],
+        "holo_set_data": [P, P, P],
+        "holo_set_probe": [P, P],
+        "holo_forward": [P, I, I, P, P, ctypes.POINTER(D)],
+        "holo_gradient": [P, I, I, P, ctypes.POINTER(D), P, P, U],
+        "holo_gradient_host": [P, I, I, P, P, P, ctypes.POINTER(D), P, P, U],
+        "holo_propagate": [P, P, P, D],
+        "holo_dot": [P, P, P, LL, ctypes.POINTER(D)],
+        "holo_step": [P, P, P, D, LL],
+        "holo_direction": [P, P, P, D, LL],
+        "holo_workspace_bytes": [P, ctypes.POINTER(LL)],
+        "holo_launch_count": [P, ctypes.POINTER(LL)],
+    }
+    for name, args in sigs.items():
+        fn = getattr(lib, name)
+        fn.argtypes = args
+        fn.restype = ctypes.c_int
+    lib.holo_status_string.argtypes = [ctypes.c_int]
+    lib.holo_status_string.restype = ctypes.c_char_p
+    lib.holo_last_error.argtypes = [P]
+    lib.holo_last_error.restype = ctypes.c_char_p
+    _lib = lib
+    return lib

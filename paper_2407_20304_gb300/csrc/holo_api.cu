@@ -1,0 +1,687 @@
+// C ABI of the holography functional library (declared in include/holo.h).
+//
+// Host side: argument validation, FP64 geometry and tables, per-plane resample boxes,
+// workspace management, and the launch sequence of one forward / gradient evaluation.
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "holo.h"
+#include "holo_internal.h"
+
+namespace holo {
+const Ops* ops_16();
+const Ops* ops_32();
+const Ops* ops_64();
+const Ops* ops_128();
+const Ops* ops_256();
+const Ops* ops_512();
+const Ops* ops_1024();
+const Ops* ops_2048();
+const Ops* ops_4096();
+
+const Ops* ops_for(int P) {
+  switch (P) {
+    case 16: return ops_16();
+    case 32: return ops_32();
+    case 64: return ops_64();
+    case 128: return ops_128();
+    case 256: return ops_256();
+    case 512: return ops_512();
+    case 1024: return ops_1024();
+    case 2048: return ops_2048();
+    case 4096: return ops_4096();
+    default: return nullptr;
+  }
+}
+}  // namespace holo
+
+using holo::LineArgs;
+using holo::PassArgs;
+using holo::PlaneDesc;
+
+struct holo_ctx {
+  holo_geometry geo{};
+  int n = 0, P = 0, J = 0, K = 0, chunk = 0;
+  float ext = 1.f;
+  double wref = 0.0;
+  cudaStream_t stream = nullptr;
+  const holo::Ops* ops = nullptr;
+  double mt[HOLO_MAX_DIST] = {}, omega[HOLO_MAX_DIST] = {}, zeta[HOLO_MAX_DIST] = {},
+         zhat[HOLO_MAX_DIST] = {};
+  // tables
+  float2* d_tw = nullptr;
+  float2* d_chirp_zhat = nullptr;   // [J][P]
+  float2* d_chirp_omega = nullptr;  // [J][P]
+  float2* d_chirp_zeta0 = nullptr;  // [P]
+  float2* d_chirp_tmp = nullptr;    // [P]
+  // planes
+  std::vector<PlaneDesc> planes;
+  PlaneDesc* d_planes = nullptr;
+  bool have_shifts = false;
+  int maxbys = 0, maxbxs = 0;
+  // data
+  const float* sqrt_d = nullptr;
+  const float* sqrt_dref = nullptr;
+  bool have_data = false;
+  // probe
+  float2* d_pj = nullptr;  // [J][P][P]
+  float2* d_b = nullptr;   // [n][n]
+  bool have_probe = false;
+  // per-plane workspace
+  float2* ybuf = nullptr;
+  long long ystride = 0;
+  float2* rbuf = nullptr;
+  float2* gkbuf = nullptr;
+  long long gkstride = 0;
+  size_t ws_bytes_planes = 0;
+  // evaluation scratch
+  float2* d_scratch = nullptr;  // P*P
+  float2* d_Gp = nullptr;       // P*P
+  float2* d_T = nullptr;        // n*n
+  float2* d_rref = nullptr;     // n*n
+  double* d_part = nullptr;
+  long long part_cap = 0;
+  double* d_red = nullptr;      // 4 doubles
+  double* h_red = nullptr;      // pinned, 4 doubles
+  // host-buffer staging
+  float2* s_psi = nullptr;
+  float2* s_gpsi = nullptr;
+  float* s_data = nullptr;
+  float2* s_q = nullptr;
+  float2* s_gq = nullptr;
+  long long bytes = 0;
+  long long launches = 0;
+  std::string err;
+};
+
+namespace {
+
+constexpr int kRefBlocks = 64;
+
+holo_status fail(holo_ctx* c, holo_status s, const std::string& msg) {
+  if (c) c->err = msg;
+  return s;
+}
+
+#define HOLO_CK(ctx, call)                                                               \
+  do {                                                                                   \
+    cudaError_t e_ = (call);                                                             \
+    if (e_ != cudaSuccess)                                                               \
+      return fail((ctx), HOLO_ERR_CUDA,                                                  \
+                  std::string(#call) + ": " + cudaGetErrorString(e_));                   \
+  } while (0)
+
+#define HOLO_LAUNCH(ctx, call)   \
+  do {                           \
+    HOLO_CK(ctx, call);          \
+    (ctx)->launches++;           \
+  } while (0)
+
+holo_status dalloc(holo_ctx* c, void** p, size_t bytes) {
+  *p = nullptr;
+  if (bytes == 0) return HOLO_OK;
+  cudaError_t e = cudaMalloc(p, bytes);
+  if (e != cudaSuccess) {
+    *p = nullptr;
+    cudaGetLastError();
+    return fail(c, e == cudaErrorMemoryAllocation ? HOLO_ERR_OOM : HOLO_ERR_CUDA,
+                std::string("cudaMalloc(") + std::to_string(bytes) + "): " + cudaGetErrorString(e));
+  }
+  c->bytes += (long long)bytes;
+  return HOLO_OK;
+}
+
+void dfree(holo_ctx* c, void* p, size_t bytes) {
+  if (p) {
+    cudaFree(p);
+    c->bytes -= (long long)bytes;
+  }
+}
+
+bool is_pow2(int x) { return x > 0 && (x & (x - 1)) == 0; }
+
+// exp(-i pi lambda z f^2) / P with f = k/(P dx), k in [-P/2, P/2)  (reading of D_z), FP64.
+std::vector<float2> chirp_table(int P, double lambda, double dx, double z) {
+  std::vector<float2> c(P);
+  const double pi = 3.14159265358979323846;
+  for (int k = 0; k < P; ++k) {
+    const double kk = k < P / 2 ? k : k - P;
+    const double f = kk / (P * dx);
+    const double ph = -pi * lambda * z * f * f;
+    c[k] = make_float2((float)(std::cos(ph) / P), (float)(std::sin(ph) / P));
+  }
+  return c;
+}
+
+// Twiddle table in the layout of holo_fft.cuh: radix-16 stage s with M(s) = P/16^(s+1) > 1
+// contributes entries [(k-1) M + mu] = exp(-2 pi i mu k 16^s / P), k = 1..15.
+std::vector<float2> twiddle_table(int P) {
+  std::vector<float2> tw;
+  int log2p = 0;
+  while ((1 << log2p) < P) ++log2p;
+  const int n16 = log2p / 4;
+  const double pi = 3.14159265358979323846;
+  long long L = 1;
+  for (int s = 0; s < n16; ++s) {
+    const long long M = P / (L * 16);
+    if (M > 1)
+      for (int k = 1; k < 16; ++k)
+        for (long long mu = 0; mu < M; ++mu) {
+          const double a = -2.0 * pi * (double)(mu * k * L) / P;
+          tw.push_back(make_float2((float)std::cos(a), (float)std::sin(a)));
+        }
+    L *= 16;
+  }
+  return tw;
+}
+
+// m~ = hi + lo with hi holding 24 - bits significant bits, so that hi * x is exact in FP32
+// for |x| < 2^bits.
+void split_mt(double mt, int P, float* hi, float* lo) {
+  int bits = 0;
+  while ((1 << bits) <= P / 2) ++bits;
+  const int sig = 24 - bits;
+  int e;
+  std::frexp(mt, &e);  // mt = f * 2^e, f in [0.5, 1)
+  const double scale = std::ldexp(1.0, sig - e);
+  const double h = std::nearbyint(mt * scale) / scale;
+  *hi = (float)h;
+  *lo = (float)(mt - h);
+}
+
+// Bounding box on the P-grid of the positions whose bilinear taps can reach psi's domain:
+// xi = m~ (X - P/2) - t + n/2 in (-1, n), widened by one pixel each side.
+void axis_box(double mt, double t, int n, int P, int* lo, int* len) {
+  const double a = P / 2 + (t - n / 2 - 1.0) / mt;
+  const double b = P / 2 + (t + n / 2) / mt;
+  int s = (int)std::floor(a) - 1, e = (int)std::ceil(b) + 2;
+  s = std::max(s, 0);
+  e = std::min(e, P);
+  *lo = s;
+  *len = std::max(e - s, 0);
+}
+
+holo_status upload(holo_ctx* c, void* dst, const void* src, size_t bytes) {
+  HOLO_CK(c, cudaMemcpyAsync(dst, src, bytes, cudaMemcpyHostToDevice, c->stream));
+  HOLO_CK(c, cudaStreamSynchronize(c->stream));
+  return HOLO_OK;
+}
+
+LineArgs line_args() {
+  LineArgs a;
+  std::memset(&a, 0, sizeof(a));
+  a.alpha = 1.f;
+  return a;
+}
+
+// 2D D_z of a field given as `rows` rows of width `w` occupying P-grid rows
+// [r_lo, r_lo + rows) and columns [c_lo, c_lo + w); the result keeps P-grid rows
+// [or_lo, or_lo + orows) and columns [oc_lo, oc_lo + ocols), written densely with row
+// pitch ocols, as out = alpha D(in) (+ out when accumulate).  Rows first, then columns.
+holo_status dstep2d(holo_ctx* c, const float2* in, int r_lo, int rows, int c_lo, int w,
+                    float2* out, int or_lo, int orows, int oc_lo, int ocols, const float2* chirp,
+                    int conj, float alpha, int accumulate) {
+  const int P = c->P;
+  LineArgs a = line_args();
+  a.in = in;
+  a.in_line_stride = w;
+  a.in_step = 1;
+  a.in_lo = c_lo;
+  a.in_len = w;
+  a.out = c->d_scratch;  // [rows][ocols]
+  a.out_line_stride = ocols;
+  a.out_step = 1;
+  a.out_lo = oc_lo;
+  a.out_len = ocols;
+  a.nlines = rows;
+  a.chirp = chirp;
+  a.conj_chirp = conj;
+  HOLO_LAUNCH(c, c->ops->rows(a, c->d_tw, c->stream));
+  LineArgs b = line_args();
+  b.in = c->d_scratch;
+  b.in_line_stride = 1;
+  b.in_step = ocols;
+  b.in_lo = r_lo;
+  b.in_len = rows;
+  b.out = out;
+  b.out_line_stride = 1;
+  b.out_step = ocols;
+  b.out_lo = or_lo;
+  b.out_len = orows;
+  b.nlines = ocols;
+  b.chirp = chirp;
+  b.conj_chirp = conj;
+  b.alpha = alpha;
+  b.accumulate = accumulate;
+  (void)P;
+  HOLO_LAUNCH(c, c->ops->cols(b, c->d_tw, c->stream));
+  return HOLO_OK;
+}
+
+holo_status check_chunk(holo_ctx* c, int k0, int nk) {
+  if (!c) return HOLO_ERR_ARG;
+  if (nk < 1 || nk > c->chunk || k0 < 0 || k0 + nk > c->K)
+    return fail(c, HOLO_ERR_ARG, "chunk [k0, k0+nk) outside [0, n_angles) or nk > chunk");
+  if (!c->have_shifts) return fail(c, HOLO_ERR_STATE, "holo_set_shifts not called");
+  if (!c->have_data) return fail(c, HOLO_ERR_STATE, "holo_set_data not called");
+  if (!c->have_probe) return fail(c, HOLO_ERR_STATE, "holo_set_probe not called");
+  return HOLO_OK;
+}
+
+PassArgs pass_args(holo_ctx* c, int k0, int nk, const void* psi) {
+  PassArgs a;
+  std::memset(&a, 0, sizeof(a));
+  a.n = c->n;
+  a.P = c->P;
+  a.J = c->J;
+  a.k0 = k0;
+  a.nk = nk;
+  a.ext = c->ext;
+  a.planes = c->d_planes;
+  a.psi = (const float2*)psi;
+  a.pj = c->d_pj;
+  a.bref = c->d_b;
+  a.sqrt_d = c->sqrt_d;
+  a.data_k0 = 0;
+  a.chirp_zhat = c->d_chirp_zhat;
+  a.ybuf = c->ybuf;
+  a.ystride = c->ystride;
+  a.rbuf = c->rbuf;
+  a.gkbuf = c->gkbuf;
+  a.gkstride = c->gkstride;
+  a.loss_part = c->d_part;
+  a.twiddles = c->d_tw;
+  int mb = 0;
+  for (int k = k0; k < k0 + nk; ++k)
+    for (int j = 0; j < c->J; ++j) mb = std::max(mb, c->planes[(size_t)k * c->J + j].bys);
+  a.max_box_rows = std::max(mb, 1);
+  return a;
+}
+
+// Passes A, B (and C, D for gradients), loss partial sums into d_red[0], reference term
+// into d_red[1] (only when k0 == 0 and w_ref != 0).
+holo_status run_eval(holo_ctx* c, PassArgs& a, bool gradient, float2* grad_q, unsigned flags) {
+  const int nbx = c->ops->pass_b_blocks_x(c->n);
+  const long long nparts = (long long)nbx * a.nk * c->J;
+  HOLO_LAUNCH(c, c->ops->pass_a(a, c->stream));
+  HOLO_LAUNCH(c, c->ops->pass_b(a, gradient ? 1 : 0, nbx, c->stream));
+  HOLO_LAUNCH(c, holo::launch_sum_f64(c->d_part, (int)nparts, c->d_red, 0, c->stream));
+  const bool ref = a.k0 == 0 && c->wref != 0.0;
+  const long long n2 = (long long)c->n * c->n;
+  if (ref) {
+    HOLO_LAUNCH(c, holo::launch_ref_residual(c->d_b, c->sqrt_dref, n2, c->d_rref,
+                                             c->d_part + nparts, kRefBlocks, c->stream));
+    HOLO_LAUNCH(c, holo::launch_sum_f64(c->d_part + nparts, kRefBlocks, c->d_red + 1, 0,
+                                        c->stream));
+  } else {
+    HOLO_CK(c, cudaMemsetAsync(c->d_red + 1, 0, sizeof(double), c->stream));
+  }
+  if (!gradient) return HOLO_OK;
+  HOLO_LAUNCH(c, c->ops->pass_c(a, c->stream));
+  HOLO_LAUNCH(c, holo::launch_pass_d(a, c->stream));
+  // grad_q = 2 [ D_{-zeta_0}( C* (ext sum_kj r_kj + w_ref r_ref) ) + sum_j D_{-omega_j}(G'_j) ]
+  // (zhat_j + omega_j = zeta_0 merges the ext-part of every plane into one propagation).
+  HOLO_LAUNCH(c, holo::launch_sum_residuals(c->rbuf, a.nk * c->J, n2, ref ? c->d_rref : nullptr,
+                                            c->ext, (float)c->wref, c->d_T, c->stream));
+  const int P = c->P, n = c->n, lo = P / 2 - n / 2;
+  const int acc = (flags & HOLO_ACCUMULATE) ? 1 : 0;
+  holo_status st = dstep2d(c, c->d_T, lo, n, lo, n, grad_q, 0, P, 0, P, c->d_chirp_zeta0, 1, 2.f,
+                           acc);
+  if (st != HOLO_OK) return st;
+  for (int j = 0; j < c->J; ++j) {
+    int r0 = P, r1 = 0, c0 = P, c1 = 0;
+    for (int k = a.k0; k < a.k0 + a.nk; ++k) {
+      const PlaneDesc& d = c->planes[(size_t)k * c->J + j];
+      if (d.bys <= 0 || d.bxs <= 0) continue;
+      r0 = std::min(r0, d.by0);
+      r1 = std::max(r1, d.by0 + d.bys);
+      c0 = std::min(c0, d.bx0);
+      c1 = std::max(c1, d.bx0 + d.bxs);
+    }
+    if (r1 <= r0 || c1 <= c0) continue;
+    HOLO_LAUNCH(c, holo::launch_reduce_g(a, c->d_Gp, j, r0, r1 - r0, c0, c1 - c0, c->stream));
+    st = dstep2d(c, c->d_Gp, r0, r1 - r0, c0, c1 - c0, grad_q, 0, P, 0, P,
+                 c->d_chirp_omega + (size_t)j * P, 1, 2.f, 1);
+    if (st != HOLO_OK) return st;
+  }
+  return HOLO_OK;
+}
+
+holo_status read_loss(holo_ctx* c, double* loss, unsigned flags) {
+  HOLO_CK(c, cudaMemcpyAsync(c->h_red, c->d_red, 2 * sizeof(double), cudaMemcpyDeviceToHost,
+                             c->stream));
+  HOLO_CK(c, cudaStreamSynchronize(c->stream));
+  const double l = c->h_red[0] + c->wref * c->h_red[1];
+  if (loss) *loss = (flags & HOLO_ACCUMULATE) ? *loss + l : l;
+  if (!std::isfinite(l)) return fail(c, HOLO_ERR_NUMERIC, "non-finite loss");
+  return HOLO_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* holo_status_string(holo_status s) {
+  switch (s) {
+    case HOLO_OK: return "ok";
+    case HOLO_ERR_ARG: return "invalid argument";
+    case HOLO_ERR_CUDA: return "CUDA error";
+    case HOLO_ERR_OOM: return "out of device memory";
+    case HOLO_ERR_TIMEOUT: return "device wait timed out";
+    case HOLO_ERR_STATE: return "call order (shifts, data or probe not set)";
+    case HOLO_ERR_NUMERIC: return "non-finite result";
+    case HOLO_ERR_UNSUPPORTED: return "unsupported size";
+  }
+  return "unknown status";
+}
+
+const char* holo_last_error(const holo_ctx* ctx) { return ctx ? ctx->err.c_str() : ""; }
+
+holo_status holo_create(const holo_geometry* geo, void* stream, holo_ctx** out) {
+  if (!out) return HOLO_ERR_ARG;
+  *out = nullptr;
+  if (!geo) return HOLO_ERR_ARG;
+  const int n = geo->n, P = geo->pad ? geo->pad : 2 * geo->n, J = geo->n_dist;
+  if (n < 16 || (n & 1) || n > P || ((P - n) & 1)) return HOLO_ERR_ARG;
+  if (geo->n_angles < 1 || J < 1 || J > HOLO_MAX_DIST) return HOLO_ERR_ARG;
+  if (geo->chunk < 0 || geo->chunk > geo->n_angles) return HOLO_ERR_ARG;
+  if (!(geo->wavelength > 0) || !(geo->pixel > 0) || !(geo->Z > 0)) return HOLO_ERR_ARG;
+  if (!(geo->z[0] > 0)) return HOLO_ERR_ARG;
+  for (int j = 1; j < J; ++j)
+    if (!(geo->z[j] > geo->z[j - 1])) return HOLO_ERR_ARG;
+  if (!(geo->z[J - 1] < geo->Z)) return HOLO_ERR_ARG;
+  if (!(geo->w_ref >= 0) || !std::isfinite(geo->w_ref) || !std::isfinite(geo->ext))
+    return HOLO_ERR_ARG;
+  if (!is_pow2(P) || P < 16) return HOLO_ERR_UNSUPPORTED;
+  const holo::Ops* ops = holo::ops_for(P);
+  if (!ops) return HOLO_ERR_UNSUPPORTED;
+
+  holo_ctx* c = new holo_ctx();
+  c->geo = *geo;
+  c->n = n;
+  c->P = P;
+  c->J = J;
+  c->K = geo->n_angles;
+  c->chunk = geo->chunk ? geo->chunk : geo->n_angles;
+  c->ext = (float)geo->ext;
+  c->wref = geo->w_ref;
+  c->stream = (cudaStream_t)stream;
+  c->ops = ops;
+  // Sec. 2 after Eq. fwd_model_cone3: m~_j = z_j/z_0, omega_j = (z_j - z_0)/m~_j,
+  // zeta_j = z_j (Z - z_j)/Z; detector-side distance zhat_j = zeta_j / m~_j^2.
+  const double z0 = geo->z[0];
+  for (int j = 0; j < J; ++j) {
+    const double z = geo->z[j];
+    c->mt[j] = z / z0;
+    c->omega[j] = (z - z0) / c->mt[j];
+    c->zeta[j] = z * (geo->Z - z) / geo->Z;
+    c->zhat[j] = c->zeta[j] / (c->mt[j] * c->mt[j]);
+  }
+  holo_status st;
+  auto bail = [&](holo_status s) {
+    holo_destroy(c);
+    return s;
+  };
+  const std::vector<float2> tw = twiddle_table(P);
+  if ((int)tw.size() != ops->twiddle_count) return bail(HOLO_ERR_UNSUPPORTED);
+  const size_t cP = sizeof(float2) * (size_t)P;
+  if ((st = dalloc(c, (void**)&c->d_tw, sizeof(float2) * std::max<size_t>(tw.size(), 1))) ||
+      (st = dalloc(c, (void**)&c->d_chirp_zhat, cP * J)) ||
+      (st = dalloc(c, (void**)&c->d_chirp_omega, cP * J)) ||
+      (st = dalloc(c, (void**)&c->d_chirp_zeta0, cP)) ||
+      (st = dalloc(c, (void**)&c->d_chirp_tmp, cP)) ||
+      (st = dalloc(c, (void**)&c->d_pj, cP * P * J)) ||
+      (st = dalloc(c, (void**)&c->d_b, sizeof(float2) * (size_t)n * n)) ||
+      (st = dalloc(c, (void**)&c->d_scratch, cP * P)) ||
+      (st = dalloc(c, (void**)&c->d_Gp, cP * P)) ||
+      (st = dalloc(c, (void**)&c->d_T, sizeof(float2) * (size_t)n * n)) ||
+      (st = dalloc(c, (void**)&c->d_rref, sizeof(float2) * (size_t)n * n)) ||
+      (st = dalloc(c, (void**)&c->d_red, 4 * sizeof(double))))
+    return bail(st);
+  if (cudaMallocHost((void**)&c->h_red, 4 * sizeof(double)) != cudaSuccess) {
+    cudaGetLastError();
+    return bail(HOLO_ERR_OOM);
+  }
+  if (!tw.empty() && (st = upload(c, c->d_tw, tw.data(), sizeof(float2) * tw.size())))
+    return bail(st);
+  for (int j = 0; j < J; ++j) {
+    auto cz = chirp_table(P, geo->wavelength, geo->pixel, c->zhat[j]);
+    auto co = chirp_table(P, geo->wavelength, geo->pixel, c->omega[j]);
+    if ((st = upload(c, c->d_chirp_zhat + (size_t)j * P, cz.data(), cP)) ||
+        (st = upload(c, c->d_chirp_omega + (size_t)j * P, co.data(), cP)))
+      return bail(st);
+  }
+  auto c0 = chirp_table(P, geo->wavelength, geo->pixel, c->zeta[0]);
+  if ((st = upload(c, c->d_chirp_zeta0, c0.data(), cP))) return bail(st);
+  *out = c;
+  return HOLO_OK;
+}
+
+holo_status holo_destroy(holo_ctx* c) {
+  if (!c) return HOLO_OK;
+  if (c->stream) cudaStreamSynchronize(c->stream);
+  void* ptrs[] = {c->d_tw,    c->d_chirp_zhat, c->d_chirp_omega, c->d_chirp_zeta0,
+                  c->d_chirp_tmp, c->d_planes, c->d_pj,          c->d_b,
+                  c->ybuf,    c->rbuf,         c->gkbuf,         c->d_scratch,
+                  c->d_Gp,    c->d_T,          c->d_rref,        c->d_part,
+                  c->d_red,   c->s_psi,        c->s_gpsi,        c->s_data,
+                  c->s_q,     c->s_gq};
+  for (void* p : ptrs)
+    if (p) cudaFree(p);
+  if (c->h_red) cudaFreeHost(c->h_red);
+  delete c;
+  return HOLO_OK;
+}
+
+holo_status holo_set_shifts(holo_ctx* c, const float* t) {
+  if (!c || !t) return fail(c, HOLO_ERR_ARG, "null argument");
+  const int n = c->n, P = c->P, J = c->J, K = c->K;
+  for (long long i = 0; i < 2LL * K * J; ++i)
+    if (!std::isfinite(t[i]) || std::fabs(t[i]) > n) return fail(c, HOLO_ERR_ARG, "bad shift");
+  c->planes.assign((size_t)K * J, PlaneDesc{});
+  int maxbys = 1, maxbxs = 1;
+  for (int k = 0; k < K; ++k)
+    for (int j = 0; j < J; ++j) {
+      PlaneDesc& d = c->planes[(size_t)k * J + j];
+      split_mt(c->mt[j], P, &d.mt_hi, &d.mt_lo);
+      d.ty = t[((size_t)k * J + j) * 2 + 0];
+      d.tx = t[((size_t)k * J + j) * 2 + 1];
+      axis_box(c->mt[j], d.ty, n, P, &d.by0, &d.bys);
+      axis_box(c->mt[j], d.tx, n, P, &d.bx0, &d.bxs);
+      maxbys = std::max(maxbys, d.bys);
+      maxbxs = std::max(maxbxs, d.bxs);
+    }
+  holo_status st;
+  if (c->d_planes) {
+    cudaFree(c->d_planes);
+    c->bytes -= (long long)(sizeof(PlaneDesc) * c->planes.size());
+    c->d_planes = nullptr;
+  }
+  if ((st = dalloc(c, (void**)&c->d_planes, sizeof(PlaneDesc) * c->planes.size()))) return st;
+  if ((st = upload(c, c->d_planes, c->planes.data(), sizeof(PlaneDesc) * c->planes.size())))
+    return st;
+  const long long ystride = (long long)maxbys * n, gkstride = (long long)maxbys * maxbxs;
+  const long long np = (long long)c->chunk * J;
+  const size_t ybytes = sizeof(float2) * (size_t)(np * ystride);
+  const size_t rbytes = sizeof(float2) * (size_t)(np * n * n);
+  const size_t gbytes = sizeof(float2) * (size_t)(np * gkstride);
+  const long long parts = (long long)c->ops->pass_b_blocks_x(n) * np + kRefBlocks + 1024;
+  if (ystride > c->ystride || gkstride > c->gkstride || !c->ybuf) {
+    dfree(c, c->ybuf, sizeof(float2) * (size_t)(np * c->ystride));
+    dfree(c, c->rbuf, rbytes);
+    dfree(c, c->gkbuf, sizeof(float2) * (size_t)(np * c->gkstride));
+    c->ybuf = c->rbuf = c->gkbuf = nullptr;
+    c->ystride = ystride;
+    c->gkstride = gkstride;
+    if ((st = dalloc(c, (void**)&c->ybuf, ybytes)) || (st = dalloc(c, (void**)&c->rbuf, rbytes)) ||
+        (st = dalloc(c, (void**)&c->gkbuf, gbytes)))
+      return st;
+  }
+  if (parts > c->part_cap) {
+    dfree(c, c->d_part, sizeof(double) * (size_t)c->part_cap);
+    c->d_part = nullptr;
+    c->part_cap = 0;
+    if ((st = dalloc(c, (void**)&c->d_part, sizeof(double) * (size_t)parts))) return st;
+    c->part_cap = parts;
+  }
+  c->maxbys = maxbys;
+  c->maxbxs = maxbxs;
+  c->have_shifts = true;
+  return HOLO_OK;
+}
+
+holo_status holo_set_data(holo_ctx* c, const float* sqrt_d, const float* sqrt_dref) {
+  if (!c) return HOLO_ERR_ARG;
+  if (!sqrt_d && !sqrt_dref) return fail(c, HOLO_ERR_ARG, "null data");
+  if (c->wref != 0.0 && !sqrt_dref) return fail(c, HOLO_ERR_ARG, "w_ref != 0 needs sqrt_dref");
+  c->sqrt_d = sqrt_d;
+  c->sqrt_dref = sqrt_dref;
+  c->have_data = sqrt_d != nullptr;
+  return HOLO_OK;
+}
+
+holo_status holo_set_probe(holo_ctx* c, const void* q) {
+  if (!c || !q) return fail(c, HOLO_ERR_ARG, "null probe");
+  const int P = c->P, n = c->n, lo = P / 2 - n / 2;
+  const size_t plane = sizeof(float2) * (size_t)P * P;
+  HOLO_CK(c, cudaMemcpyAsync(c->d_pj, q, plane, cudaMemcpyDeviceToDevice, c->stream));
+  holo_status st;
+  for (int j = 1; j < c->J; ++j) {
+    // p_j = D_{omega_j}(q)  (Eq. fwd_model_cone3)
+    st = dstep2d(c, (const float2*)q, 0, P, 0, P, c->d_pj + (size_t)j * P * P, 0, P, 0, P,
+                 c->d_chirp_omega + (size_t)j * P, 0, 1.f, 0);
+    if (st != HOLO_OK) return st;
+  }
+  // b = C D_{zeta_0}(q): the probe on the detector without the sample (Sec. 2)
+  st = dstep2d(c, (const float2*)q, 0, P, 0, P, c->d_b, lo, n, lo, n, c->d_chirp_zeta0, 0, 1.f, 0);
+  if (st != HOLO_OK) return st;
+  c->have_probe = true;
+  return HOLO_OK;
+}
+
+holo_status holo_forward(holo_ctx* c, int k0, int nk, const void* psi, void* u_out,
+                         double* loss) {
+  holo_status st = check_chunk(c, k0, nk);
+  if (st != HOLO_OK) return st;
+  if (!psi) return fail(c, HOLO_ERR_ARG, "null psi");
+  PassArgs a = pass_args(c, k0, nk, psi);
+  a.u_out = (float2*)u_out;
+  if ((st = run_eval(c, a, false, nullptr, 0))) return st;
+  return read_loss(c, loss, 0);
+}
+
+holo_status holo_gradient(holo_ctx* c, int k0, int nk, const void* psi, double* loss,
+                          void* grad_psi, void* grad_q, unsigned flags) {
+  holo_status st = check_chunk(c, k0, nk);
+  if (st != HOLO_OK) return st;
+  if (!psi || !grad_psi || !grad_q) return fail(c, HOLO_ERR_ARG, "null pointer");
+  PassArgs a = pass_args(c, k0, nk, psi);
+  a.grad_psi = (float2*)grad_psi;
+  a.accumulate = (flags & HOLO_ACCUMULATE) ? 1 : 0;
+  if ((st = run_eval(c, a, true, (float2*)grad_q, flags))) return st;
+  if (!loss) return HOLO_OK;
+  return read_loss(c, loss, flags);
+}
+
+holo_status holo_gradient_host(holo_ctx* c, int k0, int nk, const void* psi_host,
+                               const float* sqrt_d_host, const void* q_host, double* loss,
+                               void* grad_psi_host, void* grad_q_host, unsigned flags) {
+  if (!c) return HOLO_ERR_ARG;
+  if (!psi_host || !grad_psi_host || !grad_q_host) return fail(c, HOLO_ERR_ARG, "null pointer");
+  if (nk < 1 || nk > c->chunk || k0 < 0 || k0 + nk > c->K)
+    return fail(c, HOLO_ERR_ARG, "chunk [k0, k0+nk) outside [0, n_angles) or nk > chunk");
+  if (!c->have_shifts) return fail(c, HOLO_ERR_STATE, "holo_set_shifts not called");
+  if (!sqrt_d_host && !c->have_data) return fail(c, HOLO_ERR_STATE, "no data");
+  if (c->wref != 0.0 && k0 == 0 && !c->sqrt_dref)
+    return fail(c, HOLO_ERR_STATE, "reference data not registered");
+  if (!q_host && !c->have_probe) return fail(c, HOLO_ERR_STATE, "holo_set_probe not called");
+  const int n = c->n, P = c->P, J = c->J;
+  const size_t psi_bytes = sizeof(float2) * (size_t)c->chunk * n * n;
+  const size_t data_bytes = sizeof(float) * (size_t)c->chunk * J * n * n;
+  const size_t q_bytes = sizeof(float2) * (size_t)P * P;
+  holo_status st;
+  if (!c->s_psi && ((st = dalloc(c, (void**)&c->s_psi, psi_bytes)) ||
+                    (st = dalloc(c, (void**)&c->s_gpsi, psi_bytes)) ||
+                    (st = dalloc(c, (void**)&c->s_q, q_bytes)) ||
+                    (st = dalloc(c, (void**)&c->s_gq, q_bytes))))
+    return st;
+  if (sqrt_d_host && !c->s_data && (st = dalloc(c, (void**)&c->s_data, data_bytes))) return st;
+  const size_t nb = sizeof(float2) * (size_t)nk * n * n;
+  HOLO_CK(c, cudaMemcpyAsync(c->s_psi, psi_host, nb, cudaMemcpyHostToDevice, c->stream));
+  if (sqrt_d_host)
+    HOLO_CK(c, cudaMemcpyAsync(c->s_data, sqrt_d_host, sizeof(float) * (size_t)nk * J * n * n,
+                               cudaMemcpyHostToDevice, c->stream));
+  if (q_host) {
+    HOLO_CK(c, cudaMemcpyAsync(c->s_q, q_host, q_bytes, cudaMemcpyHostToDevice, c->stream));
+    if ((st = holo_set_probe(c, c->s_q))) return st;
+  }
+  PassArgs a = pass_args(c, k0, nk, c->s_psi);
+  if (sqrt_d_host) {
+    a.sqrt_d = c->s_data;
+    a.data_k0 = k0;
+  }
+  a.grad_psi = c->s_gpsi;
+  if ((st = run_eval(c, a, true, c->s_gq, 0))) return st;
+  HOLO_CK(c, cudaMemcpyAsync(grad_psi_host, c->s_gpsi, nb, cudaMemcpyDeviceToHost, c->stream));
+  HOLO_CK(c, cudaMemcpyAsync(grad_q_host, c->s_gq, q_bytes, cudaMemcpyDeviceToHost, c->stream));
+  return read_loss(c, loss, flags);
+}
+
+holo_status holo_propagate(holo_ctx* c, const void* in, void* out, double z) {
+  if (!c || !in || !out || !std::isfinite(z)) return fail(c, HOLO_ERR_ARG, "bad argument");
+  const int P = c->P;
+  auto ch = chirp_table(P, c->geo.wavelength, c->geo.pixel, z);
+  holo_status st = upload(c, c->d_chirp_tmp, ch.data(), sizeof(float2) * P);
+  if (st) return st;
+  return dstep2d(c, (const float2*)in, 0, P, 0, P, (float2*)out, 0, P, 0, P, c->d_chirp_tmp, 0,
+                 1.f, 0);
+}
+
+holo_status holo_dot(holo_ctx* c, const void* a, const void* b, long long n, double* re_out) {
+  if (!c || !a || !b || !re_out || n < 0) return fail(c, HOLO_ERR_ARG, "bad argument");
+  if (!c->d_part) {
+    holo_status st = dalloc(c, (void**)&c->d_part, sizeof(double) * 1024);
+    if (st) return st;
+    c->part_cap = 1024;
+  }
+  long long nb = (n + 256 * 16 - 1) / (256 * 16);
+  nb = std::max(1LL, std::min(nb, std::min(1024LL, c->part_cap)));
+  HOLO_LAUNCH(c, holo::launch_dot((const float2*)a, (const float2*)b, n, c->d_part, (int)nb,
+                                  c->stream));
+  HOLO_LAUNCH(c, holo::launch_sum_f64(c->d_part, (int)nb, c->d_red + 2, 0, c->stream));
+  HOLO_CK(c, cudaMemcpyAsync(c->h_red + 2, c->d_red + 2, sizeof(double), cudaMemcpyDeviceToHost,
+                             c->stream));
+  HOLO_CK(c, cudaStreamSynchronize(c->stream));
+  *re_out = c->h_red[2];
+  return HOLO_OK;
+}
+
+holo_status holo_step(holo_ctx* c, void* x, const void* eta, double gamma, long long n) {
+  if (!c || !x || !eta || n < 0 || !std::isfinite(gamma)) return fail(c, HOLO_ERR_ARG, "bad argument");
+  HOLO_LAUNCH(c, holo::launch_axpy((float2*)x, (const float2*)eta, (float)gamma, n, c->stream));
+  return HOLO_OK;
+}
+
+holo_status holo_direction(holo_ctx* c, void* eta, const void* g, double beta, long long n) {
+  if (!c || !eta || !g || n < 0 || !std::isfinite(beta)) return fail(c, HOLO_ERR_ARG, "bad argument");
+  HOLO_LAUNCH(c, holo::launch_direction((float2*)eta, (const float2*)g, (float)beta, n, c->stream));
+  return HOLO_OK;
+}
+
+holo_status holo_workspace_bytes(const holo_ctx* c, long long* bytes) {
+  if (!c || !bytes) return HOLO_ERR_ARG;
+  *bytes = c->bytes;
+  return HOLO_OK;
+}
+
+holo_status holo_launch_count(const holo_ctx* c, long long* count) {
+  if (!c || !count) return HOLO_ERR_ARG;
+  *count = c->launches;
+  return HOLO_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,292 @@
+// Register + shared-memory FFT engine for one line of length P (a power of two >= 16).
+//
+// The Fresnel operator D_z (Appendix A, Eq. defPz/defGz) is a circular convolution on
+// the P x P grid; with a separable chirp exp(-i pi lambda z (fx^2 + fy^2)) it factors into
+// one pass over rows and one over columns, each "FFT -> chirp -> inverse FFT" along a
+// line.  This header implements that line transform.
+//
+// Layout.  A line is held by T = P/16 threads, 16 complex values per thread: thread t,
+// register c holds element t + T*c ("strided natural" layout).  The forward transform
+// is a mixed-radix decimation in frequency with radices 16, 16, ..., 16, r (r in
+// {2, 4, 8} when log2 P is not a multiple of 4); every stage is a DFT over one digit in
+// registers followed by a twiddle and a shared-memory exchange.  The thread/register
+// assignment of each stage is chosen so that the forward output is again in strided
+// natural order (register rho of thread t holds frequency t + T*rho), so a pointwise
+// multiplier in frequency needs no reordering and the inverse transform (the adjoint
+// stages in reverse order) consumes that layout directly and returns the same layout.
+//
+// Exchanges write register k of thread t at t + T*k (contiguous per k) and read the
+// next stage's digit; addresses are padded a -> a + a/16 so both phases avoid shared
+// memory bank conflicts.  Twiddles come from a per-stage table in shared memory,
+// indexed [k-1][mu] so that consecutive threads read consecutive entries.
+//
+// Synchronisation is the caller's: every thread of the block calls the transform the
+// same number of times, and `SYNC()` is a block-wide barrier.
+
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace holo {
+
+// --------------------------------------------------------------------- complex helpers
+
+__device__ __forceinline__ float2 cadd(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
+__device__ __forceinline__ float2 csub(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
+__device__ __forceinline__ float2 cmul(float2 a, float2 b) {
+  return make_float2(fmaf(a.x, b.x, -a.y * b.y), fmaf(a.x, b.y, a.y * b.x));
+}
+// a * conj(b)
+__device__ __forceinline__ float2 cmulc(float2 a, float2 b) {
+  return make_float2(fmaf(a.x, b.x, a.y * b.y), fmaf(a.y, b.x, -a.x * b.y));
+}
+// conj(a) * b
+__device__ __forceinline__ float2 cconjmul(float2 a, float2 b) {
+  return make_float2(fmaf(a.x, b.x, a.y * b.y), fmaf(a.x, b.y, -a.y * b.x));
+}
+__device__ __forceinline__ float2 cscale(float2 a, float s) { return make_float2(a.x * s, a.y * s); }
+__device__ __forceinline__ float2 cconj(float2 a) { return make_float2(a.x, -a.y); }
+// multiply by -i (forward) or +i (inverse)
+template <bool INV>
+__device__ __forceinline__ float2 mul_mi(float2 a) {
+  return INV ? make_float2(-a.y, a.x) : make_float2(a.y, -a.x);
+}
+
+// --------------------------------------------------------------------- shapes
+
+__host__ __device__ constexpr int ilog2c(int x) { return x <= 1 ? 0 : 1 + ilog2c(x >> 1); }
+__host__ __device__ constexpr int ipow16(int s) { return s == 0 ? 1 : 16 * ipow16(s - 1); }
+
+__device__ __forceinline__ int spad(int a) { return a + (a >> 4); }
+
+template <int P_>
+struct Fft {
+  static constexpr int P = P_;
+  static constexpr int LOG2 = ilog2c(P);
+  static_assert((1 << LOG2) == P && P >= 16, "line length must be a power of two >= 16");
+  static constexpr int T = P / 16;                 // threads per line
+  static constexpr int N16 = LOG2 / 4;             // radix-16 stages
+  static constexpr int RB = LOG2 % 4;              // bits of the final small stage (0: none)
+  static constexpr int NST = N16 + (RB ? 1 : 0);   // number of stages
+  static constexpr int RLAST = RB ? (1 << RB) : 16;
+  static constexpr int SMEM = P + P / 16;          // padded exchange buffer, float2 entries
+  // radix-16 stage s: prefix length L = 16^s, remaining length M = P / 16^(s+1)
+  __host__ __device__ static constexpr int L(int s) { return ipow16(s); }
+  __host__ __device__ static constexpr int M(int s) { return P / ipow16(s + 1); }
+  __host__ __device__ static constexpr int tw_off(int s) {
+    return s == 0 ? 0 : tw_off(s - 1) + (M(s - 1) > 1 ? 15 * M(s - 1) : 0);
+  }
+  static constexpr int TW = tw_off(N16);           // twiddle table entries (float2)
+};
+
+// --------------------------------------------------------------------- small DFTs
+
+template <bool INV>
+__device__ __forceinline__ void dft2(float2& a, float2& b) {
+  float2 s = cadd(a, b), d = csub(a, b);
+  a = s;
+  b = d;
+}
+
+// natural order in, natural order out
+template <bool INV>
+__device__ __forceinline__ void dft4(float2& x0, float2& x1, float2& x2, float2& x3) {
+  float2 s02 = cadd(x0, x2), d02 = csub(x0, x2);
+  float2 s13 = cadd(x1, x3), d13 = mul_mi<INV>(csub(x1, x3));
+  x0 = cadd(s02, s13);
+  x2 = csub(s02, s13);
+  x1 = cadd(d02, d13);
+  x3 = csub(d02, d13);
+}
+
+template <bool INV>
+__device__ __forceinline__ void dft8(float2* v) {
+  // radix-2 decimation in time over two DFT-4s
+  float2 e0 = v[0], e1 = v[2], e2 = v[4], e3 = v[6];
+  float2 o0 = v[1], o1 = v[3], o2 = v[5], o3 = v[7];
+  dft4<INV>(e0, e1, e2, e3);
+  dft4<INV>(o0, o1, o2, o3);
+  const float h = 0.70710678118654752f;
+  // W8^1 = (1 - i)/sqrt2 forward, (1 + i)/sqrt2 inverse
+  float2 t1 = INV ? make_float2((o1.x - o1.y) * h, (o1.x + o1.y) * h)
+                  : make_float2((o1.x + o1.y) * h, (o1.y - o1.x) * h);
+  float2 t2 = mul_mi<INV>(o2);
+  // W8^3 = (-1 - i)/sqrt2 forward, (-1 + i)/sqrt2 inverse
+  float2 t3 = INV ? make_float2((-o3.x - o3.y) * h, (o3.x - o3.y) * h)
+                  : make_float2((o3.y - o3.x) * h, (-o3.x - o3.y) * h);
+  v[0] = cadd(e0, o0); v[4] = csub(e0, o0);
+  v[1] = cadd(e1, t1); v[5] = csub(e1, t1);
+  v[2] = cadd(e2, t2); v[6] = csub(e2, t2);
+  v[3] = cadd(e3, t3); v[7] = csub(e3, t3);
+}
+
+// W16^m as (cos, -sin) of 2 pi m / 16 (conjugated for the inverse)
+template <bool INV>
+__device__ __forceinline__ float2 w16(int m) {
+  const float c1 = 0.92387953251128674f, s1 = 0.38268343236508977f, h = 0.70710678118654752f;
+  float2 w;
+  switch (m) {
+    case 1: w = make_float2(c1, -s1); break;
+    case 2: w = make_float2(h, -h); break;
+    case 3: w = make_float2(s1, -c1); break;
+    case 4: w = make_float2(0.f, -1.f); break;
+    case 6: w = make_float2(-h, -h); break;
+    case 9: w = make_float2(-c1, s1); break;
+    default: w = make_float2(1.f, 0.f); break;
+  }
+  return INV ? cconj(w) : w;
+}
+
+template <bool INV>
+__device__ __forceinline__ void dft16(float2* v) {
+  // 4 x 4: DFT-4 over c2 (elements c1 + 4 c2), twiddle W16^(c1 k2), DFT-4 over c1;
+  // output index k2 + 4 k1.
+  float2 y[16];
+#pragma unroll
+  for (int c1 = 0; c1 < 4; ++c1) {
+    float2 a = v[c1], b = v[c1 + 4], c = v[c1 + 8], d = v[c1 + 12];
+    dft4<INV>(a, b, c, d);
+    y[c1 * 4 + 0] = a;
+    y[c1 * 4 + 1] = (c1 == 0) ? b : cmul(b, w16<INV>(c1 * 1));
+    y[c1 * 4 + 2] = (c1 == 0) ? c : (c1 == 2 ? mul_mi<INV>(c) : cmul(c, w16<INV>(c1 * 2)));
+    y[c1 * 4 + 3] = (c1 == 0) ? d : cmul(d, w16<INV>(c1 * 3));
+  }
+#pragma unroll
+  for (int k2 = 0; k2 < 4; ++k2) {
+    float2 a = y[0 * 4 + k2], b = y[1 * 4 + k2], c = y[2 * 4 + k2], d = y[3 * 4 + k2];
+    dft4<INV>(a, b, c, d);
+    v[k2 + 0] = a;
+    v[k2 + 4] = b;
+    v[k2 + 8] = c;
+    v[k2 + 12] = d;
+  }
+}
+
+template <int R, bool INV>
+__device__ __forceinline__ void dft_small(float2* u) {
+  if constexpr (R == 2) {
+    dft2<INV>(u[0], u[1]);
+  } else if constexpr (R == 4) {
+    dft4<INV>(u[0], u[1], u[2], u[3]);
+  } else if constexpr (R == 8) {
+    dft8<INV>(u);
+  } else {
+    dft16<INV>(u);
+  }
+}
+
+// --------------------------------------------------------------------- twiddle tables
+
+// Host-side layout of the shared twiddle table of one line length: for each radix-16
+// stage s with M(s) > 1, entries [(k-1) * M(s) + mu] = exp(-2 pi i mu k L(s) / P),
+// k = 1..15, mu = 0..M(s)-1.  Filled in FP64 on the host.
+
+template <int P>
+__device__ __forceinline__ void load_twiddles(float2* sm_tw, const float2* __restrict__ g_tw) {
+  for (int i = threadIdx.x; i < Fft<P>::TW; i += blockDim.x) sm_tw[i] = g_tw[i];
+}
+
+// --------------------------------------------------------------------- stages
+
+#define HOLO_SYNC() __syncthreads()
+
+template <int P, int S>
+__device__ __forceinline__ void fwd_from(float2 (&v)[16], float2* __restrict__ sm,
+                                         const float2* __restrict__ tw, int t) {
+  using F = Fft<P>;
+  if constexpr (S < F::N16) {
+    constexpr int M = F::M(S);
+    if constexpr (S > 0) {
+      const int mu = t % M, ka = t / M;
+#pragma unroll
+      for (int c = 0; c < 16; ++c) v[c] = sm[spad(c * M + mu + 16 * M * ka)];
+      HOLO_SYNC();
+    }
+    dft16<false>(v);
+    if constexpr (M > 1) {
+      const int mu = t % M;
+      const float2* w = tw + F::tw_off(S) + mu;
+#pragma unroll
+      for (int k = 1; k < 16; ++k) v[k] = cmul(v[k], w[(k - 1) * M]);
+    }
+    if constexpr (S < F::NST - 1) {
+#pragma unroll
+      for (int k = 0; k < 16; ++k) sm[spad(t + F::T * k)] = v[k];
+      HOLO_SYNC();
+    }
+    fwd_from<P, S + 1>(v, sm, tw, t);
+  } else if constexpr (F::RB > 0 && S == F::N16) {
+    constexpr int R = F::RLAST, G = 16 / R;
+#pragma unroll
+    for (int g = 0; g < G; ++g) {
+      float2 u[R];
+      const int ka = t + F::T * g;
+#pragma unroll
+      for (int c = 0; c < R; ++c) u[c] = sm[spad(c + R * ka)];
+      dft_small<R, false>(u);
+#pragma unroll
+      for (int k = 0; k < R; ++k) v[g + G * k] = u[k];
+    }
+    HOLO_SYNC();
+  }
+}
+
+template <int P, int S>
+__device__ __forceinline__ void inv_from(float2 (&v)[16], float2* __restrict__ sm,
+                                         const float2* __restrict__ tw, int t) {
+  using F = Fft<P>;
+  if constexpr (S == F::N16) {
+    if constexpr (F::RB > 0) {
+      constexpr int R = F::RLAST, G = 16 / R;
+#pragma unroll
+      for (int g = 0; g < G; ++g) {
+        float2 u[R];
+#pragma unroll
+        for (int k = 0; k < R; ++k) u[k] = v[g + G * k];
+        dft_small<R, true>(u);
+        const int ka = t + F::T * g;
+#pragma unroll
+        for (int c = 0; c < R; ++c) sm[spad(c + R * ka)] = u[c];
+      }
+      HOLO_SYNC();
+#pragma unroll
+      for (int k = 0; k < 16; ++k) v[k] = sm[spad(t + F::T * k)];
+      HOLO_SYNC();
+    }
+    inv_from<P, S - 1>(v, sm, tw, t);
+  } else if constexpr (S >= 0) {
+    constexpr int M = F::M(S);
+    if constexpr (M > 1) {
+      const int mu = t % M;
+      const float2* w = tw + F::tw_off(S) + mu;
+#pragma unroll
+      for (int k = 1; k < 16; ++k) v[k] = cmulc(v[k], w[(k - 1) * M]);
+    }
+    dft16<true>(v);
+    if constexpr (S > 0) {
+      const int mu = t % M, ka = t / M;
+#pragma unroll
+      for (int c = 0; c < 16; ++c) sm[spad(c * M + mu + 16 * M * ka)] = v[c];
+      HOLO_SYNC();
+#pragma unroll
+      for (int k = 0; k < 16; ++k) v[k] = sm[spad(t + F::T * k)];
+      HOLO_SYNC();
+      inv_from<P, S - 1>(v, sm, tw, t);
+    }
+  }
+}
+
+// Forward DFT (e^{-2 pi i}, unnormalised): strided natural in, strided natural out.
+template <int P>
+__device__ __forceinline__ void fft_fwd(float2 (&v)[16], float2* sm, const float2* tw, int t) {
+  fwd_from<P, 0>(v, sm, tw, t);
+}
+
+// Inverse DFT without the 1/P factor (the adjoint of fft_fwd).
+template <int P>
+__device__ __forceinline__ void fft_inv(float2 (&v)[16], float2* sm, const float2* tw, int t) {
+  inv_from<P, Fft<P>::N16>(v, sm, tw, t);
+}
+
+}  // namespace holo

@@ -1,0 +1,96 @@
+// Internal declarations shared by the C-ABI layer and the per-line-length kernel units.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace holo {
+
+// One (angle k, distance j) plane: resample parameters and the bounding box of the
+// support of R0(psi - ext) on the P x P grid (rows [by0, by0+bys), cols [bx0, bx0+bxs)).
+// m~ is split into a high part with few significant bits (so m_hi * integer is exact in
+// FP32) and a low part; see axis_tap() in holo_kernels.cuh.
+struct PlaneDesc {
+  float mt_hi, mt_lo;   // m~_j = mt_hi + mt_lo
+  float ty, tx;         // sample shift t_kj (pixels), (y, x)
+  int by0, bys;         // box rows
+  int bx0, bxs;         // box columns
+};
+
+// Generic line D-step over rows or columns of a strided complex array.
+// The line's nonzero input occupies P-grid positions [in_lo, in_lo + in_len) and is
+// read from in[line_in_base + (pos - in_lo) * in_step]; outside, the input is zero.
+// The output is written for positions [out_lo, out_lo + out_len) to
+// out[line_out_base + (pos - out_lo) * out_step], as out = alpha * D + beta * out.
+struct LineArgs {
+  const float2* in;
+  float2* out;
+  long long in_line_stride, in_step;     // element offsets
+  long long out_line_stride, out_step;
+  int nlines;
+  int in_lo, in_len, out_lo, out_len;
+  const float2* chirp;                   // P entries, exp(-i pi lambda z f^2) / P
+  int conj_chirp;                        // 1: multiply by conj(chirp) (distance -z)
+  float alpha;
+  int accumulate;                        // 1: out += alpha * D(...)
+};
+
+// Parameters of the per-plane passes of one forward / gradient evaluation.
+struct PassArgs {
+  int n, P, J;
+  int k0, nk;                  // chunk: global angles [k0, k0 + nk)
+  float ext;
+  const PlaneDesc* planes;     // [n_angles][J] (global k)
+  const float2* psi;           // [nk][n][n]
+  const float2* pj;            // [J][P][P]  probe at the sample planes
+  const float2* bref;          // [n][n]    C D_{zeta_0}(q)
+  const float* sqrt_d;         // [.][J][n][n], angle k stored at index k - data_k0
+  int data_k0;
+  const float2* chirp_zhat;    // [J][P]
+  float2* ybuf;                // per local plane: [ystride] (box rows x n)
+  long long ystride;
+  float2* rbuf;                // per local plane: [n][n] residuals (gradient only)
+  float2* gkbuf;               // per local plane: [gkstride] conj(w) v on the box
+  long long gkstride;
+  float2* u_out;               // optional [nk][J][n][n]
+  double* loss_part;           // per block of pass B
+  float2* grad_psi;            // [nk][n][n]
+  int accumulate;
+  const float2* twiddles;      // device twiddle table for this P
+  int max_box_rows;            // largest box height of the chunk (grid of passes A, C)
+};
+
+// Entry points implemented once per supported line length P.
+struct Ops {
+  int P;
+  cudaError_t (*rows)(const LineArgs&, const float2* tw, cudaStream_t);
+  cudaError_t (*cols)(const LineArgs&, const float2* tw, cudaStream_t);
+  cudaError_t (*pass_a)(const PassArgs&, cudaStream_t);
+  cudaError_t (*pass_b)(const PassArgs&, int with_adjoint, int nblocks_x, cudaStream_t);
+  cudaError_t (*pass_c)(const PassArgs&, cudaStream_t);
+  int (*pass_b_blocks_x)(int n);            // grid.x of pass B for side n
+  int twiddle_count;
+};
+
+const Ops* ops_for(int P);
+
+// Line-length independent kernels (holo_common.cu).
+cudaError_t launch_pass_d(const PassArgs& a, cudaStream_t s);
+cudaError_t launch_reduce_g(const PassArgs& a, float2* Gp, int j, int row0, int nrows, int col0,
+                            int ncols, cudaStream_t s);
+cudaError_t launch_sum_residuals(const float2* rbuf, int nplanes, long long n2, const float2* rref,
+                                 float ext, float wref, float2* out, cudaStream_t s);
+cudaError_t launch_ref_residual(const float2* bref, const float* sqrt_dref, long long n2,
+                                float2* rref, double* part, int nblocks, cudaStream_t s);
+cudaError_t launch_sum_f64(const double* part, int count, double* out, int accumulate,
+                           cudaStream_t s);
+cudaError_t launch_dot(const float2* a, const float2* b, long long n, double* part, int nblocks,
+                       cudaStream_t s);
+cudaError_t launch_axpy(float2* x, const float2* eta, float gamma, long long n, cudaStream_t s);
+cudaError_t launch_direction(float2* eta, const float2* g, float beta, long long n,
+                             cudaStream_t s);
+cudaError_t launch_scale_add(float2* out, const float2* in, float alpha, long long n,
+                             int accumulate, cudaStream_t s);
+cudaError_t launch_fill_zero(float2* out, long long n, cudaStream_t s);
+
+}  // namespace holo

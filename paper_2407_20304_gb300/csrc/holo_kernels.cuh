@@ -1,0 +1,451 @@
+// Kernels of the per-plane hot path, templated on the line length P.
+//
+// Forward model of one (k, j) plane (Eq. fwd_model_cone3 with the shifts of Eq. min1):
+//   u_kj = C D_{zhat_j}( p_j * R_kj psi_k ),  zhat_j = zeta_j / m~_j^2,  p_j = D_{omega_j} q.
+// The resample is affine, R psi = ext + w with w = R0(psi - ext) supported on a box of
+// about n/m~_j pixels per side, so by linearity
+//   u_kj = ext * C D_{zhat_j}(p_j) + C D_{zhat_j}(p_j * w_kj) = ext * b + C D_{zhat_j}(p_j * w_kj)
+// with b = C D_{zeta_0}(q) the same for every plane (Theorem t3: zhat_j + omega_j = zeta_0).
+// Only the box rows need the row transforms, and only box columns of the adjoint field
+// are needed for grad_psi and for the w-part of grad_q.  Per plane:
+//   pass A (rows of the box): x = p_j * w, row FFT, chirp, row IFFT, keep the n
+//           detector columns -> Y[box rows][n]
+//   pass B (detector columns): column FFT, chirp, IFFT, keep the n detector rows,
+//           u = ext b + (.), residual r = u - a u/|u| (Eq. gradpsi), loss partial,
+//           r stored for the ext-part of grad_q, then the adjoint column transform
+//           (conjugate chirp) on C* r, keep box rows -> V (in place of Y)
+//   pass C (rows of the box): adjoint row transform -> v on the box columns;
+//           z = conj(p_j) v, x-transpose of the bilinear resample -> h[box rows][n]
+//           (in place of V); conj(w) v -> per-plane buffer for grad_q
+//   pass D (psi rows, line-length independent): y-transpose, sum over j, times 2.
+
+#pragma once
+
+#include "holo_fft.cuh"
+#include "holo_internal.h"
+
+namespace holo {
+
+// Block shapes.  Row passes keep each line in its own threads (coalesced along rows);
+// column passes interleave C columns within a warp so that one load instruction covers
+// whole 32-byte sectors of C adjacent columns.  Line strides in shared memory are
+// chosen so that every exchange phase is free of bank conflicts (checked by simulating
+// the address patterns for all P).
+template <int P>
+struct RowCfg {
+  static constexpr int T = P / 16;
+  static constexpr int G = T >= 256 ? 1 : 256 / T;      // lines per block
+  static constexpr int NT = G * T;
+  static constexpr int LS = Fft<P>::SMEM + (P == 64 ? 1 : 0);
+  static constexpr size_t SMEM_BYTES = (size_t)(Fft<P>::TW + G * LS) * sizeof(float2);
+};
+
+template <int P>
+struct ColCfg {
+  static constexpr int T = P / 16;
+  static constexpr int C = T >= 256 ? 2 : (T >= 64 ? 4 : (P == 512 ? 16 : 256 / T));
+  static constexpr int NT = C * T;
+  static constexpr int EXTRA = P >= 4096 ? 8 : (P == 2048 ? 4 : (P == 1024 ? 3 : (P == 16 ? 0 : 1)));
+  static constexpr int LS = Fft<P>::SMEM + EXTRA;
+  static constexpr size_t SMEM_BYTES = (size_t)(Fft<P>::TW + C * LS) * sizeof(float2);
+};
+
+// ψ index of P-grid position X along one axis: xi = m~ (X - P/2) - t + n/2 (reading R4),
+// returned as floor(xi) and frac(xi).  m~ = mt_hi + mt_lo with mt_hi * (X - P/2) exact in
+// FP32, so xi is accurate to ~1e-7 pixel even for |X - P/2| in the thousands.
+__device__ __forceinline__ void axis_tap(int X, float mt_hi, float mt_lo, float t, int P, int n,
+                                         int& i0, float& f) {
+  const float x = (float)(X - P / 2);
+  const float a = mt_hi * x;
+  const float ai = floorf(a);
+  const float rest = (a - ai) + fmaf(mt_lo, x, -t);
+  const float ri = floorf(rest);
+  i0 = (int)ai + (int)ri + n / 2;
+  f = rest - ri;
+}
+
+// w = R0(psi - ext) at (row taps iy0/fy, column X): the bilinear interpolation of
+// psi - ext with taps outside the n x n domain dropped.
+__device__ __forceinline__ float2 resample_w(const float2* __restrict__ psi, int n, float ext,
+                                             int iy0, float fy, const PlaneDesc& d, int P, int X) {
+  int ix0;
+  float fx;
+  axis_tap(X, d.mt_hi, d.mt_lo, d.tx, P, n, ix0, fx);
+  const bool c0 = (unsigned)ix0 < (unsigned)n, c1 = (unsigned)(ix0 + 1) < (unsigned)n;
+  float2 w = make_float2(0.f, 0.f);
+#pragma unroll
+  for (int a = 0; a < 2; ++a) {
+    const int iy = iy0 + a;
+    if ((unsigned)iy >= (unsigned)n) continue;
+    const float wy = a ? fy : 1.f - fy;
+    const float2* row = psi + (long long)iy * n;
+    float2 s = make_float2(0.f, 0.f);
+    if (c0) {
+      const float2 p0 = __ldg(row + ix0);
+      s.x = fmaf(1.f - fx, p0.x - ext, s.x);
+      s.y = fmaf(1.f - fx, p0.y, s.y);
+    }
+    if (c1) {
+      const float2 p1 = __ldg(row + ix0 + 1);
+      s.x = fmaf(fx, p1.x - ext, s.x);
+      s.y = fmaf(fx, p1.y, s.y);
+    }
+    w.x = fmaf(wy, s.x, w.x);
+    w.y = fmaf(wy, s.y, w.y);
+  }
+  return w;
+}
+
+// Sum of per-thread FP64 values over the block; result valid in thread 0.
+__device__ __forceinline__ double block_sum_f64(double v, double* red) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  __syncthreads();
+  if (lane == 0) red[w] = v;
+  __syncthreads();
+  double s = 0.0;
+  if (threadIdx.x == 0) {
+    const int nw = (blockDim.x + 31) >> 5;
+    for (int i = 0; i < nw; ++i) s += red[i];
+  }
+  return s;
+}
+
+// ------------------------------------------------------------------ generic D-step
+
+// One "FFT -> chirp -> inverse FFT" per line, lines = rows (COLS = false) or columns.
+template <int P, bool COLS>
+__global__ void __launch_bounds__(COLS ? ColCfg<P>::NT : RowCfg<P>::NT)
+k_line_dstep(LineArgs a, const float2* __restrict__ gtw) {
+  using F = Fft<P>;
+  constexpr int G = COLS ? ColCfg<P>::C : RowCfg<P>::G;
+  constexpr int LS = COLS ? ColCfg<P>::LS : RowCfg<P>::LS;
+  extern __shared__ float2 smem[];
+  float2* tw = smem;
+  const int g = COLS ? (int)(threadIdx.x % G) : (int)(threadIdx.x / F::T);
+  const int t = COLS ? (int)(threadIdx.x / G) : (int)(threadIdx.x % F::T);
+  float2* sm = smem + F::TW + g * LS;
+  load_twiddles<P>(tw, gtw);
+  const int line = blockIdx.x * G + g;
+  const bool valid = line < a.nlines;
+  const float2* in = a.in + (long long)line * a.in_line_stride;
+  float2 v[16];
+#pragma unroll
+  for (int c = 0; c < 16; ++c) {
+    const int rel = t + F::T * c - a.in_lo;
+    v[c] = (valid && (unsigned)rel < (unsigned)a.in_len) ? in[(long long)rel * a.in_step]
+                                                         : make_float2(0.f, 0.f);
+  }
+  __syncthreads();
+  fft_fwd<P>(v, sm, tw, t);
+#pragma unroll
+  for (int c = 0; c < 16; ++c) {
+    float2 ch = __ldg(a.chirp + t + F::T * c);
+    v[c] = a.conj_chirp ? cmulc(v[c], ch) : cmul(v[c], ch);
+  }
+  fft_inv<P>(v, sm, tw, t);
+  float2* out = a.out + (long long)line * a.out_line_stride;
+#pragma unroll
+  for (int c = 0; c < 16; ++c) {
+    const int rel = t + F::T * c - a.out_lo;
+    if (valid && (unsigned)rel < (unsigned)a.out_len) {
+      float2* o = out + (long long)rel * a.out_step;
+      float2 r = cscale(v[c], a.alpha);
+      if (a.accumulate) r = cadd(r, *o);
+      *o = r;
+    }
+  }
+}
+
+// ------------------------------------------------------------------ pass A
+
+template <int P>
+__global__ void __launch_bounds__(RowCfg<P>::NT) k_pass_a(PassArgs a) {
+  using F = Fft<P>;
+  using R = RowCfg<P>;
+  extern __shared__ float2 smem[];
+  const int lp = blockIdx.y, kl = lp / a.J, j = lp % a.J;
+  const PlaneDesc d = a.planes[(long long)(a.k0 + kl) * a.J + j];
+  if ((int)blockIdx.x * R::G >= d.bys) return;   // block-uniform: whole block beyond the box
+  float2* tw = smem;
+  const int g = threadIdx.x / F::T, t = threadIdx.x % F::T;
+  float2* sm = smem + F::TW + g * R::LS;
+  load_twiddles<P>(tw, a.twiddles);
+  const int n = a.n, i = blockIdx.x * R::G + g;
+  const bool valid = i < d.bys;
+  const int Y = d.by0 + i;
+  int iy0;
+  float fy;
+  axis_tap(Y, d.mt_hi, d.mt_lo, d.ty, P, n, iy0, fy);
+  const bool rows_in = valid && ((unsigned)iy0 < (unsigned)n || (unsigned)(iy0 + 1) < (unsigned)n);
+  const float2* psi = a.psi + (long long)kl * n * n;
+  const float2* prow = a.pj + ((long long)j * P + (valid ? Y : 0)) * P;
+  float2 v[16];
+#pragma unroll
+  for (int c = 0; c < 16; ++c) {
+    const int X = t + F::T * c;
+    float2 x = make_float2(0.f, 0.f);
+    if (rows_in && (unsigned)(X - d.bx0) < (unsigned)d.bxs) {
+      const float2 w = resample_w(psi, n, a.ext, iy0, fy, d, P, X);
+      x = cmul(__ldg(prow + X), w);
+    }
+    v[c] = x;
+  }
+  __syncthreads();
+  fft_fwd<P>(v, sm, tw, t);
+  const float2* ch = a.chirp_zhat + (long long)j * P;
+#pragma unroll
+  for (int c = 0; c < 16; ++c) v[c] = cmul(v[c], __ldg(ch + t + F::T * c));
+  fft_inv<P>(v, sm, tw, t);
+  float2* yrow = a.ybuf + (long long)lp * a.ystride + (long long)i * n;
+  const int lo = P / 2 - n / 2;
+#pragma unroll
+  for (int c = 0; c < 16; ++c) {
+    const int rel = t + F::T * c - lo;
+    if (valid && (unsigned)rel < (unsigned)n) yrow[rel] = v[c];
+  }
+}
+
+// ------------------------------------------------------------------ pass B
+
+template <int P, bool ADJ>
+__global__ void __launch_bounds__(ColCfg<P>::NT) k_pass_b(PassArgs a) {
+  using F = Fft<P>;
+  using Cc = ColCfg<P>;
+  extern __shared__ float2 smem[];
+  __shared__ double red[32];
+  float2* tw = smem;
+  const int g = threadIdx.x % Cc::C, t = threadIdx.x / Cc::C;
+  float2* sm = smem + F::TW + g * Cc::LS;
+  load_twiddles<P>(tw, a.twiddles);
+  const int n = a.n;
+  const int lp = blockIdx.y, kl = lp / a.J, j = lp % a.J;
+  const long long gplane = (long long)(a.k0 + kl) * a.J + j;
+  const PlaneDesc d = a.planes[gplane];
+  const int col = blockIdx.x * Cc::C + g;
+  const bool valid = col < n;
+  float2* yb = a.ybuf + (long long)lp * a.ystride;
+  float2 v[16];
+#pragma unroll
+  for (int c = 0; c < 16; ++c) {
+    const int rel = t + F::T * c - d.by0;
+    v[c] = (valid && (unsigned)rel < (unsigned)d.bys) ? yb[(long long)rel * n + col]
+                                                       : make_float2(0.f, 0.f);
+  }
+  __syncthreads();
+  fft_fwd<P>(v, sm, tw, t);
+  const float2* ch = a.chirp_zhat + (long long)j * P;
+#pragma unroll
+  for (int c = 0; c < 16; ++c) v[c] = cmul(v[c], __ldg(ch + t + F::T * c));
+  fft_inv<P>(v, sm, tw, t);
+  const int lo = P / 2 - n / 2;
+  const float* ad = a.sqrt_d + (gplane - (long long)a.data_k0 * a.J) * n * n;
+  float2* rb = a.rbuf + (long long)lp * n * n;
+  float2* uo = a.u_out ? a.u_out + (long long)lp * n * n : nullptr;
+  float lsum = 0.f;
+#pragma unroll
+  for (int c = 0; c < 16; ++c) {
+    const int rr = t + F::T * c - lo;
+    float2 r = make_float2(0.f, 0.f);
+    if (valid && (unsigned)rr < (unsigned)n) {
+      const long long e = (long long)rr * n + col;
+      float2 u = v[c];
+      if (a.ext != 0.f) {
+        const float2 b = __ldg(a.bref + e);
+        u.x = fmaf(a.ext, b.x, u.x);
+        u.y = fmaf(a.ext, b.y, u.y);
+      }
+      const float amp = __ldg(ad + e);
+      const float mag = sqrtf(fmaf(u.x, u.x, u.y * u.y));
+      const float diff = mag - amp;
+      lsum = fmaf(diff, diff, lsum);
+      if (uo) uo[e] = u;
+      if (ADJ) {
+        const float s = mag > 0.f ? 1.f - amp / mag : 0.f;
+        r = cscale(u, s);
+        rb[e] = r;
+      }
+    }
+    v[c] = r;
+  }
+  if constexpr (ADJ) {
+    fft_fwd<P>(v, sm, tw, t);
+#pragma unroll
+    for (int c = 0; c < 16; ++c) v[c] = cmulc(v[c], __ldg(ch + t + F::T * c));
+    fft_inv<P>(v, sm, tw, t);
+#pragma unroll
+    for (int c = 0; c < 16; ++c) {
+      const int rel = t + F::T * c - d.by0;
+      if (valid && (unsigned)rel < (unsigned)d.bys) yb[(long long)rel * n + col] = v[c];
+    }
+  }
+  const double s = block_sum_f64((double)lsum, red);
+  if (threadIdx.x == 0) a.loss_part[(long long)blockIdx.y * gridDim.x + blockIdx.x] = s;
+}
+
+// ------------------------------------------------------------------ pass C
+
+template <int P>
+__global__ void __launch_bounds__(RowCfg<P>::NT) k_pass_c(PassArgs a) {
+  using F = Fft<P>;
+  using R = RowCfg<P>;
+  extern __shared__ float2 smem[];
+  const int lp = blockIdx.y, kl = lp / a.J, j = lp % a.J;
+  const PlaneDesc d = a.planes[(long long)(a.k0 + kl) * a.J + j];
+  if ((int)blockIdx.x * R::G >= d.bys) return;   // block-uniform
+  float2* tw = smem;
+  const int g = threadIdx.x / F::T, t = threadIdx.x % F::T;
+  float2* sm = smem + F::TW + g * R::LS;
+  load_twiddles<P>(tw, a.twiddles);
+  const int n = a.n, i = blockIdx.x * R::G + g;
+  const bool valid = i < d.bys;
+  const int lo = P / 2 - n / 2;
+  float2* yrow = a.ybuf + (long long)lp * a.ystride + (long long)(valid ? i : 0) * n;
+  float2 v[16];
+#pragma unroll
+  for (int c = 0; c < 16; ++c) {
+    const int rel = t + F::T * c - lo;
+    v[c] = (valid && (unsigned)rel < (unsigned)n) ? yrow[rel] : make_float2(0.f, 0.f);
+  }
+  __syncthreads();
+  fft_fwd<P>(v, sm, tw, t);
+  const float2* ch = a.chirp_zhat + (long long)j * P;
+#pragma unroll
+  for (int c = 0; c < 16; ++c) v[c] = cmulc(v[c], __ldg(ch + t + F::T * c));
+  fft_inv<P>(v, sm, tw, t);
+  // v now holds the adjoint field on this P-grid row; the exchange buffer is free.
+  const int Y = d.by0 + i;
+  int iy0;
+  float fy;
+  axis_tap(Y, d.mt_hi, d.mt_lo, d.ty, P, n, iy0, fy);
+  const float2* psi = a.psi + (long long)kl * n * n;
+  const float2* prow = a.pj + ((long long)j * P + (valid ? Y : 0)) * P;
+  float2* gk = a.gkbuf + (long long)lp * a.gkstride + (long long)(valid ? i : 0) * d.bxs;
+#pragma unroll
+  for (int c = 0; c < 16; ++c) {
+    const int X = t + F::T * c, rel = X - d.bx0;
+    if (valid && (unsigned)rel < (unsigned)d.bxs) {
+      sm[rel] = cconjmul(__ldg(prow + X), v[c]);
+      const float2 w = resample_w(psi, n, a.ext, iy0, fy, d, P, X);
+      gk[rel] = cconjmul(w, v[c]);
+    }
+  }
+  __syncthreads();
+  // x-transpose of the bilinear resample: h[ip] = sum_X wx(X, ip) z[X], gathered from the
+  // (at most two) P-grid columns whose taps reach column ip, with the same weights as the
+  // forward resample.
+  const float mt = d.mt_hi + d.mt_lo;
+#pragma unroll
+  for (int c = 0; c < 16; ++c) {
+    const int ip = t + F::T * c;
+    if (!valid || ip >= n) continue;
+    const int Xs = (int)floorf(((float)(ip - n / 2) + d.tx) / mt) + P / 2;
+    float2 h = make_float2(0.f, 0.f);
+#pragma unroll
+    for (int dX = -1; dX <= 2; ++dX) {
+      const int X = Xs + dX, rel = X - d.bx0;
+      if ((unsigned)rel >= (unsigned)d.bxs) continue;
+      int ix0;
+      float fx;
+      axis_tap(X, d.mt_hi, d.mt_lo, d.tx, P, n, ix0, fx);
+      const float wgt = (ix0 == ip) ? 1.f - fx : ((ix0 + 1 == ip) ? fx : 0.f);
+      const float2 z = sm[rel];
+      h.x = fmaf(wgt, z.x, h.x);
+      h.y = fmaf(wgt, z.y, h.y);
+    }
+    yrow[ip] = h;
+  }
+}
+
+// ------------------------------------------------------------------ launchers
+
+template <int P, bool COLS>
+cudaError_t launch_lines(const LineArgs& a, const float2* tw, cudaStream_t s) {
+  constexpr int G = COLS ? ColCfg<P>::C : RowCfg<P>::G;
+  constexpr int NT = COLS ? ColCfg<P>::NT : RowCfg<P>::NT;
+  constexpr size_t SM = COLS ? ColCfg<P>::SMEM_BYTES : RowCfg<P>::SMEM_BYTES;
+  if (a.nlines <= 0) return cudaSuccess;
+  cudaError_t e = cudaFuncSetAttribute(k_line_dstep<P, COLS>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SM);
+  if (e != cudaSuccess) return e;
+  k_line_dstep<P, COLS><<<(a.nlines + G - 1) / G, NT, SM, s>>>(a, tw);
+  return cudaGetLastError();
+}
+
+template <int P>
+cudaError_t launch_rows(const LineArgs& a, const float2* tw, cudaStream_t s) {
+  return launch_lines<P, false>(a, tw, s);
+}
+template <int P>
+cudaError_t launch_cols(const LineArgs& a, const float2* tw, cudaStream_t s) {
+  return launch_lines<P, true>(a, tw, s);
+}
+
+// grid.x of passes A and C is sized by the largest box of the chunk (blocks beyond a
+// plane's own box exit at once); it is passed through PassArgs::max_box_rows.
+template <int P>
+cudaError_t launch_pass_a(const PassArgs& a, cudaStream_t s) {
+  using R = RowCfg<P>;
+  cudaError_t e = cudaFuncSetAttribute(k_pass_a<P>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)R::SMEM_BYTES);
+  if (e != cudaSuccess) return e;
+  dim3 grid((a.max_box_rows + R::G - 1) / R::G, a.nk * a.J);
+  k_pass_a<P><<<grid, R::NT, R::SMEM_BYTES, s>>>(a);
+  return cudaGetLastError();
+}
+
+template <int P>
+int pass_b_blocks_x(int n) {
+  return (n + ColCfg<P>::C - 1) / ColCfg<P>::C;
+}
+
+template <int P>
+cudaError_t launch_pass_b(const PassArgs& a, int adj, int nbx, cudaStream_t s) {
+  using Cc = ColCfg<P>;
+  dim3 grid(nbx, a.nk * a.J);
+  cudaError_t e;
+  if (adj) {
+    e = cudaFuncSetAttribute(k_pass_b<P, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)Cc::SMEM_BYTES);
+    if (e != cudaSuccess) return e;
+    k_pass_b<P, true><<<grid, Cc::NT, Cc::SMEM_BYTES, s>>>(a);
+  } else {
+    e = cudaFuncSetAttribute(k_pass_b<P, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)Cc::SMEM_BYTES);
+    if (e != cudaSuccess) return e;
+    k_pass_b<P, false><<<grid, Cc::NT, Cc::SMEM_BYTES, s>>>(a);
+  }
+  return cudaGetLastError();
+}
+
+template <int P>
+cudaError_t launch_pass_c(const PassArgs& a, cudaStream_t s) {
+  using R = RowCfg<P>;
+  cudaError_t e = cudaFuncSetAttribute(k_pass_c<P>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)R::SMEM_BYTES);
+  if (e != cudaSuccess) return e;
+  dim3 grid((a.max_box_rows + R::G - 1) / R::G, a.nk * a.J);
+  k_pass_c<P><<<grid, R::NT, R::SMEM_BYTES, s>>>(a);
+  return cudaGetLastError();
+}
+
+template <int P>
+const Ops* make_ops() {
+  static const Ops ops = {P,
+                          launch_rows<P>,
+                          launch_cols<P>,
+                          launch_pass_a<P>,
+                          launch_pass_b<P>,
+                          launch_pass_c<P>,
+                          pass_b_blocks_x<P>,
+                          Fft<P>::TW};
+  return &ops;
+}
+
+}  // namespace holo
+
+#define HOLO_INSTANTIATE(P) \
+  namespace holo {          \
+  const Ops* ops_##P() { return make_ops<P>(); } \
+  }

@@ -1,0 +1,225 @@
+"""Python binding of the C ABI: argument marshalling only.
+
+`Holo` wraps one holo_ctx.  Device arrays are torch tensors (complex64 / float32,
+contiguous, on the context's CUDA device); every computation runs in libholo.so on the
+current torch stream at construction time.  Names follow the paper's notation: psi
+(per-angle transmittances), q (probe), shifts t_kj, sqrt_d = sqrt(d~_kj).
+"""
+
+import ctypes
+
+import numpy as np
+
+from . import _lib
+
+
+def _check(lib, ctx, status, where):
+    if status != 0:
+        detail = lib.holo_last_error(ctx).decode() if ctx else ""
+        raise _lib.HoloError(status, where, detail)
+
+
+def _ptr(t, dtype, shape=None, name="tensor"):
+    import torch
+    if not isinstance(t, torch.Tensor):
+        raise TypeError(f"{name} must be a torch tensor")
+    if t.dtype != dtype:
+        raise TypeError(f"{name} must be {dtype}, got {t.dtype}")
+    if not t.is_cuda:
+        raise ValueError(f"{name} must be a CUDA tensor")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+    if shape is not None and tuple(t.shape) != tuple(shape):
+        raise ValueError(f"{name} must have shape {tuple(shape)}, got {tuple(t.shape)}")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _host_ptr(a, dtype, shape, name):
+    if not isinstance(a, np.ndarray) or a.dtype != dtype or not a.flags.c_contiguous:
+        raise TypeError(f"{name} must be a C-contiguous numpy array of {dtype}")
+    if tuple(a.shape) != tuple(shape):
+        raise ValueError(f"{name} must have shape {tuple(shape)}, got {tuple(a.shape)}")
+    return ctypes.c_void_p(a.ctypes.data)
+
+
+class Holo:
+    """One reconstruction problem's geometry and workspace on one GPU.
+
+    n: psi/detector side; pad: P (0 -> 2n); n_angles, n_dist: N_theta, N_z; chunk: angles
+    per evaluation; wavelength, pixel, Z [m]; z: focus-to-sample distances [m];
+    w_ref: weight of the reference-image term; ext: free-space value of the resample.
+    """
+
+    def __init__(self, n, n_angles, n_dist, wavelength, pixel, Z, z, pad=0, chunk=0,
+                 w_ref=1.0, ext=1.0, stream=None):
+        import torch
+        self.lib = _lib.load()
+        if len(z) != n_dist or n_dist > _lib.MAX_DIST:
+            raise ValueError("len(z) must equal n_dist <= 8")
+        g = _lib.HoloGeometry()
+        g.n, g.pad, g.n_angles, g.n_dist, g.chunk = n, pad, n_angles, n_dist, chunk
+        g.wavelength, g.pixel, g.Z = wavelength, pixel, Z
+        for j, zj in enumerate(z):
+            g.z[j] = zj
+        g.w_ref, g.ext = w_ref, ext
+        self.geometry = g
+        self.n, self.P = n, (pad or 2 * n)
+        self.n_angles, self.n_dist = n_angles, n_dist
+        self.chunk = chunk or n_angles
+        self.device = torch.device("cuda", torch.cuda.current_device())
+        if stream is None:
+            stream = torch.cuda.current_stream(self.device)
+        self.stream = stream
+        handle = ctypes.c_void_p()
+        st = self.lib.holo_create(ctypes.byref(g), ctypes.c_void_p(stream.cuda_stream),
+                                  ctypes.byref(handle))
+        _check(self.lib, None, st, "holo_create")
+        self.ctx = handle
+        self._keep = {}
+
+    def close(self):
+        if getattr(self, "ctx", None):
+            self.lib.holo_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # ---------------------------------------------------------------- set-up
+    def set_shifts(self, t):
+        """t_kj (y, x) in pixels: float32 [n_angles][n_dist][2] (numpy, host)."""
+        t = np.ascontiguousarray(t, dtype=np.float32)
+        p = _host_ptr(t, np.float32, (self.n_angles, self.n_dist, 2), "shifts")
+        _check(self.lib, self.ctx, self.lib.holo_set_shifts(self.ctx, p), "holo_set_shifts")
+
+    def set_data(self, sqrt_d, sqrt_dref=None):
+        """sqrt(d~_kj): float32 cuda [n_angles][n_dist][n][n]; sqrt(d~^r): [n][n] or None."""
+        import torch
+        n = self.n
+        pd = ctypes.c_void_p(None)
+        if sqrt_d is not None:
+            pd = _ptr(sqrt_d, torch.float32, (self.n_angles, self.n_dist, n, n), "sqrt_d")
+        pr = ctypes.c_void_p(None)
+        if sqrt_dref is not None:
+            pr = _ptr(sqrt_dref, torch.float32, (n, n), "sqrt_dref")
+        _check(self.lib, self.ctx, self.lib.holo_set_data(self.ctx, pd, pr), "holo_set_data")
+        self._keep["data"] = (sqrt_d, sqrt_dref)
+
+    def set_probe(self, q):
+        """q: complex64 cuda [P][P]; computes p_j = D_{omega_j} q and C D_{zeta_0} q."""
+        import torch
+        p = _ptr(q, torch.complex64, (self.P, self.P), "q")
+        _check(self.lib, self.ctx, self.lib.holo_set_probe(self.ctx, p), "holo_set_probe")
+
+    # ---------------------------------------------------------------- evaluations
+    def forward(self, psi, k0=0, u_out=None):
+        """F2 over angles [k0, k0 + len(psi)); optionally the fields u_kj into u_out."""
+        import torch
+        nk = psi.shape[0]
+        pp = _ptr(psi, torch.complex64, (nk, self.n, self.n), "psi")
+        pu = ctypes.c_void_p(None)
+        if u_out is not None:
+            pu = _ptr(u_out, torch.complex64, (nk, self.n_dist, self.n, self.n), "u_out")
+        loss = ctypes.c_double(0.0)
+        st = self.lib.holo_forward(self.ctx, k0, nk, pp, pu, ctypes.byref(loss))
+        _check(self.lib, self.ctx, st, "holo_forward")
+        return loss.value
+
+    def gradient(self, psi, grad_psi=None, grad_q=None, k0=0, accumulate=False, loss_in=0.0,
+                 want_loss=True):
+        """(F2, grad_psi, grad_q) over angles [k0, k0 + len(psi)) (Eq. gradpsi)."""
+        import torch
+        nk = psi.shape[0]
+        pp = _ptr(psi, torch.complex64, (nk, self.n, self.n), "psi")
+        if grad_psi is None:
+            grad_psi = torch.empty_like(psi)
+        if grad_q is None:
+            grad_q = torch.empty((self.P, self.P), dtype=torch.complex64, device=psi.device)
+        pg = _ptr(grad_psi, torch.complex64, (nk, self.n, self.n), "grad_psi")
+        pq = _ptr(grad_q, torch.complex64, (self.P, self.P), "grad_q")
+        loss = ctypes.c_double(loss_in)
+        lp = ctypes.byref(loss) if want_loss else None
+        st = self.lib.holo_gradient(self.ctx, k0, nk, pp, lp, pg, pq,
+                                    _lib.ACCUMULATE if accumulate else 0)
+        _check(self.lib, self.ctx, st, "holo_gradient")
+        return (loss.value if want_loss else None), grad_psi, grad_q
+
+    def gradient_host(self, psi, sqrt_d=None, q=None, k0=0, grad_psi=None, grad_q=None):
+        """holo_gradient_host: numpy in, numpy out (host buffers; copies inside the call)."""
+        nk = psi.shape[0]
+        n, P = self.n, self.P
+        pp = _host_ptr(psi, np.complex64, (nk, n, n), "psi")
+        pd = ctypes.c_void_p(None)
+        if sqrt_d is not None:
+            pd = _host_ptr(sqrt_d, np.float32, (nk, self.n_dist, n, n), "sqrt_d")
+        pq = ctypes.c_void_p(None)
+        if q is not None:
+            pq = _host_ptr(q, np.complex64, (P, P), "q")
+        if grad_psi is None:
+            grad_psi = np.empty((nk, n, n), np.complex64)
+        if grad_q is None:
+            grad_q = np.empty((P, P), np.complex64)
+        pg = _host_ptr(grad_psi, np.complex64, (nk, n, n), "grad_psi")
+        pgq = _host_ptr(grad_q, np.complex64, (P, P), "grad_q")
+        loss = ctypes.c_double(0.0)
+        st = self.lib.holo_gradient_host(self.ctx, k0, nk, pp, pd, pq, ctypes.byref(loss), pg,
+                                         pgq, 0)
+        _check(self.lib, self.ctx, st, "holo_gradient_host")
+        return loss.value, grad_psi, grad_q
+
+    def propagate(self, x, z, out=None):
+        """D_z of a P x P complex64 field (Appendix A, Eq. defGz)."""
+        import torch
+        px = _ptr(x, torch.complex64, (self.P, self.P), "x")
+        if out is None:
+            out = torch.empty_like(x)
+        po = _ptr(out, torch.complex64, (self.P, self.P), "out")
+        st = self.lib.holo_propagate(self.ctx, px, po, ctypes.c_double(z))
+        _check(self.lib, self.ctx, st, "holo_propagate")
+        return out
+
+    # ---------------------------------------------------------------- CG vector ops
+    def dot(self, a, b):
+        """Re <a, b> in FP64 (Eq. DaiYuan2 inner products)."""
+        import torch
+        if a.shape != b.shape:
+            raise ValueError("shape mismatch")
+        pa = _ptr(a, torch.complex64, None, "a")
+        pb = _ptr(b, torch.complex64, None, "b")
+        out = ctypes.c_double(0.0)
+        st = self.lib.holo_dot(self.ctx, pa, pb, a.numel(), ctypes.byref(out))
+        _check(self.lib, self.ctx, st, "holo_dot")
+        return out.value
+
+    def step(self, x, eta, gamma):
+        """x += gamma * eta."""
+        import torch
+        if x.shape != eta.shape:
+            raise ValueError("shape mismatch")
+        st = self.lib.holo_step(self.ctx, _ptr(x, torch.complex64, None, "x"),
+                                _ptr(eta, torch.complex64, None, "eta"), float(gamma), x.numel())
+        _check(self.lib, self.ctx, st, "holo_step")
+
+    def direction(self, eta, g, beta):
+        """eta = -g + beta * eta (Eq. DaiYuan2)."""
+        import torch
+        if eta.shape != g.shape:
+            raise ValueError("shape mismatch")
+        st = self.lib.holo_direction(self.ctx, _ptr(eta, torch.complex64, None, "eta"),
+                                     _ptr(g, torch.complex64, None, "g"), float(beta), eta.numel())
+        _check(self.lib, self.ctx, st, "holo_direction")
+
+    def workspace_bytes(self):
+        v = ctypes.c_longlong(0)
+        _check(self.lib, self.ctx, self.lib.holo_workspace_bytes(self.ctx, ctypes.byref(v)),
+               "holo_workspace_bytes")
+        return v.value
+
+    def launch_count(self):
+        v = ctypes.c_longlong(0)
+        _check(self.lib, self.ctx, self.lib.holo_launch_count(self.ctx, ctypes.byref(v)),
+               "holo_launch_count")
+        return v.value

@@ -1,0 +1,76 @@
+"""C-ABI checks that need no GPU: the library builds, loads, exports every symbol that
+include/holo.h declares, and rejects invalid arguments before touching the device."""
+
+import ctypes
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_2407_20304_gb300 import build as b
+    b.build()
+    from paper_2407_20304_gb300 import _lib
+    return _lib.load()
+
+
+def _declared():
+    src = open(os.path.join(ROOT, "include", "holo.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(holo_[a-z_]+)\s*\(", src)))
+
+
+def test_every_declared_symbol_is_exported(lib):
+    from paper_2407_20304_gb300 import _lib
+    decl = _declared()
+    assert len(decl) >= 16
+    for name in decl:
+        assert hasattr(lib, name), name
+    assert sorted(_lib.EXPORTS) == decl
+
+
+def test_status_strings(lib):
+    for s in range(8):
+        assert lib.holo_status_string(s)
+    assert lib.holo_last_error(None) == b""
+
+
+def _geo(**kw):
+    from paper_2407_20304_gb300 import _lib
+    g = _lib.HoloGeometry()
+    base = dict(n=64, pad=128, n_angles=4, n_dist=4, chunk=0, wavelength=3.72e-11, pixel=1e-8,
+                Z=1.208, w_ref=1.0, ext=1.0)
+    base.update({k: v for k, v in kw.items() if k != "z"})
+    for k, v in base.items():
+        setattr(g, k, v)
+    for j, z in enumerate(kw.get("z", (4.6e-4, 5.1e-4, 6.2e-4, 8.3e-4))):
+        g.z[j] = z
+    return g
+
+
+@pytest.mark.parametrize("kw,expect", [
+    (dict(n=63), 1), (dict(n=8), 1), (dict(pad=32), 1), (dict(n_dist=0), 1), (dict(n_dist=9), 1),
+    (dict(z=(5e-4, 4e-4, 6e-4, 7e-4)), 1), (dict(z=(4e-4, 5e-4, 6e-4, 2.0)), 1),
+    (dict(wavelength=-1.0), 1), (dict(chunk=9), 1), (dict(n_angles=0), 1),
+    (dict(pad=96), 7), (dict(pad=8192, n=64), 7),
+])
+def test_create_rejects_bad_geometry(lib, kw, expect):
+    g = _geo(**kw)
+    out = ctypes.c_void_p(123)
+    st = lib.holo_create(ctypes.byref(g), None, ctypes.byref(out))
+    assert st == expect
+    assert out.value is None
+
+
+def test_null_arguments(lib):
+    assert lib.holo_create(None, None, None) == 1
+    assert lib.holo_destroy(None) == 0
+    d = ctypes.c_double()
+    assert lib.holo_forward(None, 0, 1, None, None, ctypes.byref(d)) == 1
+    assert lib.holo_gradient(None, 0, 1, None, None, None, None, 0) == 1
+    assert lib.holo_dot(None, None, None, 0, ctypes.byref(d)) == 1
+    assert lib.holo_step(None, None, None, 1.0, 0) == 1

@@ -1,0 +1,205 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 oracle.
+
+Tolerances (relative L2 against the oracle): loss 1e-5, gradients 1e-4, the targets the
+FP32-wavefield / FP64-reduction design must meet; fields and single propagations 1e-5.
+Inputs come from holo_synth; data are made by the oracle, never by the CUDA path.
+"""
+
+import numpy as np
+import pytest
+
+import holo_synth as hs
+from oracle import holo as oh
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+G = hs.WORKLOAD_GEOMETRY
+LOSS_TOL, GRAD_TOL, FIELD_TOL = 1e-5, 1e-4, 1e-5
+
+
+def rel(a, b):
+    return float(np.linalg.norm(np.asarray(a) - np.asarray(b)) / max(np.linalg.norm(b), 1e-300))
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    import __graft_entry__
+    __graft_entry__.build()
+
+
+def dev(a, dtype):
+    return torch.tensor(np.ascontiguousarray(a), dtype=dtype, device="cuda")
+
+
+def make_problem(n, P, K, J=4, ext=1.0, w_ref=1.0, seed=0, noiseless=False, z=None):
+    rng = hs.rng_for(hs.SEED_BASE + 7, seed)
+    z = tuple(z or G["z"][:J])
+    geo = oh.Geometry(G["wavelength"], G["pixel"], G["Z"], z, n, P, ext=ext, w_ref=w_ref)
+    w = hs.Workload("t", n, P, K, J, "ellipses", n * 40.0 / 128, 0.0, K, seed)
+    psi_true = hs.object_stack(w, range(K), rng)
+    q_true = hs.striped_probe(P, n * 40.0 / 128, rng)
+    t = hs.sample_shifts(K, J, rng).astype(np.float32).astype(np.float64)
+    sqrt_d = np.abs(oh.forward(psi_true, q_true, t, geo))
+    sqrt_dref = np.abs(oh.reference_field(q_true, geo))
+    if not noiseless:
+        sqrt_d = hs.poisson_amplitude(sqrt_d ** 2, 1e4, rng)
+        sqrt_dref = hs.poisson_amplitude(sqrt_dref ** 2, 1e4, rng)
+    psi0 = np.ones((K, n, n), np.complex128) if ext == 1.0 else hs.transmittance(
+        -0.5 * rng.uniform(0, 1, (K, n, n)))
+    q0 = hs.perturbed_probe(q_true, rng)
+    # evaluation points are rounded to complex64 so both sides see the same inputs
+    psi0 = psi0.astype(np.complex64).astype(np.complex128)
+    q0 = q0.astype(np.complex64).astype(np.complex128)
+    sqrt_d = sqrt_d.astype(np.float32).astype(np.float64)
+    sqrt_dref = sqrt_dref.astype(np.float32).astype(np.float64)
+    return dict(geo=geo, psi=psi0, q=q0, t=t, sqrt_d=sqrt_d, sqrt_dref=sqrt_dref,
+                psi_true=psi_true, q_true=q_true)
+
+
+def make_holo(pr, chunk=0):
+    from paper_2407_20304_gb300 import Holo
+    geo = pr["geo"]
+    K = pr["psi"].shape[0]
+    h = Holo(geo.n, K, geo.n_dist, geo.wavelength, geo.pixel, geo.Z, geo.z, pad=geo.P,
+             chunk=chunk, w_ref=geo.w_ref, ext=geo.ext)
+    h.set_shifts(pr["t"].astype(np.float32))
+    h.set_data(dev(pr["sqrt_d"], torch.float32),
+               dev(pr["sqrt_dref"], torch.float32) if geo.w_ref else None)
+    h.set_probe(dev(pr["q"], torch.complex64))
+    return h
+
+
+# ------------------------------------------------------------------ D_z
+
+@pytest.mark.parametrize("P", [16, 32, 64, 128, 256, 512, 1024, 2048, 4096])
+def test_propagate_matches_oracle(P):
+    from paper_2407_20304_gb300 import Holo
+    n = max(16, P // 2)
+    rng = np.random.default_rng(P)
+    x = (rng.standard_normal((P, P)) + 1j * rng.standard_normal((P, P))).astype(np.complex64)
+    h = Holo(n, 1, 1, G["wavelength"], G["pixel"], G["Z"], G["z"][:1], pad=P)
+    for z in (4.598e-4, -2.1e-4):
+        got = h.propagate(dev(x, torch.complex64), z).cpu().numpy()
+        ref = oh.propagate(x.astype(np.complex128), z, G["wavelength"], G["pixel"])
+        assert rel(got, ref) < FIELD_TOL, (P, z, rel(got, ref))
+
+
+# ------------------------------------------------------------------ forward
+
+@pytest.mark.parametrize("n,P,K,ext", [(16, 32, 2, 1.0), (32, 64, 3, 0.0), (64, 128, 2, 1.0),
+                                       (100, 256, 2, 1.0), (128, 256, 3, 1.0),
+                                       (24, 64, 1, 1.0)])
+def test_forward_fields_and_loss(n, P, K, ext):
+    pr = make_problem(n, P, K, ext=ext, seed=n + K)
+    h = make_holo(pr)
+    u = torch.empty((K, 4, n, n), dtype=torch.complex64, device="cuda")
+    loss = h.forward(dev(pr["psi"], torch.complex64), u_out=u)
+    u_ref = oh.forward(pr["psi"], pr["q"], pr["t"], pr["geo"])
+    F_ref = oh.functional(pr["psi"], pr["q"], pr["t"], pr["sqrt_d"], pr["sqrt_dref"], pr["geo"])
+    assert rel(u.cpu().numpy(), u_ref) < FIELD_TOL
+    assert abs(loss - F_ref) / F_ref < LOSS_TOL
+
+
+# ------------------------------------------------------------------ gradients
+
+@pytest.mark.parametrize("n,P,K,J,ext,w_ref", [
+    (16, 32, 2, 4, 1.0, 1.0), (32, 64, 3, 4, 1.0, 1.0), (32, 64, 2, 4, 0.0, 0.0),
+    (64, 128, 2, 4, 1.0, 0.0), (100, 256, 2, 4, 1.0, 1.0), (128, 256, 4, 4, 1.0, 1.0),
+    (64, 128, 3, 1, 1.0, 1.0), (48, 128, 2, 3, 1.0, 1.0), (256, 512, 2, 4, 1.0, 1.0),
+])
+def test_gradient_matches_oracle(n, P, K, J, ext, w_ref):
+    pr = make_problem(n, P, K, J=J, ext=ext, w_ref=w_ref, seed=3 * n + J)
+    h = make_holo(pr)
+    loss, gp, gq = h.gradient(dev(pr["psi"], torch.complex64))
+    F, gp_ref, gq_ref = oh.gradients(pr["psi"], pr["q"], pr["t"], pr["sqrt_d"], pr["sqrt_dref"],
+                                     pr["geo"])
+    assert abs(loss - F) / F < LOSS_TOL
+    assert rel(gp.cpu().numpy(), gp_ref) < GRAD_TOL
+    assert rel(gq.cpu().numpy(), gq_ref) < GRAD_TOL
+
+
+def test_chunks_accumulate_to_full_gradient():
+    pr = make_problem(64, 128, 5, seed=11)
+    h = make_holo(pr, chunk=2)
+    psi = dev(pr["psi"], torch.complex64)
+    gp = torch.zeros_like(psi)
+    gq = torch.zeros((128, 128), dtype=torch.complex64, device="cuda")
+    loss = 0.0
+    for k0 in range(0, 5, 2):
+        nk = min(2, 5 - k0)
+        loss, _, _ = h.gradient(psi[k0:k0 + nk], grad_psi=gp[k0:k0 + nk], grad_q=gq, k0=k0,
+                                accumulate=True, loss_in=loss)
+    F, gp_ref, gq_ref = oh.gradients(pr["psi"], pr["q"], pr["t"], pr["sqrt_d"], pr["sqrt_dref"],
+                                     pr["geo"])
+    assert abs(loss - F) / F < LOSS_TOL
+    assert rel(gp.cpu().numpy(), gp_ref) < GRAD_TOL
+    assert rel(gq.cpu().numpy(), gq_ref) < GRAD_TOL
+
+
+def test_gradient_host_buffers_match_device_call():
+    pr = make_problem(64, 128, 3, seed=5)
+    h = make_holo(pr)
+    loss_d, gp_d, gq_d = h.gradient(dev(pr["psi"], torch.complex64))
+    loss_h, gp_h, gq_h = h.gradient_host(pr["psi"].astype(np.complex64),
+                                         sqrt_d=pr["sqrt_d"].astype(np.float32),
+                                         q=pr["q"].astype(np.complex64))
+    assert loss_h == loss_d
+    np.testing.assert_array_equal(gp_h, gp_d.cpu().numpy())
+    np.testing.assert_array_equal(gq_h, gq_d.cpu().numpy())
+
+
+def test_zero_gradient_at_noiseless_truth():
+    pr = make_problem(64, 128, 2, seed=21, noiseless=True)
+    h = make_holo(pr)
+    h.set_probe(dev(pr["q_true"].astype(np.complex64), torch.complex64))
+    psi_t = pr["psi_true"].astype(np.complex64)
+    loss, gp, gq = h.gradient(dev(psi_t, torch.complex64))
+    loss1, gp1, gq1 = h.gradient(dev(np.ones_like(psi_t), torch.complex64))
+    assert loss < 1e-6 * loss1
+    assert np.linalg.norm(gp.cpu().numpy()) < 1e-3 * np.linalg.norm(gp1.cpu().numpy())
+
+
+def test_deterministic_repeat():
+    pr = make_problem(64, 128, 3, seed=8)
+    h = make_holo(pr)
+    psi = dev(pr["psi"], torch.complex64)
+    a = h.gradient(psi)
+    b = h.gradient(psi)
+    assert a[0] == b[0]
+    assert torch.equal(a[1], b[1]) and torch.equal(a[2], b[2])
+
+
+# ------------------------------------------------------------------ CG vector ops
+
+def test_dot_step_direction():
+    from paper_2407_20304_gb300 import Holo
+    h = Holo(16, 1, 1, G["wavelength"], G["pixel"], G["Z"], G["z"][:1], pad=32)
+    rng = np.random.default_rng(3)
+    for n in (1, 1000, 123457):
+        a = (rng.standard_normal(n) + 1j * rng.standard_normal(n)).astype(np.complex64)
+        b = (rng.standard_normal(n) + 1j * rng.standard_normal(n)).astype(np.complex64)
+        ref = np.real(np.vdot(a.astype(np.complex128), b.astype(np.complex128)))
+        got = h.dot(dev(a, torch.complex64), dev(b, torch.complex64))
+        assert abs(got - ref) <= 1e-5 * np.sqrt(n) * (abs(ref) + 1)
+        x = dev(a, torch.complex64)
+        h.step(x, dev(b, torch.complex64), 0.37)
+        np.testing.assert_allclose(x.cpu().numpy(), a + np.float32(0.37) * b, rtol=1e-6, atol=1e-6)
+        e = dev(a, torch.complex64)
+        h.direction(e, dev(b, torch.complex64), -1.5)
+        np.testing.assert_allclose(e.cpu().numpy(), -b + np.float32(-1.5) * a, rtol=1e-6, atol=1e-6)
+
+
+def test_state_and_argument_errors():
+    from paper_2407_20304_gb300 import Holo, HoloError
+    h = Holo(32, 2, 2, G["wavelength"], G["pixel"], G["Z"], G["z"][:2], pad=64)
+    psi = torch.ones((2, 32, 32), dtype=torch.complex64, device="cuda")
+    with pytest.raises(HoloError, match="STATE"):
+        h.gradient(psi)
+    h.set_shifts(np.zeros((2, 2, 2), np.float32))
+    with pytest.raises(HoloError, match="STATE"):
+        h.forward(psi)
+    with pytest.raises(HoloError, match="ARG"):
+        h.set_shifts(np.full((2, 2, 2), np.nan, np.float32))
