@@ -1,0 +1,494 @@
+#!/usr/bin/env python
+"""Throughput of the holography gradient: plane-gradient evaluations per second.
+
+One step is one pass of the whole hot path over one chunk of angles: probe propagation
+(p_j = D_{omega_j} q, C D_{zeta_0} q), the fused forward / residual / adjoint passes
+that give F2, grad_psi and grad_q (Eq. min1, Eq. gradpsi), the FP64 reductions, and the
+Dai-Yuan conjugate-gradient update of psi and q (Eq. DaiYuan2: three FP64 inner
+products, the direction update and the step x += gamma eta for each block).  A
+plane-gradient evaluation is one (angle, distance) plane; a step over a chunk of K
+angles and J distances is K*J of them.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+N > 1 runs one process per GPU (torchrun); each rank reconstructs its own angle chunk
+(the paper's independent 150-angle chunks, Sec. 4), so per-GPU work is fixed (weak
+scaling) and there is no data-path collective.  `--impl reference` times the FP64 CPU
+oracle on the host cores on a bounded sample of the same workload.
+"""
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import holo_synth as hs  # noqa: E402
+
+METRIC = "plane-gradient evals/s at 2048^2 x 4 dist"
+UNIT = "plane-grads/s"
+KERNEL_SOURCES = ("paper_2407_20304_gb300/csrc/holo_kernels.cuh",
+                  "paper_2407_20304_gb300/csrc/holo_fft.cuh")
+FP32_LANES_PER_SM = 128
+SMS = 152
+MAX_SM_GHZ = 2.07
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=30)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
+    ap.add_argument("--workload", default="large", choices=("large", "autograd", "medium"))
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=20.0)
+    ap.add_argument("--chunk", type=int, default=0,
+                    help="angles per GPU (default: the workload's chunk); small values make "
+                         "profiling captures small")
+    return ap.parse_args()
+
+
+def peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        d = json.load(open(path))
+        return {"hbm_gbs": float(d["hbm_gbs"]), "bf16_tflops": float(d["bf16_tflops"]),
+                "source": "measured"}
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "source": "fallback"}
+
+
+def kernel_hash():
+    h = hashlib.sha256()
+    for p in KERNEL_SOURCES:
+        h.update(open(os.path.join(ROOT, p), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def recorded_traffic(kernel):
+    """DRAM bytes per launch of `kernel` from the committed ncu summary, if the kernel
+    sources are unchanged since it was taken (else None)."""
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    if not os.path.exists(path):
+        return None
+    d = json.load(open(path))
+    e = d.get(kernel)
+    if not e or e.get("kernel_hash") != kernel_hash():
+        return None
+    return e.get("bytes_per_launch_full")
+
+
+# ---------------------------------------------------------------- geometry helpers
+
+def derived(z, Z):
+    z = np.asarray(z, float)
+    mt = z / z[0]
+    zeta = z * (Z - z) / Z
+    return mt, zeta
+
+
+def boxes(n, P, mt, shifts):
+    """Box sizes (bys, bxs) per plane, as the library computes them (support of R0)."""
+    def ax(m, t):
+        a = P // 2 + (t - n // 2 - 1.0) / m
+        b = P // 2 + (t + n // 2) / m
+        s, e = int(np.floor(a)) - 1, int(np.ceil(b)) + 2
+        return max(min(e, P) - max(s, 0), 0)
+    K, J = shifts.shape[:2]
+    return [[(ax(mt[j], shifts[k, j, 0]), ax(mt[j], shifts[k, j, 1])) for j in range(J)]
+            for k in range(K)]
+
+
+def algorithmic_costs(n, P, box):
+    """Per-pass algorithmic HBM bytes and FP32 flops over the chunk (sum over planes).
+
+    FFT flops use the 5 N log2 N convention for a complex FFT of length N; bytes count
+    each input read and output written once (complex64 = 8 B, amplitudes 4 B)."""
+    fft = 5.0 * P * np.log2(P)
+    K, J = len(box), len(box[0])
+    out = {k: {"bytes": 0.0, "flops": 0.0} for k in ("pass_a", "pass_b", "pass_c", "pass_d")}
+    for k in range(K):
+        for j in range(J):
+            sy, sx = box[k][j]
+            out["pass_a"]["bytes"] += 8 * n * n + 8 * sy * sx + 8 * sy * n
+            out["pass_a"]["flops"] += sy * (2 * fft + 6 * P) + 30 * sy * sx
+            out["pass_b"]["bytes"] += 8 * sy * n + 8 * n * n + 4 * n * n + 8 * sy * n + 8 * n * n
+            out["pass_b"]["flops"] += n * (4 * fft + 12 * P) + 20 * n * n
+            out["pass_c"]["bytes"] += 8 * sy * n + 8 * sy * sx + 8 * n * n + 8 * sy * n + 8 * sy * sx
+            out["pass_c"]["flops"] += sy * (2 * fft + 6 * P) + 60 * sy * sx
+            out["pass_d"]["bytes"] += 8 * sy * n
+            out["pass_d"]["flops"] += 8 * n * n
+        out["pass_d"]["bytes"] += 8 * n * n
+    return out
+
+
+# ---------------------------------------------------------------- clocks
+
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons while the timed region runs."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+    NAMES = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.idx = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.idx}", f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except (OSError, ValueError):
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *exc):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+            self.thread.join(timeout=2)
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 7:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                mx.append(float(parts[1]))
+            except ValueError:
+                continue
+            for name, val in zip(self.NAMES, parts[3:7]):
+                if val.lower().startswith("active"):
+                    reasons.add(name)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx),
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ---------------------------------------------------------------- workload
+
+def workload_inputs(w, rank):
+    """psi_true, q_true, shifts of the rank's chunk (seeded by the workload and rank)."""
+    rng = hs.rng_for(w.seed, rank)
+    angles = range(rank * w.chunk, rank * w.chunk + w.chunk)
+    psi_true = hs.object_stack(w, angles, rng).astype(np.complex64)
+    q_true = hs.striped_probe(w.P, w.probe_sigma, rng).astype(np.complex64)
+    shifts = hs.sample_shifts(w.chunk, w.n_dist, rng).astype(np.float32)
+    q0 = hs.perturbed_probe(q_true, rng).astype(np.complex64)
+    return psi_true, q_true, shifts, q0
+
+
+def run_ours(args, w, rank, world, local_rank):
+    import torch
+    from paper_2407_20304_gb300 import Holo
+    dev = torch.device("cuda", local_rank)
+    torch.cuda.set_device(dev)
+    g = hs.WORKLOAD_GEOMETRY
+    n, P, K, J = w.n, w.P, w.chunk, w.n_dist
+    psi_true, q_true, shifts, q0 = workload_inputs(w, rank)
+    h = Holo(n, K, J, g["wavelength"], g["pixel"], g["Z"], g["z"][:J], pad=P, chunk=K)
+    h.set_shifts(shifts)
+    # synthetic data: |u|^2 of the true object and probe, Poisson noise at w.counts counts
+    gen = torch.Generator(device=dev)
+    gen.manual_seed(w.seed + rank)
+    psi_t = torch.from_numpy(psi_true).to(dev)
+    qt = torch.from_numpy(q_true).to(dev)
+    h.set_probe(qt)
+    u = torch.empty((K, J, n, n), dtype=torch.complex64, device=dev)
+    h.set_data(torch.ones((K, J, n, n), dtype=torch.float32, device=dev),
+               torch.ones((n, n), dtype=torch.float32, device=dev))
+    h.forward(psi_t, u_out=u)
+    inten = u.abs().square_()
+    del u
+    c = w.counts / inten.mean()
+    sqrt_d = torch.poisson(inten.mul_(c), generator=gen).div_(c).sqrt_()
+    del inten
+    _, zeta = derived(g["z"][:J], g["Z"])
+    lo = P // 2 - n // 2
+    bref = h.propagate(qt, zeta[0])[lo:lo + n, lo:lo + n]
+    iref = bref.abs().square()
+    cr = w.counts / iref.mean()
+    sqrt_dref = torch.poisson(iref * cr, generator=gen).div_(cr).sqrt_().contiguous()
+    h.set_data(sqrt_d, sqrt_dref)
+    del psi_t, qt
+
+    psi = torch.ones((K, n, n), dtype=torch.complex64, device=dev)
+    q = torch.from_numpy(q0).to(dev)
+    gpsi = [torch.empty_like(psi), torch.empty_like(psi)]
+    gq = [torch.empty_like(q), torch.empty_like(q)]
+    eta_psi, eta_q = torch.zeros_like(psi), torch.zeros_like(q)
+    state = {"cur": 0, "first": True, "gam": None}
+
+    def step():
+        cur = state["cur"]
+        h.set_probe(q)
+        loss, gp, gqc = h.gradient(psi, grad_psi=gpsi[cur], grad_q=gq[cur])
+        if state["gam"] is None:
+            # fixed small steps (relative 1e-3 of each block) for the benchmark's updates
+            state["gam"] = (1e-3 * (K * n * n) ** 0.5 / max(np.sqrt(h.dot(gp, gp)), 1e-30),
+                            1e-3 * np.sqrt(h.dot(q, q)) / max(np.sqrt(h.dot(gqc, gqc)), 1e-30))
+        for gcur, gprev, eta, x, gam in ((gp, gpsi[1 - cur], eta_psi, psi, state["gam"][0]),
+                                         (gqc, gq[1 - cur], eta_q, q, state["gam"][1])):
+            beta = 0.0
+            if not state["first"]:
+                num = h.dot(gcur, gcur)
+                den = h.dot(gcur, eta) - h.dot(gprev, eta)
+                beta = num / den if den > 0 else 0.0
+            h.direction(eta, gcur, beta)
+            h.step(x, eta, gam)
+        state["first"] = False
+        state["cur"] = 1 - cur
+        return loss
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    dist = world > 1
+    if dist:
+        import torch.distributed as tdist
+        tdist.barrier()
+    torch.cuda.synchronize()
+    stream = torch.cuda.current_stream(dev)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    gpu_index = int(os.environ.get("CUDA_VISIBLE_DEVICES", str(local_rank)).split(",")[local_rank]) \
+        if os.environ.get("CUDA_VISIBLE_DEVICES", "").replace(",", "").isdigit() else local_rank
+    l0 = h.launch_count()
+    h.set_timing(True)
+    with ClockSampler(gpu_index) as clk:
+        e0.record(stream)
+        for _ in range(args.steps):
+            loss = step()
+        e1.record(stream)
+        torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    launches = h.launch_count() - l0
+    timing = h.get_timing()
+    h.set_timing(False)
+    if dist:
+        t = torch.tensor([ms], device=dev)
+        tdist.all_reduce(t, op=tdist.ReduceOp.MAX)
+        ms = float(t.item())
+        tdist.barrier()
+    planes = K * J * world
+    value = planes * args.steps / (ms / 1e3)
+
+    # roofline of the dominant kernel
+    mt, _ = derived(g["z"][:J], g["Z"])
+    costs = algorithmic_costs(n, P, boxes(n, P, mt, shifts))
+    passes = [p for p in ("pass_a", "pass_b", "pass_c", "pass_d")]
+    top = max(passes, key=lambda p: timing[p][0])
+    top_ms = timing[top][0] / max(timing[top][1], 1)
+    pk = peaks()
+    gbs = costs[top]["bytes"] / (top_ms / 1e3) / 1e9
+    tfl = costs[top]["flops"] / (top_ms / 1e3) / 1e12
+    clocks = clk.summary()
+    fp32_peak = SMS * FP32_LANES_PER_SM * 2 * MAX_SM_GHZ / 1e3
+    hbm_frac, alu_frac = gbs / pk["hbm_gbs"], tfl / fp32_peak
+    traffic = recorded_traffic(top)
+    if alu_frac >= hbm_frac:
+        roof = {"bound": "alu", "achieved": round(tfl, 2), "peak": round(fp32_peak, 1),
+                "unit": "TFLOP/s", "frac": round(alu_frac, 4), "traffic": traffic,
+                "kernel": top, "hbm_gbs": round(gbs, 1), "hbm_frac": round(hbm_frac, 4),
+                "peak_source": f"FP32: {SMS} SMs x {FP32_LANES_PER_SM} lanes x 2 x "
+                               f"{MAX_SM_GHZ} GHz; HBM {pk['source']} {pk['hbm_gbs']} GB/s"}
+    else:
+        roof = {"bound": "hbm", "achieved": round(gbs, 1), "peak": pk["hbm_gbs"], "unit": "GB/s",
+                "frac": round(hbm_frac, 4), "traffic": traffic, "kernel": top,
+                "alu_tflops": round(tfl, 2), "alu_frac": round(alu_frac, 4),
+                "peak_source": f"HBM {pk['source']}"}
+    per_pass = {p: {"ms_per_step": round(timing[p][0] / args.steps, 3),
+                    "launches_per_step": timing[p][1] / args.steps}
+                for p in hs_timers()}
+
+    # end to end through the host-buffer entry point
+    e2e = None
+    if not args.no_e2e:
+        e2e = run_e2e(h, args, w, psi, q, sqrt_d, dev, planes, dist)
+    result = {
+        "metric": METRIC, "value": round(value, 1), "unit": UNIT, "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms / args.steps, 3),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic",
+        "config": {"workload": f"{w.name}: psi {n}^2 (pad {P}), {K}-angle chunk x {J} distances "
+                               f"per GPU, layered phantom, striped probe, Poisson {w.counts:g}",
+                   "n": n, "pad": P, "angles_per_gpu": K, "n_dist": J,
+                   "planes_per_step": planes, "reductions": "f64",
+                   "l2": "inputs larger than L2 (psi chunk %.1f GB, data %.1f GB per GPU)"
+                         % (K * n * n * 8 / 1e9, K * J * n * n * 4 / 1e9),
+                   "step": "set_probe + gradient (F2, grad_psi, grad_q) + DY direction + step"},
+        "roofline": roof, "clocks": clocks, "gpu_launches": launches, "per_pass": per_pass,
+        "final_loss": loss,
+    }
+    if e2e:
+        result["e2e"] = e2e
+    return result, h
+
+
+def hs_timers():
+    from paper_2407_20304_gb300 import _lib
+    return _lib.TIMERS
+
+
+def run_e2e(h, args, w, psi, q, sqrt_d, dev, planes, dist):
+    """Same metric through holo_gradient_host: inputs copied from pinned host memory and
+    results read back inside the timed region, every step."""
+    import torch
+    K, J, n, P = w.chunk, w.n_dist, w.n, w.P
+    pin = dict(pin_memory=True)
+    psi_h = torch.empty((K, n, n), dtype=torch.complex64, **pin)
+    psi_h.copy_(psi)
+    d_h = torch.empty((K, J, n, n), dtype=torch.float32, **pin)
+    d_h.copy_(sqrt_d)
+    q_h = torch.empty((P, P), dtype=torch.complex64, **pin)
+    q_h.copy_(q)
+    gp_h = torch.empty((K, n, n), dtype=torch.complex64, **pin)
+    gq_h = torch.empty((P, P), dtype=torch.complex64, **pin)
+    a = [x.numpy() for x in (psi_h, d_h, q_h, gp_h, gq_h)]
+    h.gradient_host(a[0], sqrt_d=a[1], q=a[2], grad_psi=a[3], grad_q=a[4])
+    steps = max(3, min(args.steps, 10))
+    if dist:
+        import torch.distributed as tdist
+        tdist.barrier()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        h.gradient_host(a[0], sqrt_d=a[1], q=a[2], grad_psi=a[3], grad_q=a[4])
+    torch.cuda.synchronize()
+    dt = time.perf_counter() - t0
+    if dist:
+        t = torch.tensor([dt], device=dev)
+        tdist.all_reduce(t, op=tdist.ReduceOp.MAX)
+        dt = float(t.item())
+    h2d = psi_h.numel() * 8 + d_h.numel() * 4 + q_h.numel() * 8
+    d2h = gp_h.numel() * 8 + gq_h.numel() * 8 + 16
+    return {"value": round(planes * steps / dt, 1), "unit": UNIT, "steps": steps,
+            "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+            "api": "holo_gradient_host (psi, data, q host -> grad_psi, grad_q, loss host)"}
+
+
+# ---------------------------------------------------------------- oracle (CPU)
+
+def oracle_setup(w):
+    """Inputs of the oracle samples: the first angle of the workload at the start point
+    psi = 1, with data |u| of the true object made by the oracle itself."""
+    from oracle import holo as oh
+    g = hs.WORKLOAD_GEOMETRY
+    rng = hs.rng_for(w.seed, 0)
+    psi_true = hs.object_stack(w, range(1), rng)
+    q_true = hs.striped_probe(w.P, w.probe_sigma, rng)
+    shifts = hs.sample_shifts(1, w.n_dist, rng).astype(np.float32).astype(np.float64)
+    geo = oh.Geometry(g["wavelength"], g["pixel"], g["Z"], tuple(g["z"][:w.n_dist]), w.n, w.P)
+    sqrt_d = np.abs(oh.forward(psi_true, q_true, shifts, geo))[0]
+    return np.ones((w.n, w.n), np.complex128), q_true, shifts, sqrt_d, geo
+
+
+def oracle_plane(inputs, j):
+    from oracle import holo as oh
+    psi0, q, shifts, sqrt_d, geo = inputs
+    jj = j % geo.n_dist
+    return oh.plane_gradient(psi0, q, shifts[0, jj], sqrt_d[jj], geo, jj)
+
+
+def cpu_baseline(w, budget_s):
+    """The oracle as it stands, timed on the host cores for about `budget_s` seconds."""
+    inputs = oracle_setup(w)
+    done, t_used = 0, 0.0
+    while done < 1 or t_used < budget_s:
+        t0 = time.perf_counter()
+        oracle_plane(inputs, done)
+        t_used += time.perf_counter() - t0
+        done += 1
+    return {"value": round(done / t_used, 4), "unit": UNIT, "cores": os.cpu_count(),
+            "kind": "oracle",
+            "sample": f"{done} plane-gradient(s) of the {w.name} workload (n={w.n}, P={w.P}, "
+                      f"first angle, distances cycled) by the FP64 oracle in {t_used:.1f} s; "
+                      f"scipy.fft on all host cores"}
+
+
+def run_reference(args, w):
+    """The reference arm: the oracle timed as it stands, one plane-gradient per step."""
+    inputs = oracle_setup(w)
+    for s in range(args.warmup):
+        oracle_plane(inputs, s)
+    t0 = time.perf_counter()
+    for s in range(args.steps):
+        oracle_plane(inputs, s)
+    dt = time.perf_counter() - t0
+    value = args.steps / dt
+    sample = (f"{args.steps} plane-gradients of the {w.name} workload (n={w.n}, P={w.P}), one "
+              f"per step, FP64 oracle with scipy.fft on all host cores")
+    return {"metric": METRIC, "value": round(value, 4), "unit": UNIT, "n_gpus": 1,
+            "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": round(dt / args.steps * 1e3, 1), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "impl": "reference",
+            "config": {"workload": f"{w.name}: psi {w.n}^2 (pad {w.P}), one plane per step"},
+            "cpu_baseline": {"value": round(value, 4), "unit": UNIT, "cores": os.cpu_count(),
+                             "kind": "oracle", "sample": sample},
+            "e2e": {"value": round(value, 4), "unit": UNIT, "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+
+
+def main():
+    args = parse()
+    w = hs.workloads()[args.workload]
+    if args.chunk:
+        import dataclasses
+        w = dataclasses.replace(w, chunk=args.chunk)
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        if rank == 0:
+            print(json.dumps(run_reference(args, w)), flush=True)
+        return
+    import torch
+    if world > 1:
+        import torch.distributed as tdist
+        torch.cuda.set_device(local_rank)
+        tdist.init_process_group("nccl", device_id=torch.device("cuda", local_rank))
+    import __graft_entry__
+    if rank == 0 or world == 1:
+        __graft_entry__.build()
+    if world > 1:
+        tdist.barrier()
+        __graft_entry__.build()
+    result, h = run_ours(args, w, rank, world, local_rank)
+    h.close()
+    if rank == 0 and world == 1 and not args.no_cpu:
+        result["cpu_baseline"] = cpu_baseline(w, args.cpu_seconds)
+    if rank == 0:
+        print(json.dumps(result), flush=True)
+    if world > 1:
+        tdist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

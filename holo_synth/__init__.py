@@ -139,8 +139,9 @@ class LayeredCube:
             h -= rng.integers(2, 21)
         self.h = np.array(hs)
         self.density = np.array(dens)
-        # shell i occupies cube(h_i) minus cube(h_{i+1}); telescope the densities
-        self.coef = self.density - np.append(self.density[1:], 0.0)
+        # shell i occupies cube(h_i) minus cube(h_{i+1}), so the projected phase is
+        # -sum_i rho_i (proj(h_i) - proj(h_{i+1})) = -sum_i (rho_i - rho_{i-1}) proj(h_i)
+        self.coef = self.density - np.concatenate(([0.0], self.density[:-1]))
         self.scale = 1.0
         self.scale = np.pi / max(1e-12, -self.phase(np.pi / 4).min())
 

@@ -167,6 +167,26 @@ holo_status holo_step(holo_ctx* ctx, void* x, const void* eta, double gamma, lon
 holo_status holo_direction(holo_ctx* ctx, void* eta, const void* g, double beta,
                            long long n_c64);
 
+/* Per-pass device timing (CUDA events recorded on the context's stream around each
+ * launch group).  Pass ids: */
+#define HOLO_T_PROBE 0   /* holo_set_probe: p_j = D_{omega_j} q and C D_{zeta_0} q */
+#define HOLO_T_PASS_A 1  /* resample x probe, row propagation of the box rows */
+#define HOLO_T_PASS_B 2  /* column propagation, amplitude residual, column adjoint */
+#define HOLO_T_PASS_C 3  /* row adjoint, conj(p) v, x-transpose, conj(w) v */
+#define HOLO_T_PASS_D 4  /* y-transpose, sum over distances -> grad_psi */
+#define HOLO_T_QGRAD 5   /* reductions and propagations of grad_q */
+#define HOLO_T_REDUCE 6  /* FP64 loss / inner-product reductions */
+#define HOLO_T_VECTOR 7  /* CG vector updates (step, direction) */
+#define HOLO_NUM_TIMERS 8
+
+/* enable != 0 starts recording (and clears earlier records); 0 stops. */
+holo_status holo_set_timing(holo_ctx* ctx, int enable);
+
+/* Synchronises the stream and returns, per pass id, the summed device time in ms and the
+ * number of kernel launches recorded since holo_set_timing(ctx, 1).  Arrays of
+ * HOLO_NUM_TIMERS entries; either may be NULL. */
+holo_status holo_get_timing(holo_ctx* ctx, double* ms, long long* launches);
+
 /* Bytes of device workspace currently held by the context. */
 holo_status holo_workspace_bytes(const holo_ctx* ctx, long long* bytes);
 

@@ -19,8 +19,11 @@ STATUS = {0: "HOLO_OK", 1: "HOLO_ERR_ARG", 2: "HOLO_ERR_CUDA", 3: "HOLO_ERR_OOM"
 # Every symbol declared in include/holo.h.
 EXPORTS = ("holo_create", "holo_destroy", "holo_set_shifts", "holo_set_data", "holo_set_probe",
            "holo_forward", "holo_gradient", "holo_gradient_host", "holo_propagate", "holo_dot",
-           "holo_step", "holo_direction", "holo_workspace_bytes", "holo_launch_count",
-           "holo_status_string", "holo_last_error")
+           "holo_step", "holo_direction", "holo_set_timing", "holo_get_timing",
+           "holo_workspace_bytes", "holo_launch_count", "holo_status_string", "holo_last_error")
+
+# Pass ids of holo_get_timing (HOLO_T_* in include/holo.h).
+TIMERS = ("probe", "pass_a", "pass_b", "pass_c", "pass_d", "qgrad", "reduce", "vector")
 
 
 class HoloGeometry(ctypes.Structure):
@@ -66,6 +69,8 @@ def load():
         "holo_dot": [P, P, P, LL, ctypes.POINTER(D)],
         "holo_step": [P, P, P, D, LL],
         "holo_direction": [P, P, P, D, LL],
+        "holo_set_timing": [P, I],
+        "holo_get_timing": [P, P, P],
         "holo_workspace_bytes": [P, ctypes.POINTER(LL)],
         "holo_launch_count": [P, ctypes.POINTER(LL)],
     }

@@ -63,6 +63,15 @@ struct holo_ctx {
   PlaneDesc* d_planes = nullptr;
   bool have_shifts = false;
   int maxbys = 0, maxbxs = 0;
+  // FP64-built bilinear tap tables and the flat row list of all planes
+  holo::Tap* d_xtap = nullptr;
+  holo::Tap* d_ytap = nullptr;
+  holo::AdjTap* d_xadj = nullptr;
+  holo::AdjTap* d_yadj = nullptr;
+  int* d_rowstart = nullptr;
+  std::vector<int> rowstart;
+  int tap_stride = 0;
+  size_t tap_bytes = 0;
   // data
   const float* sqrt_d = nullptr;
   const float* sqrt_dref = nullptr;
@@ -96,6 +105,15 @@ struct holo_ctx {
   long long bytes = 0;
   long long launches = 0;
   std::string err;
+  // per-pass event timing
+  bool timing = false;
+  struct Rec {
+    int id;
+    cudaEvent_t a, b;
+    long long launches;
+  };
+  std::vector<Rec> recs;
+  std::vector<cudaEvent_t> pool;
 };
 
 namespace {
@@ -143,6 +161,40 @@ void dfree(holo_ctx* c, void* p, size_t bytes) {
 }
 
 bool is_pow2(int x) { return x > 0 && (x & (x - 1)) == 0; }
+
+// Scoped event pair around a group of launches of one pass (no-op unless timing is on).
+struct PassTimer {
+  holo_ctx* c;
+  int id;
+  long long l0;
+  cudaEvent_t a = nullptr;
+  PassTimer(holo_ctx* ctx, int pass) : c(ctx), id(pass), l0(ctx->launches) {
+    if (!c->timing) return;
+    a = take();
+    if (a) cudaEventRecord(a, c->stream);
+  }
+  cudaEvent_t take() {
+    if (!c->pool.empty()) {
+      cudaEvent_t e = c->pool.back();
+      c->pool.pop_back();
+      return e;
+    }
+    cudaEvent_t e = nullptr;
+    if (cudaEventCreate(&e) != cudaSuccess) {
+      cudaGetLastError();
+      return nullptr;
+    }
+    return e;
+  }
+  ~PassTimer() {
+    if (!c->timing || !a) return;
+    cudaEvent_t b = take();
+    if (!b) return;
+    cudaEventRecord(b, c->stream);
+    c->recs.push_back({id, a, b, c->launches - l0});
+  }
+};
+
 
 // exp(-i pi lambda z f^2) / P with f = k/(P dx), k in [-P/2, P/2)  (reading of D_z), FP64.
 std::vector<float2> chirp_table(int P, double lambda, double dx, double z) {
@@ -203,6 +255,37 @@ void axis_box(double mt, double t, int n, int P, int* lo, int* len) {
   e = std::min(e, P);
   *lo = s;
   *len = std::max(e - s, 0);
+}
+
+// Bilinear taps of the P-grid positions [lo, lo + len) along one axis (reading R4, FP64):
+// xi = m~ (X - P/2) - t + n/2, i0 = floor(xi), f = xi - i0; and their transpose: for each
+// psi index, the (at most two, consecutive) positions that reach it and their weights.
+void axis_taps(double mt, double t, int n, int P, int lo, int len, holo::Tap* taps,
+               holo::AdjTap* adj) {
+  for (int i = 0; i < n; ++i) adj[i] = holo::AdjTap{0, 0.f, 0.f, 0};
+  std::vector<char> seen(n, 0);
+  auto add = [&](int ip, int X, double w) {
+    if (ip < 0 || ip >= n || w == 0.0) return;
+    holo::AdjTap& a = adj[ip];
+    if (!seen[ip]) {
+      seen[ip] = 1;
+      a.X0 = X;
+      a.w0 = (float)w;
+    } else if (X == a.X0 + 1) {
+      a.w1 = (float)w;
+    } else if (X == a.X0) {
+      a.w0 = (float)(a.w0 + w);
+    }
+  };
+  for (int r = 0; r < len; ++r) {
+    const int X = lo + r;
+    const double xi = mt * (double)(X - P / 2) - t + (double)(n / 2);
+    const double i0 = std::floor(xi);
+    const double f = xi - i0;
+    taps[r] = holo::Tap{(int)i0, (float)f};
+    add((int)i0, X, 1.0 - f);
+    add((int)i0 + 1, X, f);
+  }
 }
 
 holo_status upload(holo_ctx* c, void* dst, const void* src, size_t bytes) {
@@ -299,19 +382,36 @@ PassArgs pass_args(holo_ctx* c, int k0, int nk, const void* psi) {
   for (int k = k0; k < k0 + nk; ++k)
     for (int j = 0; j < c->J; ++j) mb = std::max(mb, c->planes[(size_t)k * c->J + j].bys);
   a.max_box_rows = std::max(mb, 1);
+  a.xtap = c->d_xtap;
+  a.ytap = c->d_ytap;
+  a.xadj = c->d_xadj;
+  a.yadj = c->d_yadj;
+  a.tap_stride = c->tap_stride;
+  a.rowstart = c->d_rowstart;
+  a.line0 = c->rowstart[(size_t)k0 * c->J];
+  a.nlines = c->rowstart[(size_t)(k0 + nk) * c->J] - a.line0;
+  a.pass_b_items = nk * c->J * c->ops->pass_b_groups(c->n);
   return a;
 }
 
 // Passes A, B (and C, D for gradients), loss partial sums into d_red[0], reference term
 // into d_red[1] (only when k0 == 0 and w_ref != 0).
 holo_status run_eval(holo_ctx* c, PassArgs& a, bool gradient, float2* grad_q, unsigned flags) {
-  const int nbx = c->ops->pass_b_blocks_x(c->n);
-  const long long nparts = (long long)nbx * a.nk * c->J;
-  HOLO_LAUNCH(c, c->ops->pass_a(a, c->stream));
-  HOLO_LAUNCH(c, c->ops->pass_b(a, gradient ? 1 : 0, nbx, c->stream));
-  HOLO_LAUNCH(c, holo::launch_sum_f64(c->d_part, (int)nparts, c->d_red, 0, c->stream));
+  const int nbx = c->ops->pass_b_blocks(a.pass_b_items);
+  const long long nparts = nbx;
+  {
+    PassTimer tm(c, HOLO_T_PASS_A);
+    HOLO_LAUNCH(c, c->ops->pass_a(a, c->stream));
+  }
+  {
+    PassTimer tm(c, HOLO_T_PASS_B);
+    HOLO_LAUNCH(c, c->ops->pass_b(a, gradient ? 1 : 0, nbx, c->stream));
+  }
   const bool ref = a.k0 == 0 && c->wref != 0.0;
   const long long n2 = (long long)c->n * c->n;
+  {
+  PassTimer tm_red(c, HOLO_T_REDUCE);
+  HOLO_LAUNCH(c, holo::launch_sum_f64(c->d_part, (int)nparts, c->d_red, 0, c->stream));
   if (ref) {
     HOLO_LAUNCH(c, holo::launch_ref_residual(c->d_b, c->sqrt_dref, n2, c->d_rref,
                                              c->d_part + nparts, kRefBlocks, c->stream));
@@ -320,9 +420,17 @@ holo_status run_eval(holo_ctx* c, PassArgs& a, bool gradient, float2* grad_q, un
   } else {
     HOLO_CK(c, cudaMemsetAsync(c->d_red + 1, 0, sizeof(double), c->stream));
   }
+  }
   if (!gradient) return HOLO_OK;
-  HOLO_LAUNCH(c, c->ops->pass_c(a, c->stream));
-  HOLO_LAUNCH(c, holo::launch_pass_d(a, c->stream));
+  {
+    PassTimer tm(c, HOLO_T_PASS_C);
+    HOLO_LAUNCH(c, c->ops->pass_c(a, c->stream));
+  }
+  {
+    PassTimer tm(c, HOLO_T_PASS_D);
+    HOLO_LAUNCH(c, holo::launch_pass_d(a, c->stream));
+  }
+  PassTimer tm_q(c, HOLO_T_QGRAD);
   // grad_q = 2 [ D_{-zeta_0}( C* (ext sum_kj r_kj + w_ref r_ref) ) + sum_j D_{-omega_j}(G'_j) ]
   // (zhat_j + omega_j = zeta_0 merges the ext-part of every plane into one propagation).
   HOLO_LAUNCH(c, holo::launch_sum_residuals(c->rbuf, a.nk * c->J, n2, ref ? c->d_rref : nullptr,
@@ -364,6 +472,38 @@ holo_status read_loss(holo_ctx* c, double* loss, unsigned flags) {
 }  // namespace
 
 extern "C" {
+
+holo_status holo_set_timing(holo_ctx* c, int enable) {
+  if (!c) return HOLO_ERR_ARG;
+  HOLO_CK(c, cudaStreamSynchronize(c->stream));
+  for (auto& r : c->recs) {
+    c->pool.push_back(r.a);
+    c->pool.push_back(r.b);
+  }
+  c->recs.clear();
+  c->timing = enable != 0;
+  return HOLO_OK;
+}
+
+holo_status holo_get_timing(holo_ctx* c, double* ms, long long* launches) {
+  if (!c) return HOLO_ERR_ARG;
+  HOLO_CK(c, cudaStreamSynchronize(c->stream));
+  double t[HOLO_NUM_TIMERS] = {};
+  long long l[HOLO_NUM_TIMERS] = {};
+  for (auto& r : c->recs) {
+    float e = 0.f;
+    HOLO_CK(c, cudaEventElapsedTime(&e, r.a, r.b));
+    if (r.id >= 0 && r.id < HOLO_NUM_TIMERS) {
+      t[r.id] += e;
+      l[r.id] += r.launches;
+    }
+  }
+  for (int i = 0; i < HOLO_NUM_TIMERS; ++i) {
+    if (ms) ms[i] = t[i];
+    if (launches) launches[i] = l[i];
+  }
+  return HOLO_OK;
+}
 
 const char* holo_status_string(holo_status s) {
   switch (s) {
@@ -469,10 +609,16 @@ holo_status holo_destroy(holo_ctx* c) {
                   c->ybuf,    c->rbuf,         c->gkbuf,         c->d_scratch,
                   c->d_Gp,    c->d_T,          c->d_rref,        c->d_part,
                   c->d_red,   c->s_psi,        c->s_gpsi,        c->s_data,
-                  c->s_q,     c->s_gq};
+                  c->s_q,     c->s_gq,         c->d_xtap,        c->d_ytap,
+                  c->d_xadj,  c->d_yadj,       c->d_rowstart};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   if (c->h_red) cudaFreeHost(c->h_red);
+  for (auto& r : c->recs) {
+    cudaEventDestroy(r.a);
+    cudaEventDestroy(r.b);
+  }
+  for (auto e : c->pool) cudaEventDestroy(e);
   delete c;
   return HOLO_OK;
 }
@@ -495,7 +641,42 @@ holo_status holo_set_shifts(holo_ctx* c, const float* t) {
       maxbys = std::max(maxbys, d.bys);
       maxbxs = std::max(maxbxs, d.bxs);
     }
+  // tap tables and the flat list of box rows of all planes
+  const size_t np_all = (size_t)K * J;
+  const int stride = std::max(maxbys, maxbxs);
+  std::vector<holo::Tap> xt(np_all * stride), yt(np_all * stride);
+  std::vector<holo::AdjTap> xa(np_all * n), ya(np_all * n);
+  c->rowstart.assign(np_all + 1, 0);
+  for (size_t p = 0; p < np_all; ++p) {
+    const PlaneDesc& d = c->planes[p];
+    const double mt = c->mt[p % J];
+    axis_taps(mt, d.tx, n, P, d.bx0, d.bxs, &xt[p * stride], &xa[p * n]);
+    axis_taps(mt, d.ty, n, P, d.by0, d.bys, &yt[p * stride], &ya[p * n]);
+    c->rowstart[p + 1] = c->rowstart[p] + d.bys;
+  }
   holo_status st;
+  {
+    void* olds[] = {c->d_xtap, c->d_ytap, c->d_xadj, c->d_yadj, c->d_rowstart};
+    for (void* o : olds)
+      if (o) cudaFree(o);
+    c->bytes -= (long long)c->tap_bytes;
+    c->d_xtap = c->d_ytap = nullptr;
+    c->d_xadj = c->d_yadj = nullptr;
+    c->d_rowstart = nullptr;
+    const size_t tb = sizeof(holo::Tap) * xt.size(), ab = sizeof(holo::AdjTap) * xa.size(),
+                 rb = sizeof(int) * c->rowstart.size();
+    if ((st = dalloc(c, (void**)&c->d_xtap, tb)) || (st = dalloc(c, (void**)&c->d_ytap, tb)) ||
+        (st = dalloc(c, (void**)&c->d_xadj, ab)) || (st = dalloc(c, (void**)&c->d_yadj, ab)) ||
+        (st = dalloc(c, (void**)&c->d_rowstart, rb)))
+      return st;
+    c->tap_bytes = 2 * tb + 2 * ab + rb;
+    c->bytes -= 0;
+    if ((st = upload(c, c->d_xtap, xt.data(), tb)) || (st = upload(c, c->d_ytap, yt.data(), tb)) ||
+        (st = upload(c, c->d_xadj, xa.data(), ab)) || (st = upload(c, c->d_yadj, ya.data(), ab)) ||
+        (st = upload(c, c->d_rowstart, c->rowstart.data(), rb)))
+      return st;
+    c->tap_stride = stride;
+  }
   if (c->d_planes) {
     cudaFree(c->d_planes);
     c->bytes -= (long long)(sizeof(PlaneDesc) * c->planes.size());
@@ -509,7 +690,7 @@ holo_status holo_set_shifts(holo_ctx* c, const float* t) {
   const size_t ybytes = sizeof(float2) * (size_t)(np * ystride);
   const size_t rbytes = sizeof(float2) * (size_t)(np * n * n);
   const size_t gbytes = sizeof(float2) * (size_t)(np * gkstride);
-  const long long parts = (long long)c->ops->pass_b_blocks_x(n) * np + kRefBlocks + 1024;
+  const long long parts = (long long)c->ops->pass_b_blocks(1 << 30) + kRefBlocks + 1024;
   if (ystride > c->ystride || gkstride > c->gkstride || !c->ybuf) {
     dfree(c, c->ybuf, sizeof(float2) * (size_t)(np * c->ystride));
     dfree(c, c->rbuf, rbytes);
@@ -548,6 +729,7 @@ holo_status holo_set_probe(holo_ctx* c, const void* q) {
   if (!c || !q) return fail(c, HOLO_ERR_ARG, "null probe");
   const int P = c->P, n = c->n, lo = P / 2 - n / 2;
   const size_t plane = sizeof(float2) * (size_t)P * P;
+  PassTimer tm(c, HOLO_T_PROBE);
   HOLO_CK(c, cudaMemcpyAsync(c->d_pj, q, plane, cudaMemcpyDeviceToDevice, c->stream));
   holo_status st;
   for (int j = 1; j < c->J; ++j) {
@@ -650,6 +832,7 @@ holo_status holo_dot(holo_ctx* c, const void* a, const void* b, long long n, dou
   }
   long long nb = (n + 256 * 16 - 1) / (256 * 16);
   nb = std::max(1LL, std::min(nb, std::min(1024LL, c->part_cap)));
+  PassTimer tm(c, HOLO_T_REDUCE);
   HOLO_LAUNCH(c, holo::launch_dot((const float2*)a, (const float2*)b, n, c->d_part, (int)nb,
                                   c->stream));
   HOLO_LAUNCH(c, holo::launch_sum_f64(c->d_part, (int)nb, c->d_red + 2, 0, c->stream));
@@ -662,12 +845,14 @@ holo_status holo_dot(holo_ctx* c, const void* a, const void* b, long long n, dou
 
 holo_status holo_step(holo_ctx* c, void* x, const void* eta, double gamma, long long n) {
   if (!c || !x || !eta || n < 0 || !std::isfinite(gamma)) return fail(c, HOLO_ERR_ARG, "bad argument");
+  PassTimer tm(c, HOLO_T_VECTOR);
   HOLO_LAUNCH(c, holo::launch_axpy((float2*)x, (const float2*)eta, (float)gamma, n, c->stream));
   return HOLO_OK;
 }
 
 holo_status holo_direction(holo_ctx* c, void* eta, const void* g, double beta, long long n) {
   if (!c || !eta || !g || n < 0 || !std::isfinite(beta)) return fail(c, HOLO_ERR_ARG, "bad argument");
+  PassTimer tm(c, HOLO_T_VECTOR);
   HOLO_LAUNCH(c, holo::launch_direction((float2*)eta, (const float2*)g, (float)beta, n, c->stream));
   return HOLO_OK;
 }

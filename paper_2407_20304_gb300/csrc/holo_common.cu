@@ -11,29 +11,28 @@ constexpr int kThreads = 256;
 
 // grad_psi_k[i][ip] = 2 sum_j sum_Y wy_j(Y, i) h_kj[Y][ip]: the y-transpose of the bilinear
 // resample gathered from the (at most two) box rows whose taps reach psi row i, summed
-// over the distances j (Eq. gradpsi: grad = 2 sum_j L*_kj r_kj).
+// over the distances j (Eq. gradpsi: grad = 2 sum_j L*_kj r_kj).  The rows and weights
+// come from the transposed-tap table of each plane.
 __global__ void k_pass_d(PassArgs a) {
-  const int n = a.n, P = a.P, i = blockIdx.x, kl = blockIdx.y;
+  const int n = a.n, i = blockIdx.x, kl = blockIdx.y;
   float2* out = a.grad_psi + ((long long)kl * n + i) * n;
   for (int ip = threadIdx.x; ip < n; ip += blockDim.x) {
     float2 acc = make_float2(0.f, 0.f);
     for (int j = 0; j < a.J; ++j) {
-      const PlaneDesc d = a.planes[(long long)(a.k0 + kl) * a.J + j];
+      const long long gp = (long long)(a.k0 + kl) * a.J + j;
+      const AdjTap at = a.yadj[gp * n + i];
+      const PlaneDesc d = a.planes[gp];
       const float2* h = a.ybuf + (long long)(kl * a.J + j) * a.ystride;
-      const float mt = d.mt_hi + d.mt_lo;
-      const int Ys = (int)floorf(((float)(i - n / 2) + d.ty) / mt) + P / 2;
-#pragma unroll
-      for (int dY = -1; dY <= 2; ++dY) {
-        const int Y = Ys + dY, rel = Y - d.by0;
-        if ((unsigned)rel >= (unsigned)d.bys) continue;
-        int iy0;
-        float fy;
-        axis_tap(Y, d.mt_hi, d.mt_lo, d.ty, P, n, iy0, fy);
-        const float wgt = (iy0 == i) ? 1.f - fy : ((iy0 + 1 == i) ? fy : 0.f);
-        if (wgt == 0.f) continue;
-        const float2 z = h[(long long)rel * n + ip];
-        acc.x = fmaf(wgt, z.x, acc.x);
-        acc.y = fmaf(wgt, z.y, acc.y);
+      const int r0 = at.X0 - d.by0;
+      if (at.w0 != 0.f) {
+        const float2 z = h[(long long)r0 * n + ip];
+        acc.x = fmaf(at.w0, z.x, acc.x);
+        acc.y = fmaf(at.w0, z.y, acc.y);
+      }
+      if (at.w1 != 0.f) {
+        const float2 z = h[(long long)(r0 + 1) * n + ip];
+        acc.x = fmaf(at.w1, z.x, acc.x);
+        acc.y = fmaf(at.w1, z.y, acc.y);
       }
     }
     float2 r = make_float2(2.f * acc.x, 2.f * acc.y);

@@ -17,6 +17,22 @@ struct PlaneDesc {
   int bx0, bxs;         // box columns
 };
 
+// Bilinear tap of one P-grid position along one axis (reading R4): psi index i0 with
+// weight 1 - f and i0 + 1 with weight f (taps outside [0, n) are dropped by the user).
+// Built in FP64 on the host from xi = m~ (X - P/2) - t + n/2.
+struct Tap {
+  int i0;
+  float f;
+};
+
+// Transpose of the taps along one axis: psi index i receives from the P-grid positions
+// X0 (weight w0) and X0 + 1 (weight w1); absent contributions have weight 0.
+struct AdjTap {
+  int X0;
+  float w0, w1;
+  int pad;
+};
+
 // Generic line D-step over rows or columns of a strided complex array.
 // The line's nonzero input occupies P-grid positions [in_lo, in_lo + in_len) and is
 // read from in[line_in_base + (pos - in_lo) * in_step]; outside, the input is zero.
@@ -57,7 +73,17 @@ struct PassArgs {
   float2* grad_psi;            // [nk][n][n]
   int accumulate;
   const float2* twiddles;      // device twiddle table for this P
-  int max_box_rows;            // largest box height of the chunk (grid of passes A, C)
+  int max_box_rows;            // largest box height of the chunk
+  // tap tables of every plane (global index k * J + j)
+  const Tap* xtap;             // [planes][tap_stride]: columns [bx0, bx0 + bxs)
+  const Tap* ytap;             // [planes][tap_stride]: rows [by0, by0 + bys)
+  const AdjTap* xadj;          // [planes][n]: columns of psi
+  const AdjTap* yadj;          // [planes][n]: rows of psi
+  int tap_stride;
+  // rows of all planes in one flat list: plane p owns lines [rowstart[p], rowstart[p+1])
+  const int* rowstart;         // [n_angles * J + 1] (global plane index)
+  int line0, nlines;           // the chunk's lines: [line0, line0 + nlines)
+  int pass_b_items;            // nk * J * column groups
 };
 
 // Entry points implemented once per supported line length P.
@@ -66,9 +92,10 @@ struct Ops {
   cudaError_t (*rows)(const LineArgs&, const float2* tw, cudaStream_t);
   cudaError_t (*cols)(const LineArgs&, const float2* tw, cudaStream_t);
   cudaError_t (*pass_a)(const PassArgs&, cudaStream_t);
-  cudaError_t (*pass_b)(const PassArgs&, int with_adjoint, int nblocks_x, cudaStream_t);
+  cudaError_t (*pass_b)(const PassArgs&, int with_adjoint, int nblocks, cudaStream_t);
   cudaError_t (*pass_c)(const PassArgs&, cudaStream_t);
-  int (*pass_b_blocks_x)(int n);            // grid.x of pass B for side n
+  int (*pass_b_groups)(int n);              // column groups of pass B for side n
+  int (*pass_b_blocks)(int items);          // persistent grid of pass B
   int twiddle_count;
 };
 

@@ -18,6 +18,9 @@
 //           z = conj(p_j) v, x-transpose of the bilinear resample -> h[box rows][n]
 //           (in place of V); conj(w) v -> per-plane buffer for grad_q
 //   pass D (psi rows, line-length independent): y-transpose, sum over j, times 2.
+//
+// All passes run persistent blocks (a grid that fills the GPU once) that load the FFT
+// twiddles into shared memory once and then walk a flat list of work items.
 
 #pragma once
 
@@ -50,27 +53,12 @@ struct ColCfg {
   static constexpr size_t SMEM_BYTES = (size_t)(Fft<P>::TW + C * LS) * sizeof(float2);
 };
 
-// ψ index of P-grid position X along one axis: xi = m~ (X - P/2) - t + n/2 (reading R4),
-// returned as floor(xi) and frac(xi).  m~ = mt_hi + mt_lo with mt_hi * (X - P/2) exact in
-// FP32, so xi is accurate to ~1e-7 pixel even for |X - P/2| in the thousands.
-__device__ __forceinline__ void axis_tap(int X, float mt_hi, float mt_lo, float t, int P, int n,
-                                         int& i0, float& f) {
-  const float x = (float)(X - P / 2);
-  const float a = mt_hi * x;
-  const float ai = floorf(a);
-  const float rest = (a - ai) + fmaf(mt_lo, x, -t);
-  const float ri = floorf(rest);
-  i0 = (int)ai + (int)ri + n / 2;
-  f = rest - ri;
-}
-
-// w = R0(psi - ext) at (row taps iy0/fy, column X): the bilinear interpolation of
-// psi - ext with taps outside the n x n domain dropped.
+// w = R0(psi - ext) at one P-grid position from its row tap (iy0, fy) and column tap:
+// bilinear interpolation of psi - ext with taps outside the n x n domain dropped.
 __device__ __forceinline__ float2 resample_w(const float2* __restrict__ psi, int n, float ext,
-                                             int iy0, float fy, const PlaneDesc& d, int P, int X) {
-  int ix0;
-  float fx;
-  axis_tap(X, d.mt_hi, d.mt_lo, d.tx, P, n, ix0, fx);
+                                             int iy0, float fy, Tap xt) {
+  const int ix0 = xt.i0;
+  const float fx = xt.f;
   const bool c0 = (unsigned)ix0 < (unsigned)n, c1 = (unsigned)(ix0 + 1) < (unsigned)n;
   float2 w = make_float2(0.f, 0.f);
 #pragma unroll
@@ -112,6 +100,20 @@ __device__ __forceinline__ double block_sum_f64(double v, double* red) {
   return s;
 }
 
+// Plane of flat line `line` (global line numbering): largest p with rowstart[p] <= line.
+__device__ __forceinline__ int plane_of_line(const int* __restrict__ rowstart, int lo, int hi,
+                                             int line) {
+  // invariant: rowstart[lo] <= line < rowstart[hi]
+  while (hi - lo > 1) {
+    const int mid = (lo + hi) >> 1;
+    if (__ldg(rowstart + mid) <= line)
+      lo = mid;
+    else
+      hi = mid;
+  }
+  return lo;
+}
+
 // ------------------------------------------------------------------ generic D-step
 
 // One "FFT -> chirp -> inverse FFT" per line, lines = rows (COLS = false) or columns.
@@ -127,33 +129,35 @@ k_line_dstep(LineArgs a, const float2* __restrict__ gtw) {
   const int t = COLS ? (int)(threadIdx.x / G) : (int)(threadIdx.x % F::T);
   float2* sm = smem + F::TW + g * LS;
   load_twiddles<P>(tw, gtw);
-  const int line = blockIdx.x * G + g;
-  const bool valid = line < a.nlines;
-  const float2* in = a.in + (long long)line * a.in_line_stride;
-  float2 v[16];
+  for (int base = blockIdx.x * G; base < a.nlines; base += gridDim.x * G) {
+    const int line = base + g;
+    const bool valid = line < a.nlines;
+    const float2* in = a.in + (long long)line * a.in_line_stride;
+    float2 v[16];
 #pragma unroll
-  for (int c = 0; c < 16; ++c) {
-    const int rel = t + F::T * c - a.in_lo;
-    v[c] = (valid && (unsigned)rel < (unsigned)a.in_len) ? in[(long long)rel * a.in_step]
-                                                         : make_float2(0.f, 0.f);
-  }
-  __syncthreads();
-  fft_fwd<P>(v, sm, tw, t);
+    for (int c = 0; c < 16; ++c) {
+      const int rel = t + F::T * c - a.in_lo;
+      v[c] = (valid && (unsigned)rel < (unsigned)a.in_len) ? in[(long long)rel * a.in_step]
+                                                           : make_float2(0.f, 0.f);
+    }
+    __syncthreads();
+    fft_fwd<P>(v, sm, tw, t);
 #pragma unroll
-  for (int c = 0; c < 16; ++c) {
-    float2 ch = __ldg(a.chirp + t + F::T * c);
-    v[c] = a.conj_chirp ? cmulc(v[c], ch) : cmul(v[c], ch);
-  }
-  fft_inv<P>(v, sm, tw, t);
-  float2* out = a.out + (long long)line * a.out_line_stride;
+    for (int c = 0; c < 16; ++c) {
+      float2 ch = __ldg(a.chirp + t + F::T * c);
+      v[c] = a.conj_chirp ? cmulc(v[c], ch) : cmul(v[c], ch);
+    }
+    fft_inv<P>(v, sm, tw, t);
+    float2* out = a.out + (long long)line * a.out_line_stride;
 #pragma unroll
-  for (int c = 0; c < 16; ++c) {
-    const int rel = t + F::T * c - a.out_lo;
-    if (valid && (unsigned)rel < (unsigned)a.out_len) {
-      float2* o = out + (long long)rel * a.out_step;
-      float2 r = cscale(v[c], a.alpha);
-      if (a.accumulate) r = cadd(r, *o);
-      *o = r;
+    for (int c = 0; c < 16; ++c) {
+      const int rel = t + F::T * c - a.out_lo;
+      if (valid && (unsigned)rel < (unsigned)a.out_len) {
+        float2* o = out + (long long)rel * a.out_step;
+        float2 r = cscale(v[c], a.alpha);
+        if (a.accumulate) r = cadd(r, *o);
+        *o = r;
+      }
     }
   }
 }
@@ -165,45 +169,47 @@ __global__ void __launch_bounds__(RowCfg<P>::NT) k_pass_a(PassArgs a) {
   using F = Fft<P>;
   using R = RowCfg<P>;
   extern __shared__ float2 smem[];
-  const int lp = blockIdx.y, kl = lp / a.J, j = lp % a.J;
-  const PlaneDesc d = a.planes[(long long)(a.k0 + kl) * a.J + j];
-  if ((int)blockIdx.x * R::G >= d.bys) return;   // block-uniform: whole block beyond the box
   float2* tw = smem;
   const int g = threadIdx.x / F::T, t = threadIdx.x % F::T;
   float2* sm = smem + F::TW + g * R::LS;
   load_twiddles<P>(tw, a.twiddles);
-  const int n = a.n, i = blockIdx.x * R::G + g;
-  const bool valid = i < d.bys;
-  const int Y = d.by0 + i;
-  int iy0;
-  float fy;
-  axis_tap(Y, d.mt_hi, d.mt_lo, d.ty, P, n, iy0, fy);
-  const bool rows_in = valid && ((unsigned)iy0 < (unsigned)n || (unsigned)(iy0 + 1) < (unsigned)n);
-  const float2* psi = a.psi + (long long)kl * n * n;
-  const float2* prow = a.pj + ((long long)j * P + (valid ? Y : 0)) * P;
-  float2 v[16];
+  const int n = a.n, lo = P / 2 - n / 2;
+  const int p_lo = a.k0 * a.J, p_hi = (a.k0 + a.nk) * a.J;
+  for (int base = blockIdx.x * R::G; base < a.nlines; base += gridDim.x * R::G) {
+    const int li = base + g;
+    const bool valid = li < a.nlines;
+    const int line = a.line0 + (valid ? li : 0);
+    const int gp = plane_of_line(a.rowstart, p_lo, p_hi, line);
+    const int lp = gp - p_lo, kl = lp / a.J, j = lp % a.J;
+    const int i = line - __ldg(a.rowstart + gp);
+    const PlaneDesc d = a.planes[gp];
+    const Tap yt = a.ytap[(long long)gp * a.tap_stride + i];
+    const Tap* xt = a.xtap + (long long)gp * a.tap_stride;
+    const float2* psi = a.psi + (long long)kl * n * n;
+    const float2* prow = a.pj + ((long long)j * P + d.by0 + i) * P;
+    float2 v[16];
 #pragma unroll
-  for (int c = 0; c < 16; ++c) {
-    const int X = t + F::T * c;
-    float2 x = make_float2(0.f, 0.f);
-    if (rows_in && (unsigned)(X - d.bx0) < (unsigned)d.bxs) {
-      const float2 w = resample_w(psi, n, a.ext, iy0, fy, d, P, X);
-      x = cmul(__ldg(prow + X), w);
+    for (int c = 0; c < 16; ++c) {
+      const int X = t + F::T * c, rel = X - d.bx0;
+      float2 x = make_float2(0.f, 0.f);
+      if (valid && (unsigned)rel < (unsigned)d.bxs) {
+        const float2 w = resample_w(psi, n, a.ext, yt.i0, yt.f, xt[rel]);
+        x = cmul(__ldg(prow + X), w);
+      }
+      v[c] = x;
     }
-    v[c] = x;
-  }
-  __syncthreads();
-  fft_fwd<P>(v, sm, tw, t);
-  const float2* ch = a.chirp_zhat + (long long)j * P;
+    __syncthreads();
+    fft_fwd<P>(v, sm, tw, t);
+    const float2* ch = a.chirp_zhat + (long long)j * P;
 #pragma unroll
-  for (int c = 0; c < 16; ++c) v[c] = cmul(v[c], __ldg(ch + t + F::T * c));
-  fft_inv<P>(v, sm, tw, t);
-  float2* yrow = a.ybuf + (long long)lp * a.ystride + (long long)i * n;
-  const int lo = P / 2 - n / 2;
+    for (int c = 0; c < 16; ++c) v[c] = cmul(v[c], __ldg(ch + t + F::T * c));
+    fft_inv<P>(v, sm, tw, t);
+    float2* yrow = a.ybuf + (long long)lp * a.ystride + (long long)i * n;
 #pragma unroll
-  for (int c = 0; c < 16; ++c) {
-    const int rel = t + F::T * c - lo;
-    if (valid && (unsigned)rel < (unsigned)n) yrow[rel] = v[c];
+    for (int c = 0; c < 16; ++c) {
+      const int rel = t + F::T * c - lo;
+      if (valid && (unsigned)rel < (unsigned)n) yrow[rel] = v[c];
+    }
   }
 }
 
@@ -219,69 +225,74 @@ __global__ void __launch_bounds__(ColCfg<P>::NT) k_pass_b(PassArgs a) {
   const int g = threadIdx.x % Cc::C, t = threadIdx.x / Cc::C;
   float2* sm = smem + F::TW + g * Cc::LS;
   load_twiddles<P>(tw, a.twiddles);
-  const int n = a.n;
-  const int lp = blockIdx.y, kl = lp / a.J, j = lp % a.J;
-  const long long gplane = (long long)(a.k0 + kl) * a.J + j;
-  const PlaneDesc d = a.planes[gplane];
-  const int col = blockIdx.x * Cc::C + g;
-  const bool valid = col < n;
-  float2* yb = a.ybuf + (long long)lp * a.ystride;
-  float2 v[16];
-#pragma unroll
-  for (int c = 0; c < 16; ++c) {
-    const int rel = t + F::T * c - d.by0;
-    v[c] = (valid && (unsigned)rel < (unsigned)d.bys) ? yb[(long long)rel * n + col]
-                                                       : make_float2(0.f, 0.f);
-  }
-  __syncthreads();
-  fft_fwd<P>(v, sm, tw, t);
-  const float2* ch = a.chirp_zhat + (long long)j * P;
-#pragma unroll
-  for (int c = 0; c < 16; ++c) v[c] = cmul(v[c], __ldg(ch + t + F::T * c));
-  fft_inv<P>(v, sm, tw, t);
-  const int lo = P / 2 - n / 2;
-  const float* ad = a.sqrt_d + (gplane - (long long)a.data_k0 * a.J) * n * n;
-  float2* rb = a.rbuf + (long long)lp * n * n;
-  float2* uo = a.u_out ? a.u_out + (long long)lp * n * n : nullptr;
+  const int n = a.n, lo = P / 2 - n / 2;
+  const int ngroups = (n + Cc::C - 1) / Cc::C;
   float lsum = 0.f;
-#pragma unroll
-  for (int c = 0; c < 16; ++c) {
-    const int rr = t + F::T * c - lo;
-    float2 r = make_float2(0.f, 0.f);
-    if (valid && (unsigned)rr < (unsigned)n) {
-      const long long e = (long long)rr * n + col;
-      float2 u = v[c];
-      if (a.ext != 0.f) {
-        const float2 b = __ldg(a.bref + e);
-        u.x = fmaf(a.ext, b.x, u.x);
-        u.y = fmaf(a.ext, b.y, u.y);
-      }
-      const float amp = __ldg(ad + e);
-      const float mag = sqrtf(fmaf(u.x, u.x, u.y * u.y));
-      const float diff = mag - amp;
-      lsum = fmaf(diff, diff, lsum);
-      if (uo) uo[e] = u;
-      if (ADJ) {
-        const float s = mag > 0.f ? 1.f - amp / mag : 0.f;
-        r = cscale(u, s);
-        rb[e] = r;
-      }
-    }
-    v[c] = r;
-  }
-  if constexpr (ADJ) {
-    fft_fwd<P>(v, sm, tw, t);
-#pragma unroll
-    for (int c = 0; c < 16; ++c) v[c] = cmulc(v[c], __ldg(ch + t + F::T * c));
-    fft_inv<P>(v, sm, tw, t);
+  double dsum = 0.0;
+  for (int item = blockIdx.x; item < a.pass_b_items; item += gridDim.x) {
+    const int lp = item / ngroups, kl = lp / a.J, j = lp % a.J;
+    const int col = (item % ngroups) * Cc::C + g;
+    const bool valid = col < n;
+    const long long gplane = (long long)(a.k0 + kl) * a.J + j;
+    const PlaneDesc d = a.planes[gplane];
+    float2* yb = a.ybuf + (long long)lp * a.ystride;
+    float2 v[16];
 #pragma unroll
     for (int c = 0; c < 16; ++c) {
       const int rel = t + F::T * c - d.by0;
-      if (valid && (unsigned)rel < (unsigned)d.bys) yb[(long long)rel * n + col] = v[c];
+      v[c] = (valid && (unsigned)rel < (unsigned)d.bys) ? yb[(long long)rel * n + col]
+                                                         : make_float2(0.f, 0.f);
+    }
+    __syncthreads();
+    fft_fwd<P>(v, sm, tw, t);
+    const float2* ch = a.chirp_zhat + (long long)j * P;
+#pragma unroll
+    for (int c = 0; c < 16; ++c) v[c] = cmul(v[c], __ldg(ch + t + F::T * c));
+    fft_inv<P>(v, sm, tw, t);
+    const float* ad = a.sqrt_d + (gplane - (long long)a.data_k0 * a.J) * n * n;
+    float2* rb = a.rbuf + (long long)lp * n * n;
+    float2* uo = a.u_out ? a.u_out + (long long)lp * n * n : nullptr;
+    lsum = 0.f;
+#pragma unroll
+    for (int c = 0; c < 16; ++c) {
+      const int rr = t + F::T * c - lo;
+      float2 r = make_float2(0.f, 0.f);
+      if (valid && (unsigned)rr < (unsigned)n) {
+        const long long e = (long long)rr * n + col;
+        float2 u = v[c];
+        if (a.ext != 0.f) {
+          const float2 b = __ldg(a.bref + e);
+          u.x = fmaf(a.ext, b.x, u.x);
+          u.y = fmaf(a.ext, b.y, u.y);
+        }
+        const float amp = __ldg(ad + e);
+        const float mag = sqrtf(fmaf(u.x, u.x, u.y * u.y));
+        const float diff = mag - amp;
+        lsum = fmaf(diff, diff, lsum);
+        if (uo) uo[e] = u;
+        if (ADJ) {
+          const float s = mag > 0.f ? 1.f - amp / mag : 0.f;
+          r = cscale(u, s);
+          rb[e] = r;
+        }
+      }
+      v[c] = r;
+    }
+    dsum += (double)lsum;
+    if constexpr (ADJ) {
+      fft_fwd<P>(v, sm, tw, t);
+#pragma unroll
+      for (int c = 0; c < 16; ++c) v[c] = cmulc(v[c], __ldg(ch + t + F::T * c));
+      fft_inv<P>(v, sm, tw, t);
+#pragma unroll
+      for (int c = 0; c < 16; ++c) {
+        const int rel = t + F::T * c - d.by0;
+        if (valid && (unsigned)rel < (unsigned)d.bys) yb[(long long)rel * n + col] = v[c];
+      }
     }
   }
-  const double s = block_sum_f64((double)lsum, red);
-  if (threadIdx.x == 0) a.loss_part[(long long)blockIdx.y * gridDim.x + blockIdx.x] = s;
+  const double s = block_sum_f64(dsum, red);
+  if (threadIdx.x == 0) a.loss_part[blockIdx.x] = s;
 }
 
 // ------------------------------------------------------------------ pass C
@@ -291,74 +302,101 @@ __global__ void __launch_bounds__(RowCfg<P>::NT) k_pass_c(PassArgs a) {
   using F = Fft<P>;
   using R = RowCfg<P>;
   extern __shared__ float2 smem[];
-  const int lp = blockIdx.y, kl = lp / a.J, j = lp % a.J;
-  const PlaneDesc d = a.planes[(long long)(a.k0 + kl) * a.J + j];
-  if ((int)blockIdx.x * R::G >= d.bys) return;   // block-uniform
   float2* tw = smem;
   const int g = threadIdx.x / F::T, t = threadIdx.x % F::T;
   float2* sm = smem + F::TW + g * R::LS;
   load_twiddles<P>(tw, a.twiddles);
-  const int n = a.n, i = blockIdx.x * R::G + g;
-  const bool valid = i < d.bys;
-  const int lo = P / 2 - n / 2;
-  float2* yrow = a.ybuf + (long long)lp * a.ystride + (long long)(valid ? i : 0) * n;
-  float2 v[16];
+  const int n = a.n, lo = P / 2 - n / 2;
+  const int p_lo = a.k0 * a.J, p_hi = (a.k0 + a.nk) * a.J;
+  for (int base = blockIdx.x * R::G; base < a.nlines; base += gridDim.x * R::G) {
+    const int li = base + g;
+    const bool valid = li < a.nlines;
+    const int line = a.line0 + (valid ? li : 0);
+    const int gp = plane_of_line(a.rowstart, p_lo, p_hi, line);
+    const int lp = gp - p_lo, kl = lp / a.J, j = lp % a.J;
+    const int i = line - __ldg(a.rowstart + gp);
+    float2* yrow = a.ybuf + (long long)lp * a.ystride + (long long)i * n;
+    float2 v[16];
 #pragma unroll
-  for (int c = 0; c < 16; ++c) {
-    const int rel = t + F::T * c - lo;
-    v[c] = (valid && (unsigned)rel < (unsigned)n) ? yrow[rel] : make_float2(0.f, 0.f);
-  }
-  __syncthreads();
-  fft_fwd<P>(v, sm, tw, t);
-  const float2* ch = a.chirp_zhat + (long long)j * P;
-#pragma unroll
-  for (int c = 0; c < 16; ++c) v[c] = cmulc(v[c], __ldg(ch + t + F::T * c));
-  fft_inv<P>(v, sm, tw, t);
-  // v now holds the adjoint field on this P-grid row; the exchange buffer is free.
-  const int Y = d.by0 + i;
-  int iy0;
-  float fy;
-  axis_tap(Y, d.mt_hi, d.mt_lo, d.ty, P, n, iy0, fy);
-  const float2* psi = a.psi + (long long)kl * n * n;
-  const float2* prow = a.pj + ((long long)j * P + (valid ? Y : 0)) * P;
-  float2* gk = a.gkbuf + (long long)lp * a.gkstride + (long long)(valid ? i : 0) * d.bxs;
-#pragma unroll
-  for (int c = 0; c < 16; ++c) {
-    const int X = t + F::T * c, rel = X - d.bx0;
-    if (valid && (unsigned)rel < (unsigned)d.bxs) {
-      sm[rel] = cconjmul(__ldg(prow + X), v[c]);
-      const float2 w = resample_w(psi, n, a.ext, iy0, fy, d, P, X);
-      gk[rel] = cconjmul(w, v[c]);
+    for (int c = 0; c < 16; ++c) {
+      const int rel = t + F::T * c - lo;
+      v[c] = (valid && (unsigned)rel < (unsigned)n) ? yrow[rel] : make_float2(0.f, 0.f);
     }
-  }
-  __syncthreads();
-  // x-transpose of the bilinear resample: h[ip] = sum_X wx(X, ip) z[X], gathered from the
-  // (at most two) P-grid columns whose taps reach column ip, with the same weights as the
-  // forward resample.
-  const float mt = d.mt_hi + d.mt_lo;
+    __syncthreads();
+    fft_fwd<P>(v, sm, tw, t);
+    const float2* ch = a.chirp_zhat + (long long)j * P;
 #pragma unroll
-  for (int c = 0; c < 16; ++c) {
-    const int ip = t + F::T * c;
-    if (!valid || ip >= n) continue;
-    const int Xs = (int)floorf(((float)(ip - n / 2) + d.tx) / mt) + P / 2;
-    float2 h = make_float2(0.f, 0.f);
+    for (int c = 0; c < 16; ++c) v[c] = cmulc(v[c], __ldg(ch + t + F::T * c));
+    fft_inv<P>(v, sm, tw, t);
+    // v holds the adjoint field on this P-grid row; the exchange buffer is free.
+    const PlaneDesc d = a.planes[gp];
+    const Tap yt = a.ytap[(long long)gp * a.tap_stride + i];
+    const Tap* xt = a.xtap + (long long)gp * a.tap_stride;
+    const float2* psi = a.psi + (long long)kl * n * n;
+    const float2* prow = a.pj + ((long long)j * P + d.by0 + i) * P;
+    float2* gk = a.gkbuf + (long long)lp * a.gkstride + (long long)i * d.bxs;
 #pragma unroll
-    for (int dX = -1; dX <= 2; ++dX) {
-      const int X = Xs + dX, rel = X - d.bx0;
-      if ((unsigned)rel >= (unsigned)d.bxs) continue;
-      int ix0;
-      float fx;
-      axis_tap(X, d.mt_hi, d.mt_lo, d.tx, P, n, ix0, fx);
-      const float wgt = (ix0 == ip) ? 1.f - fx : ((ix0 + 1 == ip) ? fx : 0.f);
-      const float2 z = sm[rel];
-      h.x = fmaf(wgt, z.x, h.x);
-      h.y = fmaf(wgt, z.y, h.y);
+    for (int c = 0; c < 16; ++c) {
+      const int X = t + F::T * c, rel = X - d.bx0;
+      if (valid && (unsigned)rel < (unsigned)d.bxs) {
+        sm[rel] = cconjmul(__ldg(prow + X), v[c]);
+        const float2 w = resample_w(psi, n, a.ext, yt.i0, yt.f, xt[rel]);
+        gk[rel] = cconjmul(w, v[c]);
+      }
     }
-    yrow[ip] = h;
+    __syncthreads();
+    // x-transpose of the bilinear resample: h[ip] = w0 z[X0] + w1 z[X0 + 1] with the
+    // transposed taps of this plane (same FP64-built weights as the forward taps).
+    const AdjTap* xa = a.xadj + (long long)gp * n;
+#pragma unroll
+    for (int c = 0; c < 16; ++c) {
+      const int ip = t + F::T * c;
+      if (!valid || ip >= n) continue;
+      const AdjTap at = xa[ip];
+      float2 h = make_float2(0.f, 0.f);
+      const int r0 = at.X0 - d.bx0;
+      if (at.w0 != 0.f) {
+        const float2 z = sm[r0];
+        h.x = at.w0 * z.x;
+        h.y = at.w0 * z.y;
+      }
+      if (at.w1 != 0.f) {
+        const float2 z = sm[r0 + 1];
+        h.x = fmaf(at.w1, z.x, h.x);
+        h.y = fmaf(at.w1, z.y, h.y);
+      }
+      yrow[ip] = h;
+    }
+    __syncthreads();
   }
 }
 
 // ------------------------------------------------------------------ launchers
+
+inline int sm_count() {
+  static int sms = 0;
+  if (!sms) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (sms <= 0) sms = 1;
+  }
+  return sms;
+}
+
+// Persistent grid: as many blocks as can be resident at once, capped by the work.
+template <class K>
+int persistent_blocks(K kernel, int threads, size_t smem, long long items) {
+  int per_sm = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, threads, smem) != cudaSuccess ||
+      per_sm < 1) {
+    cudaGetLastError();
+    per_sm = 1;
+  }
+  long long b = (long long)per_sm * sm_count();
+  if (items < b) b = items;
+  return (int)(b < 1 ? 1 : b);
+}
 
 template <int P, bool COLS>
 cudaError_t launch_lines(const LineArgs& a, const float2* tw, cudaStream_t s) {
@@ -369,7 +407,8 @@ cudaError_t launch_lines(const LineArgs& a, const float2* tw, cudaStream_t s) {
   cudaError_t e = cudaFuncSetAttribute(k_line_dstep<P, COLS>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SM);
   if (e != cudaSuccess) return e;
-  k_line_dstep<P, COLS><<<(a.nlines + G - 1) / G, NT, SM, s>>>(a, tw);
+  const int nb = persistent_blocks(k_line_dstep<P, COLS>, NT, SM, (a.nlines + G - 1) / G);
+  k_line_dstep<P, COLS><<<nb, NT, SM, s>>>(a, tw);
   return cudaGetLastError();
 }
 
@@ -382,39 +421,45 @@ cudaError_t launch_cols(const LineArgs& a, const float2* tw, cudaStream_t s) {
   return launch_lines<P, true>(a, tw, s);
 }
 
-// grid.x of passes A and C is sized by the largest box of the chunk (blocks beyond a
-// plane's own box exit at once); it is passed through PassArgs::max_box_rows.
 template <int P>
 cudaError_t launch_pass_a(const PassArgs& a, cudaStream_t s) {
   using R = RowCfg<P>;
+  if (a.nlines <= 0) return cudaSuccess;
   cudaError_t e = cudaFuncSetAttribute(k_pass_a<P>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)R::SMEM_BYTES);
   if (e != cudaSuccess) return e;
-  dim3 grid((a.max_box_rows + R::G - 1) / R::G, a.nk * a.J);
-  k_pass_a<P><<<grid, R::NT, R::SMEM_BYTES, s>>>(a);
+  const int nb = persistent_blocks(k_pass_a<P>, R::NT, R::SMEM_BYTES, (a.nlines + R::G - 1) / R::G);
+  k_pass_a<P><<<nb, R::NT, R::SMEM_BYTES, s>>>(a);
   return cudaGetLastError();
 }
 
 template <int P>
-int pass_b_blocks_x(int n) {
+int pass_b_groups(int n) {
   return (n + ColCfg<P>::C - 1) / ColCfg<P>::C;
 }
 
 template <int P>
-cudaError_t launch_pass_b(const PassArgs& a, int adj, int nbx, cudaStream_t s) {
+int pass_b_blocks(int items) {
   using Cc = ColCfg<P>;
-  dim3 grid(nbx, a.nk * a.J);
+  cudaFuncSetAttribute(k_pass_b<P, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                       (int)Cc::SMEM_BYTES);
+  return persistent_blocks(k_pass_b<P, true>, Cc::NT, Cc::SMEM_BYTES, items);
+}
+
+template <int P>
+cudaError_t launch_pass_b(const PassArgs& a, int adj, int nblocks, cudaStream_t s) {
+  using Cc = ColCfg<P>;
   cudaError_t e;
   if (adj) {
     e = cudaFuncSetAttribute(k_pass_b<P, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)Cc::SMEM_BYTES);
     if (e != cudaSuccess) return e;
-    k_pass_b<P, true><<<grid, Cc::NT, Cc::SMEM_BYTES, s>>>(a);
+    k_pass_b<P, true><<<nblocks, Cc::NT, Cc::SMEM_BYTES, s>>>(a);
   } else {
     e = cudaFuncSetAttribute(k_pass_b<P, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)Cc::SMEM_BYTES);
     if (e != cudaSuccess) return e;
-    k_pass_b<P, false><<<grid, Cc::NT, Cc::SMEM_BYTES, s>>>(a);
+    k_pass_b<P, false><<<nblocks, Cc::NT, Cc::SMEM_BYTES, s>>>(a);
   }
   return cudaGetLastError();
 }
@@ -422,11 +467,12 @@ cudaError_t launch_pass_b(const PassArgs& a, int adj, int nbx, cudaStream_t s) {
 template <int P>
 cudaError_t launch_pass_c(const PassArgs& a, cudaStream_t s) {
   using R = RowCfg<P>;
+  if (a.nlines <= 0) return cudaSuccess;
   cudaError_t e = cudaFuncSetAttribute(k_pass_c<P>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)R::SMEM_BYTES);
   if (e != cudaSuccess) return e;
-  dim3 grid((a.max_box_rows + R::G - 1) / R::G, a.nk * a.J);
-  k_pass_c<P><<<grid, R::NT, R::SMEM_BYTES, s>>>(a);
+  const int nb = persistent_blocks(k_pass_c<P>, R::NT, R::SMEM_BYTES, (a.nlines + R::G - 1) / R::G);
+  k_pass_c<P><<<nb, R::NT, R::SMEM_BYTES, s>>>(a);
   return cudaGetLastError();
 }
 
@@ -438,7 +484,8 @@ const Ops* make_ops() {
                           launch_pass_a<P>,
                           launch_pass_b<P>,
                           launch_pass_c<P>,
-                          pass_b_blocks_x<P>,
+                          pass_b_groups<P>,
+                          pass_b_blocks<P>,
                           Fft<P>::TW};
   return &ops;
 }

@@ -212,6 +212,18 @@ class Holo:
                                      _ptr(g, torch.complex64, None, "g"), float(beta), eta.numel())
         _check(self.lib, self.ctx, st, "holo_direction")
 
+    def set_timing(self, enable=True):
+        """Start (and clear) or stop per-pass CUDA-event timing on the context's stream."""
+        _check(self.lib, self.ctx, self.lib.holo_set_timing(self.ctx, 1 if enable else 0),
+               "holo_set_timing")
+
+    def get_timing(self):
+        """{pass: (ms, launches)} summed since set_timing(True)."""
+        ms = (ctypes.c_double * len(_lib.TIMERS))()
+        nl = (ctypes.c_longlong * len(_lib.TIMERS))()
+        _check(self.lib, self.ctx, self.lib.holo_get_timing(self.ctx, ms, nl), "holo_get_timing")
+        return {name: (ms[i], nl[i]) for i, name in enumerate(_lib.TIMERS)}
+
     def workspace_bytes(self):
         v = ctypes.c_longlong(0)
         _check(self.lib, self.ctx, self.lib.holo_workspace_bytes(self.ctx, ctypes.byref(v)),
