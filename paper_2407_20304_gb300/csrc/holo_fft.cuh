@@ -20,8 +20,8 @@
 // memory bank conflicts.  Twiddles come from a per-stage table in shared memory,
 // indexed [k-1][mu] so that consecutive threads read consecutive entries.
 //
-// Synchronisation is the caller's: every thread of the block calls the transform the
-// same number of times, and `SYNC()` is a block-wide barrier.
+// Synchronisation: every thread of a line group calls the transform the same number of
+// times; the Sync policy is a block-wide barrier or a named barrier per line group.
 
 #pragma once
 
@@ -187,13 +187,66 @@ __device__ __forceinline__ void load_twiddles(float2* sm_tw, const float2* __res
   for (int i = threadIdx.x; i < Fft<P>::TW; i += blockDim.x) sm_tw[i] = g_tw[i];
 }
 
+// --------------------------------------------------------------------- twiddle providers
+
+// TwTable: the per-stage table in shared memory, one load per twiddle.
+struct TwTable {
+  const float2* tw;
+  template <int P, int S>
+  __device__ __forceinline__ float2 get(int mu, int k) const {
+    return tw[Fft<P>::tw_off(S) + (k - 1) * Fft<P>::M(S) + mu];
+  }
+  template <int P, int S, bool INV>
+  __device__ __forceinline__ void apply(float2 (&v)[16], int mu) const {
+    const float2* w = tw + Fft<P>::tw_off(S) + mu;
+#pragma unroll
+    for (int k = 1; k < 16; ++k)
+      v[k] = INV ? cmulc(v[k], w[(k - 1) * Fft<P>::M(S)]) : cmul(v[k], w[(k - 1) * Fft<P>::M(S)]);
+  }
+};
+
+// TwPow: one root r = W_P^{mu L(S)} from the table (entry k = 1), the powers r^k by a
+// product tree of depth <= 4 (rounding error a few ulp), no further loads.
+struct TwPow {
+  const float2* tw;
+  template <int P, int S, bool INV>
+  __device__ __forceinline__ void apply(float2 (&v)[16], int mu) const {
+    const float2 r = tw[Fft<P>::tw_off(S) + mu];
+    float2 w[16];
+    w[1] = r;
+    w[2] = cmul(r, r);
+    w[3] = cmul(w[2], r);
+    w[4] = cmul(w[2], w[2]);
+    w[5] = cmul(w[4], r);
+    w[6] = cmul(w[4], w[2]);
+    w[7] = cmul(w[4], w[3]);
+    w[8] = cmul(w[4], w[4]);
+#pragma unroll
+    for (int k = 9; k < 16; ++k) w[k] = cmul(w[8], w[k - 8]);
+#pragma unroll
+    for (int k = 1; k < 16; ++k) v[k] = INV ? cmulc(v[k], w[k]) : cmul(v[k], w[k]);
+  }
+};
+
 // --------------------------------------------------------------------- stages
 
-#define HOLO_SYNC() __syncthreads()
+// Barrier over the threads of one line group: the whole block, or a named barrier
+// (id >= 1) over the `count` threads of this line when several lines share a block.
+struct SyncBlock {
+  __device__ __forceinline__ void operator()() const { __syncthreads(); }
+};
+struct SyncNamed {
+  int id, count;
+  __device__ __forceinline__ void operator()() const {
+    asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(count) : "memory");
+  }
+};
 
-template <int P, int S>
-__device__ __forceinline__ void fwd_from(float2 (&v)[16], float2* __restrict__ sm,
-                                         const float2* __restrict__ tw, int t) {
+#define HOLO_SYNC() sync()
+
+template <int P, int S, class Sync = SyncBlock, class TW = TwTable>
+__device__ __forceinline__ void fwd_from(float2 (&v)[16], float2* __restrict__ sm, TW tw, int t,
+                                         Sync sync = Sync()) {
   using F = Fft<P>;
   if constexpr (S < F::N16) {
     constexpr int M = F::M(S);
@@ -204,18 +257,13 @@ __device__ __forceinline__ void fwd_from(float2 (&v)[16], float2* __restrict__ s
       HOLO_SYNC();
     }
     dft16<false>(v);
-    if constexpr (M > 1) {
-      const int mu = t % M;
-      const float2* w = tw + F::tw_off(S) + mu;
-#pragma unroll
-      for (int k = 1; k < 16; ++k) v[k] = cmul(v[k], w[(k - 1) * M]);
-    }
+    if constexpr (M > 1) tw.template apply<P, S, false>(v, t % M);
     if constexpr (S < F::NST - 1) {
 #pragma unroll
       for (int k = 0; k < 16; ++k) sm[spad(t + F::T * k)] = v[k];
       HOLO_SYNC();
     }
-    fwd_from<P, S + 1>(v, sm, tw, t);
+    fwd_from<P, S + 1, Sync, TW>(v, sm, tw, t, sync);
   } else if constexpr (F::RB > 0 && S == F::N16) {
     constexpr int R = F::RLAST, G = 16 / R;
 #pragma unroll
@@ -232,9 +280,9 @@ __device__ __forceinline__ void fwd_from(float2 (&v)[16], float2* __restrict__ s
   }
 }
 
-template <int P, int S>
-__device__ __forceinline__ void inv_from(float2 (&v)[16], float2* __restrict__ sm,
-                                         const float2* __restrict__ tw, int t) {
+template <int P, int S, class Sync = SyncBlock, class TW = TwTable>
+__device__ __forceinline__ void inv_from(float2 (&v)[16], float2* __restrict__ sm, TW tw, int t,
+                                         Sync sync = Sync()) {
   using F = Fft<P>;
   if constexpr (S == F::N16) {
     if constexpr (F::RB > 0) {
@@ -254,15 +302,10 @@ __device__ __forceinline__ void inv_from(float2 (&v)[16], float2* __restrict__ s
       for (int k = 0; k < 16; ++k) v[k] = sm[spad(t + F::T * k)];
       HOLO_SYNC();
     }
-    inv_from<P, S - 1>(v, sm, tw, t);
+    inv_from<P, S - 1, Sync, TW>(v, sm, tw, t, sync);
   } else if constexpr (S >= 0) {
     constexpr int M = F::M(S);
-    if constexpr (M > 1) {
-      const int mu = t % M;
-      const float2* w = tw + F::tw_off(S) + mu;
-#pragma unroll
-      for (int k = 1; k < 16; ++k) v[k] = cmulc(v[k], w[(k - 1) * M]);
-    }
+    if constexpr (M > 1) tw.template apply<P, S, true>(v, t % M);
     dft16<true>(v);
     if constexpr (S > 0) {
       const int mu = t % M, ka = t / M;
@@ -272,21 +315,29 @@ __device__ __forceinline__ void inv_from(float2 (&v)[16], float2* __restrict__ s
 #pragma unroll
       for (int k = 0; k < 16; ++k) v[k] = sm[spad(t + F::T * k)];
       HOLO_SYNC();
-      inv_from<P, S - 1>(v, sm, tw, t);
+      inv_from<P, S - 1, Sync, TW>(v, sm, tw, t, sync);
     }
   }
 }
 
 // Forward DFT (e^{-2 pi i}, unnormalised): strided natural in, strided natural out.
+template <int P, class Sync, class TW>
+__device__ __forceinline__ void fft_fwd_with(float2 (&v)[16], float2* sm, TW tw, int t, Sync sync) {
+  fwd_from<P, 0, Sync, TW>(v, sm, tw, t, sync);
+}
 template <int P>
 __device__ __forceinline__ void fft_fwd(float2 (&v)[16], float2* sm, const float2* tw, int t) {
-  fwd_from<P, 0>(v, sm, tw, t);
+  fwd_from<P, 0, SyncBlock, TwTable>(v, sm, TwTable{tw}, t, SyncBlock());
 }
 
 // Inverse DFT without the 1/P factor (the adjoint of fft_fwd).
+template <int P, class Sync, class TW>
+__device__ __forceinline__ void fft_inv_with(float2 (&v)[16], float2* sm, TW tw, int t, Sync sync) {
+  inv_from<P, Fft<P>::N16, Sync, TW>(v, sm, tw, t, sync);
+}
 template <int P>
 __device__ __forceinline__ void fft_inv(float2 (&v)[16], float2* sm, const float2* tw, int t) {
-  inv_from<P, Fft<P>::N16>(v, sm, tw, t);
+  inv_from<P, Fft<P>::N16, SyncBlock, TwTable>(v, sm, TwTable{tw}, t, SyncBlock());
 }
 
 }  // namespace holo
