@@ -11,6 +11,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "_build", "libholo.so")
 MAX_DIST = 8
 ACCUMULATE = 1
+NOALLOC_MAX_ELEMENTS = 1 << 28   # holo_dot_noalloc: capacity of its static partial-sum array
 
 STATUS = {0: "HOLO_OK", 1: "HOLO_ERR_ARG", 2: "HOLO_ERR_CUDA", 3: "HOLO_ERR_OOM",
           4: "HOLO_ERR_TIMEOUT", 5: "HOLO_ERR_STATE", 6: "HOLO_ERR_NUMERIC",
@@ -19,7 +20,7 @@ STATUS = {0: "HOLO_OK", 1: "HOLO_ERR_ARG", 2: "HOLO_ERR_CUDA", 3: "HOLO_ERR_OOM"
 # Every symbol declared in include/holo.h.
 EXPORTS = ("holo_create", "holo_destroy", "holo_set_shifts", "holo_set_data", "holo_set_probe",
            "holo_forward", "holo_gradient", "holo_gradient_host", "holo_propagate", "holo_dot",
-           "holo_step", "holo_direction", "holo_set_timing", "holo_get_timing",
+           "holo_step", "holo_direction", "holo_set_timing", "holo_get_timing", "holo_dot_noalloc",
            "holo_workspace_bytes", "holo_launch_count", "holo_status_string", "holo_last_error")
 
 # Pass ids of holo_get_timing (HOLO_T_* in include/holo.h).
@@ -69,6 +70,7 @@ def load():
         "holo_dot": [P, P, P, LL, ctypes.POINTER(D)],
         "holo_step": [P, P, P, D, LL],
         "holo_direction": [P, P, P, D, LL],
+        "holo_dot_noalloc": [P, P, LL, ctypes.POINTER(D), P],
         "holo_set_timing": [P, I],
         "holo_get_timing": [P, P, P],
         "holo_workspace_bytes": [P, ctypes.POINTER(LL)],

@@ -42,6 +42,29 @@ def _host_ptr(a, dtype, shape, name):
     return ctypes.c_void_p(a.ctypes.data)
 
 
+def dot_noalloc(a, b, stream=None):
+    """Re <a, b> through holo_dot_noalloc: no context and no device allocation.
+
+    For callers that must not allocate device memory; the partial sums live in a fixed
+    device array of the library, so len(a) <= 2**28.  Calls that overlap on the GPU race.
+    """
+    import ctypes as ct
+
+    import torch
+    lib = _lib.load()
+    if a.shape != b.shape:
+        raise ValueError("shape mismatch")
+    if a.numel() > _lib.NOALLOC_MAX_ELEMENTS:
+        raise ValueError(f"dot_noalloc handles at most {_lib.NOALLOC_MAX_ELEMENTS} elements")
+    pa = _ptr(a, torch.complex64, None, "a")
+    pb = _ptr(b, torch.complex64, None, "b")
+    s = stream if stream is not None else torch.cuda.current_stream(a.device)
+    out = ct.c_double(0.0)
+    st = lib.holo_dot_noalloc(pa, pb, a.numel(), ct.byref(out), ct.c_void_p(s.cuda_stream))
+    _check(lib, None, st, "holo_dot_noalloc")
+    return out.value
+
+
 class Holo:
     """One reconstruction problem's geometry and workspace on one GPU.
 
