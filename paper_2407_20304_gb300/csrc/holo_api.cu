@@ -397,7 +397,7 @@ PassArgs pass_args(holo_ctx* c, int k0, int nk, const void* psi) {
 // Passes A, B (and C, D for gradients), loss partial sums into d_red[0], reference term
 // into d_red[1] (only when k0 == 0 and w_ref != 0).
 holo_status run_eval(holo_ctx* c, PassArgs& a, bool gradient, float2* grad_q, unsigned flags) {
-  const int nbx = c->ops->pass_b_blocks(a.pass_b_items);
+  const int nbx = c->ops->pass_b_blocks(a.pass_b_items, c->n, a.max_box_rows);
   const long long nparts = nbx;
   {
     PassTimer tm(c, HOLO_T_PASS_A);
@@ -690,7 +690,7 @@ holo_status holo_set_shifts(holo_ctx* c, const float* t) {
   const size_t ybytes = sizeof(float2) * (size_t)(np * ystride);
   const size_t rbytes = sizeof(float2) * (size_t)(np * n * n);
   const size_t gbytes = sizeof(float2) * (size_t)(np * gkstride);
-  const long long parts = (long long)c->ops->pass_b_blocks(1 << 30) + kRefBlocks + 1024;
+  const long long parts = (long long)c->ops->pass_b_blocks(1 << 30, n, maxbys) + kRefBlocks + 1024;
   if (ystride > c->ystride || gkstride > c->gkstride || !c->ybuf) {
     dfree(c, c->ybuf, sizeof(float2) * (size_t)(np * c->ystride));
     dfree(c, c->rbuf, rbytes);

@@ -78,6 +78,11 @@ struct Fft {
     return s == 0 ? 0 : tw_off(s - 1) + (M(s - 1) > 1 ? 15 * M(s - 1) : 0);
   }
   static constexpr int TW = tw_off(N16);           // twiddle table entries (float2)
+  // compact table of the roots W_P^{mu L(s)} (k = 1 entries) of every twiddled stage
+  __host__ __device__ static constexpr int roots_off(int s) {
+    return s == 0 ? 0 : roots_off(s - 1) + (M(s - 1) > 1 ? M(s - 1) : 0);
+  }
+  static constexpr int ROOTS = roots_off(N16);
 };
 
 // --------------------------------------------------------------------- small DFTs
@@ -205,13 +210,17 @@ struct TwTable {
   }
 };
 
-// TwPow: one root r = W_P^{mu L(S)} from the table (entry k = 1), the powers r^k by a
-// product tree of depth <= 4 (rounding error a few ulp), no further loads.
+// TwPow: one root r = W_P^{mu L(S)} from the full table (entry k = 1), the powers r^k
+// by a product tree of depth <= 4 (rounding error a few ulp), no further loads.
 struct TwPow {
   const float2* tw;
   template <int P, int S, bool INV>
   __device__ __forceinline__ void apply(float2 (&v)[16], int mu) const {
     const float2 r = tw[Fft<P>::tw_off(S) + mu];
+    pow_apply<INV>(v, r);
+  }
+  template <bool INV>
+  __device__ __forceinline__ static void pow_apply(float2 (&v)[16], float2 r) {
     float2 w[16];
     w[1] = r;
     w[2] = cmul(r, r);
@@ -227,6 +236,28 @@ struct TwPow {
     for (int k = 1; k < 16; ++k) v[k] = INV ? cmulc(v[k], w[k]) : cmul(v[k], w[k]);
   }
 };
+
+// TwRoots: the same power tree from the compact root table (Fft<P>::ROOTS entries), which
+// is small enough to keep in shared memory next to the chirp.
+struct TwRoots {
+  const float2* roots;
+  template <int P, int S, bool INV>
+  __device__ __forceinline__ void apply(float2 (&v)[16], int mu) const {
+    TwPow::pow_apply<INV>(v, roots[Fft<P>::roots_off(S) + mu]);
+  }
+};
+
+// Copy the roots of every twiddled stage from the full table (block-wide).
+template <int P>
+__device__ __forceinline__ void load_roots(float2* sm_roots, const float2* __restrict__ g_tw) {
+  using F = Fft<P>;
+#pragma unroll
+  for (int st = 0; st < F::N16; ++st) {
+    if (F::M(st) > 1)
+      for (int mu = threadIdx.x; mu < F::M(st); mu += blockDim.x)
+        sm_roots[F::roots_off(st) + mu] = g_tw[F::tw_off(st) + mu];
+  }
+}
 
 // --------------------------------------------------------------------- stages
 

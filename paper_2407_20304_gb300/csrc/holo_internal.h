@@ -95,7 +95,7 @@ struct Ops {
   cudaError_t (*pass_b)(const PassArgs&, int with_adjoint, int nblocks, cudaStream_t);
   cudaError_t (*pass_c)(const PassArgs&, cudaStream_t);
   int (*pass_b_groups)(int n);              // column groups of pass B for side n
-  int (*pass_b_blocks)(int items);          // persistent grid of pass B
+  int (*pass_b_blocks)(int items, int n, int rows);  // persistent grid of pass B
   int twiddle_count;
 };
 

@@ -34,13 +34,22 @@ namespace holo {
 // whole 32-byte sectors of C adjacent columns.  Line strides in shared memory are
 // chosen so that every exchange phase is free of bank conflicts (checked by simulating
 // the address patterns for all P).
+// Shared memory of every line kernel: the twiddle roots, the half chirp table (P/2 + 1
+// entries) and the exchange lines.
+template <int P>
+struct SmemHead {
+  static constexpr int ROOTS = (Fft<P>::ROOTS + 1) & ~1;
+  static constexpr int CHIRP = (P / 2 + 2) & ~1;
+  static constexpr int WORDS = ROOTS + CHIRP;
+};
+
 template <int P>
 struct RowCfg {
   static constexpr int T = P / 16;
   static constexpr int G = T >= 256 ? 1 : 256 / T;      // lines per block
   static constexpr int NT = G * T;
   static constexpr int LS = Fft<P>::SMEM + (P == 64 ? 1 : 0);
-  static constexpr size_t SMEM_BYTES = (size_t)(Fft<P>::TW + G * LS) * sizeof(float2);
+  static constexpr size_t SMEM_BYTES = (size_t)(SmemHead<P>::WORDS + G * LS) * sizeof(float2);
 };
 
 template <int P>
@@ -50,7 +59,8 @@ struct ColCfg {
   static constexpr int NT = C * T;
   static constexpr int EXTRA = P >= 4096 ? 8 : (P == 2048 ? 4 : (P == 1024 ? 3 : (P == 16 ? 0 : 1)));
   static constexpr int LS = Fft<P>::SMEM + EXTRA;
-  static constexpr size_t SMEM_BYTES = (size_t)(Fft<P>::TW + C * LS) * sizeof(float2);
+  static constexpr size_t SMEM_BYTES = (size_t)(SmemHead<P>::WORDS + C * LS) * sizeof(float2);
+  static constexpr size_t PASS_B_SMEM = SMEM_BYTES;
 };
 
 // w = R0(psi - ext) at one P-grid position from its row tap (iy0, fy) and column tap:
@@ -100,6 +110,19 @@ __device__ __forceinline__ double block_sum_f64(double v, double* red) {
   return s;
 }
 
+// Chirp exp(-i pi lambda z f^2)/P is even in the signed frequency, so a table of the
+// P/2 + 1 non-negative frequencies suffices: entry f for f <= P/2, entry P - f above.
+template <int P>
+__device__ __forceinline__ float2 chirp_half(const float2* __restrict__ tab, int f) {
+  return tab[f <= P / 2 ? f : P - f];
+}
+
+// Copy the half chirp table of distance j into shared memory (block-wide).
+template <int P>
+__device__ __forceinline__ void load_chirp_half(float2* dst, const float2* __restrict__ src) {
+  for (int i = threadIdx.x; i <= P / 2; i += blockDim.x) dst[i] = src[i];
+}
+
 // Plane of flat line `line` (global line numbering): largest p with rowstart[p] <= line.
 __device__ __forceinline__ int plane_of_line(const int* __restrict__ rowstart, int lo, int hi,
                                              int line) {
@@ -121,14 +144,18 @@ template <int P, bool COLS>
 __global__ void __launch_bounds__(COLS ? ColCfg<P>::NT : RowCfg<P>::NT)
 k_line_dstep(LineArgs a, const float2* __restrict__ gtw) {
   using F = Fft<P>;
+  using H = SmemHead<P>;
   constexpr int G = COLS ? ColCfg<P>::C : RowCfg<P>::G;
   constexpr int LS = COLS ? ColCfg<P>::LS : RowCfg<P>::LS;
   extern __shared__ float2 smem[];
-  float2* tw = smem;
+  float2* roots = smem;
+  float2* chs = smem + H::ROOTS;
   const int g = COLS ? (int)(threadIdx.x % G) : (int)(threadIdx.x / F::T);
   const int t = COLS ? (int)(threadIdx.x / G) : (int)(threadIdx.x % F::T);
-  float2* sm = smem + F::TW + g * LS;
-  load_twiddles<P>(tw, gtw);
+  float2* sm = smem + H::WORDS + g * LS;
+  load_roots<P>(roots, gtw);
+  load_chirp_half<P>(chs, a.chirp);
+  const TwRoots tw{roots};
   for (int base = blockIdx.x * G; base < a.nlines; base += gridDim.x * G) {
     const int line = base + g;
     const bool valid = line < a.nlines;
@@ -141,13 +168,13 @@ k_line_dstep(LineArgs a, const float2* __restrict__ gtw) {
                                                            : make_float2(0.f, 0.f);
     }
     __syncthreads();
-    fft_fwd<P>(v, sm, tw, t);
+    fft_fwd_with<P>(v, sm, tw, t, SyncBlock());
 #pragma unroll
     for (int c = 0; c < 16; ++c) {
-      float2 ch = __ldg(a.chirp + t + F::T * c);
+      const float2 ch = chirp_half<P>(chs, t + F::T * c);
       v[c] = a.conj_chirp ? cmulc(v[c], ch) : cmul(v[c], ch);
     }
-    fft_inv<P>(v, sm, tw, t);
+    fft_inv_with<P>(v, sm, tw, t, SyncBlock());
     float2* out = a.out + (long long)line * a.out_line_stride;
 #pragma unroll
     for (int c = 0; c < 16; ++c) {
@@ -162,19 +189,34 @@ k_line_dstep(LineArgs a, const float2* __restrict__ gtw) {
   }
 }
 
+// Load the half chirp of distance j unless it is already resident (block-uniform j).
+template <int P>
+__device__ __forceinline__ void ensure_chirp(float2* chs, const float2* __restrict__ tables, int j,
+                                             int& jcur) {
+  if (j != jcur) {
+    __syncthreads();
+    load_chirp_half<P>(chs, tables + (long long)j * P);
+    jcur = j;
+  }
+}
+
 // ------------------------------------------------------------------ pass A
 
 template <int P>
 __global__ void __launch_bounds__(RowCfg<P>::NT) k_pass_a(PassArgs a) {
   using F = Fft<P>;
   using R = RowCfg<P>;
+  using H = SmemHead<P>;
   extern __shared__ float2 smem[];
-  float2* tw = smem;
+  float2* roots = smem;
+  float2* chs = smem + H::ROOTS;
   const int g = threadIdx.x / F::T, t = threadIdx.x % F::T;
-  float2* sm = smem + F::TW + g * R::LS;
-  load_twiddles<P>(tw, a.twiddles);
+  float2* sm = smem + H::WORDS + g * R::LS;
+  load_roots<P>(roots, a.twiddles);
+  const TwRoots tw{roots};
   const int n = a.n, lo = P / 2 - n / 2;
   const int p_lo = a.k0 * a.J, p_hi = (a.k0 + a.nk) * a.J;
+  int jcur = -1;
   for (int base = blockIdx.x * R::G; base < a.nlines; base += gridDim.x * R::G) {
     const int li = base + g;
     const bool valid = li < a.nlines;
@@ -187,6 +229,11 @@ __global__ void __launch_bounds__(RowCfg<P>::NT) k_pass_a(PassArgs a) {
     const Tap* xt = a.xtap + (long long)gp * a.tap_stride;
     const float2* psi = a.psi + (long long)kl * n * n;
     const float2* prow = a.pj + ((long long)j * P + d.by0 + i) * P;
+    float2* wrow = a.gkbuf + (long long)lp * a.gkstride + (long long)i * d.bxs;
+    // lines of one block may belong to different distances only when G > 1; the chirp
+    // table then follows the distance of the block's first line (block-uniform) and the
+    // other lines read the chirp from global memory.
+    const int jb = (plane_of_line(a.rowstart, p_lo, p_hi, a.line0 + base) - p_lo) % a.J;
     float2 v[16];
 #pragma unroll
     for (int c = 0; c < 16; ++c) {
@@ -194,16 +241,22 @@ __global__ void __launch_bounds__(RowCfg<P>::NT) k_pass_a(PassArgs a) {
       float2 x = make_float2(0.f, 0.f);
       if (valid && (unsigned)rel < (unsigned)d.bxs) {
         const float2 w = resample_w(psi, n, a.ext, yt.i0, yt.f, xt[rel]);
+        wrow[rel] = w;
         x = cmul(__ldg(prow + X), w);
       }
       v[c] = x;
     }
+    ensure_chirp<P>(chs, a.chirp_zhat, R::G == 1 ? j : jb, jcur);
     __syncthreads();
-    fft_fwd<P>(v, sm, tw, t);
-    const float2* ch = a.chirp_zhat + (long long)j * P;
+    fft_fwd_with<P>(v, sm, tw, t, SyncBlock());
+    const bool own = R::G == 1 || j == jcur;
+    const float2* chg = a.chirp_zhat + (long long)j * P;
 #pragma unroll
-    for (int c = 0; c < 16; ++c) v[c] = cmul(v[c], __ldg(ch + t + F::T * c));
-    fft_inv<P>(v, sm, tw, t);
+    for (int c = 0; c < 16; ++c) {
+      const int f = t + F::T * c;
+      v[c] = cmul(v[c], own ? chirp_half<P>(chs, f) : __ldg(chg + f));
+    }
+    fft_inv_with<P>(v, sm, tw, t, SyncBlock());
     float2* yrow = a.ybuf + (long long)lp * a.ystride + (long long)i * n;
 #pragma unroll
     for (int c = 0; c < 16; ++c) {
@@ -219,16 +272,20 @@ template <int P, bool ADJ>
 __global__ void __launch_bounds__(ColCfg<P>::NT) k_pass_b(PassArgs a) {
   using F = Fft<P>;
   using Cc = ColCfg<P>;
+  using H = SmemHead<P>;
   extern __shared__ float2 smem[];
   __shared__ double red[32];
-  float2* tw = smem;
+  float2* roots = smem;
+  float2* chs = smem + H::ROOTS;
   const int g = threadIdx.x % Cc::C, t = threadIdx.x / Cc::C;
-  float2* sm = smem + F::TW + g * Cc::LS;
-  load_twiddles<P>(tw, a.twiddles);
+  float2* sm = smem + H::WORDS + g * Cc::LS;
+  load_roots<P>(roots, a.twiddles);
+  const TwRoots tw{roots};
   const int n = a.n, lo = P / 2 - n / 2;
   const int ngroups = (n + Cc::C - 1) / Cc::C;
   float lsum = 0.f;
   double dsum = 0.0;
+  int jcur = -1;
   for (int item = blockIdx.x; item < a.pass_b_items; item += gridDim.x) {
     const int lp = item / ngroups, kl = lp / a.J, j = lp % a.J;
     const int col = (item % ngroups) * Cc::C + g;
@@ -236,6 +293,7 @@ __global__ void __launch_bounds__(ColCfg<P>::NT) k_pass_b(PassArgs a) {
     const long long gplane = (long long)(a.k0 + kl) * a.J + j;
     const PlaneDesc d = a.planes[gplane];
     float2* yb = a.ybuf + (long long)lp * a.ystride;
+    ensure_chirp<P>(chs, a.chirp_zhat, j, jcur);
     float2 v[16];
 #pragma unroll
     for (int c = 0; c < 16; ++c) {
@@ -244,11 +302,10 @@ __global__ void __launch_bounds__(ColCfg<P>::NT) k_pass_b(PassArgs a) {
                                                          : make_float2(0.f, 0.f);
     }
     __syncthreads();
-    fft_fwd<P>(v, sm, tw, t);
-    const float2* ch = a.chirp_zhat + (long long)j * P;
+    fft_fwd_with<P>(v, sm, tw, t, SyncBlock());
 #pragma unroll
-    for (int c = 0; c < 16; ++c) v[c] = cmul(v[c], __ldg(ch + t + F::T * c));
-    fft_inv<P>(v, sm, tw, t);
+    for (int c = 0; c < 16; ++c) v[c] = cmul(v[c], chirp_half<P>(chs, t + F::T * c));
+    fft_inv_with<P>(v, sm, tw, t, SyncBlock());
     const float* ad = a.sqrt_d + (gplane - (long long)a.data_k0 * a.J) * n * n;
     float2* rb = a.rbuf + (long long)lp * n * n;
     float2* uo = a.u_out ? a.u_out + (long long)lp * n * n : nullptr;
@@ -280,10 +337,10 @@ __global__ void __launch_bounds__(ColCfg<P>::NT) k_pass_b(PassArgs a) {
     }
     dsum += (double)lsum;
     if constexpr (ADJ) {
-      fft_fwd<P>(v, sm, tw, t);
+      fft_fwd_with<P>(v, sm, tw, t, SyncBlock());
 #pragma unroll
-      for (int c = 0; c < 16; ++c) v[c] = cmulc(v[c], __ldg(ch + t + F::T * c));
-      fft_inv<P>(v, sm, tw, t);
+      for (int c = 0; c < 16; ++c) v[c] = cmulc(v[c], chirp_half<P>(chs, t + F::T * c));
+      fft_inv_with<P>(v, sm, tw, t, SyncBlock());
 #pragma unroll
       for (int c = 0; c < 16; ++c) {
         const int rel = t + F::T * c - d.by0;
@@ -301,20 +358,25 @@ template <int P>
 __global__ void __launch_bounds__(RowCfg<P>::NT) k_pass_c(PassArgs a) {
   using F = Fft<P>;
   using R = RowCfg<P>;
+  using H = SmemHead<P>;
   extern __shared__ float2 smem[];
-  float2* tw = smem;
+  float2* roots = smem;
+  float2* chs = smem + H::ROOTS;
   const int g = threadIdx.x / F::T, t = threadIdx.x % F::T;
-  float2* sm = smem + F::TW + g * R::LS;
-  load_twiddles<P>(tw, a.twiddles);
+  float2* sm = smem + H::WORDS + g * R::LS;
+  load_roots<P>(roots, a.twiddles);
+  const TwRoots tw{roots};
   const int n = a.n, lo = P / 2 - n / 2;
   const int p_lo = a.k0 * a.J, p_hi = (a.k0 + a.nk) * a.J;
+  int jcur = -1;
   for (int base = blockIdx.x * R::G; base < a.nlines; base += gridDim.x * R::G) {
     const int li = base + g;
     const bool valid = li < a.nlines;
     const int line = a.line0 + (valid ? li : 0);
     const int gp = plane_of_line(a.rowstart, p_lo, p_hi, line);
-    const int lp = gp - p_lo, kl = lp / a.J, j = lp % a.J;
+    const int lp = gp - p_lo, j = lp % a.J;
     const int i = line - __ldg(a.rowstart + gp);
+    const int jb = (plane_of_line(a.rowstart, p_lo, p_hi, a.line0 + base) - p_lo) % a.J;
     float2* yrow = a.ybuf + (long long)lp * a.ystride + (long long)i * n;
     float2 v[16];
 #pragma unroll
@@ -322,17 +384,20 @@ __global__ void __launch_bounds__(RowCfg<P>::NT) k_pass_c(PassArgs a) {
       const int rel = t + F::T * c - lo;
       v[c] = (valid && (unsigned)rel < (unsigned)n) ? yrow[rel] : make_float2(0.f, 0.f);
     }
+    ensure_chirp<P>(chs, a.chirp_zhat, R::G == 1 ? j : jb, jcur);
     __syncthreads();
-    fft_fwd<P>(v, sm, tw, t);
-    const float2* ch = a.chirp_zhat + (long long)j * P;
+    fft_fwd_with<P>(v, sm, tw, t, SyncBlock());
+    const bool own = R::G == 1 || j == jcur;
+    const float2* chg = a.chirp_zhat + (long long)j * P;
 #pragma unroll
-    for (int c = 0; c < 16; ++c) v[c] = cmulc(v[c], __ldg(ch + t + F::T * c));
-    fft_inv<P>(v, sm, tw, t);
+    for (int c = 0; c < 16; ++c) {
+      const int f = t + F::T * c;
+      v[c] = cmulc(v[c], own ? chirp_half<P>(chs, f) : __ldg(chg + f));
+    }
+    fft_inv_with<P>(v, sm, tw, t, SyncBlock());
     // v holds the adjoint field on this P-grid row; the exchange buffer is free.
+    // The box holds w = R0(psi - ext) written by pass A; replace it by conj(w) v.
     const PlaneDesc d = a.planes[gp];
-    const Tap yt = a.ytap[(long long)gp * a.tap_stride + i];
-    const Tap* xt = a.xtap + (long long)gp * a.tap_stride;
-    const float2* psi = a.psi + (long long)kl * n * n;
     const float2* prow = a.pj + ((long long)j * P + d.by0 + i) * P;
     float2* gk = a.gkbuf + (long long)lp * a.gkstride + (long long)i * d.bxs;
 #pragma unroll
@@ -340,8 +405,7 @@ __global__ void __launch_bounds__(RowCfg<P>::NT) k_pass_c(PassArgs a) {
       const int X = t + F::T * c, rel = X - d.bx0;
       if (valid && (unsigned)rel < (unsigned)d.bxs) {
         sm[rel] = cconjmul(__ldg(prow + X), v[c]);
-        const float2 w = resample_w(psi, n, a.ext, yt.i0, yt.f, xt[rel]);
-        gk[rel] = cconjmul(w, v[c]);
+        gk[rel] = cconjmul(gk[rel], v[c]);
       }
     }
     __syncthreads();
@@ -438,12 +502,25 @@ int pass_b_groups(int n) {
   return (n + ColCfg<P>::C - 1) / ColCfg<P>::C;
 }
 
+inline int max_dynamic_smem() {
+  static int v = 0;
+  if (!v) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&v, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    if (v <= 0) v = 48 * 1024;
+  }
+  return v;
+}
+
 template <int P>
-int pass_b_blocks(int items) {
+int pass_b_blocks(int items, int n, int rows) {
   using Cc = ColCfg<P>;
+  (void)n;
+  (void)rows;
   cudaFuncSetAttribute(k_pass_b<P, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                       (int)Cc::SMEM_BYTES);
-  return persistent_blocks(k_pass_b<P, true>, Cc::NT, Cc::SMEM_BYTES, items);
+                       (int)Cc::PASS_B_SMEM);
+  return persistent_blocks(k_pass_b<P, true>, Cc::NT, Cc::PASS_B_SMEM, items);
 }
 
 template <int P>
@@ -452,14 +529,14 @@ cudaError_t launch_pass_b(const PassArgs& a, int adj, int nblocks, cudaStream_t 
   cudaError_t e;
   if (adj) {
     e = cudaFuncSetAttribute(k_pass_b<P, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)Cc::SMEM_BYTES);
+                             (int)Cc::PASS_B_SMEM);
     if (e != cudaSuccess) return e;
-    k_pass_b<P, true><<<nblocks, Cc::NT, Cc::SMEM_BYTES, s>>>(a);
+    k_pass_b<P, true><<<nblocks, Cc::NT, Cc::PASS_B_SMEM, s>>>(a);
   } else {
     e = cudaFuncSetAttribute(k_pass_b<P, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)Cc::SMEM_BYTES);
+                             (int)Cc::PASS_B_SMEM);
     if (e != cudaSuccess) return e;
-    k_pass_b<P, false><<<nblocks, Cc::NT, Cc::SMEM_BYTES, s>>>(a);
+    k_pass_b<P, false><<<nblocks, Cc::NT, Cc::PASS_B_SMEM, s>>>(a);
   }
   return cudaGetLastError();
 }
