@@ -52,6 +52,7 @@ def parse():
     ap.add_argument("--workload", default="large", choices=("large", "autograd", "medium"))
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-unfused", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=20.0)
     ap.add_argument("--chunk", type=int, default=0,
                     help="angles per GPU (default: the workload's chunk); small values make "
@@ -327,6 +328,11 @@ def run_ours(args, w, rank, world, local_rank):
                     "launches_per_step": timing[p][1] / args.steps}
                 for p in hs_timers()}
 
+    unfused = None
+    if not args.no_unfused:
+        shifts_np = shifts.astype(np.float64)
+        unfused = run_unfused_sample(w, torch.ones_like(psi), torch.from_numpy(q0).to(dev),
+                                     shifts_np, sqrt_d, sqrt_dref)
     # end to end through the host-buffer entry point
     e2e = None
     if not args.no_e2e:
@@ -348,6 +354,8 @@ def run_ours(args, w, rank, world, local_rank):
     }
     if e2e:
         result["e2e"] = e2e
+    if unfused:
+        result["unfused_cufft"] = unfused
     return result, h
 
 
@@ -391,6 +399,134 @@ def run_e2e(h, args, w, psi, q, sqrt_d, dev, planes, dist):
     return {"value": round(planes * steps / dt, 1), "unit": UNIT, "steps": steps,
             "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
             "api": "holo_gradient_host (psi, data, q host -> grad_psi, grad_q, loss host)"}
+
+
+# ---------------------------------------------------------------- unfused comparison
+
+class Unfused:
+    """The same F2 and gradients in the plain unfused per-plane form: cuFFT 2D transforms
+    (torch.fft) on the full P x P grid and separate elementwise kernels (resample by
+    separable gathers, chirp products, crop, residual, zero embedding, adjoint resample by
+    index_add_, G_j accumulation).  A timed comparison only; not part of the library."""
+
+    def __init__(self, n, P, geom, shifts, sqrt_d, sqrt_dref, ext=1.0, w_ref=1.0, device="cuda"):
+        import torch
+        self.t = torch
+        self.n, self.P, self.ext, self.w_ref = n, P, ext, w_ref
+        z = np.asarray(geom["z"], float)
+        Z, lam, dx = geom["Z"], geom["wavelength"], geom["pixel"]
+        mt = z / z[0]
+        self.mt = mt
+        omega, zeta = (z - z[0]) / mt, z * (Z - z) / Z
+        zhat = zeta / mt ** 2
+        k = np.arange(P, dtype=float)
+        k[k >= P // 2] -= P
+        f2 = (k / (P * dx)) ** 2
+        f2d = f2[:, None] + f2[None, :]
+
+        def H(dist):
+            return torch.from_numpy(np.exp(-1j * np.pi * lam * dist * f2d).astype(np.complex64)).to(device)
+        self.Hz = [H(d) for d in zhat]
+        self.Ho = [H(d) for d in omega]
+        self.Hr = H(zeta[0])
+        self.shifts = shifts
+        self.sqrt_d = sqrt_d            # [K][J][n][n] torch cuda
+        self.sqrt_dref = sqrt_dref
+        self.dev = device
+        self.J = len(z)
+
+    def _taps(self, mtj, tj):
+        t = self.t
+        X = t.arange(self.P, device=self.dev, dtype=t.float64) - self.P // 2
+        xi = mtj * X - tj + self.n // 2
+        i0 = t.floor(xi)
+        f = (xi - i0).float()
+        i0 = i0.long()
+        return i0, f
+
+    def _axis(self, i0, f):
+        """taps (index, weight*mask) for the two neighbours along one axis."""
+        n = self.n
+        out = []
+        for di, w in ((0, 1 - f), (1, f)):
+            idx = i0 + di
+            m = (idx >= 0) & (idx < n)
+            out.append((idx.clamp(0, n - 1), w * m.float()))
+        return out
+
+    def resample(self, psi, ky, kx):
+        """ext + R0(psi - ext) on the P x P grid (separable bilinear)."""
+        d = psi - self.ext
+        rows = sum(w[:, None] * d.index_select(0, idx) for idx, w in ky)          # [P][n]
+        full = sum(w[None, :] * rows.index_select(1, idx) for idx, w in kx)       # [P][P]
+        return full + self.ext
+
+    def resample_T(self, g, ky, kx):
+        t = self.t
+        n = self.n
+        cols = t.zeros((self.P, n), dtype=g.dtype, device=self.dev)
+        for idx, w in kx:
+            cols.index_add_(1, idx, g * w[None, :])
+        out = t.zeros((n, n), dtype=g.dtype, device=self.dev)
+        for idx, w in ky:
+            out.index_add_(0, idx, cols * w[:, None])
+        return out
+
+    def gradient(self, psi, q):
+        t = self.t
+        n, P, J = self.n, self.P, self.J
+        lo = P // 2 - n // 2
+        fft2, ifft2 = t.fft.fft2, t.fft.ifft2
+        p = [q] + [ifft2(fft2(q) * self.Ho[j]) for j in range(1, J)]
+        gpsi = t.zeros_like(psi)
+        G = [t.zeros((P, P), dtype=t.complex64, device=self.dev) for _ in range(J)]
+        loss = 0.0
+        for k in range(psi.shape[0]):
+            for j in range(J):
+                ty, tx = float(self.shifts[k, j, 0]), float(self.shifts[k, j, 1])
+                ky = self._axis(*self._taps(float(self.mt[j]), ty))
+                kx = self._axis(*self._taps(float(self.mt[j]), tx))
+                Rpsi = self.resample(psi[k], ky, kx)
+                u = ifft2(fft2(p[j] * Rpsi) * self.Hz[j])[lo:lo + n, lo:lo + n]
+                a = self.sqrt_d[k, j]
+                mag = u.abs()
+                loss += float(((mag - a) ** 2).sum(dtype=t.float64))
+                r = u * t.where(mag > 0, 1 - a / mag, t.zeros_like(mag))
+                e = t.zeros((P, P), dtype=t.complex64, device=self.dev)
+                e[lo:lo + n, lo:lo + n] = r
+                v = ifft2(fft2(e) * t.conj(self.Hz[j]))
+                gpsi[k] += 2 * self.resample_T(t.conj(p[j]) * v, ky, kx)
+                G[j] += t.conj(Rpsi) * v
+        gq = sum(2 * ifft2(fft2(G[j]) * t.conj(self.Ho[j])) for j in range(J))
+        if self.w_ref:
+            b = ifft2(fft2(q) * self.Hr)[lo:lo + n, lo:lo + n]
+            mag = b.abs()
+            loss += self.w_ref * float(((mag - self.sqrt_dref) ** 2).sum(dtype=t.float64))
+            rr = b * t.where(mag > 0, 1 - self.sqrt_dref / mag, t.zeros_like(mag))
+            e = t.zeros((P, P), dtype=t.complex64, device=self.dev)
+            e[lo:lo + n, lo:lo + n] = rr
+            gq = gq + 2 * self.w_ref * ifft2(fft2(e) * t.conj(self.Hr))
+        return loss, gpsi, gq
+
+
+def run_unfused_sample(w, psi, q, shifts, sqrt_d, sqrt_dref, angles=4):
+    """Plane-gradients/s of the unfused cuFFT form on `angles` angles of the workload."""
+    import torch
+    g = hs.WORKLOAD_GEOMETRY
+    u = Unfused(w.n, w.P, g, shifts[:angles], sqrt_d[:angles], sqrt_dref)
+    u.gradient(psi[:1], q)          # warm-up (plans, allocator)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    u.gradient(psi[:angles], q)
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    return {"value": round(angles * w.n_dist / (ms / 1e3), 1), "unit": UNIT,
+            "sample": f"{angles} angles x {w.n_dist} distances, one gradient evaluation incl. "
+                      f"probe propagation and grad_q",
+            "impl": "torch.fft (cuFFT) 2D transforms on the P x P grid + separate elementwise "
+                    "kernels, FP32"}
 
 
 # ---------------------------------------------------------------- oracle (CPU)

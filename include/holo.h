@@ -64,6 +64,8 @@ typedef enum {
 
 /* Flags of holo_gradient / holo_gradient_host. */
 #define HOLO_ACCUMULATE 1u   /* add to grad_psi, grad_q and *loss instead of overwriting */
+#define HOLO_ACCUMULATE_Q 2u /* add to grad_q and *loss only; grad_psi is overwritten (chunks
+                                of one problem own disjoint psi slices but share q) */
 
 /*
  * Instrument geometry and discretisation (Table 1 lists the paper's instrument).
@@ -134,7 +136,8 @@ holo_status holo_forward(holo_ctx* ctx, int k0, int nk, const void* psi, void* u
  * after it).  psi: dev complex64 [nk][n][n]; grad_psi: dev complex64 [nk][n][n];
  * grad_q: dev complex64 [P][P] (the chunk's contribution; the reference term is included
  * when k0 == 0).  loss: host, may be NULL.  flags: HOLO_ACCUMULATE adds to grad_psi,
- * grad_q and *loss (to sum chunks), otherwise they are overwritten. */
+ * grad_q and *loss; HOLO_ACCUMULATE_Q adds to grad_q and *loss only (summing the chunks of
+ * one problem); otherwise all are overwritten. */
 holo_status holo_gradient(holo_ctx* ctx, int k0, int nk, const void* psi, double* loss,
                           void* grad_psi, void* grad_q, unsigned flags);
 

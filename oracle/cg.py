@@ -70,12 +70,14 @@ def reconstruct(psi0, q0, shifts, sqrt_d, sqrt_dref, geo, iters, gamma0=1.0,
     F, gpsi, gq = holo.gradients(psi, q, shifts, sqrt_d, sqrt_dref, geo)
     eta_psi, eta_q = -gpsi, -gq
     trial_psi = trial_q = gamma0
-    hist = {"F": [F], "gamma_psi": [], "gamma_q": [], "beta_psi": [], "beta_q": []}
+    hist = {"F": [F], "gamma_psi": [], "gamma_q": [], "beta_psi": [], "beta_q": [],
+            "F_after_psi": []}
     for _ in range(iters):
         def f_psi(x):
             return holo.functional(x, q, shifts, sqrt_d, sqrt_dref, geo)
         gam_psi, F = backtrack(f_psi, F, psi, eta_psi, trial_psi, max_halvings)
         psi = psi + gam_psi * eta_psi
+        hist["F_after_psi"].append(F)
         gam_q = 0.0
         if update_q:
             def f_q(x):

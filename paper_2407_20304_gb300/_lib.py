@@ -11,6 +11,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "_build", "libholo.so")
 MAX_DIST = 8
 ACCUMULATE = 1
+ACCUMULATE_Q = 2
 NOALLOC_MAX_ELEMENTS = 1 << 28   # holo_dot_noalloc: capacity of its static partial-sum array
 
 STATUS = {0: "HOLO_OK", 1: "HOLO_ERR_ARG", 2: "HOLO_ERR_CUDA", 3: "HOLO_ERR_OOM",

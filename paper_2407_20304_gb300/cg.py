@@ -1,0 +1,106 @@
+"""Joint psi / q reconstruction by nonlinear conjugate gradients (Sec. 2, Eq. DaiYuan2).
+
+The driver runs on the host and issues only library calls: gradients (passes A-D), trial
+functionals for the line search (passes A-B), FP64 inner products for the Dai-Yuan
+coefficient, and the vector updates.  Reading of the paper's unspecified line search (the
+same reading as the FP64 oracle's driver): psi and q keep their own Dai-Yuan directions;
+after one shared gradient the psi step is found by halving a trial step until F decreases,
+then the q step the same way from the updated psi; a block whose trials never decrease F
+keeps step 0, so F never increases; a non-positive DY denominator restarts the block with
+-g; each block's next trial step is twice its last accepted one.
+
+Angles are processed in chunks of holo.chunk (the paper's independent angle chunks,
+Sec. 4); the loss and grad_q are summed over chunks with the library's accumulate flag.
+"""
+
+import torch
+
+
+class Reconstruction:
+    """State of a DY-CG reconstruction of psi [n_angles][n][n] and q [P][P] (CUDA, complex64)."""
+
+    def __init__(self, holo, psi, q, gamma0=1.0, max_halvings=20, update_q=True):
+        self.h = holo
+        self.psi = psi
+        self.q = q
+        self.gamma0 = gamma0
+        self.max_halvings = max_halvings
+        self.update_q = update_q
+        self.trial = [gamma0, gamma0]
+        self.g = None
+        self.eta = None
+        self.F = None
+        self.history = {"F": [], "gamma_psi": [], "gamma_q": [], "beta_psi": [], "beta_q": [],
+                        "F_after_psi": []}
+
+    # ------------------------------------------------------------------ evaluations
+    def _chunks(self):
+        K, c = self.h.n_angles, self.h.chunk
+        return [(k0, min(c, K - k0)) for k0 in range(0, K, c)]
+
+    def functional(self, psi, q=None):
+        """F2 at (psi, q); q = None keeps the probe last set (its propagations are reused)."""
+        if q is not None:
+            self.h.set_probe(q)
+        return sum(self.h.forward(psi[k0:k0 + nk], k0=k0) for k0, nk in self._chunks())
+
+    def gradient(self, psi, q, gpsi, gq):
+        self.h.set_probe(q)
+        loss = 0.0
+        for i, (k0, nk) in enumerate(self._chunks()):
+            loss, _, _ = self.h.gradient(psi[k0:k0 + nk], grad_psi=gpsi[k0:k0 + nk], grad_q=gq,
+                                         k0=k0, accumulate_q=i > 0, loss_in=loss)
+        return loss
+
+    # ------------------------------------------------------------------ iteration
+    def _backtrack(self, f, x, eta, gamma, F0, scratch):
+        for _ in range(self.max_halvings + 1):
+            scratch.copy_(x)
+            self.h.step(scratch, eta, gamma)
+            Fx = f(scratch)
+            if Fx < F0:
+                x.copy_(scratch)
+                return gamma, Fx
+            gamma *= 0.5
+        return 0.0, F0
+
+    def _direction(self, b, g_new):
+        g_old, eta = self.g[b], self.eta[b]
+        num = self.h.dot(g_new, g_new)
+        den = self.h.dot(g_new, eta) - self.h.dot(g_old, eta)
+        beta = num / den if den > 0 else 0.0
+        self.h.direction(eta, g_new, beta)
+        return beta
+
+    def run(self, iters):
+        """Run `iters` iterations; returns the history of F and the accepted steps."""
+        psi, q = self.psi, self.q
+        if self.g is None:
+            self.g = [torch.empty_like(psi), torch.empty_like(q)]
+            self.F = self.gradient(psi, q, self.g[0], self.g[1])
+            self.eta = [torch.zeros_like(psi), torch.zeros_like(q)]
+            for b in range(2):
+                self.h.direction(self.eta[b], self.g[b], 0.0)
+            self.history["F"].append(self.F)
+        scratch_psi, scratch_q = torch.empty_like(psi), torch.empty_like(q)
+        g_new = [torch.empty_like(psi), torch.empty_like(q)]
+        for _ in range(iters):
+            self.h.set_probe(q)
+            gam_psi, F = self._backtrack(lambda x: self.functional(x), psi, self.eta[0],
+                                         self.trial[0], self.F, scratch_psi)
+            self.history["F_after_psi"].append(F)
+            gam_q = 0.0
+            if self.update_q:
+                gam_q, F = self._backtrack(lambda x: self.functional(psi, x), q, self.eta[1],
+                                           self.trial[1], F, scratch_q)
+            if gam_psi > 0:
+                self.trial[0] = 2.0 * gam_psi
+            if gam_q > 0:
+                self.trial[1] = 2.0 * gam_q
+            self.F = self.gradient(psi, q, g_new[0], g_new[1])
+            betas = [self._direction(b, g_new[b]) for b in range(2)]
+            self.g, g_new = g_new, self.g
+            for key, val in (("F", self.F), ("gamma_psi", gam_psi), ("gamma_q", gam_q),
+                             ("beta_psi", betas[0]), ("beta_q", betas[1])):
+                self.history[key].append(val)
+        return self.history

@@ -436,7 +436,7 @@ holo_status run_eval(holo_ctx* c, PassArgs& a, bool gradient, float2* grad_q, un
   HOLO_LAUNCH(c, holo::launch_sum_residuals(c->rbuf, a.nk * c->J, n2, ref ? c->d_rref : nullptr,
                                             c->ext, (float)c->wref, c->d_T, c->stream));
   const int P = c->P, n = c->n, lo = P / 2 - n / 2;
-  const int acc = (flags & HOLO_ACCUMULATE) ? 1 : 0;
+  const int acc = (flags & (HOLO_ACCUMULATE | HOLO_ACCUMULATE_Q)) ? 1 : 0;
   holo_status st = dstep2d(c, c->d_T, lo, n, lo, n, grad_q, 0, P, 0, P, c->d_chirp_zeta0, 1, 2.f,
                            acc);
   if (st != HOLO_OK) return st;
@@ -464,7 +464,7 @@ holo_status read_loss(holo_ctx* c, double* loss, unsigned flags) {
                              c->stream));
   HOLO_CK(c, cudaStreamSynchronize(c->stream));
   const double l = c->h_red[0] + c->wref * c->h_red[1];
-  if (loss) *loss = (flags & HOLO_ACCUMULATE) ? *loss + l : l;
+  if (loss) *loss = (flags & (HOLO_ACCUMULATE | HOLO_ACCUMULATE_Q)) ? *loss + l : l;
   if (!std::isfinite(l)) return fail(c, HOLO_ERR_NUMERIC, "non-finite loss");
   return HOLO_OK;
 }

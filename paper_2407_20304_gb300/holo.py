@@ -152,8 +152,11 @@ class Holo:
         return loss.value
 
     def gradient(self, psi, grad_psi=None, grad_q=None, k0=0, accumulate=False, loss_in=0.0,
-                 want_loss=True):
-        """(F2, grad_psi, grad_q) over angles [k0, k0 + len(psi)) (Eq. gradpsi)."""
+                 want_loss=True, accumulate_q=False):
+        """(F2, grad_psi, grad_q) over angles [k0, k0 + len(psi)) (Eq. gradpsi).
+
+        accumulate: add to grad_psi, grad_q and loss_in; accumulate_q: add to grad_q and
+        loss_in only (the chunks of one problem own disjoint psi slices but share q)."""
         import torch
         nk = psi.shape[0]
         pp = _ptr(psi, torch.complex64, (nk, self.n, self.n), "psi")
@@ -165,8 +168,8 @@ class Holo:
         pq = _ptr(grad_q, torch.complex64, (self.P, self.P), "grad_q")
         loss = ctypes.c_double(loss_in)
         lp = ctypes.byref(loss) if want_loss else None
-        st = self.lib.holo_gradient(self.ctx, k0, nk, pp, lp, pg, pq,
-                                    _lib.ACCUMULATE if accumulate else 0)
+        flags = (_lib.ACCUMULATE if accumulate else 0) | (_lib.ACCUMULATE_Q if accumulate_q else 0)
+        st = self.lib.holo_gradient(self.ctx, k0, nk, pp, lp, pg, pq, flags)
         _check(self.lib, self.ctx, st, "holo_gradient")
         return (loss.value if want_loss else None), grad_psi, grad_q
 

@@ -1,0 +1,148 @@
+"""The autograd Function and the DY-CG driver, on the GPU through the C ABI.
+
+* HoloLoss gives the oracle's F2 and gradients (both modes: gradients kept from the
+  forward pass, or recomputed in backward).
+* At the differentiation workload's size (psi 1024^2 on 2048^2, 90 angles, 4 distances)
+  the gradients agree with central finite differences of the library's own F2
+  (step 1e-3 relative, 64 random directions).
+* The CG driver's iterates follow the FP64 oracle's driver (same line-search decisions,
+  F within FP32 rounding) and F never increases.
+"""
+
+import numpy as np
+import pytest
+
+import holo_synth as hs
+from oracle import cg as ocg
+from oracle import holo as oh
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+G = hs.WORKLOAD_GEOMETRY
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    import __graft_entry__
+    __graft_entry__.build()
+
+
+def small_problem(n=64, P=128, K=3, seed=2):
+    rng = hs.rng_for(hs.SEED_BASE + 9, seed)
+    geo = oh.Geometry(G["wavelength"], G["pixel"], G["Z"], G["z"], n, P)
+    w = hs.Workload("t", n, P, K, 4, "ellipses", n * 40.0 / 128, 0.0, K, seed)
+    psi_true = hs.object_stack(w, range(K), rng)
+    q_true = hs.striped_probe(P, n * 40.0 / 128, rng)
+    t = hs.sample_shifts(K, 4, rng).astype(np.float32).astype(np.float64)
+    sqrt_d = np.abs(oh.forward(psi_true, q_true, t, geo)).astype(np.float32)
+    sqrt_dref = np.abs(oh.reference_field(q_true, geo)).astype(np.float32)
+    psi0 = np.ones((K, n, n), np.complex64)
+    q0 = hs.perturbed_probe(q_true, rng).astype(np.complex64)
+    return geo, t, sqrt_d, sqrt_dref, psi0, q0
+
+
+def make_holo(geo, K, t, sqrt_d, sqrt_dref, chunk=0):
+    from paper_2407_20304_gb300 import Holo
+    h = Holo(geo.n, K, 4, geo.wavelength, geo.pixel, geo.Z, geo.z, pad=geo.P, chunk=chunk)
+    h.set_shifts(t.astype(np.float32))
+    h.set_data(torch.from_numpy(sqrt_d).cuda(), torch.from_numpy(sqrt_dref).cuda())
+    return h
+
+
+def rel(a, b):
+    return float(np.linalg.norm(a - b) / np.linalg.norm(b))
+
+
+@pytest.mark.parametrize("recompute", [False, True])
+def test_autograd_function_matches_oracle(recompute):
+    from paper_2407_20304_gb300.autograd import holo_loss
+    geo, t, sqrt_d, sqrt_dref, psi0, q0 = small_problem()
+    h = make_holo(geo, 3, t, sqrt_d, sqrt_dref)
+    psi = torch.from_numpy(psi0).cuda().requires_grad_(True)
+    q = torch.from_numpy(q0).cuda().requires_grad_(True)
+    loss = holo_loss(psi, q, h, recompute=recompute)
+    (3.0 * loss).backward()
+    F, gp, gq = oh.gradients(psi0.astype(np.complex128), q0.astype(np.complex128), t,
+                             sqrt_d.astype(np.float64), sqrt_dref.astype(np.float64), geo)
+    assert abs(loss.item() - F) / F < 1e-5
+    assert rel(psi.grad.cpu().numpy() / 3.0, gp) < 1e-4
+    assert rel(q.grad.cpu().numpy() / 3.0, gq) < 1e-4
+
+
+def test_autograd_finite_differences_at_differentiation_size():
+    from paper_2407_20304_gb300.autograd import holo_loss
+    w = hs.workloads()["autograd"]
+    n, P, K, J = w.n, w.P, w.n_angles, w.n_dist
+    rng = hs.rng_for(w.seed, 0)
+    t = hs.sample_shifts(K, J, rng).astype(np.float32)
+    # positive amplitudes with the workload's count statistics (no method arithmetic)
+    base = np.abs(hs.striped_probe(n, w.probe_sigma, rng)).astype(np.float32) + 0.2
+    sqrt_d = np.ascontiguousarray(np.broadcast_to(base, (K, J, n, n)))
+    sqrt_d = hs.poisson_amplitude(sqrt_d.astype(np.float64) ** 2, w.counts, rng).astype(np.float32)
+    sqrt_dref = base
+    geo = oh.Geometry(G["wavelength"], G["pixel"], G["Z"], G["z"], n, P)
+    h = make_holo(geo, K, t, sqrt_d, sqrt_dref)
+    psi = torch.from_numpy(hs.object_stack(w, range(K), rng).astype(np.complex64)).cuda()
+    q = torch.from_numpy(hs.striped_probe(P, w.probe_sigma, rng).astype(np.complex64)).cuda()
+    psi.requires_grad_(True)
+    q.requires_grad_(True)
+    loss = holo_loss(psi, q, h)
+    loss.backward()
+    gp, gq = psi.grad.detach(), q.grad.detach()
+    gen = torch.Generator(device="cuda").manual_seed(5)
+    errs = []
+    with torch.no_grad():
+        for _ in range(64):
+            hp = torch.randn(psi.shape, dtype=torch.complex64, device="cuda", generator=gen)
+            hq = torch.randn(q.shape, dtype=torch.complex64, device="cuda", generator=gen)
+            hp *= psi.norm() / hp.norm()
+            hq *= q.norm() / hq.norm()
+            eps = 1e-3
+            fp = holo_loss(psi + eps * hp, q + eps * hq, h).item()
+            fm = holo_loss(psi - eps * hp, q - eps * hq, h).item()
+            fd = (fp - fm) / (2 * eps)
+            an = float((torch.real(torch.vdot(gp.flatten(), hp.flatten()))
+                        + torch.real(torch.vdot(gq.flatten(), hq.flatten()))).item())
+            errs.append(abs(fd - an) / max(abs(an), 1e-30))
+    print(f"\nFD relative errors: median {np.median(errs):.2e}, max {np.max(errs):.2e}")
+    assert np.median(errs) < 2e-3 and np.max(errs) < 2e-2
+
+
+def test_cg_driver_follows_the_oracle_driver():
+    """Same decisions as the FP64 driver until one falls within FP32 rounding of a tie;
+    F never increases.  Where the two drivers first choose different steps, the FP64
+    driver's accepted step must have changed F by less than FP32 can resolve."""
+    from paper_2407_20304_gb300.cg import Reconstruction
+    geo, t, sqrt_d, sqrt_dref, psi0, q0 = small_problem(K=4, seed=4)
+    h = make_holo(geo, 4, t, sqrt_d, sqrt_dref, chunk=3)
+    rec = Reconstruction(h, torch.from_numpy(psi0).cuda(), torch.from_numpy(q0).cuda())
+    iters = 4
+    hist = rec.run(iters)
+    ref = ocg.reconstruct(psi0.astype(np.complex128), q0.astype(np.complex128), t,
+                          sqrt_d.astype(np.float64), sqrt_dref.astype(np.float64), geo, iters=iters)
+    F = np.array(hist["F"])
+    Fo = np.array(ref["hist"]["F"])
+    print("\nF gpu", F, "\nF oracle", Fo, "\ngamma psi", hist["gamma_psi"],
+          ref["hist"]["gamma_psi"], "\ngamma q", hist["gamma_q"], ref["hist"]["gamma_q"])
+    assert np.all(np.diff(F) <= 0)
+    assert abs(F[0] - Fo[0]) / Fo[0] < 1e-5
+    same = 0
+    while (same < iters and hist["gamma_psi"][same] == ref["hist"]["gamma_psi"][same]
+           and hist["gamma_q"][same] == ref["hist"]["gamma_q"][same]):
+        same += 1
+    assert same >= 1
+    np.testing.assert_allclose(F[:same + 1], Fo[:same + 1], rtol=1e-4)
+    if same < iters:
+        # first differing decision: a near-tie for the block whose step differs
+        # (whichever driver accepted the contested trial step saw F barely change)
+        start = Fo[same]
+        if hist["gamma_psi"][same] != ref["hist"]["gamma_psi"][same]:
+            change = min(abs(start - ref["hist"]["F_after_psi"][same]),
+                         abs(start - hist["F_after_psi"][same])) / start
+        else:
+            change = min(abs(ref["hist"]["F_after_psi"][same] - Fo[same + 1]),
+                         abs(hist["F_after_psi"][same] - F[same + 1])) / start
+        print("first different step at iteration", same, "relative change", change)
+        assert change < 1e-4

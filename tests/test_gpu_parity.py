@@ -125,13 +125,13 @@ def test_chunks_accumulate_to_full_gradient():
     pr = make_problem(64, 128, 5, seed=11)
     h = make_holo(pr, chunk=2)
     psi = dev(pr["psi"], torch.complex64)
-    gp = torch.zeros_like(psi)
-    gq = torch.zeros((128, 128), dtype=torch.complex64, device="cuda")
+    gp = torch.full_like(psi, float("nan"))     # every slice must be overwritten
+    gq = torch.full((128, 128), float("nan"), dtype=torch.complex64, device="cuda")
     loss = 0.0
     for k0 in range(0, 5, 2):
         nk = min(2, 5 - k0)
         loss, _, _ = h.gradient(psi[k0:k0 + nk], grad_psi=gp[k0:k0 + nk], grad_q=gq, k0=k0,
-                                accumulate=True, loss_in=loss)
+                                accumulate_q=k0 > 0, loss_in=loss)
     F, gp_ref, gq_ref = oh.gradients(pr["psi"], pr["q"], pr["t"], pr["sqrt_d"], pr["sqrt_dref"],
                                      pr["geo"])
     assert abs(loss - F) / F < LOSS_TOL
