@@ -49,7 +49,7 @@ def parse():
     ap.add_argument("--steps", type=int, default=30)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
-    ap.add_argument("--workload", default="large", choices=("large", "autograd", "medium"))
+    ap.add_argument("--workload", default="large", choices=("large", "autograd", "medium", "batch"))
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-unfused", action="store_true")
@@ -592,8 +592,96 @@ def run_reference(args, w):
                     "d2h_bytes_per_step": 0}}
 
 
+# ---------------------------------------------------------------- batch of reconstructions
+
+def batch_specs(seed, count=64, budget_gb=160.0):
+    """Seeded uneven batch: side n in {256, 384, 512, 1024, 2048}, 1-4 distances, 16-128
+    angles, P the next power of two >= 2n, 16-angle chunks.  Instances are dropped from the
+    largest down if the planned device memory exceeds the budget."""
+    rng = hs.rng_for(seed, 77)
+    specs = []
+    for i in range(count):
+        n = int(rng.choice([256, 384, 512, 1024, 2048]))
+        J = int(rng.integers(1, 5))
+        K = int(rng.integers(16, 129))
+        P = 16
+        while P < 2 * n:
+            P *= 2
+        chunk = min(K, 16)
+        mem = (2 * K * n * n * 8 + K * J * n * n * 4 + 4 * P * P * 8 + J * P * P * 8
+               + chunk * J * 3 * (n + 16) ** 2 * 8 + K * J * (2 * (n + 16) * 8 + 2 * n * 16))
+        specs.append({"n": n, "P": P, "J": J, "K": K, "chunk": chunk, "mem": mem, "seed": i})
+    kept = sorted(specs, key=lambda d: d["mem"])
+    while sum(d["mem"] for d in kept) > budget_gb * 1e9:
+        kept.pop()
+    ids = {d["seed"] for d in kept}
+    return [d for d in specs if d["seed"] in ids], len(specs) - len(kept)
+
+
+def run_batch(args):
+    import torch
+    from paper_2407_20304_gb300 import Holo
+    from paper_2407_20304_gb300.batch import HoloBatch, Instance
+    import __graft_entry__
+    __graft_entry__.build()
+    g = hs.WORKLOAD_GEOMETRY
+    specs, dropped = batch_specs(hs.SEED_BASE + 3000)
+    insts = []
+    for sp in specs:
+        n, P, J, K, chunk = sp["n"], sp["P"], sp["J"], sp["K"], sp["chunk"]
+        rng = hs.rng_for(hs.SEED_BASE + 3000, 1000 + sp["seed"])
+        psi_true = torch.from_numpy(hs.transmittance(hs.ellipse_phase(n, rng)).astype(np.complex64)).cuda()
+        q_true = torch.from_numpy(hs.striped_probe(P, 40.0 * n / 128, rng).astype(np.complex64)).cuda()
+        t = hs.sample_shifts(K, J, rng).astype(np.float32)
+        h = Holo(n, K, J, g["wavelength"], g["pixel"], g["Z"], g["z"][:J], pad=P, chunk=chunk)
+        h.set_shifts(t)
+        sqrt_d = torch.empty((K, J, n, n), dtype=torch.float32, device="cuda")
+        ones_ref = torch.ones((n, n), dtype=torch.float32, device="cuda")
+        h.set_data(sqrt_d, ones_ref)
+        h.set_probe(q_true)
+        gen = torch.Generator(device="cuda").manual_seed(sp["seed"])
+        for k0 in range(0, K, chunk):
+            nk = min(chunk, K - k0)
+            u = torch.empty((nk, J, n, n), dtype=torch.complex64, device="cuda")
+            h.forward(psi_true.expand(nk, n, n).contiguous(), k0=k0, u_out=u)
+            inten = u.abs().square_()
+            c = 1e4 / inten.mean()
+            sqrt_d[k0:k0 + nk] = torch.poisson(inten * c, generator=gen).div_(c).sqrt_()
+            del u, inten
+        lo = P // 2 - n // 2
+        _, zeta = derived(g["z"][:J], g["Z"])
+        bref = h.propagate(q_true, zeta[0])[lo:lo + n, lo:lo + n]
+        sqrt_dref = bref.abs().contiguous()
+        h.set_data(sqrt_d, sqrt_dref)
+        inst = Instance(h, torch.ones((K, n, n), dtype=torch.complex64, device="cuda"),
+                        q_true.clone())
+        inst.data = (sqrt_d, sqrt_dref)
+        insts.append(inst)
+    b = HoloBatch(insts)
+    loop_ms = b.time_loop(reps=2)
+    best_ms, sched, cost = b.autotune(candidates=(1, 2, 4, 8), reps=2)
+    torch.cuda.synchronize()
+    planes = b.planes
+    return {
+        "metric": "plane-gradient evals/s, batch of uneven reconstructions", "unit": UNIT,
+        "value": round(planes / (best_ms / 1e3), 1), "n_gpus": 1, "ms_per_step": round(best_ms, 3),
+        "higher_is_better": True, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": f"batch: {len(insts)} instances (sides 256-2048, pad next pow2 >= "
+                               f"2n, 1-4 distances, 16-128 angles, 16-angle chunks)"
+                               + (f", {dropped} largest dropped for the memory budget" if dropped else ""),
+                   "planes_per_step": planes,
+                   "sizes": sorted({s["n"] for s in specs})},
+        "loop": {"value": round(planes / (loop_ms / 1e3), 1), "ms_per_step": round(loop_ms, 3)},
+        "graph": {"branches": len(sched), "ms_per_step": round(best_ms, 3),
+                  "tuning": {str(k): round(v["ms"], 3) for k, v in b.tuning.items()}},
+    }
+
+
 def main():
     args = parse()
+    if args.workload == "batch":
+        print(json.dumps(run_batch(args)), flush=True)
+        return
     w = hs.workloads()[args.workload]
     if args.chunk:
         import dataclasses

@@ -203,6 +203,18 @@ holo_status holo_get_timing(holo_ctx* ctx, double* ms, long long* launches);
 holo_status holo_dot_noalloc(const void* a, const void* b, long long n_c64, double* re_out,
                              void* stream);
 
+/* Issue the context's later work on `stream` (a cudaStream_t, NULL for the legacy
+ * default stream), e.g. to place independent reconstructions on different branches of a
+ * captured CUDA graph.  The caller orders it against work already issued. */
+holo_status holo_set_stream(holo_ctx* ctx, void* stream);
+
+/* F2 accumulated on the device: the loss of the last forward / gradient evaluation
+ * (including the reference term when it had k0 == 0), plus the earlier ones since the
+ * last evaluation issued without HOLO_ACCUMULATE / HOLO_ACCUMULATE_Q.  Read after
+ * synchronising the stream; for evaluations issued without a host loss pointer, e.g.
+ * inside a captured CUDA graph. */
+holo_status holo_read_loss(holo_ctx* ctx, double* loss);
+
 /* Bytes of device workspace currently held by the context. */
 holo_status holo_workspace_bytes(const holo_ctx* ctx, long long* bytes);
 

@@ -1,0 +1,150 @@
+"""Many independent reconstructions of uneven sizes evaluated by one CUDA-graph launch.
+
+Each instance is its own problem (geometry, angles, distances, data, psi, q) with its own
+library context; one evaluation of an instance is the probe propagation and the gradient
+of F2 over all its angles (in chunks of the context's chunk size, the chunks summing
+grad_q and the loss on the device).  `HoloBatch` issues the evaluations of all instances
+either as a plain loop of launches on one stream, or captured once into a CUDA graph whose
+branches run independent instances concurrently; replaying the graph evaluates the whole
+batch with one launch from the host.
+
+The schedule (how many concurrent branches, which instances on which branch) is chosen by
+`autotune`: it measures each instance's evaluation time alone, balances the branches
+longest-first for each candidate branch count, times one replay of each candidate graph,
+and keeps the fastest.  Results do not depend on the schedule (every kernel is
+deterministic and instances share no buffers).
+"""
+
+import time
+
+import torch
+
+
+class Instance:
+    """One reconstruction problem bound to a `Holo` context."""
+
+    def __init__(self, holo, psi, q):
+        self.h = holo
+        self.psi = psi
+        self.q = q
+        self.grad_psi = torch.empty_like(psi)
+        self.grad_q = torch.empty_like(q)
+
+    def chunks(self):
+        K, c = self.h.n_angles, self.h.chunk
+        return [(k0, min(c, K - k0)) for k0 in range(0, K, c)]
+
+    def issue(self):
+        """Issue one evaluation on the context's stream (no host synchronisation)."""
+        self.h.set_probe(self.q)
+        for i, (k0, nk) in enumerate(self.chunks()):
+            self.h.gradient(self.psi[k0:k0 + nk], grad_psi=self.grad_psi[k0:k0 + nk],
+                            grad_q=self.grad_q, k0=k0, want_loss=False, accumulate_q=i > 0)
+
+    @property
+    def planes(self):
+        return self.h.n_angles * self.h.n_dist
+
+
+class HoloBatch:
+    def __init__(self, instances):
+        self.inst = list(instances)
+        self.main = torch.cuda.Stream()
+        self.side = []
+        self.graph = None
+        self.schedule = None
+        self.tuning = {}
+
+    @property
+    def planes(self):
+        return sum(i.planes for i in self.inst)
+
+    # ------------------------------------------------------------------ loop
+    def run_loop(self):
+        """The per-instance launch loop on one stream."""
+        for it in self.inst:
+            it.h.set_stream(self.main)
+            it.issue()
+
+    def losses(self):
+        return [it.h.read_loss() for it in self.inst]
+
+    # ------------------------------------------------------------------ graph
+    def _streams(self, nb):
+        while len(self.side) < nb:
+            self.side.append(torch.cuda.Stream())
+        return self.side[:nb]
+
+    def balanced(self, branches, cost):
+        """Longest-processing-time-first assignment of instances to `branches` branches."""
+        order = sorted(range(len(self.inst)), key=lambda i: -cost[i])
+        load = [0.0] * branches
+        groups = [[] for _ in range(branches)]
+        for i in order:
+            b = min(range(branches), key=lambda x: load[x])
+            groups[b].append(i)
+            load[b] += cost[i]
+        return [g for g in groups if g]
+
+    def capture(self, schedule):
+        """Capture one evaluation of every instance, branch b of `schedule` on its own stream."""
+        streams = self._streams(len(schedule))
+        torch.cuda.synchronize()
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g, stream=self.main):
+            cur = torch.cuda.current_stream()
+            for s, members in zip(streams, schedule):
+                s.wait_stream(cur)
+                for i in members:
+                    self.inst[i].h.set_stream(s)
+                    self.inst[i].issue()
+            for s in streams:
+                cur.wait_stream(s)
+        self.graph = g
+        self.schedule = schedule
+        return g
+
+    def replay(self):
+        self.graph.replay()
+
+    # ------------------------------------------------------------------ timing / tuning
+    def _time(self, fn, reps):
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(self.main)
+        for _ in range(reps):
+            fn()
+        e1.record(self.main)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / reps
+
+    def instance_costs(self):
+        """Device time (ms) of one evaluation of each instance alone."""
+        costs = []
+        for it in self.inst:
+            it.h.set_stream(self.main)
+            it.issue()                      # warm-up
+            costs.append(self._time(it.issue, 1))
+        return costs
+
+    def time_loop(self, reps=2):
+        self.run_loop()
+        return self._time(self.run_loop, reps)
+
+    def autotune(self, candidates=(1, 2, 4, 8), reps=2):
+        """Pick the branch count whose captured graph evaluates the batch fastest."""
+        cost = self.instance_costs()
+        best = None
+        for nb in candidates:
+            nb = min(nb, len(self.inst))
+            sched = self.balanced(nb, cost)
+            t0 = time.perf_counter()
+            self.capture(sched)
+            cap_s = time.perf_counter() - t0
+            self.replay()
+            ms = self._time(self.replay, reps)
+            self.tuning[nb] = {"ms": ms, "capture_s": cap_s}
+            if best is None or ms < best[0]:
+                best = (ms, sched)
+        self.capture(best[1])
+        return best[0], best[1], cost

@@ -420,6 +420,9 @@ holo_status run_eval(holo_ctx* c, PassArgs& a, bool gradient, float2* grad_q, un
   } else {
     HOLO_CK(c, cudaMemsetAsync(c->d_red + 1, 0, sizeof(double), c->stream));
   }
+  HOLO_LAUNCH(c, holo::launch_loss_total(c->d_red, c->wref,
+                                         (flags & (HOLO_ACCUMULATE | HOLO_ACCUMULATE_Q)) ? 1 : 0,
+                                         c->stream));
   }
   if (!gradient) return HOLO_OK;
   {
@@ -854,6 +857,22 @@ holo_status holo_direction(holo_ctx* c, void* eta, const void* g, double beta, l
   if (!c || !eta || !g || n < 0 || !std::isfinite(beta)) return fail(c, HOLO_ERR_ARG, "bad argument");
   PassTimer tm(c, HOLO_T_VECTOR);
   HOLO_LAUNCH(c, holo::launch_direction((float2*)eta, (const float2*)g, (float)beta, n, c->stream));
+  return HOLO_OK;
+}
+
+holo_status holo_set_stream(holo_ctx* c, void* stream) {
+  if (!c) return HOLO_ERR_ARG;
+  c->stream = (cudaStream_t)stream;
+  return HOLO_OK;
+}
+
+holo_status holo_read_loss(holo_ctx* c, double* loss) {
+  if (!c || !loss) return fail(c, HOLO_ERR_ARG, "null argument");
+  HOLO_CK(c, cudaMemcpyAsync(c->h_red + 3, c->d_red + 3, sizeof(double), cudaMemcpyDeviceToHost,
+                             c->stream));
+  HOLO_CK(c, cudaStreamSynchronize(c->stream));
+  *loss = c->h_red[3];
+  if (!std::isfinite(*loss)) return fail(c, HOLO_ERR_NUMERIC, "non-finite loss");
   return HOLO_OK;
 }
 

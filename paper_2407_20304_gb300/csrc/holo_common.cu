@@ -105,6 +105,11 @@ __global__ void k_sum_f64(const double* __restrict__ part, int count, double* ou
   if (threadIdx.x == 0) *out = accumulate ? *out + s : s;
 }
 
+// Running loss of the context: red[3] = (acc ? red[3] : 0) + red[0] + wref red[1].
+__global__ void k_loss_total(double* red, double wref, int acc) {
+  if (threadIdx.x == 0 && blockIdx.x == 0) red[3] = (acc ? red[3] : 0.0) + red[0] + wref * red[1];
+}
+
 // Re <a, b> = Re sum conj(a) b: FP32 products summed in FP32 over at most 16 elements per
 // thread-iteration, then FP64.
 __global__ void k_dot(const float2* __restrict__ a, const float2* __restrict__ b, long long n,
@@ -197,6 +202,11 @@ cudaError_t launch_ref_residual(const float2* bref, const float* sqrt_dref, long
 cudaError_t launch_sum_f64(const double* part, int count, double* out, int accumulate,
                            cudaStream_t s) {
   k_sum_f64<<<1, 1024, 0, s>>>(part, count, out, accumulate);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_loss_total(double* red, double wref, int acc, cudaStream_t s) {
+  k_loss_total<<<1, 32, 0, s>>>(red, wref, acc);
   return cudaGetLastError();
 }
 

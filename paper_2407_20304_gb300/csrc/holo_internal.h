@@ -111,6 +111,7 @@ cudaError_t launch_ref_residual(const float2* bref, const float* sqrt_dref, long
                                 float2* rref, double* part, int nblocks, cudaStream_t s);
 cudaError_t launch_sum_f64(const double* part, int count, double* out, int accumulate,
                            cudaStream_t s);
+cudaError_t launch_loss_total(double* red, double wref, int acc, cudaStream_t s);
 cudaError_t launch_dot(const float2* a, const float2* b, long long n, double* part, int nblocks,
                        cudaStream_t s);
 cudaError_t launch_axpy(float2* x, const float2* eta, float gamma, long long n, cudaStream_t s);

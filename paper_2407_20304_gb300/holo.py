@@ -238,6 +238,19 @@ class Holo:
                                      _ptr(g, torch.complex64, None, "g"), float(beta), eta.numel())
         _check(self.lib, self.ctx, st, "holo_direction")
 
+    def set_stream(self, stream):
+        """Issue later work on `stream` (a torch.cuda.Stream)."""
+        _check(self.lib, self.ctx, self.lib.holo_set_stream(self.ctx, ctypes.c_void_p(stream.cuda_stream)),
+               "holo_set_stream")
+        self.stream = stream
+
+    def read_loss(self):
+        """F2 of the last evaluation (synchronises the context's stream)."""
+        out = ctypes.c_double(0.0)
+        _check(self.lib, self.ctx, self.lib.holo_read_loss(self.ctx, ctypes.byref(out)),
+               "holo_read_loss")
+        return out.value
+
     def set_timing(self, enable=True):
         """Start (and clear) or stop per-pass CUDA-event timing on the context's stream."""
         _check(self.lib, self.ctx, self.lib.holo_set_timing(self.ctx, 1 if enable else 0),

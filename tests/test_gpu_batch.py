@@ -1,0 +1,89 @@
+"""Batched evaluation of uneven reconstructions: the captured graph (any schedule) gives
+exactly the per-instance loop's results, and those match the FP64 oracle."""
+
+import numpy as np
+import pytest
+
+import holo_synth as hs
+from oracle import holo as oh
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+G = hs.WORKLOAD_GEOMETRY
+
+
+def pad_of(n):
+    P = 16
+    while P < 2 * n:
+        P *= 2
+    return P
+
+
+@pytest.fixture(scope="module")
+def batch():
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2407_20304_gb300 import Holo
+    from paper_2407_20304_gb300.batch import HoloBatch, Instance
+    rng = hs.rng_for(hs.SEED_BASE + 3000, 0)
+    specs = [(32, 3, 2), (48, 2, 4), (64, 5, 1), (32, 4, 3), (48, 3, 2), (64, 2, 4)]
+    insts, refs = [], []
+    for i, (n, K, J) in enumerate(specs):
+        P = pad_of(n)
+        z = tuple(G["z"][:J])
+        geo = oh.Geometry(G["wavelength"], G["pixel"], G["Z"], z, n, P)
+        w = hs.Workload("b", n, P, K, J, "ellipses", n / 3, 0.0, K, i)
+        psi_true = hs.object_stack(w, range(K), rng)
+        q_true = hs.striped_probe(P, n / 3, rng)
+        t = hs.sample_shifts(K, J, rng).astype(np.float32).astype(np.float64)
+        sqrt_d = np.abs(oh.forward(psi_true, q_true, t, geo)).astype(np.float32)
+        sqrt_dref = np.abs(oh.reference_field(q_true, geo)).astype(np.float32)
+        psi0 = np.ones((K, n, n), np.complex64)
+        q0 = hs.perturbed_probe(q_true, rng).astype(np.complex64)
+        h = Holo(n, K, J, G["wavelength"], G["pixel"], G["Z"], z, pad=P, chunk=2)
+        h.set_shifts(t.astype(np.float32))
+        d, dr = torch.from_numpy(sqrt_d).cuda(), torch.from_numpy(sqrt_dref).cuda()
+        h.set_data(d, dr)
+        insts.append(Instance(h, torch.from_numpy(psi0).cuda(), torch.from_numpy(q0).cuda()))
+        refs.append(oh.gradients(psi0.astype(np.complex128), q0.astype(np.complex128), t,
+                                 sqrt_d.astype(np.float64), sqrt_dref.astype(np.float64), geo))
+    return HoloBatch(insts), refs
+
+
+def test_loop_matches_oracle(batch):
+    b, refs = batch
+    b.run_loop()
+    torch.cuda.synchronize()
+    for it, (F, gp, gq) in zip(b.inst, refs):
+        assert abs(it.h.read_loss() - F) / F < 1e-5
+        e_p = np.linalg.norm(it.grad_psi.cpu().numpy() - gp) / np.linalg.norm(gp)
+        e_q = np.linalg.norm(it.grad_q.cpu().numpy() - gq) / np.linalg.norm(gq)
+        assert e_p < 1e-4 and e_q < 1e-4
+
+
+@pytest.mark.parametrize("branches", [1, 3])
+def test_graph_replay_equals_loop(batch, branches):
+    b, _ = batch
+    b.run_loop()
+    torch.cuda.synchronize()
+    ref = [(it.h.read_loss(), it.grad_psi.clone(), it.grad_q.clone()) for it in b.inst]
+    for it in b.inst:
+        it.grad_psi.zero_()
+        it.grad_q.zero_()
+    cost = [float(it.planes) for it in b.inst]
+    b.capture(b.balanced(branches, cost))
+    b.replay()
+    b.replay()
+    torch.cuda.synchronize()
+    for it, (F, gp, gq) in zip(b.inst, ref):
+        assert it.h.read_loss() == F
+        assert torch.equal(it.grad_psi, gp) and torch.equal(it.grad_q, gq)
+
+
+def test_autotune_picks_a_schedule(batch):
+    b, _ = batch
+    ms, sched, cost = b.autotune(candidates=(1, 2, 4), reps=1)
+    assert sorted(i for g in sched for i in g) == list(range(len(b.inst)))
+    assert ms > 0 and len(b.tuning) >= 2
