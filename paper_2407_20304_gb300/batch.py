@@ -105,7 +105,9 @@ class HoloBatch:
         return g
 
     def replay(self):
-        self.graph.replay()
+        """Launch the captured graph on the batch's stream."""
+        with torch.cuda.stream(self.main):
+            self.graph.replay()
 
     # ------------------------------------------------------------------ timing / tuning
     def _time(self, fn, reps):
