@@ -83,7 +83,6 @@ struct holo_ctx {
   // per-plane workspace
   float2* ybuf = nullptr;
   long long ystride = 0;
-  float2* rbuf = nullptr;
   float2* gkbuf = nullptr;
   long long gkstride = 0;
   size_t ws_bytes_planes = 0;
@@ -373,7 +372,9 @@ PassArgs pass_args(holo_ctx* c, int k0, int nk, const void* psi) {
   a.chirp_zhat = c->d_chirp_zhat;
   a.ybuf = c->ybuf;
   a.ystride = c->ystride;
-  a.rbuf = c->rbuf;
+  a.tq = c->d_T;
+  a.rref = nullptr;
+  a.wref = (float)c->wref;
   a.gkbuf = c->gkbuf;
   a.gkstride = c->gkstride;
   a.loss_part = c->d_part;
@@ -390,7 +391,7 @@ PassArgs pass_args(holo_ctx* c, int k0, int nk, const void* psi) {
   a.rowstart = c->d_rowstart;
   a.line0 = c->rowstart[(size_t)k0 * c->J];
   a.nlines = c->rowstart[(size_t)(k0 + nk) * c->J] - a.line0;
-  a.pass_b_items = nk * c->J * c->ops->pass_b_groups(c->n);
+  a.pass_b_items = c->ops->pass_b_groups(c->n);
   return a;
 }
 
@@ -399,6 +400,21 @@ PassArgs pass_args(holo_ctx* c, int k0, int nk, const void* psi) {
 holo_status run_eval(holo_ctx* c, PassArgs& a, bool gradient, float2* grad_q, unsigned flags) {
   const int nbx = c->ops->pass_b_blocks(a.pass_b_items, c->n, a.max_box_rows);
   const long long nparts = nbx;
+  const bool ref = a.k0 == 0 && c->wref != 0.0;
+  const long long n2 = (long long)c->n * c->n;
+  {
+    PassTimer tm_red(c, HOLO_T_REDUCE);
+    if (ref) {
+      // reference residual first: pass B folds w_ref r_ref into the grad_q source
+      HOLO_LAUNCH(c, holo::launch_ref_residual(c->d_b, c->sqrt_dref, n2, c->d_rref,
+                                               c->d_part + nparts, kRefBlocks, c->stream));
+      HOLO_LAUNCH(c, holo::launch_sum_f64(c->d_part + nparts, kRefBlocks, c->d_red + 1, 0,
+                                          c->stream));
+      a.rref = c->d_rref;
+    } else {
+      HOLO_CK(c, cudaMemsetAsync(c->d_red + 1, 0, sizeof(double), c->stream));
+    }
+  }
   {
     PassTimer tm(c, HOLO_T_PASS_A);
     HOLO_LAUNCH(c, c->ops->pass_a(a, c->stream));
@@ -407,22 +423,12 @@ holo_status run_eval(holo_ctx* c, PassArgs& a, bool gradient, float2* grad_q, un
     PassTimer tm(c, HOLO_T_PASS_B);
     HOLO_LAUNCH(c, c->ops->pass_b(a, gradient ? 1 : 0, nbx, c->stream));
   }
-  const bool ref = a.k0 == 0 && c->wref != 0.0;
-  const long long n2 = (long long)c->n * c->n;
   {
-  PassTimer tm_red(c, HOLO_T_REDUCE);
-  HOLO_LAUNCH(c, holo::launch_sum_f64(c->d_part, (int)nparts, c->d_red, 0, c->stream));
-  if (ref) {
-    HOLO_LAUNCH(c, holo::launch_ref_residual(c->d_b, c->sqrt_dref, n2, c->d_rref,
-                                             c->d_part + nparts, kRefBlocks, c->stream));
-    HOLO_LAUNCH(c, holo::launch_sum_f64(c->d_part + nparts, kRefBlocks, c->d_red + 1, 0,
-                                        c->stream));
-  } else {
-    HOLO_CK(c, cudaMemsetAsync(c->d_red + 1, 0, sizeof(double), c->stream));
-  }
-  HOLO_LAUNCH(c, holo::launch_loss_total(c->d_red, c->wref,
-                                         (flags & (HOLO_ACCUMULATE | HOLO_ACCUMULATE_Q)) ? 1 : 0,
-                                         c->stream));
+    PassTimer tm_red(c, HOLO_T_REDUCE);
+    HOLO_LAUNCH(c, holo::launch_sum_f64(c->d_part, (int)nparts, c->d_red, 0, c->stream));
+    HOLO_LAUNCH(c, holo::launch_loss_total(c->d_red, c->wref,
+                                           (flags & (HOLO_ACCUMULATE | HOLO_ACCUMULATE_Q)) ? 1 : 0,
+                                           c->stream));
   }
   if (!gradient) return HOLO_OK;
   {
@@ -434,10 +440,9 @@ holo_status run_eval(holo_ctx* c, PassArgs& a, bool gradient, float2* grad_q, un
     HOLO_LAUNCH(c, holo::launch_pass_d(a, c->stream));
   }
   PassTimer tm_q(c, HOLO_T_QGRAD);
-  // grad_q = 2 [ D_{-zeta_0}( C* (ext sum_kj r_kj + w_ref r_ref) ) + sum_j D_{-omega_j}(G'_j) ]
-  // (zhat_j + omega_j = zeta_0 merges the ext-part of every plane into one propagation).
-  HOLO_LAUNCH(c, holo::launch_sum_residuals(c->rbuf, a.nk * c->J, n2, ref ? c->d_rref : nullptr,
-                                            c->ext, (float)c->wref, c->d_T, c->stream));
+  // grad_q = 2 [ D_{-zeta_0}( C* T ) + sum_j D_{-omega_j}(G'_j) ] with T = ext sum_kj r_kj +
+  // w_ref r_ref written by pass B (zhat_j + omega_j = zeta_0 merges the ext-part of every
+  // plane into one propagation).
   const int P = c->P, n = c->n, lo = P / 2 - n / 2;
   const int acc = (flags & (HOLO_ACCUMULATE | HOLO_ACCUMULATE_Q)) ? 1 : 0;
   holo_status st = dstep2d(c, c->d_T, lo, n, lo, n, grad_q, 0, P, 0, P, c->d_chirp_zeta0, 1, 2.f,
@@ -609,7 +614,7 @@ holo_status holo_destroy(holo_ctx* c) {
   if (c->stream) cudaStreamSynchronize(c->stream);
   void* ptrs[] = {c->d_tw,    c->d_chirp_zhat, c->d_chirp_omega, c->d_chirp_zeta0,
                   c->d_chirp_tmp, c->d_planes, c->d_pj,          c->d_b,
-                  c->ybuf,    c->rbuf,         c->gkbuf,         c->d_scratch,
+                  c->ybuf,    c->gkbuf,        c->d_scratch,
                   c->d_Gp,    c->d_T,          c->d_rref,        c->d_part,
                   c->d_red,   c->s_psi,        c->s_gpsi,        c->s_data,
                   c->s_q,     c->s_gq,         c->d_xtap,        c->d_ytap,
@@ -691,18 +696,15 @@ holo_status holo_set_shifts(holo_ctx* c, const float* t) {
   const long long ystride = (long long)maxbys * n, gkstride = (long long)maxbys * maxbxs;
   const long long np = (long long)c->chunk * J;
   const size_t ybytes = sizeof(float2) * (size_t)(np * ystride);
-  const size_t rbytes = sizeof(float2) * (size_t)(np * n * n);
   const size_t gbytes = sizeof(float2) * (size_t)(np * gkstride);
   const long long parts = (long long)c->ops->pass_b_blocks(1 << 30, n, maxbys) + kRefBlocks + 1024;
   if (ystride > c->ystride || gkstride > c->gkstride || !c->ybuf) {
     dfree(c, c->ybuf, sizeof(float2) * (size_t)(np * c->ystride));
-    dfree(c, c->rbuf, rbytes);
     dfree(c, c->gkbuf, sizeof(float2) * (size_t)(np * c->gkstride));
-    c->ybuf = c->rbuf = c->gkbuf = nullptr;
+    c->ybuf = c->gkbuf = nullptr;
     c->ystride = ystride;
     c->gkstride = gkstride;
-    if ((st = dalloc(c, (void**)&c->ybuf, ybytes)) || (st = dalloc(c, (void**)&c->rbuf, rbytes)) ||
-        (st = dalloc(c, (void**)&c->gkbuf, gbytes)))
+    if ((st = dalloc(c, (void**)&c->ybuf, ybytes)) || (st = dalloc(c, (void**)&c->gkbuf, gbytes)))
       return st;
   }
   if (parts > c->part_cap) {

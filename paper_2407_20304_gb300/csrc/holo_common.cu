@@ -59,24 +59,6 @@ __global__ void k_reduce_g(PassArgs a, float2* Gp, int j, int row0, int nrows, i
   }
 }
 
-// out = ext * sum_p r_p + wref * rref   (fixed summation order over planes)
-__global__ void k_sum_residuals(const float2* __restrict__ rbuf, int nplanes, long long n2,
-                                const float2* __restrict__ rref, float ext, float wref,
-                                float2* __restrict__ out) {
-  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n2;
-       e += (long long)gridDim.x * blockDim.x) {
-    float2 acc = make_float2(0.f, 0.f);
-    for (int p = 0; p < nplanes; ++p) acc = cadd(acc, rbuf[(long long)p * n2 + e]);
-    acc = cscale(acc, ext);
-    if (rref) {
-      const float2 r = rref[e];
-      acc.x = fmaf(wref, r.x, acc.x);
-      acc.y = fmaf(wref, r.y, acc.y);
-    }
-    out[e] = acc;
-  }
-}
-
 // Reference-image term (Eq. min1, second norm): r_ref = b - a b/|b|, loss partials.
 __global__ void k_ref_residual(const float2* __restrict__ b, const float* __restrict__ aref,
                                long long n2, float2* __restrict__ rref, double* part) {
@@ -184,12 +166,6 @@ cudaError_t launch_reduce_g(const PassArgs& a, float2* Gp, int j, int row0, int 
   const long long total = (long long)nrows * ncols;
   if (total <= 0) return cudaSuccess;
   k_reduce_g<<<grid_for(total), kThreads, 0, s>>>(a, Gp, j, row0, nrows, col0, ncols);
-  return cudaGetLastError();
-}
-
-cudaError_t launch_sum_residuals(const float2* rbuf, int nplanes, long long n2, const float2* rref,
-                                 float ext, float wref, float2* out, cudaStream_t s) {
-  k_sum_residuals<<<grid_for(n2), kThreads, 0, s>>>(rbuf, nplanes, n2, rref, ext, wref, out);
   return cudaGetLastError();
 }
 

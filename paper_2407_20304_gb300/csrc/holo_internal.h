@@ -65,7 +65,9 @@ struct PassArgs {
   const float2* chirp_zhat;    // [J][P]
   float2* ybuf;                // per local plane: [ystride] (box rows x n)
   long long ystride;
-  float2* rbuf;                // per local plane: [n][n] residuals (gradient only)
+  float2* tq;                  // [n][n]: ext sum_kj r_kj + w_ref r_ref (gradient only)
+  const float2* rref;          // [n][n] reference residual, or null
+  float wref;
   float2* gkbuf;               // per local plane: [gkstride] conj(w) v on the box
   long long gkstride;
   float2* u_out;               // optional [nk][J][n][n]
@@ -83,7 +85,7 @@ struct PassArgs {
   // rows of all planes in one flat list: plane p owns lines [rowstart[p], rowstart[p+1])
   const int* rowstart;         // [n_angles * J + 1] (global plane index)
   int line0, nlines;           // the chunk's lines: [line0, line0 + nlines)
-  int pass_b_items;            // nk * J * column groups
+  int pass_b_items;            // column groups of pass B
 };
 
 // Entry points implemented once per supported line length P.
@@ -105,8 +107,6 @@ const Ops* ops_for(int P);
 cudaError_t launch_pass_d(const PassArgs& a, cudaStream_t s);
 cudaError_t launch_reduce_g(const PassArgs& a, float2* Gp, int j, int row0, int nrows, int col0,
                             int ncols, cudaStream_t s);
-cudaError_t launch_sum_residuals(const float2* rbuf, int nplanes, long long n2, const float2* rref,
-                                 float ext, float wref, float2* out, cudaStream_t s);
 cudaError_t launch_ref_residual(const float2* bref, const float* sqrt_dref, long long n2,
                                 float2* rref, double* part, int nblocks, cudaStream_t s);
 cudaError_t launch_sum_f64(const double* part, int count, double* out, int accumulate,

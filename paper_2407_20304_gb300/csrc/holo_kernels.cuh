@@ -268,83 +268,124 @@ __global__ void __launch_bounds__(RowCfg<P>::NT) k_pass_a(PassArgs a) {
 
 // ------------------------------------------------------------------ pass B
 
+// Shared memory of pass B: head, C exchange lines, the reference field slice b[n][C] and
+// the residual sum S[n][C] of the block's column group.
+template <int P>
+size_t pass_b_smem(int n) {
+  return (size_t)(SmemHead<P>::WORDS + ColCfg<P>::C * ColCfg<P>::LS + 2 * n * ColCfg<P>::C) *
+         sizeof(float2);
+}
+
+// Each block owns whole column groups (C adjacent detector columns) and walks every plane
+// of the chunk for them, distance-major: the columns of b = C D_{zeta_0} q are read once,
+// and S = sum_kj r_kj is accumulated in shared memory in a fixed order and written once
+// (with the reference residual) as the source of the ext-part of grad_q.  Every S / b slot
+// is owned by one thread (its crop rows of its column), so no barrier guards them.
 template <int P, bool ADJ>
 __global__ void __launch_bounds__(ColCfg<P>::NT) k_pass_b(PassArgs a) {
   using F = Fft<P>;
   using Cc = ColCfg<P>;
   using H = SmemHead<P>;
+  constexpr int C = Cc::C;
   extern __shared__ float2 smem[];
   __shared__ double red[32];
   float2* roots = smem;
   float2* chs = smem + H::ROOTS;
-  const int g = threadIdx.x % Cc::C, t = threadIdx.x / Cc::C;
+  const int g = threadIdx.x % C, t = threadIdx.x / C;
   float2* sm = smem + H::WORDS + g * Cc::LS;
+  const int n = a.n, lo = P / 2 - n / 2;
+  float2* sb = smem + H::WORDS + C * Cc::LS;
+  float2* sS = sb + n * C;
   load_roots<P>(roots, a.twiddles);
   const TwRoots tw{roots};
-  const int n = a.n, lo = P / 2 - n / 2;
-  const int ngroups = (n + Cc::C - 1) / Cc::C;
-  float lsum = 0.f;
+  const int ngroups = (n + C - 1) / C;
   double dsum = 0.0;
   int jcur = -1;
-  for (int item = blockIdx.x; item < a.pass_b_items; item += gridDim.x) {
-    const int lp = item / ngroups, kl = lp / a.J, j = lp % a.J;
-    const int col = (item % ngroups) * Cc::C + g;
+  for (int cg = blockIdx.x; cg < ngroups; cg += gridDim.x) {
+    const int col = cg * C + g;
     const bool valid = col < n;
-    const long long gplane = (long long)(a.k0 + kl) * a.J + j;
-    const PlaneDesc d = a.planes[gplane];
-    float2* yb = a.ybuf + (long long)lp * a.ystride;
-    ensure_chirp<P>(chs, a.chirp_zhat, j, jcur);
-    float2 v[16];
-#pragma unroll
-    for (int c = 0; c < 16; ++c) {
-      const int rel = t + F::T * c - d.by0;
-      v[c] = (valid && (unsigned)rel < (unsigned)d.bys) ? yb[(long long)rel * n + col]
-                                                         : make_float2(0.f, 0.f);
-    }
-    __syncthreads();
-    fft_fwd_with<P>(v, sm, tw, t, SyncBlock());
-#pragma unroll
-    for (int c = 0; c < 16; ++c) v[c] = cmul(v[c], chirp_half<P>(chs, t + F::T * c));
-    fft_inv_with<P>(v, sm, tw, t, SyncBlock());
-    const float* ad = a.sqrt_d + (gplane - (long long)a.data_k0 * a.J) * n * n;
-    float2* rb = a.rbuf + (long long)lp * n * n;
-    float2* uo = a.u_out ? a.u_out + (long long)lp * n * n : nullptr;
-    lsum = 0.f;
 #pragma unroll
     for (int c = 0; c < 16; ++c) {
       const int rr = t + F::T * c - lo;
-      float2 r = make_float2(0.f, 0.f);
-      if (valid && (unsigned)rr < (unsigned)n) {
-        const long long e = (long long)rr * n + col;
-        float2 u = v[c];
-        if (a.ext != 0.f) {
-          const float2 b = __ldg(a.bref + e);
-          u.x = fmaf(a.ext, b.x, u.x);
-          u.y = fmaf(a.ext, b.y, u.y);
+      if ((unsigned)rr < (unsigned)n) {
+        sb[rr * C + g] = (valid && a.ext != 0.f) ? __ldg(a.bref + (long long)rr * n + col)
+                                                 : make_float2(0.f, 0.f);
+        if (ADJ) sS[rr * C + g] = make_float2(0.f, 0.f);
+      }
+    }
+    for (int j = 0; j < a.J; ++j) {
+      ensure_chirp<P>(chs, a.chirp_zhat, j, jcur);
+      for (int kl = 0; kl < a.nk; ++kl) {
+        const int lp = kl * a.J + j;
+        const long long gplane = (long long)(a.k0 + kl) * a.J + j;
+        const PlaneDesc d = a.planes[gplane];
+        float2* yb = a.ybuf + (long long)lp * a.ystride;
+        float2 v[16];
+#pragma unroll
+        for (int c = 0; c < 16; ++c) {
+          const int rel = t + F::T * c - d.by0;
+          v[c] = (valid && (unsigned)rel < (unsigned)d.bys) ? yb[(long long)rel * n + col]
+                                                             : make_float2(0.f, 0.f);
         }
-        const float amp = __ldg(ad + e);
-        const float mag = sqrtf(fmaf(u.x, u.x, u.y * u.y));
-        const float diff = mag - amp;
-        lsum = fmaf(diff, diff, lsum);
-        if (uo) uo[e] = u;
-        if (ADJ) {
-          const float s = mag > 0.f ? 1.f - amp / mag : 0.f;
-          r = cscale(u, s);
-          rb[e] = r;
+        __syncthreads();
+        fft_fwd_with<P>(v, sm, tw, t, SyncBlock());
+#pragma unroll
+        for (int c = 0; c < 16; ++c) v[c] = cmul(v[c], chirp_half<P>(chs, t + F::T * c));
+        fft_inv_with<P>(v, sm, tw, t, SyncBlock());
+        const float* ad = a.sqrt_d + (gplane - (long long)a.data_k0 * a.J) * n * n;
+        float2* uo = a.u_out ? a.u_out + (long long)lp * n * n : nullptr;
+        float lsum = 0.f;
+#pragma unroll
+        for (int c = 0; c < 16; ++c) {
+          const int rr = t + F::T * c - lo;
+          float2 r = make_float2(0.f, 0.f);
+          if (valid && (unsigned)rr < (unsigned)n) {
+            const long long e = (long long)rr * n + col;
+            float2 u = v[c];
+            const float2 b = sb[rr * C + g];
+            u.x = fmaf(a.ext, b.x, u.x);
+            u.y = fmaf(a.ext, b.y, u.y);
+            const float amp = __ldg(ad + e);
+            const float mag = sqrtf(fmaf(u.x, u.x, u.y * u.y));
+            const float diff = mag - amp;
+            lsum = fmaf(diff, diff, lsum);
+            if (uo) uo[e] = u;
+            if (ADJ) {
+              const float s = mag > 0.f ? 1.f - amp / mag : 0.f;
+              r = cscale(u, s);
+              sS[rr * C + g] = cadd(sS[rr * C + g], r);
+            }
+          }
+          v[c] = r;
+        }
+        dsum += (double)lsum;
+        if constexpr (ADJ) {
+          fft_fwd_with<P>(v, sm, tw, t, SyncBlock());
+#pragma unroll
+          for (int c = 0; c < 16; ++c) v[c] = cmulc(v[c], chirp_half<P>(chs, t + F::T * c));
+          fft_inv_with<P>(v, sm, tw, t, SyncBlock());
+#pragma unroll
+          for (int c = 0; c < 16; ++c) {
+            const int rel = t + F::T * c - d.by0;
+            if (valid && (unsigned)rel < (unsigned)d.bys) yb[(long long)rel * n + col] = v[c];
+          }
         }
       }
-      v[c] = r;
     }
-    dsum += (double)lsum;
     if constexpr (ADJ) {
-      fft_fwd_with<P>(v, sm, tw, t, SyncBlock());
-#pragma unroll
-      for (int c = 0; c < 16; ++c) v[c] = cmulc(v[c], chirp_half<P>(chs, t + F::T * c));
-      fft_inv_with<P>(v, sm, tw, t, SyncBlock());
 #pragma unroll
       for (int c = 0; c < 16; ++c) {
-        const int rel = t + F::T * c - d.by0;
-        if (valid && (unsigned)rel < (unsigned)d.bys) yb[(long long)rel * n + col] = v[c];
+        const int rr = t + F::T * c - lo;
+        if (valid && (unsigned)rr < (unsigned)n) {
+          const long long e = (long long)rr * n + col;
+          float2 acc = cscale(sS[rr * C + g], a.ext);
+          if (a.rref) {
+            const float2 q = __ldg(a.rref + e);
+            acc.x = fmaf(a.wref, q.x, acc.x);
+            acc.y = fmaf(a.wref, q.y, acc.y);
+          }
+          a.tq[e] = acc;
+        }
       }
     }
   }
@@ -516,27 +557,27 @@ inline int max_dynamic_smem() {
 template <int P>
 int pass_b_blocks(int items, int n, int rows) {
   using Cc = ColCfg<P>;
-  (void)n;
   (void)rows;
-  cudaFuncSetAttribute(k_pass_b<P, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                       (int)Cc::PASS_B_SMEM);
-  return persistent_blocks(k_pass_b<P, true>, Cc::NT, Cc::PASS_B_SMEM, items);
+  const size_t sm = pass_b_smem<P>(n);
+  cudaFuncSetAttribute(k_pass_b<P, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  return persistent_blocks(k_pass_b<P, true>, Cc::NT, sm, items);
 }
 
 template <int P>
 cudaError_t launch_pass_b(const PassArgs& a, int adj, int nblocks, cudaStream_t s) {
   using Cc = ColCfg<P>;
+  const size_t sm = pass_b_smem<P>(a.n);
   cudaError_t e;
   if (adj) {
     e = cudaFuncSetAttribute(k_pass_b<P, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)Cc::PASS_B_SMEM);
+                             (int)sm);
     if (e != cudaSuccess) return e;
-    k_pass_b<P, true><<<nblocks, Cc::NT, Cc::PASS_B_SMEM, s>>>(a);
+    k_pass_b<P, true><<<nblocks, Cc::NT, sm, s>>>(a);
   } else {
     e = cudaFuncSetAttribute(k_pass_b<P, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)Cc::PASS_B_SMEM);
+                             (int)sm);
     if (e != cudaSuccess) return e;
-    k_pass_b<P, false><<<nblocks, Cc::NT, Cc::PASS_B_SMEM, s>>>(a);
+    k_pass_b<P, false><<<nblocks, Cc::NT, sm, s>>>(a);
   }
   return cudaGetLastError();
 }
