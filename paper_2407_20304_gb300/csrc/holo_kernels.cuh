@@ -50,6 +50,9 @@ struct RowCfg {
   static constexpr int NT = G * T;
   static constexpr int LS = Fft<P>::SMEM + (P == 64 ? 1 : 0);
   static constexpr size_t SMEM_BYTES = (size_t)(SmemHead<P>::WORDS + G * LS) * sizeof(float2);
+  // resident blocks per SM asked of ptxas: 3 where the row passes then fit in 80 registers
+  // without spilling (checked with -Xptxas -v), else 2
+  static constexpr int MINB = P == 4096 ? 3 : 2;
 };
 
 template <int P>
@@ -203,7 +206,7 @@ __device__ __forceinline__ void ensure_chirp(float2* chs, const float2* __restri
 // ------------------------------------------------------------------ pass A
 
 template <int P>
-__global__ void __launch_bounds__(RowCfg<P>::NT) k_pass_a(PassArgs a) {
+__global__ void __launch_bounds__(RowCfg<P>::NT, RowCfg<P>::MINB) k_pass_a(PassArgs a) {
   using F = Fft<P>;
   using R = RowCfg<P>;
   using H = SmemHead<P>;
@@ -396,7 +399,7 @@ __global__ void __launch_bounds__(ColCfg<P>::NT) k_pass_b(PassArgs a) {
 // ------------------------------------------------------------------ pass C
 
 template <int P>
-__global__ void __launch_bounds__(RowCfg<P>::NT) k_pass_c(PassArgs a) {
+__global__ void __launch_bounds__(RowCfg<P>::NT, RowCfg<P>::MINB) k_pass_c(PassArgs a) {
   using F = Fft<P>;
   using R = RowCfg<P>;
   using H = SmemHead<P>;
