@@ -22,6 +22,13 @@ const Ops* ops_512();
 const Ops* ops_1024();
 const Ops* ops_2048();
 const Ops* ops_4096();
+const Ops* ops_48();
+const Ops* ops_96();
+const Ops* ops_192();
+const Ops* ops_384();
+const Ops* ops_768();
+const Ops* ops_1536();
+const Ops* ops_3072();
 
 const Ops* ops_for(int P) {
   switch (P) {
@@ -34,6 +41,13 @@ const Ops* ops_for(int P) {
     case 1024: return ops_1024();
     case 2048: return ops_2048();
     case 4096: return ops_4096();
+    case 48: return ops_48();
+    case 96: return ops_96();
+    case 192: return ops_192();
+    case 384: return ops_384();
+    case 768: return ops_768();
+    case 1536: return ops_1536();
+    case 3072: return ops_3072();
     default: return nullptr;
   }
 }
@@ -208,26 +222,41 @@ std::vector<float2> chirp_table(int P, double lambda, double dx, double z) {
   return c;
 }
 
-// Twiddle table in the layout of holo_fft.cuh: radix-16 stage s with M(s) = P/16^(s+1) > 1
-// contributes entries [(k-1) M + mu] = exp(-2 pi i mu k 16^s / P), k = 1..15.
+// Twiddle table in the layout of holo_fft.cuh for P = PB or 3 PB (PB a power of two):
+// radix-16 stage s with M(s) = PB/16^(s+1) > 1 contributes entries
+// [(k-1) M + mu] = exp(-2 pi i mu k 16^s / PB), k = 1..15; for P = 3 PB the radix-3 step
+// adds exp(-2 pi i r n / P) for r = 1, 2 (outer) and n < PB (inner).
 std::vector<float2> twiddle_table(int P) {
   std::vector<float2> tw;
+  const int PB = P % 3 == 0 ? P / 3 : P;
   int log2p = 0;
-  while ((1 << log2p) < P) ++log2p;
+  while ((1 << log2p) < PB) ++log2p;
   const int n16 = log2p / 4;
   const double pi = 3.14159265358979323846;
   long long L = 1;
   for (int s = 0; s < n16; ++s) {
-    const long long M = P / (L * 16);
+    const long long M = PB / (L * 16);
     if (M > 1)
       for (int k = 1; k < 16; ++k)
         for (long long mu = 0; mu < M; ++mu) {
-          const double a = -2.0 * pi * (double)(mu * k * L) / P;
+          const double a = -2.0 * pi * (double)(mu * k * L) / PB;
           tw.push_back(make_float2((float)std::cos(a), (float)std::sin(a)));
         }
     L *= 16;
   }
+  if (PB != P)
+    for (int r = 1; r <= 2; ++r)
+      for (int nn = 0; nn < PB; ++nn) {
+        const double a = -2.0 * pi * (double)(r * nn) / P;
+        tw.push_back(make_float2((float)std::cos(a), (float)std::sin(a)));
+      }
   return tw;
+}
+
+// Line lengths with kernels: 2^k (16 .. 4096) and 3 * 2^k (48 .. 3072).
+bool supported_line(int P) {
+  const int PB = P % 3 == 0 ? P / 3 : P;
+  return is_pow2(PB) && PB >= 16 && P <= 4096;
 }
 
 // m~ = hi + lo with hi holding 24 - bits significant bits, so that hi * x is exact in FP32
@@ -544,7 +573,7 @@ holo_status holo_create(const holo_geometry* geo, void* stream, holo_ctx** out) 
   if (!(geo->z[J - 1] < geo->Z)) return HOLO_ERR_ARG;
   if (!(geo->w_ref >= 0) || !std::isfinite(geo->w_ref) || !std::isfinite(geo->ext))
     return HOLO_ERR_ARG;
-  if (!is_pow2(P) || P < 16) return HOLO_ERR_UNSUPPORTED;
+  if (!supported_line(P)) return HOLO_ERR_UNSUPPORTED;
   const holo::Ops* ops = holo::ops_for(P);
   if (!ops) return HOLO_ERR_UNSUPPORTED;
 

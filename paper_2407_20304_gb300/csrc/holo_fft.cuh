@@ -1,4 +1,5 @@
-// Register + shared-memory FFT engine for one line of length P (a power of two >= 16).
+// Register + shared-memory FFT engine for one line of length P: a power of two >= 16, or
+// three times one (P = 3 PB, PB >= 16).
 //
 // The Fresnel operator D_z (Appendix A, Eq. defPz/defGz) is a circular convolution on
 // the P x P grid; with a separable chirp exp(-i pi lambda z (fx^2 + fy^2)) it factors into
@@ -20,8 +21,18 @@
 // memory bank conflicts.  Twiddles come from a per-stage table in shared memory,
 // indexed [k-1][mu] so that consecutive threads read consecutive entries.
 //
+// P = 3 PB.  The T = P/16 threads form three groups of TB = PB/16; thread t = q TB + i
+// holds element i + TB c + PB q (pos).  The forward transform first takes one radix-3
+// decimation-in-frequency step through shared memory: group q forms
+//   y_q[n] = W_P^{n q} (x[n] + W_3^q x[n + PB] + W_3^{2q} x[n + 2 PB]),  n = i + TB c,
+// which is one output of each of the PB three-point butterflies, then group q transforms
+// y_q with the power-of-two engine above on its own third of the buffer.  Register rho of
+// thread (q, i) then holds frequency 3 (i + TB rho) + q (fpos).  The inverse runs the
+// adjoint steps in reverse order and returns the pos layout.
+//
 // Synchronisation: every thread of a line group calls the transform the same number of
-// times; the Sync policy is a block-wide barrier or a named barrier per line group.
+// times; the Sync policy is a block-wide barrier or a named barrier per line group.  The
+// buffer must be free when a transform starts, and is free again when it returns.
 
 #pragma once
 
@@ -60,29 +71,44 @@ __host__ __device__ constexpr int ipow16(int s) { return s == 0 ? 1 : 16 * ipow1
 
 __device__ __forceinline__ int spad(int a) { return a + (a >> 4); }
 
+__host__ __device__ constexpr bool is_pow2c(int x) { return x > 0 && (x & (x - 1)) == 0; }
+
 template <int P_>
 struct Fft {
   static constexpr int P = P_;
-  static constexpr int LOG2 = ilog2c(P);
-  static_assert((1 << LOG2) == P && P >= 16, "line length must be a power of two >= 16");
+  static constexpr bool R3 = P % 3 == 0;           // one radix-3 step, then three sub-lines
+  static constexpr int PB = R3 ? P / 3 : P;        // power-of-two (sub-)line length
+  static_assert(is_pow2c(PB) && PB >= 16, "line length must be 2^k or 3 * 2^k with 2^k >= 16");
+  static constexpr int LOG2 = ilog2c(PB);
   static constexpr int T = P / 16;                 // threads per line
+  static constexpr int TB = PB / 16;               // threads per power-of-two sub-line
   static constexpr int N16 = LOG2 / 4;             // radix-16 stages
   static constexpr int RB = LOG2 % 4;              // bits of the final small stage (0: none)
   static constexpr int NST = N16 + (RB ? 1 : 0);   // number of stages
   static constexpr int RLAST = RB ? (1 << RB) : 16;
   static constexpr int SMEM = P + P / 16;          // padded exchange buffer, float2 entries
-  // radix-16 stage s: prefix length L = 16^s, remaining length M = P / 16^(s+1)
+  // radix-16 stage s: prefix length L = 16^s, remaining length M = PB / 16^(s+1)
   __host__ __device__ static constexpr int L(int s) { return ipow16(s); }
-  __host__ __device__ static constexpr int M(int s) { return P / ipow16(s + 1); }
+  __host__ __device__ static constexpr int M(int s) { return PB / ipow16(s + 1); }
   __host__ __device__ static constexpr int tw_off(int s) {
     return s == 0 ? 0 : tw_off(s - 1) + (M(s - 1) > 1 ? 15 * M(s - 1) : 0);
   }
-  static constexpr int TW = tw_off(N16);           // twiddle table entries (float2)
-  // compact table of the roots W_P^{mu L(s)} (k = 1 entries) of every twiddled stage
+  static constexpr int TW_BASE = tw_off(N16);      // radix-16 twiddle entries (float2)
+  // compact table of the roots W_PB^{mu L(s)} (k = 1 entries) of every twiddled stage
   __host__ __device__ static constexpr int roots_off(int s) {
     return s == 0 ? 0 : roots_off(s - 1) + (M(s - 1) > 1 ? M(s - 1) : 0);
   }
-  static constexpr int ROOTS = roots_off(N16);
+  static constexpr int ROOTS_BASE = roots_off(N16);
+  // radix-3 step: W_P^n and W_P^{2n}, n < PB, appended to both tables
+  static constexpr int TW = TW_BASE + (R3 ? 2 * PB : 0);
+  static constexpr int ROOTS = ROOTS_BASE + (R3 ? 2 * PB : 0);
+  // line element held in register c of thread t, and the frequency it holds after fft_fwd
+  __host__ __device__ static constexpr int pos(int t, int c) {
+    return R3 ? t % TB + TB * c + PB * (t / TB) : t + T * c;
+  }
+  __host__ __device__ static constexpr int fpos(int t, int c) {
+    return R3 ? 3 * (t % TB + TB * c) + t / TB : t + T * c;
+  }
 };
 
 // --------------------------------------------------------------------- small DFTs
@@ -184,8 +210,9 @@ __device__ __forceinline__ void dft_small(float2* u) {
 // --------------------------------------------------------------------- twiddle tables
 
 // Host-side layout of the shared twiddle table of one line length: for each radix-16
-// stage s with M(s) > 1, entries [(k-1) * M(s) + mu] = exp(-2 pi i mu k L(s) / P),
-// k = 1..15, mu = 0..M(s)-1.  Filled in FP64 on the host.
+// stage s with M(s) > 1, entries [(k-1) * M(s) + mu] = exp(-2 pi i mu k L(s) / PB),
+// k = 1..15, mu = 0..M(s)-1; for P = 3 PB then [n] = exp(-2 pi i n / P) and
+// [PB + n] = exp(-2 pi i 2n / P), n < PB.  Filled in FP64 on the host.
 
 template <int P>
 __device__ __forceinline__ void load_twiddles(float2* sm_tw, const float2* __restrict__ g_tw) {
@@ -197,6 +224,11 @@ __device__ __forceinline__ void load_twiddles(float2* sm_tw, const float2* __res
 // TwTable: the per-stage table in shared memory, one load per twiddle.
 struct TwTable {
   const float2* tw;
+  // radix-3 twiddle W_P^{(idx / PB + 1)(idx % PB)}
+  template <int P>
+  __device__ __forceinline__ float2 r3(int idx) const {
+    return tw[Fft<P>::TW_BASE + idx];
+  }
   template <int P, int S>
   __device__ __forceinline__ float2 get(int mu, int k) const {
     return tw[Fft<P>::tw_off(S) + (k - 1) * Fft<P>::M(S) + mu];
@@ -214,6 +246,10 @@ struct TwTable {
 // by a product tree of depth <= 4 (rounding error a few ulp), no further loads.
 struct TwPow {
   const float2* tw;
+  template <int P>
+  __device__ __forceinline__ float2 r3(int idx) const {
+    return tw[Fft<P>::TW_BASE + idx];
+  }
   template <int P, int S, bool INV>
   __device__ __forceinline__ void apply(float2 (&v)[16], int mu) const {
     const float2 r = tw[Fft<P>::tw_off(S) + mu];
@@ -241,6 +277,10 @@ struct TwPow {
 // is small enough to keep in shared memory next to the chirp.
 struct TwRoots {
   const float2* roots;
+  template <int P>
+  __device__ __forceinline__ float2 r3(int idx) const {
+    return roots[Fft<P>::ROOTS_BASE + idx];
+  }
   template <int P, int S, bool INV>
   __device__ __forceinline__ void apply(float2 (&v)[16], int mu) const {
     TwPow::pow_apply<INV>(v, roots[Fft<P>::roots_off(S) + mu]);
@@ -257,6 +297,9 @@ __device__ __forceinline__ void load_roots(float2* sm_roots, const float2* __res
       for (int mu = threadIdx.x; mu < F::M(st); mu += blockDim.x)
         sm_roots[F::roots_off(st) + mu] = g_tw[F::tw_off(st) + mu];
   }
+  if constexpr (F::R3)
+    for (int i = threadIdx.x; i < 2 * F::PB; i += blockDim.x)
+      sm_roots[F::ROOTS_BASE + i] = g_tw[F::TW_BASE + i];
 }
 
 // --------------------------------------------------------------------- stages
@@ -351,24 +394,94 @@ __device__ __forceinline__ void inv_from(float2 (&v)[16], float2* __restrict__ s
   }
 }
 
-// Forward DFT (e^{-2 pi i}, unnormalised): strided natural in, strided natural out.
+// Radix-3 steps of P = 3 PB (see the layout notes at the top).  v[c] of thread (q, i) is
+// element n + PB q (n = i + TB c) on entry to r3_split and frequency-side y_q[n] on exit;
+// r3_merge is its adjoint (conjugate twiddles and roots of unity, no 1/3).
+template <int P, bool INV, class Sync, class TW>
+__device__ __forceinline__ void r3_butterfly_third(float2 (&v)[16], float2* __restrict__ sm, TW tw,
+                                                   int t, Sync sync) {
+  using F = Fft<P>;
+  constexpr int PB = F::PB, TB = F::TB;
+  const float h3 = 0.86602540378443865f;  // sqrt(3)/2
+  const int q = t / TB, i = t % TB;
+  // output q of the butterfly (x0, x1, x2): x0 + w^q x1 + w^{2q} x2 with w = W_3 (forward)
+  // or conj(W_3) (inverse), i.e. x0 - (x1 + x2)/2 -/+ i sqrt(3)/2 (x1 - x2) for q = 1, 2
+  const float sg = ((q == 1) != INV) ? -h3 : h3;
+#pragma unroll
+  for (int c = 0; c < 16; ++c) {
+    const int n = i + TB * c;
+    const float2 x0 = sm[spad(n)], x1 = sm[spad(n + PB)], x2 = sm[spad(n + 2 * PB)];
+    const float2 su = cadd(x1, x2), df = csub(x1, x2);
+    float2 y;
+    if (q == 0) {
+      y = cadd(x0, su);
+    } else {
+      y.x = fmaf(-0.5f, su.x, x0.x) - sg * df.y;
+      y.y = fmaf(-0.5f, su.y, x0.y) + sg * df.x;
+    }
+    v[c] = y;
+  }
+  (void)tw;
+  sync();
+}
+
+template <int P, class Sync, class TW>
+__device__ __forceinline__ void r3_fwd(float2 (&v)[16], float2* sm, TW tw, int t, Sync sync) {
+  using F = Fft<P>;
+  constexpr int PB = F::PB, TB = F::TB;
+  const int q = t / TB, i = t % TB;
+#pragma unroll
+  for (int c = 0; c < 16; ++c) sm[spad(i + TB * c + PB * q)] = v[c];
+  sync();
+  r3_butterfly_third<P, false>(v, sm, tw, t, sync);
+  if (q > 0) {
+#pragma unroll
+    for (int c = 0; c < 16; ++c) v[c] = cmul(v[c], tw.template r3<P>((q - 1) * PB + i + TB * c));
+  }
+  fwd_from<PB, 0, Sync, TW>(v, sm + q * Fft<PB>::SMEM, tw, i, sync);
+}
+
+template <int P, class Sync, class TW>
+__device__ __forceinline__ void r3_inv(float2 (&v)[16], float2* sm, TW tw, int t, Sync sync) {
+  using F = Fft<P>;
+  constexpr int PB = F::PB, TB = F::TB;
+  const int q = t / TB, i = t % TB;
+  inv_from<PB, Fft<PB>::N16, Sync, TW>(v, sm + q * Fft<PB>::SMEM, tw, i, sync);
+  if (q > 0) {
+#pragma unroll
+    for (int c = 0; c < 16; ++c) v[c] = cmulc(v[c], tw.template r3<P>((q - 1) * PB + i + TB * c));
+  }
+#pragma unroll
+  for (int c = 0; c < 16; ++c) sm[spad(i + TB * c + PB * q)] = v[c];
+  sync();
+  r3_butterfly_third<P, true>(v, sm, tw, t, sync);
+}
+
+// Forward DFT (e^{-2 pi i}, unnormalised): pos layout in, fpos layout out (both strided
+// natural when P is a power of two).
 template <int P, class Sync, class TW>
 __device__ __forceinline__ void fft_fwd_with(float2 (&v)[16], float2* sm, TW tw, int t, Sync sync) {
-  fwd_from<P, 0, Sync, TW>(v, sm, tw, t, sync);
+  if constexpr (Fft<P>::R3)
+    r3_fwd<P, Sync, TW>(v, sm, tw, t, sync);
+  else
+    fwd_from<P, 0, Sync, TW>(v, sm, tw, t, sync);
 }
 template <int P>
 __device__ __forceinline__ void fft_fwd(float2 (&v)[16], float2* sm, const float2* tw, int t) {
-  fwd_from<P, 0, SyncBlock, TwTable>(v, sm, TwTable{tw}, t, SyncBlock());
+  fft_fwd_with<P, SyncBlock, TwTable>(v, sm, TwTable{tw}, t, SyncBlock());
 }
 
-// Inverse DFT without the 1/P factor (the adjoint of fft_fwd).
+// Inverse DFT without the 1/P factor (the adjoint of fft_fwd): fpos in, pos out.
 template <int P, class Sync, class TW>
 __device__ __forceinline__ void fft_inv_with(float2 (&v)[16], float2* sm, TW tw, int t, Sync sync) {
-  inv_from<P, Fft<P>::N16, Sync, TW>(v, sm, tw, t, sync);
+  if constexpr (Fft<P>::R3)
+    r3_inv<P, Sync, TW>(v, sm, tw, t, sync);
+  else
+    inv_from<P, Fft<P>::N16, Sync, TW>(v, sm, tw, t, sync);
 }
 template <int P>
 __device__ __forceinline__ void fft_inv(float2 (&v)[16], float2* sm, const float2* tw, int t) {
-  inv_from<P, Fft<P>::N16, SyncBlock, TwTable>(v, sm, TwTable{tw}, t, SyncBlock());
+  fft_inv_with<P, SyncBlock, TwTable>(v, sm, TwTable{tw}, t, SyncBlock());
 }
 
 }  // namespace holo

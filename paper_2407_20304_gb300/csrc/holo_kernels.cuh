@@ -43,12 +43,17 @@ struct SmemHead {
   static constexpr int WORDS = ROOTS + CHIRP;
 };
 
+// Lines per row block: about 256 threads, whole warps.
+__host__ __device__ constexpr int row_lines(int T, int g = 0) {
+  return T >= 256 ? 1 : (g == 0 ? row_lines(T, 256 / T) : ((g * T) % 32 ? row_lines(T, g - 1) : g));
+}
+
 template <int P>
 struct RowCfg {
   static constexpr int T = P / 16;
-  static constexpr int G = T >= 256 ? 1 : 256 / T;      // lines per block
+  static constexpr int G = row_lines(T);                // lines per block
   static constexpr int NT = G * T;
-  static constexpr int LS = Fft<P>::SMEM + (P == 64 ? 1 : 0);
+  static constexpr int LS = Fft<P>::SMEM + (P == 64 || P == 192 ? 1 : 0);
   static constexpr size_t SMEM_BYTES = (size_t)(SmemHead<P>::WORDS + G * LS) * sizeof(float2);
   // resident blocks per SM asked of ptxas: 3 where the row passes then fit in 80 registers
   // without spilling (checked with -Xptxas -v), else 2
@@ -58,9 +63,13 @@ struct RowCfg {
 template <int P>
 struct ColCfg {
   static constexpr int T = P / 16;
-  static constexpr int C = T >= 256 ? 2 : (T >= 64 ? 4 : (P == 512 ? 16 : 256 / T));
+  static constexpr int C =
+      Fft<P>::R3 ? (T >= 192 ? 2 : (T >= 24 ? 4 : (T >= 12 ? 8 : (T >= 6 ? 16 : 32))))
+                 : (T >= 256 ? 2 : (T >= 64 ? 4 : (P == 512 ? 16 : 256 / T)));
   static constexpr int NT = C * T;
-  static constexpr int EXTRA = P >= 4096 ? 8 : (P == 2048 ? 4 : (P == 1024 ? 3 : (P == 16 ? 0 : 1)));
+  static constexpr int EXTRA =
+      Fft<P>::R3 ? (P == 768 ? 4 : (P == 1536 ? 3 : (P == 96 || P == 192 || P == 384 ? 1 : 0)))
+                 : (P >= 4096 ? 8 : (P == 2048 ? 4 : (P == 1024 ? 3 : (P == 16 ? 0 : 1))));
   static constexpr int LS = Fft<P>::SMEM + EXTRA;
   static constexpr size_t SMEM_BYTES = (size_t)(SmemHead<P>::WORDS + C * LS) * sizeof(float2);
   static constexpr size_t PASS_B_SMEM = SMEM_BYTES;
@@ -166,7 +175,7 @@ k_line_dstep(LineArgs a, const float2* __restrict__ gtw) {
     float2 v[16];
 #pragma unroll
     for (int c = 0; c < 16; ++c) {
-      const int rel = t + F::T * c - a.in_lo;
+      const int rel = F::pos(t, c) - a.in_lo;
       v[c] = (valid && (unsigned)rel < (unsigned)a.in_len) ? in[(long long)rel * a.in_step]
                                                            : make_float2(0.f, 0.f);
     }
@@ -174,14 +183,14 @@ k_line_dstep(LineArgs a, const float2* __restrict__ gtw) {
     fft_fwd_with<P>(v, sm, tw, t, SyncBlock());
 #pragma unroll
     for (int c = 0; c < 16; ++c) {
-      const float2 ch = chirp_half<P>(chs, t + F::T * c);
+      const float2 ch = chirp_half<P>(chs, F::fpos(t, c));
       v[c] = a.conj_chirp ? cmulc(v[c], ch) : cmul(v[c], ch);
     }
     fft_inv_with<P>(v, sm, tw, t, SyncBlock());
     float2* out = a.out + (long long)line * a.out_line_stride;
 #pragma unroll
     for (int c = 0; c < 16; ++c) {
-      const int rel = t + F::T * c - a.out_lo;
+      const int rel = F::pos(t, c) - a.out_lo;
       if (valid && (unsigned)rel < (unsigned)a.out_len) {
         float2* o = out + (long long)rel * a.out_step;
         float2 r = cscale(v[c], a.alpha);
@@ -240,7 +249,7 @@ __global__ void __launch_bounds__(RowCfg<P>::NT, RowCfg<P>::MINB) k_pass_a(PassA
     float2 v[16];
 #pragma unroll
     for (int c = 0; c < 16; ++c) {
-      const int X = t + F::T * c, rel = X - d.bx0;
+      const int X = F::pos(t, c), rel = X - d.bx0;
       float2 x = make_float2(0.f, 0.f);
       if (valid && (unsigned)rel < (unsigned)d.bxs) {
         const float2 w = resample_w(psi, n, a.ext, yt.i0, yt.f, xt[rel]);
@@ -256,14 +265,14 @@ __global__ void __launch_bounds__(RowCfg<P>::NT, RowCfg<P>::MINB) k_pass_a(PassA
     const float2* chg = a.chirp_zhat + (long long)j * P;
 #pragma unroll
     for (int c = 0; c < 16; ++c) {
-      const int f = t + F::T * c;
+      const int f = F::fpos(t, c);
       v[c] = cmul(v[c], own ? chirp_half<P>(chs, f) : __ldg(chg + f));
     }
     fft_inv_with<P>(v, sm, tw, t, SyncBlock());
     float2* yrow = a.ybuf + (long long)lp * a.ystride + (long long)i * n;
 #pragma unroll
     for (int c = 0; c < 16; ++c) {
-      const int rel = t + F::T * c - lo;
+      const int rel = F::pos(t, c) - lo;
       if (valid && (unsigned)rel < (unsigned)n) yrow[rel] = v[c];
     }
   }
@@ -313,7 +322,7 @@ __global__ void __launch_bounds__(ColCfg<P>::NT) k_pass_b(PassArgs a) {
     const bool valid = col < n;
 #pragma unroll
     for (int c = 0; c < 16; ++c) {
-      const int rr = t + F::T * c - lo;
+      const int rr = F::pos(t, c) - lo;
       if ((unsigned)rr < (unsigned)n) {
         sb[rr * C + g] = (valid && a.ext != 0.f) ? __ldg(a.bref + (long long)rr * n + col)
                                                  : make_float2(0.f, 0.f);
@@ -330,7 +339,7 @@ __global__ void __launch_bounds__(ColCfg<P>::NT) k_pass_b(PassArgs a) {
         float2 v[16];
 #pragma unroll
         for (int c = 0; c < 16; ++c) {
-          const int rel = t + F::T * c - d.by0;
+          const int rel = F::pos(t, c) - d.by0;
           v[c] = (valid && (unsigned)rel < (unsigned)d.bys) ? yb[(long long)rel * n + col]
                                                              : make_float2(0.f, 0.f);
         }
@@ -342,23 +351,23 @@ __global__ void __launch_bounds__(ColCfg<P>::NT) k_pass_b(PassArgs a) {
           const float* adn = a.sqrt_d + (gplane + a.J - (long long)a.data_k0 * a.J) * n * n + col;
 #pragma unroll
           for (int c = 0; c < 16; ++c) {
-            const int rel = t + F::T * c - d.by0;
+            const int rel = F::pos(t, c) - d.by0;
             if (rel >= 0 && rel < d.bys + 8 && rel < a.max_box_rows) prefetch_l2(ybn + (long long)rel * n);
-            const int rr = t + F::T * c - lo;
+            const int rr = F::pos(t, c) - lo;
             if ((unsigned)rr < (unsigned)n) prefetch_l2(adn + (long long)rr * n);
           }
         }
         __syncthreads();
         fft_fwd_with<P>(v, sm, tw, t, SyncBlock());
 #pragma unroll
-        for (int c = 0; c < 16; ++c) v[c] = cmul(v[c], chirp_half<P>(chs, t + F::T * c));
+        for (int c = 0; c < 16; ++c) v[c] = cmul(v[c], chirp_half<P>(chs, F::fpos(t, c)));
         fft_inv_with<P>(v, sm, tw, t, SyncBlock());
         const float* ad = a.sqrt_d + (gplane - (long long)a.data_k0 * a.J) * n * n;
         float2* uo = a.u_out ? a.u_out + (long long)lp * n * n : nullptr;
         float lsum = 0.f;
 #pragma unroll
         for (int c = 0; c < 16; ++c) {
-          const int rr = t + F::T * c - lo;
+          const int rr = F::pos(t, c) - lo;
           float2 r = make_float2(0.f, 0.f);
           if (valid && (unsigned)rr < (unsigned)n) {
             const long long e = (long long)rr * n + col;
@@ -383,11 +392,11 @@ __global__ void __launch_bounds__(ColCfg<P>::NT) k_pass_b(PassArgs a) {
         if constexpr (ADJ) {
           fft_fwd_with<P>(v, sm, tw, t, SyncBlock());
 #pragma unroll
-          for (int c = 0; c < 16; ++c) v[c] = cmulc(v[c], chirp_half<P>(chs, t + F::T * c));
+          for (int c = 0; c < 16; ++c) v[c] = cmulc(v[c], chirp_half<P>(chs, F::fpos(t, c)));
           fft_inv_with<P>(v, sm, tw, t, SyncBlock());
 #pragma unroll
           for (int c = 0; c < 16; ++c) {
-            const int rel = t + F::T * c - d.by0;
+            const int rel = F::pos(t, c) - d.by0;
             if (valid && (unsigned)rel < (unsigned)d.bys) yb[(long long)rel * n + col] = v[c];
           }
         }
@@ -396,7 +405,7 @@ __global__ void __launch_bounds__(ColCfg<P>::NT) k_pass_b(PassArgs a) {
     if constexpr (ADJ) {
 #pragma unroll
       for (int c = 0; c < 16; ++c) {
-        const int rr = t + F::T * c - lo;
+        const int rr = F::pos(t, c) - lo;
         if (valid && (unsigned)rr < (unsigned)n) {
           const long long e = (long long)rr * n + col;
           float2 acc = cscale(sS[rr * C + g], a.ext);
@@ -443,7 +452,7 @@ __global__ void __launch_bounds__(RowCfg<P>::NT, RowCfg<P>::MINB) k_pass_c(PassA
     float2 v[16];
 #pragma unroll
     for (int c = 0; c < 16; ++c) {
-      const int rel = t + F::T * c - lo;
+      const int rel = F::pos(t, c) - lo;
       v[c] = (valid && (unsigned)rel < (unsigned)n) ? yrow[rel] : make_float2(0.f, 0.f);
     }
     ensure_chirp<P>(chs, a.chirp_zhat, R::G == 1 ? j : jb, jcur);
@@ -453,7 +462,7 @@ __global__ void __launch_bounds__(RowCfg<P>::NT, RowCfg<P>::MINB) k_pass_c(PassA
     const float2* chg = a.chirp_zhat + (long long)j * P;
 #pragma unroll
     for (int c = 0; c < 16; ++c) {
-      const int f = t + F::T * c;
+      const int f = F::fpos(t, c);
       v[c] = cmulc(v[c], own ? chirp_half<P>(chs, f) : __ldg(chg + f));
     }
     fft_inv_with<P>(v, sm, tw, t, SyncBlock());
@@ -464,7 +473,7 @@ __global__ void __launch_bounds__(RowCfg<P>::NT, RowCfg<P>::MINB) k_pass_c(PassA
     float2* gk = a.gkbuf + (long long)lp * a.gkstride + (long long)i * d.bxs;
 #pragma unroll
     for (int c = 0; c < 16; ++c) {
-      const int X = t + F::T * c, rel = X - d.bx0;
+      const int X = F::pos(t, c), rel = X - d.bx0;
       if (valid && (unsigned)rel < (unsigned)d.bxs) {
         sm[rel] = cconjmul(__ldg(prow + X), v[c]);
         gk[rel] = cconjmul(gk[rel], v[c]);
@@ -476,7 +485,7 @@ __global__ void __launch_bounds__(RowCfg<P>::NT, RowCfg<P>::MINB) k_pass_c(PassA
     const AdjTap* xa = a.xadj + (long long)gp * n;
 #pragma unroll
     for (int c = 0; c < 16; ++c) {
-      const int ip = t + F::T * c;
+      const int ip = F::pos(t, c);
       if (!valid || ip >= n) continue;
       const AdjTap at = xa[ip];
       float2 h = make_float2(0.f, 0.f);

@@ -56,7 +56,7 @@ def _geo(**kw):
     (dict(n=63), 1), (dict(n=8), 1), (dict(pad=32), 1), (dict(n_dist=0), 1), (dict(n_dist=9), 1),
     (dict(z=(5e-4, 4e-4, 6e-4, 7e-4)), 1), (dict(z=(4e-4, 5e-4, 6e-4, 2.0)), 1),
     (dict(wavelength=-1.0), 1), (dict(chunk=9), 1), (dict(n_angles=0), 1),
-    (dict(pad=96), 7), (dict(pad=8192, n=64), 7),
+    (dict(pad=80), 7), (dict(pad=112), 7), (dict(pad=6144, n=64), 7), (dict(pad=8192, n=64), 7),
 ])
 def test_create_rejects_bad_geometry(lib, kw, expect):
     g = _geo(**kw)

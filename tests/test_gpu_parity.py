@@ -74,7 +74,8 @@ def make_holo(pr, chunk=0):
 
 # ------------------------------------------------------------------ D_z
 
-@pytest.mark.parametrize("P", [16, 32, 64, 128, 256, 512, 1024, 2048, 4096])
+@pytest.mark.parametrize("P", [16, 32, 64, 128, 256, 512, 1024, 2048, 4096,
+                               48, 96, 192, 384, 768, 1536, 3072])
 def test_propagate_matches_oracle(P):
     from paper_2407_20304_gb300 import Holo
     n = max(16, P // 2)
@@ -91,7 +92,8 @@ def test_propagate_matches_oracle(P):
 
 @pytest.mark.parametrize("n,P,K,ext", [(16, 32, 2, 1.0), (32, 64, 3, 0.0), (64, 128, 2, 1.0),
                                        (100, 256, 2, 1.0), (128, 256, 3, 1.0),
-                                       (24, 64, 1, 1.0)])
+                                       (24, 64, 1, 1.0), (24, 48, 2, 1.0), (48, 96, 2, 0.0),
+                                       (96, 192, 2, 1.0), (192, 384, 2, 1.0)])
 def test_forward_fields_and_loss(n, P, K, ext):
     pr = make_problem(n, P, K, ext=ext, seed=n + K)
     h = make_holo(pr)
@@ -109,6 +111,9 @@ def test_forward_fields_and_loss(n, P, K, ext):
     (16, 32, 2, 4, 1.0, 1.0), (32, 64, 3, 4, 1.0, 1.0), (32, 64, 2, 4, 0.0, 0.0),
     (64, 128, 2, 4, 1.0, 0.0), (100, 256, 2, 4, 1.0, 1.0), (128, 256, 4, 4, 1.0, 1.0),
     (64, 128, 3, 1, 1.0, 1.0), (48, 128, 2, 3, 1.0, 1.0), (256, 512, 2, 4, 1.0, 1.0),
+    # line lengths 3 * 2^k (radix-3 step)
+    (24, 48, 2, 4, 1.0, 1.0), (48, 96, 3, 4, 1.0, 1.0), (96, 192, 2, 3, 1.0, 0.0),
+    (192, 384, 2, 4, 0.0, 0.0), (384, 768, 2, 4, 1.0, 1.0), (700, 1536, 1, 2, 1.0, 1.0),
 ])
 def test_gradient_matches_oracle(n, P, K, J, ext, w_ref):
     pr = make_problem(n, P, K, J=J, ext=ext, w_ref=w_ref, seed=3 * n + J)
