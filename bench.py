@@ -259,11 +259,10 @@ def run_ours(args, w, rank, world, local_rank):
                                          (gqc, gq[1 - cur], eta_q, q, state["gam"][1])):
             beta = 0.0
             if not state["first"]:
-                num = h.dot(gcur, gcur)
-                den = h.dot(gcur, eta) - h.dot(gprev, eta)
+                num, d_new, d_old = h.dy_dots(gcur, gprev, eta)
+                den = d_new - d_old
                 beta = num / den if den > 0 else 0.0
-            h.direction(eta, gcur, beta)
-            h.step(x, eta, gam)
+            h.direction_step(x, eta, gcur, beta, gam)
         state["first"] = False
         state["cur"] = 1 - cur
         return loss
@@ -348,7 +347,7 @@ def run_ours(args, w, rank, world, local_rank):
                    "planes_per_step": planes, "reductions": "f64",
                    "l2": "inputs larger than L2 (psi chunk %.1f GB, data %.1f GB per GPU)"
                          % (K * n * n * 8 / 1e9, K * J * n * n * 4 / 1e9),
-                   "step": "set_probe + gradient (F2, grad_psi, grad_q) + DY direction + step"},
+                   "step": "set_probe + gradient (F2, grad_psi, grad_q) + DY inner products + fused direction/step"},
         "roofline": roof, "clocks": clocks, "gpu_launches": launches, "per_pass": per_pass,
         "final_loss": loss,
     }

@@ -57,7 +57,7 @@ typedef enum {
   HOLO_ERR_TIMEOUT = 4,     /* a bounded device wait gave up */
   HOLO_ERR_STATE = 5,       /* call order: shifts / data / probe not set yet */
   HOLO_ERR_NUMERIC = 6,     /* non-finite loss */
-  HOLO_ERR_UNSUPPORTED = 7  /* valid but unsupported size (e.g. P not a power of two) */
+  HOLO_ERR_UNSUPPORTED = 7  /* valid but unsupported size (e.g. P = 80 or P > 4096) */
 } holo_status;
 
 #define HOLO_MAX_DIST 8
@@ -71,7 +71,8 @@ typedef enum {
  * Instrument geometry and discretisation (Table 1 lists the paper's instrument).
  *   n           psi / detector side in pixels; even, 16 <= n <= pad.
  *   pad         P, the side of the grid on which q lives and fields propagate; 0 means
- *               2n.  Supported: powers of two 16 .. 4096 with P - n even.
+ *               2n.  Supported: 2^k (16 .. 4096) and 3 * 2^k (48 .. 3072), with
+ *               P - n even.
  *   n_angles    N_theta: number of projection angles of the whole problem (indexing of
  *               shifts and data).
  *   n_dist      N_z: number of sample planes, 1 .. HOLO_MAX_DIST.
@@ -169,6 +170,19 @@ holo_status holo_step(holo_ctx* ctx, void* x, const void* eta, double gamma, lon
  * Eq. DaiYuan2 (beta = 0 restarts with the steepest-descent direction). */
 holo_status holo_direction(holo_ctx* ctx, void* eta, const void* g, double beta,
                            long long n_c64);
+
+/* The three inner products of the Dai-Yuan coefficient (Eq. DaiYuan2) in one pass over
+ * the vectors (dev complex64 [n_c64] each): out[0] = Re <g, g>, out[1] = Re <g, eta>,
+ * out[2] = Re <g_prev, eta>, each accumulated like holo_dot (FP32 over 16 elements, then
+ * FP64), so beta_DY = out[0] / (out[1] - out[2]).  out: host double[3], written before the
+ * call returns (the context's stream is synchronised). */
+holo_status holo_dy_dots(holo_ctx* ctx, const void* g, const void* g_prev, const void* eta,
+                         long long n_c64, double* out);
+
+/* eta = -g + beta * eta, then x += gamma * eta with the new eta, in one pass over the
+ * vectors (dev complex64 [n_c64] each): holo_direction followed by holo_step, bit for bit. */
+holo_status holo_direction_step(holo_ctx* ctx, void* x, void* eta, const void* g, double beta,
+                                double gamma, long long n_c64);
 
 /* Per-pass device timing (CUDA events recorded on the context's stream around each
  * launch group).  Pass ids: */

@@ -66,8 +66,8 @@ class Reconstruction:
 
     def _direction(self, b, g_new):
         g_old, eta = self.g[b], self.eta[b]
-        num = self.h.dot(g_new, g_new)
-        den = self.h.dot(g_new, eta) - self.h.dot(g_old, eta)
+        num, d_new, d_old = self.h.dy_dots(g_new, g_old, eta)
+        den = d_new - d_old
         beta = num / den if den > 0 else 0.0
         self.h.direction(eta, g_new, beta)
         return beta

@@ -82,8 +82,8 @@ struct holo_ctx {
   holo::Tap* d_ytap = nullptr;
   holo::AdjTap* d_xadj = nullptr;
   holo::AdjTap* d_yadj = nullptr;
-  int* d_rowstart = nullptr;
-  std::vector<int> rowstart;
+  int2* d_lines = nullptr;      // line -> {plane, box row}
+  std::vector<int> rowstart;    // first line of each plane (host)
   int tap_stride = 0;
   size_t tap_bytes = 0;
   // data
@@ -107,8 +107,9 @@ struct holo_ctx {
   float2* d_rref = nullptr;     // n*n
   double* d_part = nullptr;
   long long part_cap = 0;
-  double* d_red = nullptr;      // 4 doubles
-  double* h_red = nullptr;      // pinned, 4 doubles
+  double* d_dot3 = nullptr;     // partial sums of holo_dy_dots: 3 x (8 x SM count)
+  double* d_red = nullptr;      // 8 doubles: loss, reference term, dot, running loss, DY dots
+  double* h_red = nullptr;      // pinned, 8 doubles
   // host-buffer staging
   float2* s_psi = nullptr;
   float2* s_gpsi = nullptr;
@@ -417,7 +418,7 @@ PassArgs pass_args(holo_ctx* c, int k0, int nk, const void* psi) {
   a.xadj = c->d_xadj;
   a.yadj = c->d_yadj;
   a.tap_stride = c->tap_stride;
-  a.rowstart = c->d_rowstart;
+  a.lines = c->d_lines;
   a.line0 = c->rowstart[(size_t)k0 * c->J];
   a.nlines = c->rowstart[(size_t)(k0 + nk) * c->J] - a.line0;
   a.pass_b_items = c->ops->pass_b_groups(c->n);
@@ -617,9 +618,9 @@ holo_status holo_create(const holo_geometry* geo, void* stream, holo_ctx** out) 
       (st = dalloc(c, (void**)&c->d_Gp, cP * P)) ||
       (st = dalloc(c, (void**)&c->d_T, sizeof(float2) * (size_t)n * n)) ||
       (st = dalloc(c, (void**)&c->d_rref, sizeof(float2) * (size_t)n * n)) ||
-      (st = dalloc(c, (void**)&c->d_red, 4 * sizeof(double))))
+      (st = dalloc(c, (void**)&c->d_red, 8 * sizeof(double))))
     return bail(st);
-  if (cudaMallocHost((void**)&c->h_red, 4 * sizeof(double)) != cudaSuccess) {
+  if (cudaMallocHost((void**)&c->h_red, 8 * sizeof(double)) != cudaSuccess) {
     cudaGetLastError();
     return bail(HOLO_ERR_OOM);
   }
@@ -645,9 +646,9 @@ holo_status holo_destroy(holo_ctx* c) {
                   c->d_chirp_tmp, c->d_planes, c->d_pj,          c->d_b,
                   c->ybuf,    c->gkbuf,        c->d_scratch,
                   c->d_Gp,    c->d_T,          c->d_rref,        c->d_part,
-                  c->d_red,   c->s_psi,        c->s_gpsi,        c->s_data,
+                  c->d_red,   c->d_dot3,       c->s_psi,         c->s_gpsi,        c->s_data,
                   c->s_q,     c->s_gq,         c->d_xtap,        c->d_ytap,
-                  c->d_xadj,  c->d_yadj,       c->d_rowstart};
+                  c->d_xadj,  c->d_yadj,       c->d_lines};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   if (c->h_red) cudaFreeHost(c->h_red);
@@ -691,26 +692,29 @@ holo_status holo_set_shifts(holo_ctx* c, const float* t) {
     axis_taps(mt, d.ty, n, P, d.by0, d.bys, &yt[p * stride], &ya[p * n]);
     c->rowstart[p + 1] = c->rowstart[p] + d.bys;
   }
+  std::vector<int2> lines((size_t)c->rowstart[np_all]);
+  for (size_t p = 0; p < np_all; ++p)
+    for (int r = 0; r < c->planes[p].bys; ++r) lines[(size_t)c->rowstart[p] + r] = make_int2((int)p, r);
   holo_status st;
   {
-    void* olds[] = {c->d_xtap, c->d_ytap, c->d_xadj, c->d_yadj, c->d_rowstart};
+    void* olds[] = {c->d_xtap, c->d_ytap, c->d_xadj, c->d_yadj, c->d_lines};
     for (void* o : olds)
       if (o) cudaFree(o);
     c->bytes -= (long long)c->tap_bytes;
     c->d_xtap = c->d_ytap = nullptr;
     c->d_xadj = c->d_yadj = nullptr;
-    c->d_rowstart = nullptr;
+    c->d_lines = nullptr;
     const size_t tb = sizeof(holo::Tap) * xt.size(), ab = sizeof(holo::AdjTap) * xa.size(),
-                 rb = sizeof(int) * c->rowstart.size();
+                 rb = sizeof(int2) * lines.size();
     if ((st = dalloc(c, (void**)&c->d_xtap, tb)) || (st = dalloc(c, (void**)&c->d_ytap, tb)) ||
         (st = dalloc(c, (void**)&c->d_xadj, ab)) || (st = dalloc(c, (void**)&c->d_yadj, ab)) ||
-        (st = dalloc(c, (void**)&c->d_rowstart, rb)))
+        (st = dalloc(c, (void**)&c->d_lines, rb)))
       return st;
     c->tap_bytes = 2 * tb + 2 * ab + rb;
     c->bytes -= 0;
     if ((st = upload(c, c->d_xtap, xt.data(), tb)) || (st = upload(c, c->d_ytap, yt.data(), tb)) ||
         (st = upload(c, c->d_xadj, xa.data(), ab)) || (st = upload(c, c->d_yadj, ya.data(), ab)) ||
-        (st = upload(c, c->d_rowstart, c->rowstart.data(), rb)))
+        (st = upload(c, c->d_lines, lines.data(), rb)))
       return st;
     c->tap_stride = stride;
   }
@@ -874,6 +878,46 @@ holo_status holo_dot(holo_ctx* c, const void* a, const void* b, long long n, dou
                              c->stream));
   HOLO_CK(c, cudaStreamSynchronize(c->stream));
   *re_out = c->h_red[2];
+  return HOLO_OK;
+}
+
+holo_status holo_dy_dots(holo_ctx* c, const void* g, const void* g_prev, const void* eta,
+                         long long n, double* out) {
+  if (!c || !g || !g_prev || !eta || !out || n < 0) return fail(c, HOLO_ERR_ARG, "bad argument");
+  // enough blocks to fill every SM (8 resident blocks of 256 threads each)
+  int dev = 0, sms = 0;
+  cudaGetDevice(&dev);
+  if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms < 1) {
+    cudaGetLastError();
+    sms = 1;
+  }
+  const long long cap = 8LL * sms;
+  if (!c->d_dot3) {
+    holo_status st = dalloc(c, (void**)&c->d_dot3, sizeof(double) * 3 * cap);
+    if (st) return st;
+  }
+  long long nb = (n + 256 * 16 - 1) / (256 * 16);
+  nb = std::max(1LL, std::min(nb, cap));
+  PassTimer tm(c, HOLO_T_REDUCE);
+  HOLO_LAUNCH(c, holo::launch_dot3((const float2*)g, (const float2*)g_prev, (const float2*)eta, n,
+                                   c->d_dot3, (int)nb, c->stream));
+  for (int i = 0; i < 3; ++i)
+    HOLO_LAUNCH(c, holo::launch_sum_f64(c->d_dot3 + i * nb, (int)nb, c->d_red + 4 + i, 0,
+                                        c->stream));
+  HOLO_CK(c, cudaMemcpyAsync(c->h_red + 4, c->d_red + 4, 3 * sizeof(double),
+                             cudaMemcpyDeviceToHost, c->stream));
+  HOLO_CK(c, cudaStreamSynchronize(c->stream));
+  for (int i = 0; i < 3; ++i) out[i] = c->h_red[4 + i];
+  return HOLO_OK;
+}
+
+holo_status holo_direction_step(holo_ctx* c, void* x, void* eta, const void* g, double beta,
+                                double gamma, long long n) {
+  if (!c || !x || !eta || !g || n < 0 || !std::isfinite(beta) || !std::isfinite(gamma))
+    return fail(c, HOLO_ERR_ARG, "bad argument");
+  PassTimer tm(c, HOLO_T_VECTOR);
+  HOLO_LAUNCH(c, holo::launch_direction_step((float2*)x, (float2*)eta, (const float2*)g,
+                                             (float)beta, (float)gamma, n, c->stream));
   return HOLO_OK;
 }
 

@@ -1,5 +1,6 @@
 // Line-length independent kernels: pass D (grad_psi), the reductions feeding grad_q and the
 // loss, FP64 inner products (Eq. DaiYuan2 coefficients) and the CG vector updates.
+#include "holo.h"
 #include "holo_internal.h"
 #include "holo_kernels.cuh"
 
@@ -13,49 +14,103 @@ constexpr int kThreads = 256;
 // resample gathered from the (at most two) box rows whose taps reach psi row i, summed
 // over the distances j (Eq. gradpsi: grad = 2 sum_j L*_kj r_kj).  The rows and weights
 // come from the transposed-tap table of each plane.
-__global__ void k_pass_d(PassArgs a) {
+// One block per (psi row i, angle kl): the transposed row taps of every distance are read
+// once into shared memory, then each thread sums its column pairs over j with all the
+// 16-byte loads of one pair issued together.  h rows start on 16-byte boundaries (n even).
+__global__ void __launch_bounds__(256) k_pass_d(PassArgs a) {
   const int n = a.n, i = blockIdx.x, kl = blockIdx.y;
+  __shared__ const float4* row[HOLO_MAX_DIST];
+  __shared__ float w0s[HOLO_MAX_DIST], w1s[HOLO_MAX_DIST];
+  if (threadIdx.x < a.J) {
+    const int j = threadIdx.x;
+    const long long gp = (long long)(a.k0 + kl) * a.J + j;
+    const AdjTap at = a.yadj[gp * n + i];
+    const PlaneDesc d = a.planes[gp];
+    const float2* h = a.ybuf + (long long)(kl * a.J + j) * a.ystride;
+    // rows X0 and X0 + 1 of the box; a zero weight marks a tap outside it (never read)
+    row[j] = reinterpret_cast<const float4*>(h + (long long)(at.X0 - d.by0) * n);
+    w0s[j] = at.w0;
+    w1s[j] = at.w1;
+  }
+  __syncthreads();
+  const int half = n / 2;
   float2* out = a.grad_psi + ((long long)kl * n + i) * n;
-  for (int ip = threadIdx.x; ip < n; ip += blockDim.x) {
-    float2 acc = make_float2(0.f, 0.f);
-    for (int j = 0; j < a.J; ++j) {
-      const long long gp = (long long)(a.k0 + kl) * a.J + j;
-      const AdjTap at = a.yadj[gp * n + i];
-      const PlaneDesc d = a.planes[gp];
-      const float2* h = a.ybuf + (long long)(kl * a.J + j) * a.ystride;
-      const int r0 = at.X0 - d.by0;
-      if (at.w0 != 0.f) {
-        const float2 z = h[(long long)r0 * n + ip];
-        acc.x = fmaf(at.w0, z.x, acc.x);
-        acc.y = fmaf(at.w0, z.y, acc.y);
-      }
-      if (at.w1 != 0.f) {
-        const float2 z = h[(long long)(r0 + 1) * n + ip];
-        acc.x = fmaf(at.w1, z.x, acc.x);
-        acc.y = fmaf(at.w1, z.y, acc.y);
+  for (int p = threadIdx.x; p < half; p += blockDim.x) {
+    float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+    for (int j = 0; j < HOLO_MAX_DIST; ++j) {
+      if (j < a.J) {
+        const float w0 = w0s[j], w1 = w1s[j];
+        if (w0 != 0.f) {
+          const float4 z = __ldg(row[j] + p);
+          acc.x = fmaf(w0, z.x, acc.x);
+          acc.y = fmaf(w0, z.y, acc.y);
+          acc.z = fmaf(w0, z.z, acc.z);
+          acc.w = fmaf(w0, z.w, acc.w);
+        }
+        if (w1 != 0.f) {
+          const float4 z = __ldg(row[j] + half + p);
+          acc.x = fmaf(w1, z.x, acc.x);
+          acc.y = fmaf(w1, z.y, acc.y);
+          acc.z = fmaf(w1, z.z, acc.z);
+          acc.w = fmaf(w1, z.w, acc.w);
+        }
       }
     }
-    float2 r = make_float2(2.f * acc.x, 2.f * acc.y);
-    if (a.accumulate) r = cadd(r, out[ip]);
-    out[ip] = r;
+    float2 r0 = make_float2(2.f * acc.x, 2.f * acc.y), r1 = make_float2(2.f * acc.z, 2.f * acc.w);
+    if (a.accumulate) {
+      r0 = cadd(r0, out[2 * p]);
+      r1 = cadd(r1, out[2 * p + 1]);
+    }
+    out[2 * p] = r0;
+    out[2 * p + 1] = r1;
   }
 }
 
-// G'_j on the union box of the chunk: sum over angles (fixed order) of conj(w_kj) v_kj.
-__global__ void k_reduce_g(PassArgs a, float2* Gp, int j, int row0, int nrows, int col0,
-                           int ncols) {
+// G'_j on the union box of the chunk: sum over angles (ascending, a fixed order) of
+// conj(w_kj) v_kj.  Each thread owns kReduceEpt elements; the box descriptors of the angles
+// are staged in shared memory a tile at a time, and the loads of a few angles are issued
+// together (the additions stay in angle order).
+constexpr int kReduceEpt = 4;
+constexpr int kReduceTile = 128;
+__global__ void __launch_bounds__(256) k_reduce_g(PassArgs a, float2* Gp, int j, int row0, int nrows,
+                                                  int col0, int ncols) {
+  __shared__ int4 box[kReduceTile];
   const long long total = (long long)nrows * ncols;
-  for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < total;
-       idx += (long long)gridDim.x * blockDim.x) {
-    const int Y = row0 + (int)(idx / ncols), X = col0 + (int)(idx % ncols);
-    float2 acc = make_float2(0.f, 0.f);
-    for (int kl = 0; kl < a.nk; ++kl) {
-      const PlaneDesc d = a.planes[(long long)(a.k0 + kl) * a.J + j];
-      const int ry = Y - d.by0, rx = X - d.bx0;
-      if ((unsigned)ry < (unsigned)d.bys && (unsigned)rx < (unsigned)d.bxs)
-        acc = cadd(acc, a.gkbuf[(long long)(kl * a.J + j) * a.gkstride + (long long)ry * d.bxs + rx]);
+  const long long base = (long long)blockIdx.x * blockDim.x * kReduceEpt + threadIdx.x;
+  int Y[kReduceEpt], X[kReduceEpt];
+  float2 acc[kReduceEpt];
+#pragma unroll
+  for (int e = 0; e < kReduceEpt; ++e) {
+    const long long idx = base + (long long)e * blockDim.x;
+    Y[e] = idx < total ? row0 + (int)(idx / ncols) : -(1 << 30);
+    X[e] = idx < total ? col0 + (int)(idx % ncols) : -(1 << 30);
+    acc[e] = make_float2(0.f, 0.f);
+  }
+  for (int kt = 0; kt < a.nk; kt += kReduceTile) {
+    const int nt = min(kReduceTile, a.nk - kt);
+    __syncthreads();
+    if (threadIdx.x < nt) {
+      const PlaneDesc d = a.planes[(long long)(a.k0 + kt + threadIdx.x) * a.J + j];
+      box[threadIdx.x] = make_int4(d.by0, d.bys, d.bx0, d.bxs);
     }
-    Gp[idx] = acc;
+    __syncthreads();
+#pragma unroll 4
+    for (int kk = 0; kk < nt; ++kk) {
+      const int4 d = box[kk];
+      const float2* gk = a.gkbuf + (long long)((kt + kk) * a.J + j) * a.gkstride;
+#pragma unroll
+      for (int e = 0; e < kReduceEpt; ++e) {
+        const int ry = Y[e] - d.x, rx = X[e] - d.z;
+        if ((unsigned)ry < (unsigned)d.y && (unsigned)rx < (unsigned)d.w)
+          acc[e] = cadd(acc[e], __ldg(gk + (long long)ry * d.w + rx));
+      }
+    }
+  }
+#pragma unroll
+  for (int e = 0; e < kReduceEpt; ++e) {
+    const long long idx = base + (long long)e * blockDim.x;
+    if (idx < total) Gp[idx] = acc[e];
   }
 }
 
@@ -113,6 +168,50 @@ __global__ void k_dot(const float2* __restrict__ a, const float2* __restrict__ b
   if (threadIdx.x == 0) part[blockIdx.x] = s;
 }
 
+// The three inner products of the Dai-Yuan coefficient in one pass: Re<g, g>, Re<g, eta>,
+// Re<g_prev, eta>, with the grouping of k_dot (FP32 over 16 elements, then FP64).  Partial
+// sums of block b go to part[b], part[nb + b], part[2 nb + b].
+__global__ void k_dot3(const float2* __restrict__ g, const float2* __restrict__ gp,
+                       const float2* __restrict__ eta, long long n, double* part) {
+  __shared__ double red[32];
+  double a0 = 0.0, a1 = 0.0, a2 = 0.0;
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  while (e < n) {
+    float s0 = 0.f, s1 = 0.f, s2 = 0.f;
+#pragma unroll 4
+    for (int r = 0; r < 16 && e < n; ++r, e += stride) {
+      const float2 x = g[e], y = gp[e], d = eta[e];
+      s0 = fmaf(x.x, x.x, fmaf(x.y, x.y, s0));
+      s1 = fmaf(x.x, d.x, fmaf(x.y, d.y, s1));
+      s2 = fmaf(y.x, d.x, fmaf(y.y, d.y, s2));
+    }
+    a0 += (double)s0;
+    a1 += (double)s1;
+    a2 += (double)s2;
+  }
+  const double r0 = block_sum_f64(a0, red);
+  const double r1 = block_sum_f64(a1, red);
+  const double r2 = block_sum_f64(a2, red);
+  if (threadIdx.x == 0) {
+    part[blockIdx.x] = r0;
+    part[gridDim.x + blockIdx.x] = r1;
+    part[2 * gridDim.x + blockIdx.x] = r2;
+  }
+}
+
+// eta = -g + beta eta, then x += gamma eta (the new eta): holo_direction then holo_step.
+__global__ void k_direction_step(float2* __restrict__ x, float2* __restrict__ eta,
+                                 const float2* __restrict__ g, float beta, float gamma, long long n) {
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n;
+       e += (long long)gridDim.x * blockDim.x) {
+    const float2 a = eta[e], d = g[e], xo = x[e];
+    const float2 en = make_float2(fmaf(beta, a.x, -d.x), fmaf(beta, a.y, -d.y));
+    eta[e] = en;
+    x[e] = make_float2(fmaf(gamma, en.x, xo.x), fmaf(gamma, en.y, xo.y));
+  }
+}
+
 __global__ void k_axpy(float2* __restrict__ x, const float2* __restrict__ eta, float gamma,
                        long long n) {
   for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n;
@@ -157,7 +256,7 @@ int grid_for(long long n) {
 
 cudaError_t launch_pass_d(const PassArgs& a, cudaStream_t s) {
   dim3 grid(a.n, a.nk);
-  k_pass_d<<<grid, a.n >= 1024 ? 512 : kThreads, 0, s>>>(a);
+  k_pass_d<<<grid, 256, 0, s>>>(a);
   return cudaGetLastError();
 }
 
@@ -165,7 +264,8 @@ cudaError_t launch_reduce_g(const PassArgs& a, float2* Gp, int j, int row0, int 
                             int ncols, cudaStream_t s) {
   const long long total = (long long)nrows * ncols;
   if (total <= 0) return cudaSuccess;
-  k_reduce_g<<<grid_for(total), kThreads, 0, s>>>(a, Gp, j, row0, nrows, col0, ncols);
+  const long long per = 256LL * kReduceEpt;
+  k_reduce_g<<<(unsigned)((total + per - 1) / per), 256, 0, s>>>(a, Gp, j, row0, nrows, col0, ncols);
   return cudaGetLastError();
 }
 
@@ -189,6 +289,19 @@ cudaError_t launch_loss_total(double* red, double wref, int acc, cudaStream_t s)
 cudaError_t launch_dot(const float2* a, const float2* b, long long n, double* part, int nblocks,
                        cudaStream_t s) {
   k_dot<<<nblocks, kThreads, 0, s>>>(a, b, n, part);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_dot3(const float2* g, const float2* gp, const float2* eta, long long n,
+                        double* part, int nblocks, cudaStream_t s) {
+  k_dot3<<<nblocks, kThreads, 0, s>>>(g, gp, eta, n, part);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_direction_step(float2* x, float2* eta, const float2* g, float beta, float gamma,
+                                  long long n, cudaStream_t s) {
+  if (n <= 0) return cudaSuccess;
+  k_direction_step<<<grid_for(n), kThreads, 0, s>>>(x, eta, g, beta, gamma, n);
   return cudaGetLastError();
 }
 

@@ -82,8 +82,9 @@ struct PassArgs {
   const AdjTap* xadj;          // [planes][n]: columns of psi
   const AdjTap* yadj;          // [planes][n]: rows of psi
   int tap_stride;
-  // rows of all planes in one flat list: plane p owns lines [rowstart[p], rowstart[p+1])
-  const int* rowstart;         // [n_angles * J + 1] (global plane index)
+  // rows of all planes in one flat list (plane p owns a contiguous run of its box rows):
+  // line -> {global plane, row within the plane's box}
+  const int2* lines;           // [total box rows of all planes]
   int line0, nlines;           // the chunk's lines: [line0, line0 + nlines)
   int pass_b_items;            // column groups of pass B
 };
@@ -114,6 +115,10 @@ cudaError_t launch_sum_f64(const double* part, int count, double* out, int accum
 cudaError_t launch_loss_total(double* red, double wref, int acc, cudaStream_t s);
 cudaError_t launch_dot(const float2* a, const float2* b, long long n, double* part, int nblocks,
                        cudaStream_t s);
+cudaError_t launch_dot3(const float2* g, const float2* gp, const float2* eta, long long n,
+                        double* part, int nblocks, cudaStream_t s);
+cudaError_t launch_direction_step(float2* x, float2* eta, const float2* g, float beta, float gamma,
+                                  long long n, cudaStream_t s);
 cudaError_t launch_axpy(float2* x, const float2* eta, float gamma, long long n, cudaStream_t s);
 cudaError_t launch_direction(float2* eta, const float2* g, float beta, long long n,
                              cudaStream_t s);

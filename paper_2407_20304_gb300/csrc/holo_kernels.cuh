@@ -135,18 +135,8 @@ __device__ __forceinline__ void load_chirp_half(float2* dst, const float2* __res
   for (int i = threadIdx.x; i <= P / 2; i += blockDim.x) dst[i] = src[i];
 }
 
-// Plane of flat line `line` (global line numbering): largest p with rowstart[p] <= line.
-__device__ __forceinline__ int plane_of_line(const int* __restrict__ rowstart, int lo, int hi,
-                                             int line) {
-  // invariant: rowstart[lo] <= line < rowstart[hi]
-  while (hi - lo > 1) {
-    const int mid = (lo + hi) >> 1;
-    if (__ldg(rowstart + mid) <= line)
-      lo = mid;
-    else
-      hi = mid;
-  }
-  return lo;
+__device__ __forceinline__ void prefetch_l2(const void* p) {
+  asm volatile("prefetch.global.L2 [%0];" ::"l"(p));
 }
 
 // ------------------------------------------------------------------ generic D-step
@@ -227,15 +217,15 @@ __global__ void __launch_bounds__(RowCfg<P>::NT, RowCfg<P>::MINB) k_pass_a(PassA
   load_roots<P>(roots, a.twiddles);
   const TwRoots tw{roots};
   const int n = a.n, lo = P / 2 - n / 2;
-  const int p_lo = a.k0 * a.J, p_hi = (a.k0 + a.nk) * a.J;
+  const int p_lo = a.k0 * a.J;
   int jcur = -1;
   for (int base = blockIdx.x * R::G; base < a.nlines; base += gridDim.x * R::G) {
     const int li = base + g;
     const bool valid = li < a.nlines;
     const int line = a.line0 + (valid ? li : 0);
-    const int gp = plane_of_line(a.rowstart, p_lo, p_hi, line);
+    const int2 L = __ldg(a.lines + line);
+    const int gp = L.x, i = L.y;
     const int lp = gp - p_lo, kl = lp / a.J, j = lp % a.J;
-    const int i = line - __ldg(a.rowstart + gp);
     const PlaneDesc d = a.planes[gp];
     const Tap yt = a.ytap[(long long)gp * a.tap_stride + i];
     const Tap* xt = a.xtap + (long long)gp * a.tap_stride;
@@ -245,7 +235,7 @@ __global__ void __launch_bounds__(RowCfg<P>::NT, RowCfg<P>::MINB) k_pass_a(PassA
     // lines of one block may belong to different distances only when G > 1; the chirp
     // table then follows the distance of the block's first line (block-uniform) and the
     // other lines read the chirp from global memory.
-    const int jb = (plane_of_line(a.rowstart, p_lo, p_hi, a.line0 + base) - p_lo) % a.J;
+    const int jb = (__ldg(a.lines + a.line0 + base).x - p_lo) % a.J;
     float2 v[16];
 #pragma unroll
     for (int c = 0; c < 16; ++c) {
@@ -286,10 +276,6 @@ template <int P>
 size_t pass_b_smem(int n) {
   return (size_t)(SmemHead<P>::WORDS + ColCfg<P>::C * ColCfg<P>::LS + 2 * n * ColCfg<P>::C) *
          sizeof(float2);
-}
-
-__device__ __forceinline__ void prefetch_l2(const void* p) {
-  asm volatile("prefetch.global.L2 [%0];" ::"l"(p));
 }
 
 // Each block owns whole column groups (C adjacent detector columns) and walks every plane
@@ -438,16 +424,16 @@ __global__ void __launch_bounds__(RowCfg<P>::NT, RowCfg<P>::MINB) k_pass_c(PassA
   load_roots<P>(roots, a.twiddles);
   const TwRoots tw{roots};
   const int n = a.n, lo = P / 2 - n / 2;
-  const int p_lo = a.k0 * a.J, p_hi = (a.k0 + a.nk) * a.J;
+  const int p_lo = a.k0 * a.J;
   int jcur = -1;
   for (int base = blockIdx.x * R::G; base < a.nlines; base += gridDim.x * R::G) {
     const int li = base + g;
     const bool valid = li < a.nlines;
     const int line = a.line0 + (valid ? li : 0);
-    const int gp = plane_of_line(a.rowstart, p_lo, p_hi, line);
+    const int2 L = __ldg(a.lines + line);
+    const int gp = L.x, i = L.y;
     const int lp = gp - p_lo, j = lp % a.J;
-    const int i = line - __ldg(a.rowstart + gp);
-    const int jb = (plane_of_line(a.rowstart, p_lo, p_hi, a.line0 + base) - p_lo) % a.J;
+    const int jb = (__ldg(a.lines + a.line0 + base).x - p_lo) % a.J;
     float2* yrow = a.ybuf + (long long)lp * a.ystride + (long long)i * n;
     float2 v[16];
 #pragma unroll

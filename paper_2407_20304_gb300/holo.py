@@ -238,6 +238,29 @@ class Holo:
                                      _ptr(g, torch.complex64, None, "g"), float(beta), eta.numel())
         _check(self.lib, self.ctx, st, "holo_direction")
 
+    def dy_dots(self, g, g_prev, eta):
+        """(Re <g, g>, Re <g, eta>, Re <g_prev, eta>) in one pass (Eq. DaiYuan2)."""
+        import torch
+        if not (g.shape == g_prev.shape == eta.shape):
+            raise ValueError("shape mismatch")
+        out = (ctypes.c_double * 3)()
+        st = self.lib.holo_dy_dots(self.ctx, _ptr(g, torch.complex64, None, "g"),
+                                   _ptr(g_prev, torch.complex64, None, "g_prev"),
+                                   _ptr(eta, torch.complex64, None, "eta"), g.numel(), out)
+        _check(self.lib, self.ctx, st, "holo_dy_dots")
+        return out[0], out[1], out[2]
+
+    def direction_step(self, x, eta, g, beta, gamma):
+        """eta = -g + beta * eta, then x += gamma * eta, in one pass."""
+        import torch
+        if not (x.shape == eta.shape == g.shape):
+            raise ValueError("shape mismatch")
+        st = self.lib.holo_direction_step(self.ctx, _ptr(x, torch.complex64, None, "x"),
+                                          _ptr(eta, torch.complex64, None, "eta"),
+                                          _ptr(g, torch.complex64, None, "g"), float(beta),
+                                          float(gamma), x.numel())
+        _check(self.lib, self.ctx, st, "holo_direction_step")
+
     def set_stream(self, stream):
         """Issue later work on `stream` (a torch.cuda.Stream)."""
         _check(self.lib, self.ctx, self.lib.holo_set_stream(self.ctx, ctypes.c_void_p(stream.cuda_stream)),

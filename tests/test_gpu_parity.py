@@ -197,6 +197,36 @@ def test_dot_step_direction():
         np.testing.assert_allclose(e.cpu().numpy(), -b + np.float32(-1.5) * a, rtol=1e-6, atol=1e-6)
 
 
+def test_dy_dots_and_fused_direction_step():
+    """One-pass DY inner products against FP64 NumPy and against the oracle's beta; the
+    fused direction + step equals holo_direction then holo_step bit for bit."""
+    from paper_2407_20304_gb300 import Holo
+    from oracle import cg as ocg
+    h = Holo(16, 1, 1, G["wavelength"], G["pixel"], G["Z"], G["z"][:1], pad=32)
+    rng = np.random.default_rng(5)
+    for n in (1, 4097, 300001):
+        g, gp, eta, x = [(rng.standard_normal(n) + 1j * rng.standard_normal(n)).astype(np.complex64)
+                         for _ in range(4)]
+        got = h.dy_dots(dev(g, torch.complex64), dev(gp, torch.complex64), dev(eta, torch.complex64))
+        c = lambda u: u.astype(np.complex128)
+        ref = (np.real(np.vdot(c(g), c(g))), np.real(np.vdot(c(g), c(eta))),
+               np.real(np.vdot(c(gp), c(eta))))
+        for a_, b_ in zip(got, ref):
+            assert abs(a_ - b_) <= 1e-5 * np.sqrt(n) * (abs(b_) + 1)
+        beta_ref = ocg.dai_yuan_beta(c(g), c(gp), c(eta))
+        den = got[1] - got[2]
+        if abs(den) > 1e-3 * np.sqrt(n):
+            assert (den > 0) == (beta_ref is not None)
+        if den > 0 and beta_ref is not None:
+            assert abs(got[0] / den - beta_ref) <= 1e-4 * abs(beta_ref) + 1e-12
+        x1, e1 = dev(x, torch.complex64), dev(eta, torch.complex64)
+        h.direction(e1, dev(g, torch.complex64), 0.63)
+        h.step(x1, e1, -0.21)
+        x2, e2 = dev(x, torch.complex64), dev(eta, torch.complex64)
+        h.direction_step(x2, e2, dev(g, torch.complex64), 0.63, -0.21)
+        assert torch.equal(x1, x2) and torch.equal(e1, e2)
+
+
 def test_state_and_argument_errors():
     from paper_2407_20304_gb300 import Holo, HoloError
     h = Holo(32, 2, 2, G["wavelength"], G["pixel"], G["Z"], G["z"][:2], pad=64)
