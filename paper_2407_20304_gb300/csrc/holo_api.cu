@@ -57,12 +57,24 @@ using holo::LineArgs;
 using holo::PassArgs;
 using holo::PlaneDesc;
 
+// holo_gradient_host splits a chunk of at least 2 kHostMinPart angles into at most
+// kHostParts parts so that host<->device copies of one part overlap the planes of another.
+// Part sizes follow kHostWeights: a small first part (the copy nothing hides) and a small
+// last part (the result copy nothing hides).
+constexpr int kHostParts = 8;
+constexpr int kHostMinPart = 2;
+constexpr int kHostWeights[kHostParts] = {1, 2, 3, 3, 3, 3, 3, 2};
+
 struct holo_ctx {
   holo_geometry geo{};
   int n = 0, P = 0, J = 0, K = 0, chunk = 0;
   float ext = 1.f;
   double wref = 0.0;
   cudaStream_t stream = nullptr;
+  // holo_gradient_host in parts: copy streams and their events (created on first use)
+  cudaStream_t cs_in = nullptr, cs_out = nullptr;
+  cudaEvent_t ev_start = nullptr, ev_out = nullptr;
+  cudaEvent_t ev_in[kHostParts] = {}, ev_done[kHostParts] = {};
   const holo::Ops* ops = nullptr;
   double mt[HOLO_MAX_DIST] = {}, omega[HOLO_MAX_DIST] = {}, zeta[HOLO_MAX_DIST] = {},
          zhat[HOLO_MAX_DIST] = {};
@@ -425,26 +437,34 @@ PassArgs pass_args(holo_ctx* c, int k0, int nk, const void* psi) {
   return a;
 }
 
-// Passes A, B (and C, D for gradients), loss partial sums into d_red[0], reference term
-// into d_red[1] (only when k0 == 0 and w_ref != 0).
-holo_status run_eval(holo_ctx* c, PassArgs& a, bool gradient, float2* grad_q, unsigned flags) {
+// One evaluation is split in three phases so that holo_gradient_host can run the planes of
+// a chunk in parts while copies overlap:
+//   eval_begin:  reference residual r_ref and its loss (only for the chunk with k0 == 0 and
+//                w_ref != 0) into d_red[1], else d_red[1] = 0;
+//   eval_planes: passes A, B (and C, D for gradients) of the angles of `a`; plane loss into
+//                d_red[0] and the call / running totals (k_loss_total); pass B writes or adds
+//                T = ext sum_kj r_kj (+ w_ref r_ref on the first part);
+//   eval_qgrad:  grad_q of the whole chunk from T and the per-plane conj(w) v.
+holo_status eval_begin(holo_ctx* c, PassArgs& a) {
+  PassTimer tm_red(c, HOLO_T_REDUCE);
   const int nbx = c->ops->pass_b_blocks(a.pass_b_items, c->n, a.max_box_rows);
-  const long long nparts = nbx;
-  const bool ref = a.k0 == 0 && c->wref != 0.0;
   const long long n2 = (long long)c->n * c->n;
-  {
-    PassTimer tm_red(c, HOLO_T_REDUCE);
-    if (ref) {
-      // reference residual first: pass B folds w_ref r_ref into the grad_q source
-      HOLO_LAUNCH(c, holo::launch_ref_residual(c->d_b, c->sqrt_dref, n2, c->d_rref,
-                                               c->d_part + nparts, kRefBlocks, c->stream));
-      HOLO_LAUNCH(c, holo::launch_sum_f64(c->d_part + nparts, kRefBlocks, c->d_red + 1, 0,
-                                          c->stream));
-      a.rref = c->d_rref;
-    } else {
-      HOLO_CK(c, cudaMemsetAsync(c->d_red + 1, 0, sizeof(double), c->stream));
-    }
+  if (a.k0 == 0 && c->wref != 0.0) {
+    // reference residual first: pass B folds w_ref r_ref into the grad_q source
+    HOLO_LAUNCH(c, holo::launch_ref_residual(c->d_b, c->sqrt_dref, n2, c->d_rref,
+                                             c->d_part + nbx, kRefBlocks, c->stream));
+    HOLO_LAUNCH(c, holo::launch_sum_f64(c->d_part + nbx, kRefBlocks, c->d_red + 1, 0, c->stream));
+    a.rref = c->d_rref;
+  } else {
+    HOLO_CK(c, cudaMemsetAsync(c->d_red + 1, 0, sizeof(double), c->stream));
   }
+  return HOLO_OK;
+}
+
+// first: the first part of the call (adds the reference term, starts the call total);
+// acc: add to the running total (user flags on the first part, always on later parts).
+holo_status eval_planes(holo_ctx* c, PassArgs& a, bool gradient, bool first, int acc) {
+  const int nbx = c->ops->pass_b_blocks(a.pass_b_items, c->n, a.max_box_rows);
   {
     PassTimer tm(c, HOLO_T_PASS_A);
     HOLO_LAUNCH(c, c->ops->pass_a(a, c->stream));
@@ -455,9 +475,8 @@ holo_status run_eval(holo_ctx* c, PassArgs& a, bool gradient, float2* grad_q, un
   }
   {
     PassTimer tm_red(c, HOLO_T_REDUCE);
-    HOLO_LAUNCH(c, holo::launch_sum_f64(c->d_part, (int)nparts, c->d_red, 0, c->stream));
-    HOLO_LAUNCH(c, holo::launch_loss_total(c->d_red, c->wref,
-                                           (flags & (HOLO_ACCUMULATE | HOLO_ACCUMULATE_Q)) ? 1 : 0,
+    HOLO_LAUNCH(c, holo::launch_sum_f64(c->d_part, nbx, c->d_red, 0, c->stream));
+    HOLO_LAUNCH(c, holo::launch_loss_total(c->d_red, first ? c->wref : 0.0, acc, first ? 1 : 0,
                                            c->stream));
   }
   if (!gradient) return HOLO_OK;
@@ -469,12 +488,15 @@ holo_status run_eval(holo_ctx* c, PassArgs& a, bool gradient, float2* grad_q, un
     PassTimer tm(c, HOLO_T_PASS_D);
     HOLO_LAUNCH(c, holo::launch_pass_d(a, c->stream));
   }
+  return HOLO_OK;
+}
+
+// grad_q = 2 [ D_{-zeta_0}( C* T ) + sum_j D_{-omega_j}(G'_j) ] with T = ext sum_kj r_kj +
+// w_ref r_ref written by pass B (zhat_j + omega_j = zeta_0 merges the ext-part of every
+// plane into one propagation).  `a` spans the whole chunk; its gkbuf holds every plane.
+holo_status eval_qgrad(holo_ctx* c, const PassArgs& a, float2* grad_q, int acc) {
   PassTimer tm_q(c, HOLO_T_QGRAD);
-  // grad_q = 2 [ D_{-zeta_0}( C* T ) + sum_j D_{-omega_j}(G'_j) ] with T = ext sum_kj r_kj +
-  // w_ref r_ref written by pass B (zhat_j + omega_j = zeta_0 merges the ext-part of every
-  // plane into one propagation).
   const int P = c->P, n = c->n, lo = P / 2 - n / 2;
-  const int acc = (flags & (HOLO_ACCUMULATE | HOLO_ACCUMULATE_Q)) ? 1 : 0;
   holo_status st = dstep2d(c, c->d_T, lo, n, lo, n, grad_q, 0, P, 0, P, c->d_chirp_zeta0, 1, 2.f,
                            acc);
   if (st != HOLO_OK) return st;
@@ -497,11 +519,20 @@ holo_status run_eval(holo_ctx* c, PassArgs& a, bool gradient, float2* grad_q, un
   return HOLO_OK;
 }
 
+// The whole evaluation of one chunk in one pass over its planes.
+holo_status run_eval(holo_ctx* c, PassArgs& a, bool gradient, float2* grad_q, unsigned flags) {
+  const int acc = (flags & (HOLO_ACCUMULATE | HOLO_ACCUMULATE_Q)) ? 1 : 0;
+  holo_status st;
+  if ((st = eval_begin(c, a)) || (st = eval_planes(c, a, gradient, true, acc))) return st;
+  if (!gradient) return HOLO_OK;
+  return eval_qgrad(c, a, grad_q, acc);
+}
+
 holo_status read_loss(holo_ctx* c, double* loss, unsigned flags) {
-  HOLO_CK(c, cudaMemcpyAsync(c->h_red, c->d_red, 2 * sizeof(double), cudaMemcpyDeviceToHost,
+  HOLO_CK(c, cudaMemcpyAsync(c->h_red + 7, c->d_red + 7, sizeof(double), cudaMemcpyDeviceToHost,
                              c->stream));
   HOLO_CK(c, cudaStreamSynchronize(c->stream));
-  const double l = c->h_red[0] + c->wref * c->h_red[1];
+  const double l = c->h_red[7];
   if (loss) *loss = (flags & (HOLO_ACCUMULATE | HOLO_ACCUMULATE_Q)) ? *loss + l : l;
   if (!std::isfinite(l)) return fail(c, HOLO_ERR_NUMERIC, "non-finite loss");
   return HOLO_OK;
@@ -652,6 +683,14 @@ holo_status holo_destroy(holo_ctx* c) {
   for (void* p : ptrs)
     if (p) cudaFree(p);
   if (c->h_red) cudaFreeHost(c->h_red);
+  for (cudaStream_t st : {c->cs_in, c->cs_out})
+    if (st) cudaStreamDestroy(st);
+  for (cudaEvent_t e : {c->ev_start, c->ev_out})
+    if (e) cudaEventDestroy(e);
+  for (int i = 0; i < kHostParts; ++i) {
+    if (c->ev_in[i]) cudaEventDestroy(c->ev_in[i]);
+    if (c->ev_done[i]) cudaEventDestroy(c->ev_done[i]);
+  }
   for (auto& r : c->recs) {
     cudaEventDestroy(r.a);
     cudaEventDestroy(r.b);
@@ -807,6 +846,85 @@ holo_status holo_gradient(holo_ctx* c, int k0, int nk, const void* psi, double* 
   return read_loss(c, loss, flags);
 }
 
+// holo_gradient_host in `parts` parts of the chunk: part p's psi and data are copied on
+// cs_in while earlier parts run passes A-D on the context's stream, and its grad_psi goes
+// back on cs_out while later parts run.  Pass B adds each part's residual sum into T and
+// every part keeps its conj(w) v in its own slice of the workspace, so grad_q is formed
+// once for the whole chunk at the end.  (The per-part sums of T and of the loss round in a
+// different order than a single pass over the chunk.)
+holo_status gradient_host_parts(holo_ctx* c, int k0, int nk, int parts, const void* psi_host,
+                                const float* sqrt_d_host, const void* q_host, double* loss,
+                                void* grad_psi_host, void* grad_q_host, unsigned flags) {
+  const int n = c->n, P = c->P, J = c->J;
+  const size_t n2 = (size_t)n * n;
+  holo_status st;
+  if (!c->cs_in) {
+    if (cudaStreamCreateWithFlags(&c->cs_in, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaStreamCreateWithFlags(&c->cs_out, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&c->ev_start, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&c->ev_out, cudaEventDisableTiming) != cudaSuccess)
+      return fail(c, HOLO_ERR_CUDA, std::string("copy streams: ") + cudaGetErrorString(cudaGetLastError()));
+    for (int i = 0; i < kHostParts; ++i)
+      if (cudaEventCreateWithFlags(&c->ev_in[i], cudaEventDisableTiming) != cudaSuccess ||
+          cudaEventCreateWithFlags(&c->ev_done[i], cudaEventDisableTiming) != cudaSuccess)
+        return fail(c, HOLO_ERR_CUDA, std::string("copy events: ") + cudaGetErrorString(cudaGetLastError()));
+  }
+  if (q_host) {
+    HOLO_CK(c, cudaMemcpyAsync(c->s_q, q_host, sizeof(float2) * (size_t)P * P,
+                               cudaMemcpyHostToDevice, c->stream));
+    if ((st = holo_set_probe(c, c->s_q))) return st;
+  }
+  // copies start once everything issued earlier on the context's stream is done
+  HOLO_CK(c, cudaEventRecord(c->ev_start, c->stream));
+  HOLO_CK(c, cudaStreamWaitEvent(c->cs_in, c->ev_start, 0));
+  HOLO_CK(c, cudaStreamWaitEvent(c->cs_out, c->ev_start, 0));
+  int wsum = 0;
+  for (int p = 0; p < parts; ++p) wsum += kHostWeights[p];
+  // part p covers [bound(p), bound(p + 1)) (rounded weight prefix sums); with nk >= 2 parts
+  // every part is non-empty (checked for every nk up to 2000)
+  auto bound = [&](int p) {
+    int w = 0;
+    for (int q = 0; q < p; ++q) w += kHostWeights[q];
+    return p == parts ? nk : (int)(((long long)nk * w + wsum / 2) / wsum);
+  };
+  for (int p = 0; p < parts; ++p) {
+    const int b0 = bound(p), m = bound(p + 1) - b0;
+    HOLO_CK(c, cudaMemcpyAsync(c->s_psi + b0 * n2, static_cast<const float2*>(psi_host) + b0 * n2,
+                               sizeof(float2) * m * n2, cudaMemcpyHostToDevice, c->cs_in));
+    if (sqrt_d_host)
+      HOLO_CK(c, cudaMemcpyAsync(c->s_data + (size_t)b0 * J * n2, sqrt_d_host + (size_t)b0 * J * n2,
+                                 sizeof(float) * m * J * n2, cudaMemcpyHostToDevice, c->cs_in));
+    HOLO_CK(c, cudaEventRecord(c->ev_in[p], c->cs_in));
+  }
+  PassArgs whole = pass_args(c, k0, nk, c->s_psi);
+  if ((st = eval_begin(c, whole))) return st;
+  const int acc = (flags & (HOLO_ACCUMULATE | HOLO_ACCUMULATE_Q)) ? 1 : 0;
+  for (int p = 0; p < parts; ++p) {
+    const int b0 = bound(p), m = bound(p + 1) - b0;
+    HOLO_CK(c, cudaStreamWaitEvent(c->stream, c->ev_in[p], 0));
+    PassArgs a = pass_args(c, k0 + b0, m, c->s_psi + b0 * n2);
+    if (sqrt_d_host) {
+      a.sqrt_d = c->s_data + (size_t)b0 * J * n2;
+      a.data_k0 = k0 + b0;
+    }
+    a.grad_psi = c->s_gpsi + b0 * n2;
+    a.gkbuf = c->gkbuf + (size_t)b0 * J * c->gkstride;
+    a.rref = p == 0 ? whole.rref : nullptr;
+    a.tq_accumulate = p > 0;
+    if ((st = eval_planes(c, a, true, p == 0, p == 0 ? acc : 1))) return st;
+    HOLO_CK(c, cudaEventRecord(c->ev_done[p], c->stream));
+    HOLO_CK(c, cudaStreamWaitEvent(c->cs_out, c->ev_done[p], 0));
+    HOLO_CK(c, cudaMemcpyAsync(static_cast<float2*>(grad_psi_host) + b0 * n2, c->s_gpsi + b0 * n2,
+                               sizeof(float2) * m * n2, cudaMemcpyDeviceToHost, c->cs_out));
+  }
+  if ((st = eval_qgrad(c, whole, c->s_gq, 0))) return st;
+  HOLO_CK(c, cudaMemcpyAsync(grad_q_host, c->s_gq, sizeof(float2) * (size_t)P * P,
+                             cudaMemcpyDeviceToHost, c->stream));
+  HOLO_CK(c, cudaEventRecord(c->ev_out, c->cs_out));
+  HOLO_CK(c, cudaStreamWaitEvent(c->stream, c->ev_out, 0));
+  return read_loss(c, loss, flags);
+}
+
 holo_status holo_gradient_host(holo_ctx* c, int k0, int nk, const void* psi_host,
                                const float* sqrt_d_host, const void* q_host, double* loss,
                                void* grad_psi_host, void* grad_q_host, unsigned flags) {
@@ -830,6 +948,10 @@ holo_status holo_gradient_host(holo_ctx* c, int k0, int nk, const void* psi_host
                     (st = dalloc(c, (void**)&c->s_gq, q_bytes))))
     return st;
   if (sqrt_d_host && !c->s_data && (st = dalloc(c, (void**)&c->s_data, data_bytes))) return st;
+  const int parts = nk >= 2 * kHostMinPart ? std::min(kHostParts, nk / kHostMinPart) : 1;
+  if (parts > 1)
+    return gradient_host_parts(c, k0, nk, parts, psi_host, sqrt_d_host, q_host, loss,
+                               grad_psi_host, grad_q_host, flags);
   const size_t nb = sizeof(float2) * (size_t)nk * n * n;
   HOLO_CK(c, cudaMemcpyAsync(c->s_psi, psi_host, nb, cudaMemcpyHostToDevice, c->stream));
   if (sqrt_d_host)

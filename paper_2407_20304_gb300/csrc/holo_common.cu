@@ -143,8 +143,14 @@ __global__ void k_sum_f64(const double* __restrict__ part, int count, double* ou
 }
 
 // Running loss of the context: red[3] = (acc ? red[3] : 0) + red[0] + wref red[1].
-__global__ void k_loss_total(double* red, double wref, int acc) {
-  if (threadIdx.x == 0 && blockIdx.x == 0) red[3] = (acc ? red[3] : 0.0) + red[0] + wref * red[1];
+// red[0]: plane loss of the last launch group, red[1]: reference term.  red[3] is the
+// running total across calls (holo_read_loss), red[7] the total of the current call.
+__global__ void k_loss_total(double* red, double wref, int acc, int first) {
+  if (threadIdx.x == 0 && blockIdx.x == 0) {
+    const double l = red[0] + wref * red[1];
+    red[3] = (acc ? red[3] : 0.0) + l;
+    red[7] = (first ? 0.0 : red[7]) + l;
+  }
 }
 
 // Re <a, b> = Re sum conj(a) b: FP32 products summed in FP32 over at most 16 elements per
@@ -281,8 +287,8 @@ cudaError_t launch_sum_f64(const double* part, int count, double* out, int accum
   return cudaGetLastError();
 }
 
-cudaError_t launch_loss_total(double* red, double wref, int acc, cudaStream_t s) {
-  k_loss_total<<<1, 32, 0, s>>>(red, wref, acc);
+cudaError_t launch_loss_total(double* red, double wref, int acc, int first, cudaStream_t s) {
+  k_loss_total<<<1, 32, 0, s>>>(red, wref, acc, first);
   return cudaGetLastError();
 }
 

@@ -66,6 +66,7 @@ struct PassArgs {
   float2* ybuf;                // per local plane: [ystride] (box rows x n)
   long long ystride;
   float2* tq;                  // [n][n]: ext sum_kj r_kj + w_ref r_ref (gradient only)
+  int tq_accumulate;           // add to tq instead of overwriting (later parts of a chunk)
   const float2* rref;          // [n][n] reference residual, or null
   float wref;
   float2* gkbuf;               // per local plane: [gkstride] conj(w) v on the box
@@ -112,7 +113,7 @@ cudaError_t launch_ref_residual(const float2* bref, const float* sqrt_dref, long
                                 float2* rref, double* part, int nblocks, cudaStream_t s);
 cudaError_t launch_sum_f64(const double* part, int count, double* out, int accumulate,
                            cudaStream_t s);
-cudaError_t launch_loss_total(double* red, double wref, int acc, cudaStream_t s);
+cudaError_t launch_loss_total(double* red, double wref, int acc, int first, cudaStream_t s);
 cudaError_t launch_dot(const float2* a, const float2* b, long long n, double* part, int nblocks,
                        cudaStream_t s);
 cudaError_t launch_dot3(const float2* g, const float2* gp, const float2* eta, long long n,

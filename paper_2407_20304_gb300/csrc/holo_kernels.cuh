@@ -395,6 +395,7 @@ __global__ void __launch_bounds__(ColCfg<P>::NT) k_pass_b(PassArgs a) {
         if (valid && (unsigned)rr < (unsigned)n) {
           const long long e = (long long)rr * n + col;
           float2 acc = cscale(sS[rr * C + g], a.ext);
+          if (a.tq_accumulate) acc = cadd(acc, a.tq[e]);
           if (a.rref) {
             const float2 q = __ldg(a.rref + e);
             acc.x = fmaf(a.wref, q.x, acc.x);

@@ -156,6 +156,25 @@ def test_gradient_host_buffers_match_device_call():
     np.testing.assert_array_equal(gq_h, gq_d.cpu().numpy())
 
 
+def test_gradient_host_in_parts_matches_device_call():
+    """12 angles are evaluated in three parts with overlapped copies: grad_psi is bit for bit
+    the device call's (each angle's planes are independent); T, hence grad_q, and the loss
+    sum the parts in another order, so they agree to rounding."""
+    pr = make_problem(64, 128, 12, seed=7)
+    h = make_holo(pr)
+    loss_d, gp_d, gq_d = h.gradient(dev(pr["psi"], torch.complex64))
+    for _ in range(2):
+        loss_h, gp_h, gq_h = h.gradient_host(pr["psi"].astype(np.complex64),
+                                             sqrt_d=pr["sqrt_d"].astype(np.float32),
+                                             q=pr["q"].astype(np.complex64))
+        np.testing.assert_array_equal(gp_h, gp_d.cpu().numpy())
+        assert abs(loss_h - loss_d) <= 1e-12 * abs(loss_d)
+        assert rel(gq_h, gq_d.cpu().numpy()) < 1e-6
+    F, _, gq_ref = oh.gradients(pr["psi"], pr["q"], pr["t"], pr["sqrt_d"], pr["sqrt_dref"], pr["geo"])
+    assert abs(loss_h - F) / F < LOSS_TOL
+    assert rel(gq_h, gq_ref) < GRAD_TOL
+
+
 def test_zero_gradient_at_noiseless_truth():
     pr = make_problem(64, 128, 2, seed=21, noiseless=True)
     h = make_holo(pr)
