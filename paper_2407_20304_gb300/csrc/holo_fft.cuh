@@ -43,8 +43,35 @@ namespace holo {
 
 // --------------------------------------------------------------------- complex helpers
 
+// Packed two-lane FP32 add / subtract (PTX add/sub .f32x2, sm_100 and later): both
+// components of a complex value in one instruction, with the same IEEE rounding as two scalar
+// operations (outputs are bit-identical to the scalar form; the issue slots of the butterfly
+// additions halve).  HOLO_SCALAR_COMPLEX selects the scalar form.
+#if !defined(HOLO_SCALAR_COMPLEX)
+__device__ __forceinline__ unsigned long long pk(float2 a) {
+  unsigned long long r;
+  asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(a.x), "f"(a.y));
+  return r;
+}
+__device__ __forceinline__ float2 upk(unsigned long long r) {
+  float2 a;
+  asm("mov.b64 {%0, %1}, %2;" : "=f"(a.x), "=f"(a.y) : "l"(r));
+  return a;
+}
+__device__ __forceinline__ float2 cadd(float2 a, float2 b) {
+  unsigned long long d;
+  asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(pk(a)), "l"(pk(b)));
+  return upk(d);
+}
+__device__ __forceinline__ float2 csub(float2 a, float2 b) {
+  unsigned long long d;
+  asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(pk(a)), "l"(pk(b)));
+  return upk(d);
+}
+#else
 __device__ __forceinline__ float2 cadd(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
 __device__ __forceinline__ float2 csub(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
+#endif
 __device__ __forceinline__ float2 cmul(float2 a, float2 b) {
   return make_float2(fmaf(a.x, b.x, -a.y * b.y), fmaf(a.x, b.y, a.y * b.x));
 }
@@ -123,12 +150,14 @@ __device__ __forceinline__ void dft2(float2& a, float2& b) {
 // natural order in, natural order out
 template <bool INV>
 __device__ __forceinline__ void dft4(float2& x0, float2& x1, float2& x2, float2& x3) {
-  float2 s02 = cadd(x0, x2), d02 = csub(x0, x2);
-  float2 s13 = cadd(x1, x3), d13 = mul_mi<INV>(csub(x1, x3));
+  const float2 s02 = cadd(x0, x2), d02 = csub(x0, x2);
+  const float2 s13 = cadd(x1, x3), e = csub(x1, x3);
   x0 = cadd(s02, s13);
   x2 = csub(s02, s13);
-  x1 = cadd(d02, d13);
-  x3 = csub(d02, d13);
+  // d02 +/- (-i e) forward, d02 +/- (i e) inverse, the swap folded into scalar adds
+  const float2 p = make_float2(d02.x + e.y, d02.y - e.x), m = make_float2(d02.x - e.y, d02.y + e.x);
+  x1 = INV ? m : p;
+  x3 = INV ? p : m;
 }
 
 template <bool INV>
