@@ -135,10 +135,6 @@ __device__ __forceinline__ void load_chirp_half(float2* dst, const float2* __res
   for (int i = threadIdx.x; i <= P / 2; i += blockDim.x) dst[i] = src[i];
 }
 
-__device__ __forceinline__ void prefetch_l2(const void* p) {
-  asm volatile("prefetch.global.L2 [%0];" ::"l"(p));
-}
-
 // ------------------------------------------------------------------ generic D-step
 
 // One "FFT -> chirp -> inverse FFT" per line, lines = rows (COLS = false) or columns.
@@ -328,20 +324,6 @@ __global__ void __launch_bounds__(ColCfg<P>::NT) k_pass_b(PassArgs a) {
           const int rel = F::pos(t, c) - d.by0;
           v[c] = (valid && (unsigned)rel < (unsigned)d.bys) ? yb[(long long)rel * n + col]
                                                              : make_float2(0.f, 0.f);
-        }
-        // The next angle at this distance reads the same columns: ask L2 for its box rows
-        // (its box has the same height up to the shift, so the current row range plus a
-        // margin covers it) and its data rows while this item is transformed.
-        if (kl + 1 < a.nk && g == 0 && valid) {
-          const float2* ybn = yb + (long long)a.J * a.ystride + col;
-          const float* adn = a.sqrt_d + (gplane + a.J - (long long)a.data_k0 * a.J) * n * n + col;
-#pragma unroll
-          for (int c = 0; c < 16; ++c) {
-            const int rel = F::pos(t, c) - d.by0;
-            if (rel >= 0 && rel < d.bys + 8 && rel < a.max_box_rows) prefetch_l2(ybn + (long long)rel * n);
-            const int rr = F::pos(t, c) - lo;
-            if ((unsigned)rr < (unsigned)n) prefetch_l2(adn + (long long)rr * n);
-          }
         }
         __syncthreads();
         fft_fwd_with<P>(v, sm, tw, t, SyncBlock());
