@@ -869,12 +869,8 @@ holo_status gradient_host_parts(holo_ctx* c, int k0, int nk, int parts, const vo
           cudaEventCreateWithFlags(&c->ev_done[i], cudaEventDisableTiming) != cudaSuccess)
         return fail(c, HOLO_ERR_CUDA, std::string("copy events: ") + cudaGetErrorString(cudaGetLastError()));
   }
-  if (q_host) {
-    HOLO_CK(c, cudaMemcpyAsync(c->s_q, q_host, sizeof(float2) * (size_t)P * P,
-                               cudaMemcpyHostToDevice, c->stream));
-    if ((st = holo_set_probe(c, c->s_q))) return st;
-  }
-  // copies start once everything issued earlier on the context's stream is done
+  // copies start once everything issued earlier on the context's stream is done; the
+  // probe (copy and propagation) then runs on the context's stream beside the first copies
   HOLO_CK(c, cudaEventRecord(c->ev_start, c->stream));
   HOLO_CK(c, cudaStreamWaitEvent(c->cs_in, c->ev_start, 0));
   HOLO_CK(c, cudaStreamWaitEvent(c->cs_out, c->ev_start, 0));
@@ -895,6 +891,11 @@ holo_status gradient_host_parts(holo_ctx* c, int k0, int nk, int parts, const vo
       HOLO_CK(c, cudaMemcpyAsync(c->s_data + (size_t)b0 * J * n2, sqrt_d_host + (size_t)b0 * J * n2,
                                  sizeof(float) * m * J * n2, cudaMemcpyHostToDevice, c->cs_in));
     HOLO_CK(c, cudaEventRecord(c->ev_in[p], c->cs_in));
+  }
+  if (q_host) {
+    HOLO_CK(c, cudaMemcpyAsync(c->s_q, q_host, sizeof(float2) * (size_t)P * P,
+                               cudaMemcpyHostToDevice, c->stream));
+    if ((st = holo_set_probe(c, c->s_q))) return st;
   }
   PassArgs whole = pass_args(c, k0, nk, c->s_psi);
   if ((st = eval_begin(c, whole))) return st;
