@@ -203,6 +203,22 @@ def amplitude_residual(u, a):
     return u - a * phase
 
 
+def intensity_residual(u, d):
+    """r1 = 2 (|u|^2 - d) u: the F1 counterpart of r (Eq. min2).  The real gradient of
+    (|u|^2 - d)^2 with respect to u is 4 (|u|^2 - d) u = 2 r1, as the real gradient of
+    (|u| - a)^2 is 2 r for F2."""
+    u = np.asarray(u, dtype=np.complex128)
+    return 2.0 * (np.abs(u) ** 2 - d) * u
+
+
+def _plane_loss_f2(u, a):
+    return float(np.sum((np.abs(u) - a) ** 2))
+
+
+def _plane_loss_f1(u, d):
+    return float(np.sum((np.abs(u) ** 2 - d) ** 2))
+
+
 def functional(psi, q, shifts, sqrt_d, sqrt_dref, geo):
     """F2 of Eq. min1: sum_kj || |u_kj| - sqrt(d~_kj) ||^2 + w_ref || |D_{zeta_0} q| - sqrt(d~^r) ||^2."""
     u = forward(psi, q, shifts, geo)
@@ -213,16 +229,22 @@ def functional(psi, q, shifts, sqrt_d, sqrt_dref, geo):
     return F
 
 
-def gradients(psi, q, shifts, sqrt_d, sqrt_dref, geo):
-    """F2 and its gradients (Eq. gradpsi and the probe gradient after it).
+def functional_f1(psi, q, shifts, d, d_ref, geo):
+    """F1 of Eq. min2: sum_kj || |u_kj|^2 - d~_kj ||^2 + w_ref || |D_{zeta_0} q|^2 - d~^r ||^2
+    (d are intensities; the paper's reference term has weight 1)."""
+    u = forward(psi, q, shifts, geo)
+    F = float(np.sum((np.abs(u) ** 2 - d) ** 2))
+    if geo.w_ref != 0.0:
+        uref = reference_field(q, geo)
+        F += geo.w_ref * float(np.sum((np.abs(uref) ** 2 - d_ref) ** 2))
+    return F
 
-    grad_psi_k = 2 sum_j R0_kj^T( conj(p_j) * D_{-zhat_j}(C* r_kj) )
+
+def _gradients(psi, q, shifts, data, data_ref, geo, plane_loss, residual):
+    """Loss and real gradients for a per-pixel loss of u whose real gradient is 2 residual(u):
+    grad_psi_k = 2 sum_j R0_kj^T( conj(p_j) * D_{-zhat_j}(C* r_kj) ),
     grad_q     = 2 [ sum_j D_{-omega_j}( sum_k conj(R_kj psi_k) * D_{-zhat_j}(C* r_kj) )
-                     + w_ref D_{-zeta_0}(C* r_ref) ]
-    with r = u - sqrt(d~) u/|u|.  These are real gradients for <a,b> = Re sum conj(a) b:
-    dF(x; h) = Re <grad, h>.
-    Returns (F, grad_psi [K][n][n], grad_q [P][P]).
-    """
+                     + w_ref D_{-zeta_0}(C* r_ref) ]."""
     psi = np.asarray(psi, dtype=np.complex128)
     d = derived_geometry(geo.z, geo.Z)
     lam, dx, n, P = geo.wavelength, geo.pixel, geo.n, geo.P
@@ -235,8 +257,8 @@ def gradients(psi, q, shifts, sqrt_d, sqrt_dref, geo):
         for j in range(J):
             Rpsi = resample(psi[k], d["mt"][j], shifts[k][j], P, geo.ext)
             u = crop(propagate(p[j] * Rpsi, d["zhat"][j], lam, dx), n)
-            F += float(np.sum((np.abs(u) - sqrt_d[k][j]) ** 2))
-            r = amplitude_residual(u, sqrt_d[k][j])
+            F += plane_loss(u, data[k][j])
+            r = residual(u, data[k][j])
             v = propagate(embed(r, P), -d["zhat"][j], lam, dx)
             gpsi[k] += 2.0 * resample_adjoint(np.conj(p[j]) * v, d["mt"][j], shifts[k][j], n)
             G[j] += np.conj(Rpsi) * v
@@ -245,10 +267,29 @@ def gradients(psi, q, shifts, sqrt_d, sqrt_dref, geo):
         gq += 2.0 * propagate(G[j], -d["omega"][j], lam, dx)
     if geo.w_ref != 0.0:
         uref = reference_field(q, geo)
-        F += geo.w_ref * float(np.sum((np.abs(uref) - sqrt_dref) ** 2))
-        rref = amplitude_residual(uref, sqrt_dref)
+        F += geo.w_ref * plane_loss(uref, data_ref)
+        rref = residual(uref, data_ref)
         gq += 2.0 * geo.w_ref * propagate(embed(rref, P), -d["zeta"][0], lam, dx)
     return F, gpsi, gq
+
+
+def gradients(psi, q, shifts, sqrt_d, sqrt_dref, geo):
+    """F2 and its gradients (Eq. gradpsi and the probe gradient after it).
+
+    grad_psi_k = 2 sum_j R0_kj^T( conj(p_j) * D_{-zhat_j}(C* r_kj) )
+    grad_q     = 2 [ sum_j D_{-omega_j}( sum_k conj(R_kj psi_k) * D_{-zhat_j}(C* r_kj) )
+                     + w_ref D_{-zeta_0}(C* r_ref) ]
+    with r = u - sqrt(d~) u/|u|.  These are real gradients for <a,b> = Re sum conj(a) b:
+    dF(x; h) = Re <grad, h>.
+    Returns (F, grad_psi [K][n][n], grad_q [P][P]).
+    """
+    return _gradients(psi, q, shifts, sqrt_d, sqrt_dref, geo, _plane_loss_f2, amplitude_residual)
+
+
+def gradients_f1(psi, q, shifts, d, d_ref, geo):
+    """F1 (Eq. min2) and its gradients: the chain of ``gradients`` with r replaced by
+    r1 = 2 (|u|^2 - d~) u and intensities d~ as data."""
+    return _gradients(psi, q, shifts, d, d_ref, geo, _plane_loss_f1, intensity_residual)
 
 
 def plane_gradient(psi_k, q, t_kj, sqrt_d_kj, geo, j):

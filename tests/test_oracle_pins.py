@@ -333,6 +333,53 @@ def test_gradients_central_finite_differences(ext, w_ref):
         assert fd == pytest.approx(an, rel=1e-7)
 
 
+@pytest.mark.parametrize("ext,w_ref", [(1.0, 1.0), (0.0, 0.0), (1.0, 0.0)])
+def test_f1_gradients_central_finite_differences(ext, w_ref):
+    """F1 (Eq. min2, intensities as data): central differences of the functional equal
+    Re<grad, h>, which pins r1 = 2 (|u|^2 - d) u through the shared adjoint chain."""
+    geo, psi, q, t, sqrt_d, sqrt_dref = _small_problem(ext=ext, w_ref=w_ref)
+    d, dref = sqrt_d ** 2, (sqrt_dref ** 2 if sqrt_dref is not None else None)
+    F, gpsi, gq = holo.gradients_f1(psi, q, t, d, dref, geo)
+    assert F == pytest.approx(holo.functional_f1(psi, q, t, d, dref, geo), rel=1e-13)
+    rng = _rng(19)
+    for _ in range(6):
+        hpsi, hq = _crandn(rng, *psi.shape), _crandn(rng, *q.shape)
+        eps = 1e-6
+        fp = holo.functional_f1(psi + eps * hpsi, q + eps * hq, t, d, dref, geo)
+        fm = holo.functional_f1(psi - eps * hpsi, q - eps * hq, t, d, dref, geo)
+        fd = (fp - fm) / (2 * eps)
+        an = cg.re_inner(gpsi, hpsi) + cg.re_inner(gq, hq)
+        assert fd == pytest.approx(an, rel=1e-7)
+
+
+def test_f1_pixel_gradient_closed_form():
+    """For one pixel, (|u|^2 - d)^2 has real gradient 4 (|u|^2 - d) u = 2 r1: checked against
+    the derivative along 1 and i written out by hand."""
+    rng = _rng(23)
+    for _ in range(20):
+        u = complex(rng.standard_normal(), rng.standard_normal())
+        dd = rng.uniform(0.0, 2.0)
+        r1 = complex(holo.intensity_residual(np.array([u]), dd)[0])
+        f = lambda z: (abs(z) ** 2 - dd) ** 2
+        # d f(u + s)/ds at s = 0 for real s is 2 (|u|^2 - d) * 2 Re(u); for imaginary s it is
+        # 2 (|u|^2 - d) * 2 Im(u); the real gradient g has Re<g, 1> and Re<g, i> equal to those
+        g = 2 * r1
+        assert (g.conjugate() * 1).real == pytest.approx(4 * (abs(u) ** 2 - dd) * u.real, rel=1e-12)
+        assert (g.conjugate() * 1j).real == pytest.approx(4 * (abs(u) ** 2 - dd) * u.imag, rel=1e-12)
+        h = 1e-6
+        assert (f(u + h) - f(u - h)) / (2 * h) == pytest.approx((g.conjugate()).real, rel=1e-6)
+
+
+def test_f1_loss_zero_and_gradient_zero_at_truth():
+    geo, psi, q, t, sqrt_d, sqrt_dref = _small_problem(noiseless=True)
+    d, dref = sqrt_d ** 2, sqrt_dref ** 2
+    F, gpsi, gq = holo.gradients_f1(psi, q, t, d, dref, geo)
+    assert F < 1e-24
+    _, gpsi1, gq1 = holo.gradients_f1(np.ones_like(psi), q, t, d, dref, geo)
+    assert np.linalg.norm(gpsi) <= 1e-12 * np.linalg.norm(gpsi1)
+    assert np.linalg.norm(gq) <= 1e-12 * np.linalg.norm(gq1)
+
+
 def test_plane_gradient_decomposition():
     """Per-plane terms summed over (k, j) reproduce the full gradient."""
     geo, psi, q, t, sqrt_d, sqrt_dref = _small_problem(w_ref=0.0)
