@@ -50,6 +50,9 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
     ap.add_argument("--workload", default="large", choices=("large", "autograd", "medium", "batch"))
+    ap.add_argument("--functional", choices=("amplitude", "intensity"), default="amplitude",
+                    help="F2 of Eq. min1 (amplitudes, the default) or F1 of Eq. min2 "
+                         "(intensities); the unfused and oracle legs are F2 only")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-unfused", action="store_true")
@@ -246,6 +249,13 @@ def run_ours(args, w, rank, world, local_rank):
     iref = bref.abs().square()
     cr = w.counts / iref.mean()
     sqrt_dref = torch.poisson(iref * cr, generator=gen).div_(cr).sqrt_().contiguous()
+    f1 = args.functional == "intensity"
+    if f1:
+        # F1 reads intensities: the same Poisson data, squared back
+        h.set_functional("intensity")
+        sqrt_d.square_()
+        sqrt_dref.square_()
+        args.no_unfused = args.no_cpu = True
     h.set_data(sqrt_d, sqrt_dref)
     del psi_t, qt
 
@@ -348,7 +358,8 @@ def run_ours(args, w, rank, world, local_rank):
         unfused = run_unfused_sample(w, torch.ones_like(psi), torch.from_numpy(q0).to(dev),
                                      shifts_np, sqrt_d, sqrt_dref)
     result = {
-        "metric": METRIC, "value": round(value, 1), "unit": UNIT, "n_gpus": world,
+        "metric": METRIC + (" (F1 intensity functional)" if f1 else ""), "value": round(value, 1),
+        "unit": UNIT, "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms / args.steps, 3),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
         "data": "synthetic",
@@ -358,7 +369,8 @@ def run_ours(args, w, rank, world, local_rank):
                    "planes_per_step": planes, "reductions": "f64",
                    "l2": "inputs larger than L2 (psi chunk %.1f GB, data %.1f GB per GPU)"
                          % (K * n * n * 8 / 1e9, K * J * n * n * 4 / 1e9),
-                   "step": "set_probe + gradient (F2, grad_psi, grad_q) + DY inner products + fused direction/step"},
+                   "functional": "F1 (Eq. min2, intensities)" if f1 else "F2 (Eq. min1, amplitudes)",
+                   "step": "set_probe + gradient (F, grad_psi, grad_q) + DY inner products + fused direction/step"},
         "roofline": roof, "clocks": clocks, "gpu_launches": launches, "per_pass": per_pass,
         "final_loss": loss,
     }

@@ -62,6 +62,10 @@ typedef enum {
 
 #define HOLO_MAX_DIST 8
 
+/* Functionals (holo_set_functional). */
+#define HOLO_F2_AMPLITUDE 0 /* F2 of Eq. min1: data are amplitudes sqrt(d~) (the default) */
+#define HOLO_F1_INTENSITY 1 /* F1 of Eq. min2: data are intensities d~ */
+
 /* Flags of holo_gradient / holo_gradient_host. */
 #define HOLO_ACCUMULATE 1u   /* add to grad_psi, grad_q and *loss instead of overwriting */
 #define HOLO_ACCUMULATE_Q 2u /* add to grad_q and *loss only; grad_psi is overwritten (chunks
@@ -170,6 +174,14 @@ holo_status holo_step(holo_ctx* ctx, void* x, const void* eta, double gamma, lon
  * Eq. DaiYuan2 (beta = 0 restarts with the steepest-descent direction). */
 holo_status holo_direction(holo_ctx* ctx, void* eta, const void* g, double beta,
                            long long n_c64);
+
+/* Select the functional that holo_forward / holo_gradient(_host) evaluate from now on:
+ * HOLO_F2_AMPLITUDE (Eq. min1, |u| against the amplitudes sqrt(d~), the default) or
+ * HOLO_F1_INTENSITY (Eq. min2, |u|^2 against the intensities d~; the reference term likewise,
+ * weighted by w_ref).  The data registered with holo_set_data (and passed to
+ * holo_gradient_host) are read as amplitudes or intensities accordingly.  F1's gradients use
+ * r = 2 (|u|^2 - d~) u in place of r = u - sqrt(d~) u/|u|.  HOLO_ERR_ARG for other values. */
+holo_status holo_set_functional(holo_ctx* ctx, int functional);
 
 /* The three inner products of the Dai-Yuan coefficient (Eq. DaiYuan2) in one pass over
  * the vectors (dev complex64 [n_c64] each): out[0] = Re <g, g>, out[1] = Re <g, eta>,

@@ -10,6 +10,7 @@ import os
 HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "_build", "libholo.so")
 MAX_DIST = 8
+F2_AMPLITUDE, F1_INTENSITY = 0, 1   # holo_set_functional
 ACCUMULATE = 1
 ACCUMULATE_Q = 2
 NOALLOC_MAX_ELEMENTS = 1 << 28   # holo_dot_noalloc: capacity of its static partial-sum array
@@ -21,7 +22,7 @@ STATUS = {0: "HOLO_OK", 1: "HOLO_ERR_ARG", 2: "HOLO_ERR_CUDA", 3: "HOLO_ERR_OOM"
 # Every symbol declared in include/holo.h.
 EXPORTS = ("holo_create", "holo_destroy", "holo_set_shifts", "holo_set_data", "holo_set_probe",
            "holo_forward", "holo_gradient", "holo_gradient_host", "holo_propagate", "holo_dot",
-           "holo_step", "holo_direction", "holo_dy_dots", "holo_direction_step", "holo_set_timing", "holo_get_timing", "holo_dot_noalloc",
+           "holo_step", "holo_direction", "holo_dy_dots", "holo_direction_step", "holo_set_functional", "holo_set_timing", "holo_get_timing", "holo_dot_noalloc",
            "holo_set_stream", "holo_read_loss",
            "holo_workspace_bytes", "holo_launch_count", "holo_status_string", "holo_last_error")
 
@@ -73,6 +74,7 @@ def load():
         "holo_step": [P, P, P, D, LL],
         "holo_direction": [P, P, P, D, LL],
         "holo_dy_dots": [P, P, P, P, LL, ctypes.POINTER(D)],
+        "holo_set_functional": [P, ctypes.c_int],
         "holo_direction_step": [P, P, P, P, D, D, LL],
         "holo_dot_noalloc": [P, P, LL, ctypes.POINTER(D), P],
         "holo_set_stream": [P, P],

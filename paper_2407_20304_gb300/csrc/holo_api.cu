@@ -70,6 +70,7 @@ struct holo_ctx {
   int n = 0, P = 0, J = 0, K = 0, chunk = 0;
   float ext = 1.f;
   double wref = 0.0;
+  int functional = HOLO_F2_AMPLITUDE;
   cudaStream_t stream = nullptr;
   // holo_gradient_host in parts: copy streams and their events (created on first use)
   cudaStream_t cs_in = nullptr, cs_out = nullptr;
@@ -415,6 +416,7 @@ PassArgs pass_args(holo_ctx* c, int k0, int nk, const void* psi) {
   a.ybuf = c->ybuf;
   a.ystride = c->ystride;
   a.tq = c->d_T;
+  a.functional = c->functional;
   a.rref = nullptr;
   a.wref = (float)c->wref;
   a.gkbuf = c->gkbuf;
@@ -452,7 +454,8 @@ holo_status eval_begin(holo_ctx* c, PassArgs& a) {
   if (a.k0 == 0 && c->wref != 0.0) {
     // reference residual first: pass B folds w_ref r_ref into the grad_q source
     HOLO_LAUNCH(c, holo::launch_ref_residual(c->d_b, c->sqrt_dref, n2, c->d_rref,
-                                             c->d_part + nbx, kRefBlocks, c->stream));
+                                             c->d_part + nbx, kRefBlocks, c->functional,
+                                             c->stream));
     HOLO_LAUNCH(c, holo::launch_sum_f64(c->d_part + nbx, kRefBlocks, c->d_red + 1, 0, c->stream));
     a.rref = c->d_rref;
   } else {
@@ -1055,6 +1058,14 @@ holo_status holo_direction(holo_ctx* c, void* eta, const void* g, double beta, l
   if (!c || !eta || !g || n < 0 || !std::isfinite(beta)) return fail(c, HOLO_ERR_ARG, "bad argument");
   PassTimer tm(c, HOLO_T_VECTOR);
   HOLO_LAUNCH(c, holo::launch_direction((float2*)eta, (const float2*)g, (float)beta, n, c->stream));
+  return HOLO_OK;
+}
+
+holo_status holo_set_functional(holo_ctx* c, int functional) {
+  if (!c) return HOLO_ERR_ARG;
+  if (functional != HOLO_F2_AMPLITUDE && functional != HOLO_F1_INTENSITY)
+    return fail(c, HOLO_ERR_ARG, "functional must be HOLO_F2_AMPLITUDE or HOLO_F1_INTENSITY");
+  c->functional = functional;
   return HOLO_OK;
 }
 

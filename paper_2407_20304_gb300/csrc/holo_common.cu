@@ -116,17 +116,25 @@ __global__ void __launch_bounds__(256) k_reduce_g(PassArgs a, float2* Gp, int j,
 
 // Reference-image term (Eq. min1, second norm): r_ref = b - a b/|b|, loss partials.
 __global__ void k_ref_residual(const float2* __restrict__ b, const float* __restrict__ aref,
-                               long long n2, float2* __restrict__ rref, double* part) {
+                               long long n2, float2* __restrict__ rref, double* part,
+                               int functional) {
   __shared__ double red[32];
   double acc = 0.0;
   for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n2;
        e += (long long)gridDim.x * blockDim.x) {
     const float2 u = b[e];
-    const float amp = aref[e];
-    const float mag = sqrtf(fmaf(u.x, u.x, u.y * u.y));
-    const float diff = mag - amp;
+    const float dat = aref[e];
+    const float i2 = fmaf(u.x, u.x, u.y * u.y);
+    float diff, s;
+    if (functional) {  // F1: (|b|^2 - d_ref)^2, r = 2 (|b|^2 - d_ref) b
+      diff = i2 - dat;
+      s = 2.f * diff;
+    } else {           // F2: (|b| - a_ref)^2, r = b - a_ref b/|b|
+      const float mag = sqrtf(i2);
+      diff = mag - dat;
+      s = mag > 0.f ? 1.f - dat / mag : 0.f;
+    }
     acc += (double)(diff * diff);
-    const float s = mag > 0.f ? 1.f - amp / mag : 0.f;
     rref[e] = cscale(u, s);
   }
   const double s = block_sum_f64(acc, red);
@@ -276,8 +284,9 @@ cudaError_t launch_reduce_g(const PassArgs& a, float2* Gp, int j, int row0, int 
 }
 
 cudaError_t launch_ref_residual(const float2* bref, const float* sqrt_dref, long long n2,
-                                float2* rref, double* part, int nblocks, cudaStream_t s) {
-  k_ref_residual<<<nblocks, kThreads, 0, s>>>(bref, sqrt_dref, n2, rref, part);
+                                float2* rref, double* part, int nblocks, int functional,
+                                cudaStream_t s) {
+  k_ref_residual<<<nblocks, kThreads, 0, s>>>(bref, sqrt_dref, n2, rref, part, functional);
   return cudaGetLastError();
 }
 

@@ -67,6 +67,7 @@ struct PassArgs {
   long long ystride;
   float2* tq;                  // [n][n]: ext sum_kj r_kj + w_ref r_ref (gradient only)
   int tq_accumulate;           // add to tq instead of overwriting (later parts of a chunk)
+  int functional;              // 0: F2 (amplitudes, Eq. min1), 1: F1 (intensities, Eq. min2)
   const float2* rref;          // [n][n] reference residual, or null
   float wref;
   float2* gkbuf;               // per local plane: [gkstride] conj(w) v on the box
@@ -110,7 +111,8 @@ cudaError_t launch_pass_d(const PassArgs& a, cudaStream_t s);
 cudaError_t launch_reduce_g(const PassArgs& a, float2* Gp, int j, int row0, int nrows, int col0,
                             int ncols, cudaStream_t s);
 cudaError_t launch_ref_residual(const float2* bref, const float* sqrt_dref, long long n2,
-                                float2* rref, double* part, int nblocks, cudaStream_t s);
+                                float2* rref, double* part, int nblocks, int functional,
+                                cudaStream_t s);
 cudaError_t launch_sum_f64(const double* part, int count, double* out, int accumulate,
                            cudaStream_t s);
 cudaError_t launch_loss_total(double* red, double wref, int acc, int first, cudaStream_t s);

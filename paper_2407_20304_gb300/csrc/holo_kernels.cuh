@@ -343,13 +343,22 @@ __global__ void __launch_bounds__(ColCfg<P>::NT) k_pass_b(PassArgs a) {
             const float2 b = sb[rr * C + g];
             u.x = fmaf(a.ext, b.x, u.x);
             u.y = fmaf(a.ext, b.y, u.y);
-            const float amp = __ldg(ad + e);
-            const float mag = sqrtf(fmaf(u.x, u.x, u.y * u.y));
-            const float diff = mag - amp;
+            const float dat = __ldg(ad + e);
+            const float i2 = fmaf(u.x, u.x, u.y * u.y);
+            // F2: (|u| - a)^2, r = u - a u/|u| (u/|u| := 0 at |u| = 0);
+            // F1: (|u|^2 - d)^2, r = 2 (|u|^2 - d) u
+            float diff, s;
+            if (a.functional) {
+              diff = i2 - dat;
+              s = 2.f * diff;
+            } else {
+              const float mag = sqrtf(i2);
+              diff = mag - dat;
+              s = mag > 0.f ? 1.f - dat / mag : 0.f;
+            }
             lsum = fmaf(diff, diff, lsum);
             if (uo) uo[e] = u;
             if (ADJ) {
-              const float s = mag > 0.f ? 1.f - amp / mag : 0.f;
               r = cscale(u, s);
               sS[rr * C + g] = cadd(sS[rr * C + g], r);
             }

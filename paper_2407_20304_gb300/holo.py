@@ -99,6 +99,7 @@ class Holo:
         _check(self.lib, None, st, "holo_create")
         self.ctx = handle
         self._keep = {}
+        self.functional = "amplitude"
 
     def close(self):
         if getattr(self, "ctx", None):
@@ -237,6 +238,14 @@ class Holo:
         st = self.lib.holo_direction(self.ctx, _ptr(eta, torch.complex64, None, "eta"),
                                      _ptr(g, torch.complex64, None, "g"), float(beta), eta.numel())
         _check(self.lib, self.ctx, st, "holo_direction")
+
+    def set_functional(self, which):
+        """'amplitude' (F2, Eq. min1; data are amplitudes) or 'intensity' (F1, Eq. min2; data
+        are intensities) for the evaluations that follow."""
+        code = {"amplitude": _lib.F2_AMPLITUDE, "intensity": _lib.F1_INTENSITY}[which]
+        _check(self.lib, self.ctx, self.lib.holo_set_functional(self.ctx, code),
+               "holo_set_functional")
+        self.functional = which
 
     def dy_dots(self, g, g_prev, eta):
         """(Re <g, g>, Re <g, eta>, Re <g_prev, eta>) in one pass (Eq. DaiYuan2)."""

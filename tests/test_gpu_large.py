@@ -111,3 +111,27 @@ def test_loss_and_grad_q_on_a_four_angle_chunk(problem):
     print(f"4-angle chunk: loss {e_l:.2e}, grad_q {e_q:.2e}, grad_psi (max over angles) {e_p:.2e}")
     assert e_l < LOSS_TOL and e_q < GRAD_TOL and e_p < GRAD_TOL
     h.close()
+
+
+def test_intensity_functional_on_a_four_angle_chunk(problem):
+    """F1 (Eq. min2) at full size: loss and both gradients of a 4-angle chunk against the
+    oracle's gradients_f1 (intensities d = sqrt_d^2 as data)."""
+    pr = problem
+    ks = list(SAMPLED)
+    d = np.ascontiguousarray(pr["sqrt_d"][ks]).astype(np.float64) ** 2
+    dref = pr["sqrt_dref"].astype(np.float64) ** 2
+    h = _holo(pr, 4, np.ascontiguousarray(pr["sqrt_d"][ks]))
+    h.set_functional("intensity")
+    h.set_data(torch.from_numpy(d.astype(np.float32)).cuda(), torch.from_numpy(dref.astype(np.float32)).cuda())
+    h.set_shifts(pr["t"][ks].astype(np.float32))
+    psi = np.ascontiguousarray(pr["psi0"][ks])
+    loss, gp, gq = h.gradient(torch.from_numpy(psi).cuda())
+    F, gp_ref, gq_ref = oh.gradients_f1(psi.astype(np.complex128), pr["q0"], pr["t"][ks],
+                                        d.astype(np.float32).astype(np.float64),
+                                        dref.astype(np.float32).astype(np.float64), pr["geo"])
+    e_l = abs(loss - F) / F
+    e_p = rel(gp.cpu().numpy().astype(np.complex128), gp_ref)
+    e_q = rel(gq.cpu().numpy().astype(np.complex128), gq_ref)
+    print(f"F1 4-angle chunk: loss {e_l:.2e}, grad_psi {e_p:.2e}, grad_q {e_q:.2e}")
+    assert e_l < LOSS_TOL and e_p < GRAD_TOL and e_q < GRAD_TOL
+    h.close()

@@ -126,6 +126,31 @@ def test_gradient_matches_oracle(n, P, K, J, ext, w_ref):
     assert rel(gq.cpu().numpy(), gq_ref) < GRAD_TOL
 
 
+@pytest.mark.parametrize("n,P,K,J,ext,w_ref", [
+    (16, 32, 2, 4, 1.0, 1.0), (64, 128, 3, 4, 1.0, 1.0), (48, 96, 2, 3, 0.0, 0.0),
+    (128, 256, 2, 4, 1.0, 1.0), (256, 512, 2, 2, 1.0, 0.0),
+])
+def test_intensity_functional_matches_oracle(n, P, K, J, ext, w_ref):
+    """F1 (Eq. min2): intensities as data, r = 2 (|u|^2 - d) u; forward loss and gradients
+    against the oracle's functional_f1 / gradients_f1."""
+    pr = make_problem(n, P, K, J=J, ext=ext, w_ref=w_ref, seed=5 * n + J)
+    d = pr["sqrt_d"] ** 2
+    dref = pr["sqrt_dref"] ** 2 if w_ref else None
+    h = make_holo(pr)
+    h.set_functional("intensity")
+    h.set_data(dev(d, torch.float32), dev(dref, torch.float32) if w_ref else None)
+    loss_f = h.forward(dev(pr["psi"], torch.complex64))
+    loss, gp, gq = h.gradient(dev(pr["psi"], torch.complex64))
+    F, gp_ref, gq_ref = oh.gradients_f1(pr["psi"], pr["q"], pr["t"], d, dref, pr["geo"])
+    assert abs(loss_f - F) / F < LOSS_TOL and abs(loss - F) / F < LOSS_TOL
+    assert rel(gp.cpu().numpy(), gp_ref) < GRAD_TOL
+    assert rel(gq.cpu().numpy(), gq_ref) < GRAD_TOL
+    h.set_functional("amplitude")
+    h.set_data(dev(pr["sqrt_d"], torch.float32), dev(pr["sqrt_dref"], torch.float32) if w_ref else None)
+    F2 = oh.functional(pr["psi"], pr["q"], pr["t"], pr["sqrt_d"], pr["sqrt_dref"], pr["geo"])
+    assert abs(h.forward(dev(pr["psi"], torch.complex64)) - F2) / F2 < LOSS_TOL
+
+
 def test_chunks_accumulate_to_full_gradient():
     pr = make_problem(64, 128, 5, seed=11)
     h = make_holo(pr, chunk=2)
@@ -257,3 +282,6 @@ def test_state_and_argument_errors():
         h.forward(psi)
     with pytest.raises(HoloError, match="ARG"):
         h.set_shifts(np.full((2, 2, 2), np.nan, np.float32))
+    assert h.lib.holo_set_functional(h.ctx, 7) == 1      # HOLO_ERR_ARG
+    with pytest.raises(KeyError):
+        h.set_functional("phase")
