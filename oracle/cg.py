@@ -1,4 +1,5 @@
-"""FP64 nonlinear conjugate gradients with the Dai-Yuan direction (Sec. 2, Eq. DaiYuan2).
+"""FP64 nonlinear conjugate gradients (Sec. 2): the Dai-Yuan direction of Eq. DaiYuan2 and
+the Fletcher-Reeves / Polak-Ribiere-Polyak formulas the paper names beside it.
 
 TEST INFRASTRUCTURE ONLY (see the package docstring).
 
@@ -43,6 +44,54 @@ def dai_yuan_direction(g_new, g_old, eta):
     return -g_new + beta * eta, beta
 
 
+def fletcher_reeves_beta(g_new, g_old):
+    """beta_FR = ||g_new||^2 / ||g_old||^2 (Fletcher-Reeves, named in Sec. 2); None if
+    g_old = 0."""
+    den = re_inner(g_old, g_old)
+    return re_inner(g_new, g_new) / den if den > 0.0 else None
+
+
+def polak_ribiere_beta(g_new, g_old):
+    """beta_PRP = Re <g_new, g_new - g_old> / ||g_old||^2 (Polak-Ribiere-Polyak, named in
+    Sec. 2); None if g_old = 0."""
+    den = re_inner(g_old, g_old)
+    return (re_inner(g_new, g_new) - re_inner(g_new, g_old)) / den if den > 0.0 else None
+
+
+def direction(g_new, g_old, eta, rule="dai-yuan"):
+    """Next CG direction -g_new + beta eta for rule 'dai-yuan' (Eq. DaiYuan2),
+    'fletcher-reeves' or 'polak-ribiere'.  Dai-Yuan restarts (-g_new) when its denominator
+    is not positive (reading R7); the other two restart when beta is undefined or the new
+    direction is not a descent direction (Re <g_new, eta_new> >= 0)."""
+    if rule == "dai-yuan":
+        return dai_yuan_direction(g_new, g_old, eta)
+    beta = fletcher_reeves_beta(g_new, g_old) if rule == "fletcher-reeves" else \
+        polak_ribiere_beta(g_new, g_old)
+    if beta is None:
+        return -g_new, 0.0
+    e = -g_new + beta * eta
+    if not re_inner(g_new, e) < 0.0:
+        return -g_new, 0.0
+    return e, beta
+
+
+def armijo(f, f0, slope, x, eta, gamma0, max_halvings, c=1e-4):
+    """Largest gamma in {gamma0 / 2^i} (i <= max_halvings) with the sufficient decrease
+    f(x + gamma eta) <= f0 + c gamma slope, slope = Re <grad f(x), eta> < 0.
+
+    Returns (gamma, f_new); gamma = 0 and f_new = f0 when no trial qualifies or eta is not a
+    descent direction."""
+    if not slope < 0.0:
+        return 0.0, f0
+    gamma = gamma0
+    for _ in range(max_halvings + 1):
+        fx = f(x + gamma * eta)
+        if fx <= f0 + c * gamma * slope:
+            return gamma, fx
+        gamma *= 0.5
+    return 0.0, f0
+
+
 def backtrack(f, f0, x, eta, gamma0, max_halvings):
     """Largest gamma in {gamma0 / 2^i} (i <= max_halvings) with f(x + gamma eta) < f0.
 
@@ -58,12 +107,14 @@ def backtrack(f, f0, x, eta, gamma0, max_halvings):
 
 
 def reconstruct(psi0, q0, shifts, sqrt_d, sqrt_dref, geo, iters, gamma0=1.0,
-                max_halvings=20, update_q=True):
-    """Joint psi / q reconstruction by DY conjugate gradients (Sec. 2).
+                max_halvings=20, update_q=True, rule="dai-yuan", line_search="backtracking"):
+    """Joint psi / q reconstruction by nonlinear conjugate gradients (Sec. 2).
 
-    Returns a dict with the final psi, q and per-iteration F, gamma_psi, gamma_q.
-    The initial trial step of each block is twice its last accepted step (gamma0 at
-    the first iteration).
+    rule: the direction formula ('dai-yuan' of Eq. DaiYuan2, 'fletcher-reeves',
+    'polak-ribiere'); line_search: 'backtracking' (first decrease of F, reading R7) or
+    'armijo' (sufficient decrease with c = 1e-4).  Returns a dict with the final psi, q and
+    per-iteration F, gamma_psi, gamma_q, beta_psi, beta_q.  The initial trial step of each
+    block is twice its last accepted step (gamma0 at the first iteration).
     """
     psi = np.array(psi0, dtype=np.complex128)
     q = np.array(q0, dtype=np.complex128)
@@ -72,23 +123,31 @@ def reconstruct(psi0, q0, shifts, sqrt_d, sqrt_dref, geo, iters, gamma0=1.0,
     trial_psi = trial_q = gamma0
     hist = {"F": [F], "gamma_psi": [], "gamma_q": [], "beta_psi": [], "beta_q": [],
             "F_after_psi": []}
+
+    def search(f, F0, g, x, eta, trial):
+        if line_search == "armijo":
+            return armijo(f, F0, re_inner(g, eta), x, eta, trial, max_halvings)
+        return backtrack(f, F0, x, eta, trial, max_halvings)
+
     for _ in range(iters):
         def f_psi(x):
             return holo.functional(x, q, shifts, sqrt_d, sqrt_dref, geo)
-        gam_psi, F = backtrack(f_psi, F, psi, eta_psi, trial_psi, max_halvings)
+        gam_psi, F = search(f_psi, F, gpsi, psi, eta_psi, trial_psi)
         psi = psi + gam_psi * eta_psi
         hist["F_after_psi"].append(F)
         gam_q = 0.0
         if update_q:
             def f_q(x):
                 return holo.functional(psi, x, shifts, sqrt_d, sqrt_dref, geo)
-            gam_q, F = backtrack(f_q, F, q, eta_q, trial_q, max_halvings)
+            # the q gradient at the updated psi is not evaluated; the slope of the Armijo
+            # test uses the gradient of the last evaluation
+            gam_q, F = search(f_q, F, gq, q, eta_q, trial_q)
             q = q + gam_q * eta_q
         trial_psi = 2.0 * gam_psi if gam_psi > 0 else trial_psi
         trial_q = 2.0 * gam_q if gam_q > 0 else trial_q
         F_new, gpsi_new, gq_new = holo.gradients(psi, q, shifts, sqrt_d, sqrt_dref, geo)
-        eta_psi, b_psi = dai_yuan_direction(gpsi_new, gpsi, eta_psi)
-        eta_q, b_q = dai_yuan_direction(gq_new, gq, eta_q)
+        eta_psi, b_psi = direction(gpsi_new, gpsi, eta_psi, rule)
+        eta_q, b_q = direction(gq_new, gq, eta_q, rule)
         gpsi, gq, F = gpsi_new, gq_new, F_new
         hist["F"].append(F)
         hist["gamma_psi"].append(gam_psi)

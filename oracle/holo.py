@@ -176,6 +176,19 @@ def reference_field(q, geo):
     return crop(propagate(q, d["zeta"][0], geo.wavelength, geo.pixel), geo.n)
 
 
+def initial_probe(sqrt_dref, geo):
+    """Initial probe: the reference image propagated back to sample plane 0 (Sec. 2, on the
+    initial guess), q0 = D_{-zeta_0}(E sqrt(d~^r)).  Reading: E embeds the n x n amplitude in
+    the P x P grid by repeating its edge values (a zero border would add an edge the probe
+    does not have); C D_{zeta_0} q0 = sqrt(d~^r) exactly since D_{zeta_0} D_{-zeta_0} = I."""
+    n, P = geo.n, geo.P
+    lo = P // 2 - n // 2
+    a = np.asarray(sqrt_dref, dtype=np.float64)
+    ext = np.pad(a, ((lo, P - n - lo), (lo, P - n - lo)), mode="edge").astype(np.complex128)
+    d = derived_geometry(geo.z, geo.Z)
+    return propagate(ext, -d["zeta"][0], geo.wavelength, geo.pixel)
+
+
 def forward(psi, q, shifts, geo):
     """Detector wavefields u_kj = C D_{zeta_j/m~_j^2}( D_{omega_j}(q) * M_{1/m~_j} S_{t_kj} psi_k ).
 

@@ -432,6 +432,92 @@ def test_dai_yuan_reproduces_linear_cg_on_quadratic():
         np.testing.assert_allclose(x, lin[it], rtol=1e-10, atol=1e-12)
 
 
+@pytest.mark.parametrize("rule", ["fletcher-reeves", "polak-ribiere", "dai-yuan"])
+def test_cg_rules_reproduce_linear_cg_on_quadratic(rule):
+    """With an exact line search on f = 1/2 x^T A x - b^T x the Fletcher-Reeves,
+    Polak-Ribiere-Polyak and Dai-Yuan formulas all give the iterates of textbook linear CG."""
+    rng = _rng(12)
+    m = 10
+    B = rng.standard_normal((m, m))
+    A = B @ B.T + m * np.eye(m)
+    b = rng.standard_normal(m)
+    x_lin, r = np.zeros(m), b.copy()
+    p = r.copy()
+    lin = []
+    for _ in range(5):
+        al = (r @ r) / (p @ A @ p)
+        x_lin = x_lin + al * p
+        r_new = r - al * (A @ p)
+        p = r_new + (r_new @ r_new) / (r @ r) * p
+        r = r_new
+        lin.append(x_lin.copy())
+    x = np.zeros(m)
+    g = A @ x - b
+    eta = -g
+    for it in range(5):
+        gam = -(g @ eta) / (eta @ A @ eta)
+        x = x + gam * eta
+        g_new = A @ x - b
+        eta, beta = cg.direction(g_new, g, eta, rule)
+        assert beta > 0
+        g = g_new
+        np.testing.assert_allclose(x, lin[it], rtol=1e-10, atol=1e-12)
+
+
+def test_prp_restarts_when_the_gradient_repeats():
+    """Polak-Ribiere-Polyak vanishes when the gradient does not change (its automatic restart);
+    Fletcher-Reeves is then 1; for g_new = 0 both vanish."""
+    rng = _rng(17)
+    g = _crandn(rng, 5, 4)
+    assert cg.polak_ribiere_beta(g, g) == pytest.approx(0.0, abs=1e-14)
+    assert cg.fletcher_reeves_beta(g, g) == pytest.approx(1.0, rel=1e-14)
+    assert cg.polak_ribiere_beta(2 * g, g) == pytest.approx(2.0, rel=1e-14)  # (4 - 2) |g|^2 / |g|^2
+    assert cg.fletcher_reeves_beta(np.zeros_like(g), g) == 0.0
+
+
+def test_armijo_accepts_only_sufficient_decrease():
+    """On f(x) = |x|^2 with a steepest-descent direction the Armijo rule accepts the first
+    halving of gamma0 that meets f(x + g eta) <= f(x) + c g slope, and returns 0 for an ascent
+    direction."""
+    f = lambda v: float(np.sum(np.abs(v) ** 2))
+    x = np.array([3.0 + 1.0j, -2.0])
+    grad = 2 * x
+    eta = -grad
+    slope = cg.re_inner(grad, eta)
+    gam, fx = cg.armijo(f, f(x), slope, x, eta, 4.0, 20, c=0.3)
+    # f(x - 2 g x) = (1 - 2 g)^2 f(x); sufficient decrease needs (1 - 2g)^2 <= 1 - 1.2 g,
+    # i.e. g <= 0.7; halving from 4 gives 0.5
+    assert gam == 0.5 and fx == pytest.approx(0.0)
+    assert cg.armijo(f, f(x), cg.re_inner(grad, -eta), x, -eta, 1.0, 20) == (0.0, f(x))
+
+
+@pytest.mark.parametrize("rule,ls", [("dai-yuan", "armijo"), ("fletcher-reeves", "backtracking"),
+                                     ("polak-ribiere", "armijo")])
+def test_reconstruction_variants_are_monotone(rule, ls):
+    geo, psi, q, t, sqrt_d, sqrt_dref = _small_problem(n=16, P=32, K=2, noiseless=True, seed=6)
+    rng = _rng(13)
+    out = cg.reconstruct(np.ones_like(psi), hs.perturbed_probe(q, rng), t, sqrt_d, sqrt_dref,
+                         geo, iters=4, rule=rule, line_search=ls)
+    F = np.array(out["hist"]["F"])
+    assert np.all(np.diff(F) <= 0.0) and F[-1] < F[0]
+
+
+def test_initial_probe_reproduces_reference_amplitude():
+    """q0 = D_{-zeta_0}(E sqrt(d~^r)): propagating it forward by zeta_0 returns the edge-padded
+    reference amplitude, whose detector crop is sqrt(d~^r) (Sec. 2, initial guess)."""
+    geo, psi, q, t, sqrt_d, sqrt_dref = _small_problem(n=16, P=32, K=1, seed=3)
+    q0 = holo.initial_probe(sqrt_dref, geo)
+    back = holo.propagate(q0, holo.derived_geometry(geo.z, geo.Z)["zeta"][0], geo.wavelength,
+                          geo.pixel)
+    np.testing.assert_allclose(holo.crop(back, geo.n), sqrt_dref, atol=1e-12)
+    lo = geo.P // 2 - geo.n // 2
+    # border rows repeat the first / last data row, border corners the corner value
+    np.testing.assert_allclose(back[0, lo:lo + geo.n], sqrt_dref[0], atol=1e-12)
+    np.testing.assert_allclose(back[-1, lo:lo + geo.n], sqrt_dref[-1], atol=1e-12)
+    assert abs(back[0, 0] - sqrt_dref[0, 0]) < 1e-12 and abs(back[0].imag).max() < 1e-12
+    np.testing.assert_allclose(holo.reference_field(q0, geo), sqrt_dref, atol=1e-12)
+
+
 def test_reconstruction_is_monotone():
     """The line search never lets F increase (Sec. 2, after Eq. DaiYuan2)."""
     geo, psi, q, t, sqrt_d, sqrt_dref = _small_problem(n=16, P=32, K=2, noiseless=True, seed=6)
