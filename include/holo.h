@@ -175,6 +175,12 @@ holo_status holo_step(holo_ctx* ctx, void* x, const void* eta, double gamma, lon
 holo_status holo_direction(holo_ctx* ctx, void* eta, const void* g, double beta,
                            long long n_c64);
 
+/* Initial probe (Sec. 2, on the initial guess): the reference image propagated back to
+ * sample plane 0, q_out = D_{-zeta_0}(E sqrt_dref), where E embeds the n x n amplitude
+ * sqrt_dref (dev f32 [n][n]) in the P x P grid by repeating its edge values.  q_out: dev
+ * complex64 [P][P], caller-owned.  Asynchronous on the context's stream. */
+holo_status holo_initial_probe(holo_ctx* ctx, const float* sqrt_dref, void* q_out);
+
 /* Select the functional that holo_forward / holo_gradient(_host) evaluate from now on:
  * HOLO_F2_AMPLITUDE (Eq. min1, |u| against the amplitudes sqrt(d~), the default) or
  * HOLO_F1_INTENSITY (Eq. min2, |u|^2 against the intensities d~; the reference term likewise,

@@ -1,4 +1,5 @@
-"""Joint psi / q reconstruction by nonlinear conjugate gradients (Sec. 2, Eq. DaiYuan2).
+"""Joint psi / q reconstruction by nonlinear conjugate gradients (Sec. 2, Eq. DaiYuan2, and
+the Fletcher-Reeves / Polak-Ribiere-Polyak formulas the paper names beside it).
 
 The driver runs on the host and issues only library calls: gradients (passes A-D), trial
 functionals for the line search (passes A-B), FP64 inner products for the Dai-Yuan
@@ -7,7 +8,13 @@ same reading as the FP64 oracle's driver): psi and q keep their own Dai-Yuan dir
 after one shared gradient the psi step is found by halving a trial step until F decreases,
 then the q step the same way from the updated psi; a block whose trials never decrease F
 keeps step 0, so F never increases; a non-positive DY denominator restarts the block with
--g; each block's next trial step is twice its last accepted one.
+-g; each block's next trial step is twice its last accepted one.  Options: the direction
+rule ('dai-yuan', 'fletcher-reeves', 'polak-ribiere'; the latter two restart with -g when beta
+is undefined or the new direction is not a descent direction) and the line search
+('backtracking' as above, or 'armijo': the first halving with F <= F0 + 1e-4 gamma
+Re <g, eta>, the q block using the gradient of the last evaluation).  The FP64 oracle driver
+(oracle/cg.py) takes the same steps.  The initial probe of the paper (the reference image
+propagated back to plane 0) is Holo.initial_probe.
 
 Angles are processed in chunks of holo.chunk (the paper's independent angle chunks,
 Sec. 4); the loss and grad_q are summed over chunks with the library's accumulate flag.
@@ -19,16 +26,27 @@ import torch
 class Reconstruction:
     """State of a DY-CG reconstruction of psi [n_angles][n][n] and q [P][P] (CUDA, complex64)."""
 
-    def __init__(self, holo, psi, q, gamma0=1.0, max_halvings=20, update_q=True):
+    RULES = ("dai-yuan", "fletcher-reeves", "polak-ribiere")
+    SEARCHES = ("backtracking", "armijo")
+    ARMIJO_C = 1e-4
+
+    def __init__(self, holo, psi, q, gamma0=1.0, max_halvings=20, update_q=True,
+                 rule="dai-yuan", line_search="backtracking"):
+        if rule not in self.RULES or line_search not in self.SEARCHES:
+            raise ValueError(f"rule in {self.RULES}, line_search in {self.SEARCHES}")
         self.h = holo
         self.psi = psi
         self.q = q
         self.gamma0 = gamma0
         self.max_halvings = max_halvings
         self.update_q = update_q
+        self.rule = rule
+        self.line_search = line_search
         self.trial = [gamma0, gamma0]
         self.g = None
         self.eta = None
+        self.gg = [None, None]       # ||g||^2 of each block's current gradient
+        self.slope = [None, None]    # Re <g, eta> of each block's current direction
         self.F = None
         self.history = {"F": [], "gamma_psi": [], "gamma_q": [], "beta_psi": [], "beta_q": [],
                         "F_after_psi": []}
@@ -53,23 +71,42 @@ class Reconstruction:
         return loss
 
     # ------------------------------------------------------------------ iteration
-    def _backtrack(self, f, x, eta, gamma, F0, scratch):
+    def _backtrack(self, f, x, eta, gamma, F0, scratch, slope):
+        armijo = self.line_search == "armijo"
+        if armijo and not slope < 0.0:
+            return 0.0, F0
         for _ in range(self.max_halvings + 1):
             scratch.copy_(x)
             self.h.step(scratch, eta, gamma)
             Fx = f(scratch)
-            if Fx < F0:
+            if (Fx <= F0 + self.ARMIJO_C * gamma * slope) if armijo else (Fx < F0):
                 x.copy_(scratch)
                 return gamma, Fx
             gamma *= 0.5
         return 0.0, F0
 
     def _direction(self, b, g_new):
+        """eta = -g_new + beta eta for the chosen rule; records ||g_new||^2 and the slope
+        Re <g_new, eta_new> from the same inner products."""
         g_old, eta = self.g[b], self.eta[b]
         num, d_new, d_old = self.h.dy_dots(g_new, g_old, eta)
-        den = d_new - d_old
-        beta = num / den if den > 0 else 0.0
+        beta = None
+        if self.rule == "dai-yuan":
+            den = d_new - d_old
+            beta = num / den if den > 0 else None
+        else:
+            oo = self.gg[b]
+            if oo and oo > 0:
+                if self.rule == "fletcher-reeves":
+                    beta = num / oo
+                else:
+                    beta = (num - self.h.dot(g_new, g_old)) / oo
+            if beta is not None and not (-num + beta * d_new) < 0.0:
+                beta = None
+        beta = 0.0 if beta is None else beta
         self.h.direction(eta, g_new, beta)
+        self.gg[b] = num
+        self.slope[b] = -num + beta * d_new
         return beta
 
     def run(self, iters):
@@ -81,18 +118,20 @@ class Reconstruction:
             self.eta = [torch.zeros_like(psi), torch.zeros_like(q)]
             for b in range(2):
                 self.h.direction(self.eta[b], self.g[b], 0.0)
+                self.gg[b] = self.h.dot(self.g[b], self.g[b])
+                self.slope[b] = -self.gg[b]
             self.history["F"].append(self.F)
         scratch_psi, scratch_q = torch.empty_like(psi), torch.empty_like(q)
         g_new = [torch.empty_like(psi), torch.empty_like(q)]
         for _ in range(iters):
             self.h.set_probe(q)
             gam_psi, F = self._backtrack(lambda x: self.functional(x), psi, self.eta[0],
-                                         self.trial[0], self.F, scratch_psi)
+                                         self.trial[0], self.F, scratch_psi, self.slope[0])
             self.history["F_after_psi"].append(F)
             gam_q = 0.0
             if self.update_q:
                 gam_q, F = self._backtrack(lambda x: self.functional(psi, x), q, self.eta[1],
-                                           self.trial[1], F, scratch_q)
+                                           self.trial[1], F, scratch_q, self.slope[1])
             if gam_psi > 0:
                 self.trial[0] = 2.0 * gam_psi
             if gam_q > 0:

@@ -1061,6 +1061,14 @@ holo_status holo_direction(holo_ctx* c, void* eta, const void* g, double beta, l
   return HOLO_OK;
 }
 
+holo_status holo_initial_probe(holo_ctx* c, const float* sqrt_dref, void* q_out) {
+  if (!c || !sqrt_dref || !q_out) return fail(c, HOLO_ERR_ARG, "null argument");
+  const int P = c->P;
+  HOLO_LAUNCH(c, holo::launch_embed_edge(sqrt_dref, c->n, P, (float2*)q_out, c->stream));
+  return dstep2d(c, (const float2*)q_out, 0, P, 0, P, (float2*)q_out, 0, P, 0, P,
+                 c->d_chirp_zeta0, 1, 1.f, 0);
+}
+
 holo_status holo_set_functional(holo_ctx* c, int functional) {
   if (!c) return HOLO_ERR_ARG;
   if (functional != HOLO_F2_AMPLITUDE && functional != HOLO_F1_INTENSITY)

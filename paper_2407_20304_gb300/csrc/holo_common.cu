@@ -141,6 +141,19 @@ __global__ void k_ref_residual(const float2* __restrict__ b, const float* __rest
   if (threadIdx.x == 0) part[blockIdx.x] = s;
 }
 
+// q[Y][X] = a[clamp(Y - lo)][clamp(X - lo)]: an n x n amplitude embedded in the P x P grid
+// with its edge values repeated (the initial probe's source before D_{-zeta_0}).
+__global__ void k_embed_edge(const float* __restrict__ a, int n, int P, float2* __restrict__ q) {
+  const int lo = P / 2 - n / 2;
+  const long long total = (long long)P * P;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
+       e += (long long)gridDim.x * blockDim.x) {
+    const int Y = (int)(e / P), X = (int)(e % P);
+    const int i = min(max(Y - lo, 0), n - 1), j = min(max(X - lo, 0), n - 1);
+    q[e] = make_float2(a[(long long)i * n + j], 0.f);
+  }
+}
+
 // Deterministic single-block sum of FP64 partials.
 __global__ void k_sum_f64(const double* __restrict__ part, int count, double* out, int accumulate) {
   __shared__ double red[32];
@@ -287,6 +300,11 @@ cudaError_t launch_ref_residual(const float2* bref, const float* sqrt_dref, long
                                 float2* rref, double* part, int nblocks, int functional,
                                 cudaStream_t s) {
   k_ref_residual<<<nblocks, kThreads, 0, s>>>(bref, sqrt_dref, n2, rref, part, functional);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_embed_edge(const float* a, int n, int P, float2* q, cudaStream_t s) {
+  k_embed_edge<<<grid_for((long long)P * P), kThreads, 0, s>>>(a, n, P, q);
   return cudaGetLastError();
 }
 

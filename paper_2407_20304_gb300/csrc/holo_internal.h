@@ -113,6 +113,7 @@ cudaError_t launch_reduce_g(const PassArgs& a, float2* Gp, int j, int row0, int 
 cudaError_t launch_ref_residual(const float2* bref, const float* sqrt_dref, long long n2,
                                 float2* rref, double* part, int nblocks, int functional,
                                 cudaStream_t s);
+cudaError_t launch_embed_edge(const float* a, int n, int P, float2* q, cudaStream_t s);
 cudaError_t launch_sum_f64(const double* part, int count, double* out, int accumulate,
                            cudaStream_t s);
 cudaError_t launch_loss_total(double* red, double wref, int acc, int first, cudaStream_t s);

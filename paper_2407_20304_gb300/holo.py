@@ -239,6 +239,18 @@ class Holo:
                                      _ptr(g, torch.complex64, None, "g"), float(beta), eta.numel())
         _check(self.lib, self.ctx, st, "holo_direction")
 
+    def initial_probe(self, sqrt_dref, out=None):
+        """q0 = D_{-zeta_0} of the reference amplitude embedded with repeated edges (the
+        paper's initial probe: the reference image propagated back to sample plane 0)."""
+        import torch
+        pa = _ptr(sqrt_dref, torch.float32, (self.n, self.n), "sqrt_dref")
+        if out is None:
+            out = torch.empty((self.P, self.P), dtype=torch.complex64, device=self.device)
+        po = _ptr(out, torch.complex64, (self.P, self.P), "out")
+        _check(self.lib, self.ctx, self.lib.holo_initial_probe(self.ctx, pa, po),
+               "holo_initial_probe")
+        return out
+
     def set_functional(self, which):
         """'amplitude' (F2, Eq. min1; data are amplitudes) or 'intensity' (F1, Eq. min2; data
         are intensities) for the evaluations that follow."""

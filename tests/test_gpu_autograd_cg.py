@@ -110,18 +110,24 @@ def test_autograd_finite_differences_at_differentiation_size():
     assert np.median(errs) < 2e-3 and np.max(errs) < 2e-2
 
 
-def test_cg_driver_follows_the_oracle_driver():
+@pytest.mark.parametrize("rule,line_search", [("dai-yuan", "backtracking"),
+                                              ("fletcher-reeves", "armijo"),
+                                              ("polak-ribiere", "backtracking"),
+                                              ("dai-yuan", "armijo")])
+def test_cg_driver_follows_the_oracle_driver(rule, line_search):
     """Same decisions as the FP64 driver until one falls within FP32 rounding of a tie;
     F never increases.  Where the two drivers first choose different steps, the FP64
     driver's accepted step must have changed F by less than FP32 can resolve."""
     from paper_2407_20304_gb300.cg import Reconstruction
     geo, t, sqrt_d, sqrt_dref, psi0, q0 = small_problem(K=4, seed=4)
     h = make_holo(geo, 4, t, sqrt_d, sqrt_dref, chunk=3)
-    rec = Reconstruction(h, torch.from_numpy(psi0).cuda(), torch.from_numpy(q0).cuda())
+    rec = Reconstruction(h, torch.from_numpy(psi0).cuda(), torch.from_numpy(q0).cuda(),
+                         rule=rule, line_search=line_search)
     iters = 4
     hist = rec.run(iters)
     ref = ocg.reconstruct(psi0.astype(np.complex128), q0.astype(np.complex128), t,
-                          sqrt_d.astype(np.float64), sqrt_dref.astype(np.float64), geo, iters=iters)
+                          sqrt_d.astype(np.float64), sqrt_dref.astype(np.float64), geo, iters=iters,
+                          rule=rule, line_search=line_search)
     F = np.array(hist["F"])
     Fo = np.array(ref["hist"]["F"])
     print("\nF gpu", F, "\nF oracle", Fo, "\ngamma psi", hist["gamma_psi"],
@@ -146,3 +152,17 @@ def test_cg_driver_follows_the_oracle_driver():
                          abs(hist["F_after_psi"][same] - F[same + 1])) / start
         print("first different step at iteration", same, "relative change", change)
         assert change < 1e-4
+
+
+@pytest.mark.parametrize("n,P", [(64, 128), (48, 96), (256, 512)])
+def test_initial_probe_matches_oracle(n, P):
+    """The paper's initial probe (reference image propagated back to plane 0) against the
+    oracle's initial_probe."""
+    from paper_2407_20304_gb300 import Holo
+    rng = np.random.default_rng(n)
+    geo = oh.Geometry(G["wavelength"], G["pixel"], G["Z"], G["z"], n, P)
+    a = (1.0 + 0.3 * rng.standard_normal((n, n))).astype(np.float32)
+    h = Holo(n, 1, 4, geo.wavelength, geo.pixel, geo.Z, geo.z, pad=P)
+    got = h.initial_probe(torch.from_numpy(a).cuda()).cpu().numpy()
+    ref = oh.initial_probe(a.astype(np.float64), geo)
+    assert rel(got.astype(np.complex128), ref) < 1e-5
