@@ -49,7 +49,10 @@ def parse():
     ap.add_argument("--steps", type=int, default=30)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
-    ap.add_argument("--workload", default="large", choices=("large", "autograd", "medium", "batch"))
+    ap.add_argument("--workload", default="large",
+                    choices=("large", "autograd", "medium", "batch", "recon"))
+    ap.add_argument("--recon-iters", type=int, default=200,
+                    help="CG iterations of --workload recon (convergence run)")
     ap.add_argument("--functional", choices=("amplitude", "intensity"), default="amplitude",
                     help="F2 of Eq. min1 (amplitudes, the default) or F1 of Eq. min2 "
                          "(intensities); the unfused and oracle legs are F2 only")
@@ -614,6 +617,86 @@ def run_reference(args, w):
                     "d2h_bytes_per_step": 0}}
 
 
+# ---------------------------------------------------------------- reconstruction (convergence)
+
+def run_recon(args):
+    """Joint psi / q DY-CG reconstructions (Sec. 2) on a 16-angle chunk of the medium workload
+    (psi 512^2 on 1024^2, 4 distances, layered phantom, striped probe), from psi = 1 and the
+    paper's initial probe (the reference image propagated back to plane 0), on noise-free and
+    on Poisson (1e4 counts) data: F per iteration and the relative errors of psi and q against
+    the synthetic truth, as in Fig. conv.  Wall-clock time of the whole driver (host-driven,
+    line searches included)."""
+    import torch
+    from paper_2407_20304_gb300 import Holo
+    from paper_2407_20304_gb300.cg import Reconstruction
+    import __graft_entry__
+    __graft_entry__.build()
+    w = hs.workloads()["medium"]
+    g = hs.WORKLOAD_GEOMETRY
+    n, P, J, K = w.n, w.P, w.n_dist, 16
+    rng = hs.rng_for(w.seed, 31)
+    psi_true = torch.from_numpy(hs.object_stack(w, range(K), rng).astype(np.complex64)).cuda()
+    q_true = torch.from_numpy(hs.striped_probe(P, w.probe_sigma, rng).astype(np.complex64)).cuda()
+    shifts = hs.sample_shifts(K, J, rng).astype(np.float32)
+    _, zeta = derived(g["z"][:J], g["Z"])
+    lo = P // 2 - n // 2
+    runs = {}
+    for label, counts in (("noise-free", None), ("noisy", w.counts)):
+        h = Holo(n, K, J, g["wavelength"], g["pixel"], g["Z"], g["z"][:J], pad=P)
+        h.set_shifts(shifts)
+        h.set_data(torch.ones((K, J, n, n), dtype=torch.float32, device="cuda"),
+                   torch.ones((n, n), dtype=torch.float32, device="cuda"))
+        h.set_probe(q_true)
+        u = torch.empty((K, J, n, n), dtype=torch.complex64, device="cuda")
+        h.forward(psi_true, u_out=u)
+        inten = u.abs().square()
+        iref = h.propagate(q_true, zeta[0])[lo:lo + n, lo:lo + n].abs().square()
+        if counts:
+            gen = torch.Generator(device="cuda").manual_seed(w.seed + 77)
+            c = counts / inten.mean()
+            inten = torch.poisson(inten * c, generator=gen) / c
+            cr = counts / iref.mean()
+            iref = torch.poisson(iref * cr, generator=gen) / cr
+        sqrt_d, sqrt_dref = inten.sqrt().contiguous(), iref.sqrt().contiguous()
+        h.set_data(sqrt_d, sqrt_dref)
+        q0 = h.initial_probe(sqrt_dref)
+        psi = torch.ones((K, n, n), dtype=torch.complex64, device="cuda")
+        rec = Reconstruction(h, psi, q0.clone())
+        err = {"psi": [], "q": []}
+        checkpoints = []
+        t_run = 0.0
+        done = 0
+        step = 10
+        while done < args.recon_iters:
+            m = min(step, args.recon_iters - done)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            rec.run(m)
+            torch.cuda.synchronize()
+            t_run += time.perf_counter() - t0
+            done += m
+            checkpoints.append(done)
+            err["psi"].append(float((rec.psi - psi_true).norm() / psi_true.norm()))
+            err["q"].append(float((rec.q - q_true).norm() / q_true.norm()))
+        F = rec.history["F"]
+        gaps = sum(1 for a, b in zip(rec.history["gamma_psi"], rec.history["gamma_q"]) if a == 0 or b == 0)
+        runs[label] = {"iterations": done, "seconds": round(t_run, 3),
+                       "iterations_per_s": round(done / t_run, 2),
+                       "F_first": F[0], "F_last": F[-1],
+                       "F_every_10": [F[i] for i in checkpoints],
+                       "rel_err_psi_every_10": err["psi"], "rel_err_q_every_10": err["q"],
+                       "monotone": all(b <= a for a, b in zip(F, F[1:])),
+                       "iterations_with_a_zero_step": gaps}
+        h.close()
+    return {"metric": "CG iterations/s, joint psi/q reconstruction (16 angles, 512^2 on 1024^2, 4 dist)",
+            "value": runs["noise-free"]["iterations_per_s"], "unit": "it/s", "n_gpus": 1,
+            "higher_is_better": True, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": "recon: medium workload chunk, psi0 = 1, q0 = reference image "
+                                   "propagated back to plane 0, DY directions, backtracking",
+                       "iterations": args.recon_iters},
+            "runs": runs}
+
+
 # ---------------------------------------------------------------- batch of reconstructions
 
 def batch_specs(seed, count=64, budget_gb=160.0):
@@ -701,6 +784,9 @@ def main():
     args = parse()
     if args.workload == "batch":
         print(json.dumps(run_batch(args)), flush=True)
+        return
+    if args.workload == "recon":
+        print(json.dumps(run_recon(args)), flush=True)
         return
     w = hs.workloads()[args.workload]
     if args.chunk:
