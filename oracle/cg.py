@@ -155,3 +155,31 @@ def reconstruct(psi0, q0, shifts, sqrt_d, sqrt_dref, geo, iters, gamma0=1.0,
         hist["beta_psi"].append(b_psi)
         hist["beta_q"].append(b_q)
     return {"psi": psi, "q": q, "hist": hist}
+
+
+def reconstruct_hierarchical(sqrt_d, sqrt_dref, shifts, geo, levels, q0=None, **kw):
+    """Hierarchical reconstruction (Sec. 3, on speeding up): for each (b, iters) of `levels`,
+    from the coarsest binning b to b = 1, run `reconstruct` on data binned by b (pixel b dx,
+    side n/b on a P/b grid, shifts t/b), starting from psi = 1 and the initial probe of the
+    binned reference image at the first level and from the previous level's psi and q
+    upsampled twice as dense afterwards.  Returns the list of per-level results."""
+    import dataclasses
+    out = []
+    psi = q = None
+    for i, (b, iters) in enumerate(levels):
+        g = dataclasses.replace(geo, n=geo.n // b, P=geo.P // b, pixel=geo.pixel * b)
+        d = holo.bin_amplitudes(sqrt_d, b)
+        dr = holo.bin_amplitudes(sqrt_dref, b) if sqrt_dref is not None else None
+        t = np.asarray(shifts, np.float64) / b
+        if i == 0:
+            psi = np.ones((d.shape[0], g.n, g.n), np.complex128)
+            q = holo.initial_probe(dr, g) if q0 is None else q0
+        else:
+            factor = levels[i - 1][0] // b
+            while factor > 1:
+                psi, q = holo.upsample2(psi), holo.upsample2(q)
+                factor //= 2
+        res = reconstruct(psi, q, t, d, dr, g, iters, **kw)
+        psi, q = res["psi"], res["q"]
+        out.append({"b": b, "psi": psi, "q": q, "hist": res["hist"]})
+    return out

@@ -176,6 +176,39 @@ def reference_field(q, geo):
     return crop(propagate(q, d["zeta"][0], geo.wavelength, geo.pixel), geo.n)
 
 
+def bin_amplitudes(a, b):
+    """Data binning of the hierarchical scheme (Sec. 3, on speeding up): intensities a^2
+    averaged over b x b pixel blocks of the last two axes, returned as amplitudes,
+    sqrt(mean_{b x b} a^2).  The side must be a multiple of b."""
+    a = np.asarray(a, dtype=np.float64)
+    n = a.shape[-1]
+    m = n // b
+    blocks = (a ** 2).reshape(a.shape[:-2] + (m, b, m, b))
+    return np.sqrt(blocks.mean(axis=(-3, -1)))
+
+
+def _upsample2_axis(x, axis):
+    """Linear interpolation to twice as many pixels along `axis` (pixel centres: fine pixel
+    2m sits at coarse coordinate m - 1/4, fine pixel 2m + 1 at m + 1/4), edges clamped."""
+    x = np.moveaxis(np.asarray(x), axis, -1)
+    N = x.shape[-1]
+    out = np.empty(x.shape[:-1] + (2 * N,), dtype=np.result_type(x, np.float64))
+    for f in range(2 * N):
+        c = (f + 0.5) / 2.0 - 0.5
+        i0 = int(np.floor(c))
+        w = c - i0
+        a, b = min(max(i0, 0), N - 1), min(max(i0 + 1, 0), N - 1)
+        out[..., f] = (1.0 - w) * x[..., a] + w * x[..., b]
+    return np.moveaxis(out, -1, axis)
+
+
+def upsample2(x):
+    """Extrapolation of a recovered field (psi or q) to a grid twice as dense (Sec. 3, on
+    speeding up); reading: separable linear interpolation at the fine pixel centres with
+    clamped edges."""
+    return _upsample2_axis(_upsample2_axis(x, -1), -2)
+
+
 def initial_probe(sqrt_dref, geo):
     """Initial probe: the reference image propagated back to sample plane 0 (Sec. 2, on the
     initial guess), q0 = D_{-zeta_0}(E sqrt(d~^r)).  Reading: E embeds the n x n amplitude in

@@ -518,6 +518,56 @@ def test_initial_probe_reproduces_reference_amplitude():
     np.testing.assert_allclose(holo.reference_field(q0, geo), sqrt_dref, atol=1e-12)
 
 
+def test_bin_amplitudes_conserves_intensity_and_constants():
+    """Binning averages intensities: a constant stays, block-constant intensities bin exactly,
+    and the mean intensity is preserved."""
+    rng = _rng(29)
+    a = rng.uniform(0.2, 2.0, (3, 16, 16))
+    for b in (1, 2, 4, 8):
+        ab = holo.bin_amplitudes(a, b)
+        assert ab.shape == (3, 16 // b, 16 // b)
+        assert np.mean(ab ** 2) == pytest.approx(np.mean(a ** 2), rel=1e-13)
+    np.testing.assert_allclose(holo.bin_amplitudes(np.full((8, 8), 1.7), 4), 1.7, rtol=1e-14)
+    blocks = rng.uniform(0.5, 1.5, (4, 4))
+    fine = np.sqrt(np.kron(blocks ** 2, np.ones((2, 2))))
+    np.testing.assert_allclose(holo.bin_amplitudes(fine, 2), np.sqrt(blocks ** 2), rtol=1e-14)
+
+
+def test_upsample2_is_linear_interpolation_at_pixel_centres():
+    """Twice-as-dense extrapolation: constants stay, a linear ramp is reproduced at the
+    interior fine pixel centres (coarse coordinate (f + 1/2)/2 - 1/2), the edges are clamped,
+    and the mean of each fine pixel pair is the [1/8, 3/4, 1/8] smoothing of the coarse row."""
+    N = 9
+    ramp = 0.3 * np.arange(N) - 1.1
+    up = holo.upsample2(np.tile(ramp, (N, 1)))
+    f = np.arange(2 * N)
+    want = 0.3 * ((f + 0.5) / 2 - 0.5) - 1.1
+    np.testing.assert_allclose(up[4, 1:-1], want[1:-1], rtol=1e-13, atol=1e-14)
+    assert up[4, 0] == pytest.approx(ramp[0]) and up[4, -1] == pytest.approx(ramp[-1])
+    np.testing.assert_allclose(holo.upsample2(np.full((5, 5), 2.0 - 1.0j)), 2.0 - 1.0j, rtol=1e-14)
+    rng = _rng(31)
+    x = rng.standard_normal(N)
+    u = holo._upsample2_axis(x, -1)
+    pair = 0.5 * (u[0::2] + u[1::2])
+    np.testing.assert_allclose(pair[1:-1], 0.125 * x[:-2] + 0.75 * x[1:-1] + 0.125 * x[2:], rtol=1e-13)
+
+
+def test_hierarchical_reconstruction_levels():
+    """The hierarchical driver: one level without binning is the plain driver from psi = 1 and
+    the initial probe; with binning every level is monotone, sizes double, and the last level
+    works on the full grid."""
+    geo, psi, q, t, sqrt_d, sqrt_dref = _small_problem(n=32, P=64, K=2, noiseless=True, seed=8)
+    one = cg.reconstruct_hierarchical(sqrt_d, sqrt_dref, t, geo, [(1, 3)])
+    ref = cg.reconstruct(np.ones_like(psi), holo.initial_probe(sqrt_dref, geo), t, sqrt_d,
+                         sqrt_dref, geo, 3)
+    np.testing.assert_allclose(one[0]["hist"]["F"], ref["hist"]["F"], rtol=1e-13)
+    lev = cg.reconstruct_hierarchical(sqrt_d, sqrt_dref, t, geo, [(4, 3), (2, 3), (1, 3)])
+    assert [r["psi"].shape[-1] for r in lev] == [8, 16, 32] and lev[-1]["q"].shape == (64, 64)
+    for r in lev:
+        F = np.array(r["hist"]["F"])
+        assert np.all(np.diff(F) <= 0.0)
+
+
 def test_reconstruction_is_monotone():
     """The line search never lets F increase (Sec. 2, after Eq. DaiYuan2)."""
     geo, psi, q, t, sqrt_d, sqrt_dref = _small_problem(n=16, P=32, K=2, noiseless=True, seed=6)
