@@ -50,7 +50,7 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
     ap.add_argument("--workload", default="large",
-                    choices=("large", "autograd", "medium", "batch", "recon"))
+                    choices=("large", "autograd", "medium", "batch", "recon", "hier"))
     ap.add_argument("--recon-iters", type=int, default=200,
                     help="CG iterations of --workload recon (convergence run)")
     ap.add_argument("--functional", choices=("amplitude", "intensity"), default="amplitude",
@@ -697,6 +697,76 @@ def run_recon(args):
             "runs": runs}
 
 
+def run_hier(args):
+    """Hierarchical reconstruction (Sec. 3) against a flat one with the same wall-clock budget
+    on the recon problem (16 angles of the medium workload, noise-free data): levels bin 8, 4,
+    2, 1 with 400, 200, 100, 50 iterations, then the unbinned driver alone for as long as the
+    hierarchy took.  Reports F on the full grid and the psi error of both."""
+    import torch
+    from paper_2407_20304_gb300 import Holo
+    from paper_2407_20304_gb300.cg import Reconstruction
+    from paper_2407_20304_gb300.hierarchy import Hierarchy
+    import __graft_entry__
+    __graft_entry__.build()
+    w = hs.workloads()["medium"]
+    g = hs.WORKLOAD_GEOMETRY
+    n, P, J, K = w.n, w.P, w.n_dist, 16
+    rng = hs.rng_for(w.seed, 31)
+    psi_true = torch.from_numpy(hs.object_stack(w, range(K), rng).astype(np.complex64)).cuda()
+    q_true = torch.from_numpy(hs.striped_probe(P, w.probe_sigma, rng).astype(np.complex64)).cuda()
+    shifts = hs.sample_shifts(K, J, rng).astype(np.float32)
+    _, zeta = derived(g["z"][:J], g["Z"])
+    lo = P // 2 - n // 2
+    h = Holo(n, K, J, g["wavelength"], g["pixel"], g["Z"], g["z"][:J], pad=P)
+    h.set_shifts(shifts)
+    h.set_data(torch.ones((K, J, n, n), dtype=torch.float32, device="cuda"),
+               torch.ones((n, n), dtype=torch.float32, device="cuda"))
+    h.set_probe(q_true)
+    u = torch.empty((K, J, n, n), dtype=torch.complex64, device="cuda")
+    h.forward(psi_true, u_out=u)
+    sqrt_d = u.abs().contiguous()
+    sqrt_dref = h.propagate(q_true, zeta[0])[lo:lo + n, lo:lo + n].abs().contiguous()
+    del u
+    h.set_data(sqrt_d, sqrt_dref)
+    levels = ((8, 400), (4, 200), (2, 100), (1, 50))
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    hier = Hierarchy(n, K, J, g["wavelength"], g["pixel"], g["Z"], g["z"][:J], shifts, pad=P,
+                     levels=levels)
+    psi_h, q_h = hier.run(sqrt_d, sqrt_dref)
+    torch.cuda.synchronize()
+    t_hier = time.perf_counter() - t0
+    h.set_probe(q_h)
+    F_h = h.forward(psi_h)
+    err_h = float((psi_h - psi_true).norm() / psi_true.norm())
+    # flat: the unbinned driver for the same wall time
+    q0 = h.initial_probe(sqrt_dref)
+    rec = Reconstruction(h, torch.ones((K, n, n), dtype=torch.complex64, device="cuda"), q0.clone())
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    its = 0
+    while time.perf_counter() - t0 < t_hier:
+        rec.run(10)
+        its += 10
+    torch.cuda.synchronize()
+    t_flat = time.perf_counter() - t0
+    F_f = rec.history["F"][-1]
+    err_f = float((rec.psi - psi_true).norm() / psi_true.norm())
+    h.close()
+    per_level = [{"binning": r["b"], "iterations": len(r["history"]["F"]) - 1,
+                  "F_first": r["history"]["F"][0], "F_last": r["history"]["F"][-1]}
+                 for r in hier.results]
+    return {"metric": "full-grid F after equal wall time, hierarchical vs flat reconstruction",
+            "value": round(F_h, 4), "unit": "F2", "higher_is_better": False, "n_gpus": 1,
+            "dtype": "f32", "data": "synthetic",
+            "config": {"workload": "hier: 16 angles of the medium workload (psi 512^2 on 1024^2, "
+                                   "4 distances), noise-free, levels " + str(levels)},
+            "hierarchical": {"seconds": round(t_hier, 3), "F_full_grid": F_h,
+                             "rel_err_psi": err_h, "levels": per_level},
+            "flat": {"seconds": round(t_flat, 3), "iterations": its, "F_full_grid": F_f,
+                     "rel_err_psi": err_f}}
+
+
 # ---------------------------------------------------------------- batch of reconstructions
 
 def batch_specs(seed, count=64, budget_gb=160.0):
@@ -787,6 +857,9 @@ def main():
         return
     if args.workload == "recon":
         print(json.dumps(run_recon(args)), flush=True)
+        return
+    if args.workload == "hier":
+        print(json.dumps(run_hier(args)), flush=True)
         return
     w = hs.workloads()[args.workload]
     if args.chunk:

@@ -175,6 +175,19 @@ holo_status holo_step(holo_ctx* ctx, void* x, const void* eta, double gamma, lon
 holo_status holo_direction(holo_ctx* ctx, void* eta, const void* g, double beta,
                            long long n_c64);
 
+/* Hierarchical reconstruction (Sec. 3, on speeding up: iterations on binned data, then the
+ * recovered object and probe extrapolated to a grid twice as dense).  Context-free,
+ * asynchronous on `stream` (a cudaStream_t, NULL for the legacy stream).
+ * holo_bin_amplitudes: count amplitude images (dev f32 [count][n][n]) -> binned amplitudes
+ *   (dev f32 [count][n/b][n/b]) = sqrt(mean of a^2 over b x b blocks), i.e. the intensities
+ *   are averaged.  HOLO_ERR_ARG unless n is a multiple of b >= 1.
+ * holo_upsample2: count complex images (dev complex64 [count][n][n]) -> [count][2n][2n] by
+ *   linear interpolation at the fine pixel centres (fine pixel f at coarse coordinate
+ *   (f + 1/2)/2 - 1/2), edges clamped.  in and out must not overlap. */
+holo_status holo_bin_amplitudes(const float* in, long long count, int n, int b, float* out,
+                                void* stream);
+holo_status holo_upsample2(const void* in, long long count, int n, void* out, void* stream);
+
 /* Initial probe (Sec. 2, on the initial guess): the reference image propagated back to
  * sample plane 0, q_out = D_{-zeta_0}(E sqrt_dref), where E embeds the n x n amplitude
  * sqrt_dref (dev f32 [n][n]) in the P x P grid by repeating its edge values.  q_out: dev

@@ -23,7 +23,8 @@ STATUS = {0: "HOLO_OK", 1: "HOLO_ERR_ARG", 2: "HOLO_ERR_CUDA", 3: "HOLO_ERR_OOM"
 EXPORTS = ("holo_create", "holo_destroy", "holo_set_shifts", "holo_set_data", "holo_set_probe",
            "holo_forward", "holo_gradient", "holo_gradient_host", "holo_propagate", "holo_dot",
            "holo_step", "holo_direction", "holo_dy_dots", "holo_direction_step", "holo_set_functional",
-           "holo_initial_probe", "holo_set_timing", "holo_get_timing", "holo_dot_noalloc",
+           "holo_initial_probe", "holo_bin_amplitudes", "holo_upsample2", "holo_set_timing",
+           "holo_get_timing", "holo_dot_noalloc",
            "holo_set_stream", "holo_read_loss",
            "holo_workspace_bytes", "holo_launch_count", "holo_status_string", "holo_last_error")
 
@@ -77,6 +78,8 @@ def load():
         "holo_dy_dots": [P, P, P, P, LL, ctypes.POINTER(D)],
         "holo_set_functional": [P, ctypes.c_int],
         "holo_initial_probe": [P, P, P],
+        "holo_bin_amplitudes": [P, LL, ctypes.c_int, ctypes.c_int, P, P],
+        "holo_upsample2": [P, LL, ctypes.c_int, P, P],
         "holo_direction_step": [P, P, P, P, D, D, LL],
         "holo_dot_noalloc": [P, P, LL, ctypes.POINTER(D), P],
         "holo_set_stream": [P, P],

@@ -1061,6 +1061,22 @@ holo_status holo_direction(holo_ctx* c, void* eta, const void* g, double beta, l
   return HOLO_OK;
 }
 
+holo_status holo_bin_amplitudes(const float* in, long long count, int n, int b, float* out,
+                                void* stream) {
+  if (!in || !out || count < 0 || n < 1 || b < 1 || n % b) return HOLO_ERR_ARG;
+  if (holo::launch_bin_amplitudes(in, count, n, b, out, (cudaStream_t)stream) != cudaSuccess)
+    return HOLO_ERR_CUDA;
+  return HOLO_OK;
+}
+
+holo_status holo_upsample2(const void* in, long long count, int n, void* out, void* stream) {
+  if (!in || !out || count < 0 || n < 1 || in == out) return HOLO_ERR_ARG;
+  if (holo::launch_upsample2((const float2*)in, count, n, (float2*)out, (cudaStream_t)stream) !=
+      cudaSuccess)
+    return HOLO_ERR_CUDA;
+  return HOLO_OK;
+}
+
 holo_status holo_initial_probe(holo_ctx* c, const float* sqrt_dref, void* q_out) {
   if (!c || !sqrt_dref || !q_out) return fail(c, HOLO_ERR_ARG, "null argument");
   const int P = c->P;

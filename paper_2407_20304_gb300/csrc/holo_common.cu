@@ -154,6 +154,55 @@ __global__ void k_embed_edge(const float* __restrict__ a, int n, int P, float2* 
   }
 }
 
+// Hierarchical reconstruction: out = sqrt(mean of in^2 over b x b blocks), count images of
+// n x n -> (n/b) x (n/b); one thread per output pixel.
+__global__ void k_bin_amplitudes(const float* __restrict__ in, long long count, int n, int b,
+                                 float* __restrict__ out) {
+  const int m = n / b;
+  const long long total = count * m * m;
+  const float inv = 1.f / (float)(b * b);
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
+       e += (long long)gridDim.x * blockDim.x) {
+    const long long img = e / ((long long)m * m);
+    const int r = (int)(e % ((long long)m * m));
+    const int i = r / m, j = r % m;
+    const float* src = in + img * n * n + (long long)(i * b) * n + j * b;
+    float acc = 0.f;
+    for (int y = 0; y < b; ++y)
+      for (int x = 0; x < b; ++x) {
+        const float v = src[(long long)y * n + x];
+        acc = fmaf(v, v, acc);
+      }
+    out[e] = sqrtf(acc * inv);
+  }
+}
+
+// Linear interpolation to a twice-as-dense grid: fine pixel f sits at coarse coordinate
+// (f + 1/2)/2 - 1/2 (weights 3/4 and 1/4 of the two nearest coarse pixels), edges clamped;
+// count complex images of N x N -> 2N x 2N.
+__global__ void k_upsample2(const float2* __restrict__ in, long long count, int N,
+                            float2* __restrict__ out) {
+  const int M = 2 * N;
+  const long long total = count * M * M;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
+       e += (long long)gridDim.x * blockDim.x) {
+    const long long img = e / ((long long)M * M);
+    const int r = (int)(e % ((long long)M * M));
+    const int fy = r / M, fx = r % M;
+    // nearest coarse pixel m = f / 2 gets 3/4; its neighbour on the side of f gets 1/4
+    const int my = fy >> 1, mx = fx >> 1;
+    const int ny = min(max(my + ((fy & 1) ? 1 : -1), 0), N - 1);
+    const int nx = min(max(mx + ((fx & 1) ? 1 : -1), 0), N - 1);
+    const float2* src = in + img * N * N;
+    const float2 a = src[(long long)my * N + mx], b = src[(long long)my * N + nx];
+    const float2 c = src[(long long)ny * N + mx], d = src[(long long)ny * N + nx];
+    float2 v;
+    v.x = 0.5625f * a.x + 0.1875f * (b.x + c.x) + 0.0625f * d.x;
+    v.y = 0.5625f * a.y + 0.1875f * (b.y + c.y) + 0.0625f * d.y;
+    out[e] = v;
+  }
+}
+
 // Deterministic single-block sum of FP64 partials.
 __global__ void k_sum_f64(const double* __restrict__ part, int count, double* out, int accumulate) {
   __shared__ double red[32];
@@ -305,6 +354,22 @@ cudaError_t launch_ref_residual(const float2* bref, const float* sqrt_dref, long
 
 cudaError_t launch_embed_edge(const float* a, int n, int P, float2* q, cudaStream_t s) {
   k_embed_edge<<<grid_for((long long)P * P), kThreads, 0, s>>>(a, n, P, q);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_bin_amplitudes(const float* in, long long count, int n, int b, float* out,
+                                  cudaStream_t s) {
+  const long long total = count * (n / b) * (long long)(n / b);
+  if (total <= 0) return cudaSuccess;
+  k_bin_amplitudes<<<grid_for(total), kThreads, 0, s>>>(in, count, n, b, out);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_upsample2(const float2* in, long long count, int N, float2* out,
+                             cudaStream_t s) {
+  const long long total = count * 4LL * N * N;
+  if (total <= 0) return cudaSuccess;
+  k_upsample2<<<grid_for(total), kThreads, 0, s>>>(in, count, N, out);
   return cudaGetLastError();
 }
 

@@ -114,6 +114,10 @@ cudaError_t launch_ref_residual(const float2* bref, const float* sqrt_dref, long
                                 float2* rref, double* part, int nblocks, int functional,
                                 cudaStream_t s);
 cudaError_t launch_embed_edge(const float* a, int n, int P, float2* q, cudaStream_t s);
+cudaError_t launch_bin_amplitudes(const float* in, long long count, int n, int b, float* out,
+                                  cudaStream_t s);
+cudaError_t launch_upsample2(const float2* in, long long count, int N, float2* out,
+                             cudaStream_t s);
 cudaError_t launch_sum_f64(const double* part, int count, double* out, int accumulate,
                            cudaStream_t s);
 cudaError_t launch_loss_total(double* red, double wref, int acc, int first, cudaStream_t s);

@@ -65,6 +65,40 @@ def dot_noalloc(a, b, stream=None):
     return out.value
 
 
+def bin_amplitudes(a, b, stream=None):
+    """Amplitudes [..., n, n] (float32 CUDA) binned by b: sqrt of the mean intensity of each
+    b x b block (holo_bin_amplitudes)."""
+    import torch
+    n = a.shape[-1]
+    if a.shape[-2] != n or n % b:
+        raise ValueError("square images with a side divisible by b")
+    out = torch.empty(a.shape[:-2] + (n // b, n // b), dtype=torch.float32, device=a.device)
+    pa = _ptr(a, torch.float32, None, "a")
+    s = stream if stream is not None else torch.cuda.current_stream(a.device)
+    st = _lib.load().holo_bin_amplitudes(pa, a.numel() // (n * n), n, b,
+                                         _ptr(out, torch.float32, None, "out"),
+                                         ctypes.c_void_p(s.cuda_stream))
+    _check(_lib.load(), None, st, "holo_bin_amplitudes")
+    return out
+
+
+def upsample2(x, stream=None):
+    """Complex fields [..., n, n] (complex64 CUDA) extrapolated to [..., 2n, 2n] by linear
+    interpolation at the fine pixel centres (holo_upsample2)."""
+    import torch
+    n = x.shape[-1]
+    if x.shape[-2] != n:
+        raise ValueError("square images")
+    out = torch.empty(x.shape[:-2] + (2 * n, 2 * n), dtype=torch.complex64, device=x.device)
+    px = _ptr(x, torch.complex64, None, "x")
+    s = stream if stream is not None else torch.cuda.current_stream(x.device)
+    st = _lib.load().holo_upsample2(px, x.numel() // (n * n), n,
+                                    _ptr(out, torch.complex64, None, "out"),
+                                    ctypes.c_void_p(s.cuda_stream))
+    _check(_lib.load(), None, st, "holo_upsample2")
+    return out
+
+
 class Holo:
     """One reconstruction problem's geometry and workspace on one GPU.
 

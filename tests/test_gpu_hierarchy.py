@@ -1,0 +1,75 @@
+"""Hierarchical reconstruction on the GPU (binning, twice-as-dense extrapolation, levels of
+the joint driver) against the FP64 oracle."""
+
+import numpy as np
+import pytest
+
+import holo_synth as hs
+from oracle import cg as ocg
+from oracle import holo as oh
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+G = hs.WORKLOAD_GEOMETRY
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    import __graft_entry__
+    __graft_entry__.build()
+
+
+def rel(a, b):
+    return float(np.linalg.norm(a - b) / np.linalg.norm(b))
+
+
+@pytest.mark.parametrize("n,b,count", [(64, 2, 3), (64, 8, 1), (96, 4, 2), (16, 1, 1)])
+def test_binning_matches_oracle(n, b, count):
+    from paper_2407_20304_gb300.holo import bin_amplitudes
+    rng = np.random.default_rng(n + b)
+    a = rng.uniform(0.1, 2.0, (count, n, n)).astype(np.float32)
+    got = bin_amplitudes(torch.from_numpy(a).cuda(), b).cpu().numpy()
+    assert got.shape == (count, n // b, n // b)
+    assert rel(got.astype(np.float64), oh.bin_amplitudes(a.astype(np.float64), b)) < 1e-6
+
+
+@pytest.mark.parametrize("n,count", [(8, 1), (33, 2), (128, 3)])
+def test_upsampling_matches_oracle(n, count):
+    from paper_2407_20304_gb300.holo import upsample2
+    rng = np.random.default_rng(n)
+    x = (rng.standard_normal((count, n, n)) + 1j * rng.standard_normal((count, n, n))).astype(np.complex64)
+    got = upsample2(torch.from_numpy(x).cuda()).cpu().numpy()
+    assert got.shape == (count, 2 * n, 2 * n)
+    assert rel(got.astype(np.complex128), oh.upsample2(x.astype(np.complex128))) < 1e-6
+
+
+def test_hierarchy_follows_the_oracle():
+    """Three levels (bin 4, 2, 1) of 3 iterations each: the first level's F history matches the
+    FP64 driver's, every level is monotone, and the final F agrees to a few per cent (FP32
+    line-search decisions may part from FP64 ones at near-ties and the levels compound)."""
+    from paper_2407_20304_gb300.hierarchy import Hierarchy
+    n, P, K, J = 64, 128, 2, 4
+    rng = hs.rng_for(hs.SEED_BASE + 11, 0)
+    geo = oh.Geometry(G["wavelength"], G["pixel"], G["Z"], G["z"], n, P)
+    w = hs.Workload("h", n, P, K, J, "ellipses", n * 40.0 / 128, 0.0, K, 0)
+    psi_true = hs.object_stack(w, range(K), rng)
+    q_true = hs.striped_probe(P, n * 40.0 / 128, rng)
+    t = hs.sample_shifts(K, J, rng).astype(np.float32).astype(np.float64)
+    sqrt_d = np.abs(oh.forward(psi_true, q_true, t, geo)).astype(np.float32)
+    sqrt_dref = np.abs(oh.reference_field(q_true, geo)).astype(np.float32)
+    levels = [(4, 3), (2, 3), (1, 3)]
+    hier = Hierarchy(n, K, J, geo.wavelength, geo.pixel, geo.Z, geo.z, t, pad=P, levels=levels)
+    psi, q = hier.run(torch.from_numpy(sqrt_d).cuda(), torch.from_numpy(sqrt_dref).cuda())
+    ref = ocg.reconstruct_hierarchical(sqrt_d.astype(np.float64), sqrt_dref.astype(np.float64),
+                                       t, geo, levels)
+    assert psi.shape == (K, n, n) and q.shape == (P, P)
+    for lvl, (mine, theirs) in enumerate(zip(hier.results, ref)):
+        F, Fo = np.array(mine["history"]["F"]), np.array(theirs["hist"]["F"])
+        print(f"level b={mine['b']}: F gpu {F} oracle {Fo}")
+        assert np.all(np.diff(F) <= 0)
+        if lvl == 0:
+            np.testing.assert_allclose(F[:2], Fo[:2], rtol=1e-4)
+    Fl, Fol = hier.results[-1]["history"]["F"][-1], ref[-1]["hist"]["F"][-1]
+    assert abs(Fl - Fol) / Fol < 5e-2
