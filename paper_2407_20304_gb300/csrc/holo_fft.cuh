@@ -32,7 +32,10 @@
 //
 // Synchronisation: every thread of a line group calls the transform the same number of
 // times; the Sync policy is a block-wide barrier or a named barrier per line group.  The
-// buffer must be free when a transform starts, and is free again when it returns.
+// buffer must be free when a transform starts.  It is free again when fft_inv returns; after
+// fft_fwd at P = 4096 other thread groups may still read their rows of the last (group-local)
+// exchange, so an fft_inv may follow directly (it starts on the same threads' rows) and any
+// other use of the buffer needs a barrier first.
 
 #pragma once
 
@@ -97,6 +100,7 @@ __host__ __device__ constexpr int ilog2c(int x) { return x <= 1 ? 0 : 1 + ilog2c
 __host__ __device__ constexpr int ipow16(int s) { return s == 0 ? 1 : 16 * ipow16(s - 1); }
 
 __device__ __forceinline__ int spad(int a) { return a + (a >> 4); }
+__host__ __device__ constexpr int spad_c(int a) { return a + (a >> 4); }
 
 __host__ __device__ constexpr bool is_pow2c(int x) { return x > 0 && (x & (x - 1)) == 0; }
 
@@ -129,12 +133,18 @@ struct Fft {
   // radix-3 step: W_P^n and W_P^{2n}, n < PB, appended to both tables
   static constexpr int TW = TW_BASE + (R3 ? 2 * PB : 0);
   static constexpr int ROOTS = ROOTS_BASE + (R3 ? 2 * PB : 0);
+  // P = 4096: the exchange before the last radix-16 stage stays inside each group of 16
+  // threads t = 16a .. 16a + 15 (which every kernel keeps in one warp), so it needs a warp
+  // barrier only; the last stage then numbers its threads k1 + 16 a (see fwd_from).
+  static constexpr bool HW = !R3 && RB == 0 && N16 == 3;
+  static constexpr int HW_ROW = 17, HW_GROUP = 16 * 17;  // group region: 16 rows of 17
   // line element held in register c of thread t, and the frequency it holds after fft_fwd
   __host__ __device__ static constexpr int pos(int t, int c) {
     return R3 ? t % TB + TB * c + PB * (t / TB) : t + T * c;
   }
   __host__ __device__ static constexpr int fpos(int t, int c) {
-    return R3 ? 3 * (t % TB + TB * c) + t / TB : t + T * c;
+    return R3 ? 3 * (t % TB + TB * c) + t / TB
+              : (HW ? (t >> 4) + (T / 16) * (t & 15) + T * c : t + T * c);
   }
 };
 
@@ -353,7 +363,14 @@ __device__ __forceinline__ void fwd_from(float2 (&v)[16], float2* __restrict__ s
   using F = Fft<P>;
   if constexpr (S < F::N16) {
     constexpr int M = F::M(S);
-    if constexpr (S > 0) {
+    constexpr bool group_in = F::HW && S == F::N16 - 1, group_out = F::HW && S == F::N16 - 2;
+    if constexpr (group_in) {
+      // thread 16 a + k1 takes digit d0 of (a, k1) from the rows its group wrote; no barrier
+      // after the read: the only later writes to these rows come from the same threads
+      const float2* hr = sm + (t >> 4) * F::HW_GROUP + F::HW_ROW * (t & 15);
+#pragma unroll
+      for (int c = 0; c < 16; ++c) v[c] = hr[c];
+    } else if constexpr (S > 0) {
       const int mu = t % M, ka = t / M;
 #pragma unroll
       for (int c = 0; c < 16; ++c) v[c] = sm[spad(c * M + mu + 16 * M * ka)];
@@ -361,7 +378,13 @@ __device__ __forceinline__ void fwd_from(float2 (&v)[16], float2* __restrict__ s
     }
     dft16<false>(v);
     if constexpr (M > 1) tw.template apply<P, S, false>(v, t % M);
-    if constexpr (S < F::NST - 1) {
+    if constexpr (group_out) {
+      // thread 16 a + mu holds digit k1 = k of (mu, a): row k, column mu of its group's region
+      float2* hr = sm + (t >> 4) * F::HW_GROUP + (t & 15);
+#pragma unroll
+      for (int k = 0; k < 16; ++k) hr[F::HW_ROW * k] = v[k];
+      __syncwarp();
+    } else if constexpr (S < F::NST - 1) {
 #pragma unroll
       for (int k = 0; k < 16; ++k) sm[spad(t + F::T * k)] = v[k];
       HOLO_SYNC();
@@ -410,8 +433,20 @@ __device__ __forceinline__ void inv_from(float2 (&v)[16], float2* __restrict__ s
     constexpr int M = F::M(S);
     if constexpr (M > 1) tw.template apply<P, S, true>(v, t % M);
     dft16<true>(v);
-    if constexpr (S > 0) {
+    if constexpr (F::HW && S == F::N16 - 1) {
+      // adjoint of the group exchange: thread 16 a + k1 writes its row, thread 16 a + mu
+      // reads column mu back
+      float2* hr = sm + (t >> 4) * F::HW_GROUP;
+#pragma unroll
+      for (int c = 0; c < 16; ++c) hr[F::HW_ROW * (t & 15) + c] = v[c];
+      __syncwarp();
+#pragma unroll
+      for (int k = 0; k < 16; ++k) v[k] = hr[F::HW_ROW * k + (t & 15)];
+      inv_from<P, S - 1, Sync, TW>(v, sm, tw, t, sync);
+    } else if constexpr (S > 0) {
       const int mu = t % M, ka = t / M;
+      // other groups may still be reading their rows of the group exchange
+      if constexpr (F::HW && S == F::N16 - 2) HOLO_SYNC();
 #pragma unroll
       for (int c = 0; c < 16; ++c) sm[spad(c * M + mu + 16 * M * ka)] = v[c];
       HOLO_SYNC();

@@ -39,7 +39,9 @@ namespace holo {
 template <int P>
 struct SmemHead {
   static constexpr int ROOTS = (Fft<P>::ROOTS + 1) & ~1;
-  static constexpr int CHIRP = (P / 2 + 2) & ~1;
+  // half chirp table; padded (entry i at i + i/16) where the frequency layout makes lanes
+  // read entries 16 apart (Fft<P>::HW), so those reads stay free of bank conflicts
+  static constexpr int CHIRP = ((Fft<P>::HW ? spad_c(P / 2) : P / 2) + 2) & ~1;
   static constexpr int WORDS = ROOTS + CHIRP;
 };
 
@@ -126,13 +128,14 @@ __device__ __forceinline__ double block_sum_f64(double v, double* red) {
 // P/2 + 1 non-negative frequencies suffices: entry f for f <= P/2, entry P - f above.
 template <int P>
 __device__ __forceinline__ float2 chirp_half(const float2* __restrict__ tab, int f) {
-  return tab[f <= P / 2 ? f : P - f];
+  const int i = f <= P / 2 ? f : P - f;
+  return tab[Fft<P>::HW ? spad(i) : i];
 }
 
 // Copy the half chirp table of distance j into shared memory (block-wide).
 template <int P>
 __device__ __forceinline__ void load_chirp_half(float2* dst, const float2* __restrict__ src) {
-  for (int i = threadIdx.x; i <= P / 2; i += blockDim.x) dst[i] = src[i];
+  for (int i = threadIdx.x; i <= P / 2; i += blockDim.x) dst[Fft<P>::HW ? spad(i) : i] = src[i];
 }
 
 // ------------------------------------------------------------------ generic D-step
