@@ -121,6 +121,8 @@ struct holo_ctx {
   double* d_part = nullptr;
   long long part_cap = 0;
   double* d_dot3 = nullptr;     // partial sums of holo_dy_dots: 3 x (8 x SM count)
+  float2* d_tpart = nullptr;    // pass B (plane-split form): partial residual sums
+  size_t tpart_bytes = 0;
   double* d_red = nullptr;      // 8 doubles: loss, reference term, dot, running loss, DY dots
   double* h_red = nullptr;      // pinned, 8 doubles
   // host-buffer staging
@@ -447,6 +449,39 @@ PassArgs pass_args(holo_ctx* c, int k0, int nk, const void* psi) {
 //                d_red[0] and the call / running totals (k_loss_total); pass B writes or adds
 //                T = ext sum_kj r_kj (+ w_ref r_ref on the first part);
 //   eval_qgrad:  grad_q of the whole chunk from T and the per-plane conj(w) v.
+// Pass B's grid.  Whole column groups go to the blocks in rounds; when that leaves a partial
+// last round and fewer than three full ones (small n), the plane-split form spreads the
+// last round's (group, plane) items over all blocks, and its partial residual sums need
+// tslots slots of [n][C] per block.
+holo_status pass_b_grid(holo_ctx* c, PassArgs& a, bool gradient, int* nblocks) {
+  const int groups = a.pass_b_items;
+  const int full = c->ops->pass_b_blocks(1 << 30, c->n, a.max_box_rows);
+  a.pb_split = groups % full != 0 && groups / full < 3;
+  a.tslots = 0;
+  if (!a.pb_split) {
+    *nblocks = std::min(full, groups);
+    return HOLO_OK;
+  }
+  const long long per = (long long)a.J * a.nk;
+  const int nbx = c->ops->pass_b_blocks_split((long long)groups * per, c->n);
+  const long long rounds = groups / nbx, tail = groups - rounds * nbx, titems = tail * per;
+  const long long range = (titems + nbx - 1) / nbx;
+  a.tslots = titems > 0 ? (int)((range + per - 1) / per + 1) : 0;
+  *nblocks = nbx;
+  if (!gradient) return HOLO_OK;
+  const size_t need = sizeof(float2) * (size_t)nbx * a.tslots * c->n * c->ops->pass_b_cols;
+  if (need > c->tpart_bytes) {
+    dfree(c, c->d_tpart, c->tpart_bytes);
+    c->d_tpart = nullptr;
+    c->tpart_bytes = 0;
+    holo_status st = dalloc(c, (void**)&c->d_tpart, need);
+    if (st) return st;
+    c->tpart_bytes = need;
+  }
+  a.tpart = c->d_tpart;
+  return HOLO_OK;
+}
+
 holo_status eval_begin(holo_ctx* c, PassArgs& a) {
   PassTimer tm_red(c, HOLO_T_REDUCE);
   const int nbx = c->ops->pass_b_blocks(a.pass_b_items, c->n, a.max_box_rows);
@@ -467,7 +502,11 @@ holo_status eval_begin(holo_ctx* c, PassArgs& a) {
 // first: the first part of the call (adds the reference term, starts the call total);
 // acc: add to the running total (user flags on the first part, always on later parts).
 holo_status eval_planes(holo_ctx* c, PassArgs& a, bool gradient, bool first, int acc) {
-  const int nbx = c->ops->pass_b_blocks(a.pass_b_items, c->n, a.max_box_rows);
+  int nbx = 0;
+  {
+    holo_status st = pass_b_grid(c, a, gradient, &nbx);
+    if (st) return st;
+  }
   {
     PassTimer tm(c, HOLO_T_PASS_A);
     HOLO_LAUNCH(c, c->ops->pass_a(a, c->stream));
@@ -475,6 +514,8 @@ holo_status eval_planes(holo_ctx* c, PassArgs& a, bool gradient, bool first, int
   {
     PassTimer tm(c, HOLO_T_PASS_B);
     HOLO_LAUNCH(c, c->ops->pass_b(a, gradient ? 1 : 0, nbx, c->stream));
+    // the last round's combine kernel of the plane-split form
+    if (gradient && a.pb_split && a.pass_b_items % nbx) c->launches++;
   }
   {
     PassTimer tm_red(c, HOLO_T_REDUCE);
@@ -680,7 +721,8 @@ holo_status holo_destroy(holo_ctx* c) {
                   c->d_chirp_tmp, c->d_planes, c->d_pj,          c->d_b,
                   c->ybuf,    c->gkbuf,        c->d_scratch,
                   c->d_Gp,    c->d_T,          c->d_rref,        c->d_part,
-                  c->d_red,   c->d_dot3,       c->s_psi,         c->s_gpsi,        c->s_data,
+                  c->d_red,   c->d_dot3,       c->d_tpart,       c->s_psi,         c->s_gpsi,
+                  c->s_data,
                   c->s_q,     c->s_gq,         c->d_xtap,        c->d_ytap,
                   c->d_xadj,  c->d_yadj,       c->d_lines};
   for (void* p : ptrs)

@@ -67,6 +67,9 @@ struct PassArgs {
   long long ystride;
   float2* tq;                  // [n][n]: ext sum_kj r_kj + w_ref r_ref (gradient only)
   int tq_accumulate;           // add to tq instead of overwriting (later parts of a chunk)
+  int pb_split;                // pass B: last round split by planes (k_pass_b_split)
+  float2* tpart;               // ... its partial S: per block tslots slots of [n][C]
+  int tslots;
   int functional;              // 0: F2 (amplitudes, Eq. min1), 1: F1 (intensities, Eq. min2)
   const float2* rref;          // [n][n] reference residual, or null
   float wref;
@@ -101,7 +104,9 @@ struct Ops {
   cudaError_t (*pass_c)(const PassArgs&, cudaStream_t);
   int (*pass_b_groups)(int n);              // column groups of pass B for side n
   int (*pass_b_blocks)(int items, int n, int rows);  // persistent grid of pass B
+  int (*pass_b_blocks_split)(long long items, int n);  // ... of its plane-split form
   int twiddle_count;
+  int pass_b_cols;                          // columns per pass-B group (C)
 };
 
 const Ops* ops_for(int P);

@@ -404,6 +404,207 @@ __global__ void __launch_bounds__(ColCfg<P>::NT) k_pass_b(PassArgs a) {
   if (threadIdx.x == 0) a.loss_part[blockIdx.x] = s;
 }
 
+// Pass B when the column groups do not fill the GPU a few times over (fewer than three full
+// rounds): whole groups in rounds as k_pass_b, then the (group, plane) items of the last,
+// partial round split evenly over all blocks in (group, distance, angle) order.  Each block
+// leaves S of every group it touched in its own slot; k_pass_b_tail adds the slots in block
+// order (a fixed order) into T.  The item body is k_pass_b's.
+template <int P, bool ADJ>
+__global__ void __launch_bounds__(ColCfg<P>::NT) k_pass_b_split(PassArgs a) {
+  using F = Fft<P>;
+  using Cc = ColCfg<P>;
+  using H = SmemHead<P>;
+  constexpr int C = Cc::C;
+  extern __shared__ float2 smem[];
+  __shared__ double red[32];
+  float2* roots = smem;
+  float2* chs = smem + H::ROOTS;
+  const int g = threadIdx.x % C, t = threadIdx.x / C;
+  float2* sm = smem + H::WORDS + g * Cc::LS;
+  const int n = a.n, lo = P / 2 - n / 2;
+  float2* sb = smem + H::WORDS + C * Cc::LS;
+  float2* sS = sb + n * C;
+  load_roots<P>(roots, a.twiddles);
+  const TwRoots tw{roots};
+  const int ngroups = (n + C - 1) / C;
+  double dsum = 0.0;
+  int jcur = -1;
+
+  auto begin_group = [&](int cg) {
+    const int col = cg * C + g;
+    const bool valid = col < n;
+#pragma unroll
+    for (int c = 0; c < 16; ++c) {
+      const int rr = F::pos(t, c) - lo;
+      if ((unsigned)rr < (unsigned)n) {
+        sb[rr * C + g] = (valid && a.ext != 0.f) ? __ldg(a.bref + (long long)rr * n + col)
+                                                 : make_float2(0.f, 0.f);
+        if (ADJ) sS[rr * C + g] = make_float2(0.f, 0.f);
+      }
+    }
+  };
+  auto item = [&](int cg, int j, int kl) {
+    const int col = cg * C + g;
+    const bool valid = col < n;
+    const int lp = kl * a.J + j;
+    const long long gplane = (long long)(a.k0 + kl) * a.J + j;
+    const PlaneDesc d = a.planes[gplane];
+    float2* yb = a.ybuf + (long long)lp * a.ystride;
+    float2 v[16];
+#pragma unroll
+    for (int c = 0; c < 16; ++c) {
+      const int rel = F::pos(t, c) - d.by0;
+      v[c] = (valid && (unsigned)rel < (unsigned)d.bys) ? yb[(long long)rel * n + col]
+                                                         : make_float2(0.f, 0.f);
+    }
+    __syncthreads();
+    fft_fwd_with<P>(v, sm, tw, t, SyncBlock());
+#pragma unroll
+    for (int c = 0; c < 16; ++c) v[c] = cmul(v[c], chirp_half<P>(chs, F::fpos(t, c)));
+    fft_inv_with<P>(v, sm, tw, t, SyncBlock());
+    const float* ad = a.sqrt_d + (gplane - (long long)a.data_k0 * a.J) * n * n;
+    float2* uo = a.u_out ? a.u_out + (long long)lp * n * n : nullptr;
+    float lsum = 0.f;
+#pragma unroll
+    for (int c = 0; c < 16; ++c) {
+      const int rr = F::pos(t, c) - lo;
+      float2 r = make_float2(0.f, 0.f);
+      if (valid && (unsigned)rr < (unsigned)n) {
+        const long long e = (long long)rr * n + col;
+        float2 u = v[c];
+        const float2 b = sb[rr * C + g];
+        u.x = fmaf(a.ext, b.x, u.x);
+        u.y = fmaf(a.ext, b.y, u.y);
+        const float dat = __ldg(ad + e);
+        const float i2 = fmaf(u.x, u.x, u.y * u.y);
+        float diff, s;
+        if (a.functional) {
+          diff = i2 - dat;
+          s = 2.f * diff;
+        } else {
+          const float mag = sqrtf(i2);
+          diff = mag - dat;
+          s = mag > 0.f ? 1.f - dat / mag : 0.f;
+        }
+        lsum = fmaf(diff, diff, lsum);
+        if (uo) uo[e] = u;
+        if (ADJ) {
+          r = cscale(u, s);
+          sS[rr * C + g] = cadd(sS[rr * C + g], r);
+        }
+      }
+      v[c] = r;
+    }
+    dsum += (double)lsum;
+    if constexpr (ADJ) {
+      fft_fwd_with<P>(v, sm, tw, t, SyncBlock());
+#pragma unroll
+      for (int c = 0; c < 16; ++c) v[c] = cmulc(v[c], chirp_half<P>(chs, F::fpos(t, c)));
+      fft_inv_with<P>(v, sm, tw, t, SyncBlock());
+#pragma unroll
+      for (int c = 0; c < 16; ++c) {
+        const int rel = F::pos(t, c) - d.by0;
+        if (valid && (unsigned)rel < (unsigned)d.bys) yb[(long long)rel * n + col] = v[c];
+      }
+    }
+  };
+
+  const int rounds = ngroups / gridDim.x;
+  for (int m = 0; m < rounds; ++m) {
+    const int cg = blockIdx.x + m * gridDim.x;
+    begin_group(cg);
+    for (int j = 0; j < a.J; ++j) {
+      ensure_chirp<P>(chs, a.chirp_zhat, j, jcur);
+      for (int kl = 0; kl < a.nk; ++kl) item(cg, j, kl);
+    }
+    if constexpr (ADJ) {
+      const int col = cg * C + g;
+#pragma unroll
+      for (int c = 0; c < 16; ++c) {
+        const int rr = F::pos(t, c) - lo;
+        if (col < n && (unsigned)rr < (unsigned)n) {
+          const long long e = (long long)rr * n + col;
+          float2 acc = cscale(sS[rr * C + g], a.ext);
+          if (a.tq_accumulate) acc = cadd(acc, a.tq[e]);
+          if (a.rref) {
+            const float2 q = __ldg(a.rref + e);
+            acc.x = fmaf(a.wref, q.x, acc.x);
+            acc.y = fmaf(a.wref, q.y, acc.y);
+          }
+          a.tq[e] = acc;
+        }
+      }
+    }
+  }
+  const int tail = ngroups - rounds * gridDim.x;
+  const long long per = (long long)a.J * a.nk;
+  const long long titems = (long long)tail * per;
+  const long long i0 = titems * blockIdx.x / gridDim.x, i1 = titems * (blockIdx.x + 1) / gridDim.x;
+  int slot = 0;
+  for (long long it = i0; it < i1; ++slot) {
+    const int tg = (int)(it / per);
+    const long long pend = min(per, i1 - (long long)tg * per);
+    const int cg = rounds * gridDim.x + tg;
+    begin_group(cg);
+    for (long long p = it - (long long)tg * per; p < pend; ++p) {
+      const int j = (int)(p / a.nk), kl = (int)(p - (long long)j * a.nk);
+      ensure_chirp<P>(chs, a.chirp_zhat, j, jcur);
+      item(cg, j, kl);
+    }
+    if constexpr (ADJ) {
+      float2* dst = a.tpart + ((long long)blockIdx.x * a.tslots + slot) * n * C;
+#pragma unroll
+      for (int c = 0; c < 16; ++c) {
+        const int rr = F::pos(t, c) - lo;
+        if ((unsigned)rr < (unsigned)n) dst[rr * C + g] = sS[rr * C + g];
+      }
+    }
+    it = (long long)tg * per + pend;
+  }
+  const double s = block_sum_f64(dsum, red);
+  if (threadIdx.x == 0) a.loss_part[blockIdx.x] = s;
+}
+
+// T of the last round's column groups of k_pass_b_split: the slots of every block whose item
+// range met the group, added in block order, then T = ext S (+ T) (+ w_ref r_ref) as in
+// k_pass_b.  One block per tail group.
+template <int P>
+__global__ void k_pass_b_tail(PassArgs a, int nblocks) {
+  constexpr int C = ColCfg<P>::C;
+  const int n = a.n;
+  const int ngroups = (n + C - 1) / C;
+  const int rounds = ngroups / nblocks, tail = ngroups - rounds * nblocks;
+  const long long per = (long long)a.J * a.nk, titems = (long long)tail * per;
+  const int tg = blockIdx.x;
+  if (tg >= tail) return;
+  const int cg = rounds * nblocks + tg;
+  const long long g0 = (long long)tg * per, g1 = g0 + per;
+  // blocks whose ranges [titems b / nblocks, titems (b + 1) / nblocks) meet [g0, g1)
+  const int blo = max(0, (int)(g0 * nblocks / titems) - 1);
+  const int bhi = min(nblocks - 1, (int)(g1 * nblocks / titems) + 1);
+  for (int e = threadIdx.x; e < n * C; e += blockDim.x) {
+    const int rr = e / C, g = e % C, col = cg * C + g;
+    float2 S = make_float2(0.f, 0.f);
+    for (int b = blo; b <= bhi; ++b) {
+      const long long i0 = titems * b / nblocks, i1 = titems * (b + 1) / nblocks;
+      if (i1 <= g0 || i0 >= g1 || i0 >= i1) continue;
+      const int slot = tg - (int)(i0 / per);
+      S = cadd(S, a.tpart[((long long)b * a.tslots + slot) * n * C + e]);
+    }
+    if (col < n) {
+      const long long ie = (long long)rr * n + col;
+      float2 acc = cscale(S, a.ext);
+      if (a.tq_accumulate) acc = cadd(acc, a.tq[ie]);
+      if (a.rref) {
+        const float2 q = __ldg(a.rref + ie);
+        acc.x = fmaf(a.wref, q.x, acc.x);
+        acc.y = fmaf(a.wref, q.y, acc.y);
+      }
+      a.tq[ie] = acc;
+    }
+  }
+}
+
 // ------------------------------------------------------------------ pass C
 
 template <int P>
@@ -575,9 +776,37 @@ int pass_b_blocks(int items, int n, int rows) {
 }
 
 template <int P>
+int pass_b_blocks_split(long long items, int n) {
+  using Cc = ColCfg<P>;
+  const size_t sm = pass_b_smem<P>(n);
+  cudaFuncSetAttribute(k_pass_b_split<P, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                       (int)sm);
+  return persistent_blocks(k_pass_b_split<P, true>, Cc::NT, sm, items);
+}
+
+template <int P, bool ADJ>
+cudaError_t launch_pass_b_split(const PassArgs& a, int nblocks, size_t sm, cudaStream_t s) {
+  using Cc = ColCfg<P>;
+  cudaError_t e = cudaFuncSetAttribute(k_pass_b_split<P, ADJ>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  if (e != cudaSuccess) return e;
+  k_pass_b_split<P, ADJ><<<nblocks, Cc::NT, sm, s>>>(a);
+  const int ngroups = (a.n + Cc::C - 1) / Cc::C, tail = ngroups - (ngroups / nblocks) * nblocks;
+  if (ADJ && tail > 0) {
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    k_pass_b_tail<P><<<tail, 256, 0, s>>>(a, nblocks);
+  }
+  return cudaGetLastError();
+}
+
+template <int P>
 cudaError_t launch_pass_b(const PassArgs& a, int adj, int nblocks, cudaStream_t s) {
   using Cc = ColCfg<P>;
   const size_t sm = pass_b_smem<P>(a.n);
+  if (a.pb_split)
+    return adj ? launch_pass_b_split<P, true>(a, nblocks, sm, s)
+               : launch_pass_b_split<P, false>(a, nblocks, sm, s);
   cudaError_t e;
   if (adj) {
     e = cudaFuncSetAttribute(k_pass_b<P, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -615,7 +844,9 @@ const Ops* make_ops() {
                           launch_pass_c<P>,
                           pass_b_groups<P>,
                           pass_b_blocks<P>,
-                          Fft<P>::TW};
+                          pass_b_blocks_split<P>,
+                          Fft<P>::TW,
+                          ColCfg<P>::C};
   return &ops;
 }
 
