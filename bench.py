@@ -610,7 +610,10 @@ def run_reference(args, w):
             "ms_per_step": round(dt / args.steps * 1e3, 1), "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "impl": "reference",
-            "config": {"workload": f"{w.name}: psi {w.n}^2 (pad {w.P}), one plane per step"},
+            "config": {"workload": f"{w.name}: psi {w.n}^2 (pad {w.P}), {w.chunk}-angle chunk x "
+                                   f"{w.n_dist} distances per GPU, layered phantom, striped probe, "
+                                   f"Poisson {w.counts:g}",
+                       "sample": "one plane-gradient of that workload per timed step"},
             "cpu_baseline": {"value": round(value, 4), "unit": UNIT, "cores": os.cpu_count(),
                              "kind": "oracle", "sample": sample},
             "e2e": {"value": round(value, 4), "unit": UNIT, "h2d_bytes_per_step": 0,
