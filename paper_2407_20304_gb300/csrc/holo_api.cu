@@ -897,7 +897,7 @@ holo_status holo_gradient(holo_ctx* c, int k0, int nk, const void* psi, double* 
 // every part keeps its conj(w) v in its own slice of the workspace, so grad_q is formed
 // once for the whole chunk at the end.  (The per-part sums of T and of the loss round in a
 // different order than a single pass over the chunk.)
-holo_status gradient_host_parts(holo_ctx* c, int k0, int nk, int parts, const void* psi_host,
+static holo_status gradient_host_parts(holo_ctx* c, int k0, int nk, int parts, const void* psi_host,
                                 const float* sqrt_d_host, const void* q_host, double* loss,
                                 void* grad_psi_host, void* grad_q_host, unsigned flags) {
   const int n = c->n, P = c->P, J = c->J;
@@ -971,9 +971,29 @@ holo_status gradient_host_parts(holo_ctx* c, int k0, int nk, int parts, const vo
   return read_loss(c, loss, flags);
 }
 
+static holo_status gradient_host_impl(holo_ctx* c, int k0, int nk, const void* psi_host,
+                                     const float* sqrt_d_host, const void* q_host, double* loss,
+                                     void* grad_psi_host, void* grad_q_host, unsigned flags);
+
 holo_status holo_gradient_host(holo_ctx* c, int k0, int nk, const void* psi_host,
                                const float* sqrt_d_host, const void* q_host, double* loss,
                                void* grad_psi_host, void* grad_q_host, unsigned flags) {
+  const holo_status st = gradient_host_impl(c, k0, nk, psi_host, sqrt_d_host, q_host, loss,
+                                            grad_psi_host, grad_q_host, flags);
+  if (st != HOLO_OK && c) {
+    // copies issued before the failure may still read or write the caller's host buffers:
+    // let them finish before returning
+    if (c->cs_in) cudaStreamSynchronize(c->cs_in);
+    if (c->cs_out) cudaStreamSynchronize(c->cs_out);
+    cudaStreamSynchronize(c->stream);
+    cudaGetLastError();
+  }
+  return st;
+}
+
+static holo_status gradient_host_impl(holo_ctx* c, int k0, int nk, const void* psi_host,
+                                     const float* sqrt_d_host, const void* q_host, double* loss,
+                                     void* grad_psi_host, void* grad_q_host, unsigned flags) {
   if (!c) return HOLO_ERR_ARG;
   if (!psi_host || !grad_psi_host || !grad_q_host) return fail(c, HOLO_ERR_ARG, "null pointer");
   if (nk < 1 || nk > c->chunk || k0 < 0 || k0 + nk > c->K)
