@@ -200,6 +200,46 @@ def test_gradient_host_in_parts_matches_device_call():
     assert rel(gq_h, gq_ref) < GRAD_TOL
 
 
+@pytest.mark.parametrize("functional", ["amplitude", "intensity"])
+def test_gradient_host_chunks_in_parts(functional):
+    """16 angles in two host calls of 8 (k0 = 0 with the reference term, k0 = 8 without),
+    each run in parts: grad_psi slices are the device calls' bit for bit, and loss and grad_q
+    summed over the calls match the device evaluation of all 16 angles to rounding (F1 and
+    F2)."""
+    pr = make_problem(64, 128, 16, seed=21)
+    f1 = functional == "intensity"
+    d = pr["sqrt_d"] ** 2 if f1 else pr["sqrt_d"]
+    dref = pr["sqrt_dref"] ** 2 if f1 else pr["sqrt_dref"]
+    from paper_2407_20304_gb300 import Holo
+    geo = pr["geo"]
+    h = Holo(geo.n, 16, geo.n_dist, geo.wavelength, geo.pixel, geo.Z, geo.z, pad=geo.P, chunk=8,
+             w_ref=geo.w_ref, ext=geo.ext)
+    h.set_functional(functional)
+    h.set_shifts(pr["t"].astype(np.float32))
+    h.set_data(dev(d, torch.float32), dev(dref, torch.float32))
+    h.set_probe(dev(pr["q"], torch.complex64))
+    psi = dev(pr["psi"], torch.complex64)
+    gp_d = torch.empty_like(psi)
+    gq_d = torch.empty((geo.P, geo.P), dtype=torch.complex64, device="cuda")
+    loss_d = 0.0
+    for i, k0 in enumerate((0, 8)):
+        loss_d, _, _ = h.gradient(psi[k0:k0 + 8], grad_psi=gp_d[k0:k0 + 8], grad_q=gq_d, k0=k0,
+                                  accumulate_q=i > 0, loss_in=loss_d)
+    loss_h, gq_h = 0.0, np.zeros((geo.P, geo.P), np.complex64)
+    for k0 in (0, 8):
+        l, gp_h, g = h.gradient_host(pr["psi"][k0:k0 + 8].astype(np.complex64),
+                                     sqrt_d=np.ascontiguousarray(d[k0:k0 + 8]).astype(np.float32),
+                                     q=pr["q"].astype(np.complex64), k0=k0)
+        np.testing.assert_array_equal(gp_h, gp_d[k0:k0 + 8].cpu().numpy())
+        loss_h += l
+        gq_h += g
+    assert abs(loss_h - loss_d) <= 1e-6 * abs(loss_d)
+    assert rel(gq_h, gq_d.cpu().numpy()) < 1e-5
+    ref = (oh.gradients_f1 if f1 else oh.gradients)(pr["psi"], pr["q"], pr["t"], d, dref, geo)
+    assert abs(loss_h - ref[0]) / ref[0] < LOSS_TOL
+    assert rel(gq_h, ref[2]) < GRAD_TOL
+
+
 def test_zero_gradient_at_noiseless_truth():
     pr = make_problem(64, 128, 2, seed=21, noiseless=True)
     h = make_holo(pr)
