@@ -57,9 +57,9 @@ struct RowCfg {
   static constexpr int NT = G * T;
   static constexpr int LS = Fft<P>::SMEM + (P == 64 || P == 192 ? 1 : 0);
   static constexpr size_t SMEM_BYTES = (size_t)(SmemHead<P>::WORDS + G * LS) * sizeof(float2);
-  // resident blocks per SM asked of ptxas: 3 where the row passes then fit in 80 registers
-  // without spilling (checked with -Xptxas -v), else 2
-  static constexpr int MINB = P == 4096 ? 3 : 2;
+  // resident blocks per SM asked of ptxas: 3 where that measured faster (the row passes then
+  // fit in 80-96 registers with at most ~100 bytes of spills), else 2
+  static constexpr int MINB = P == 4096 || P == 2048 || P == 1024 || P == 768 ? 3 : 2;
 };
 
 template <int P>
