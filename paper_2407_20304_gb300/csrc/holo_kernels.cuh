@@ -466,10 +466,17 @@ __global__ void __launch_bounds__(ColCfg<P>::NT) k_pass_b_split(PassArgs a) {
     }
     __syncthreads();
     fft_fwd_with<P>(v, sm, tw, t, SyncBlock());
+    // the data of the crop rows are fetched now, so the inverse transform hides their latency
+    const float* ad = a.sqrt_d + (gplane - (long long)a.data_k0 * a.J) * n * n;
+    float dats[16];
+#pragma unroll
+    for (int c = 0; c < 16; ++c) {
+      const int rr = F::pos(t, c) - lo;
+      dats[c] = (valid && (unsigned)rr < (unsigned)n) ? __ldg(ad + (long long)rr * n + col) : 0.f;
+    }
 #pragma unroll
     for (int c = 0; c < 16; ++c) v[c] = cmul(v[c], chirp_half<P>(chs, F::fpos(t, c)));
     fft_inv_with<P>(v, sm, tw, t, SyncBlock());
-    const float* ad = a.sqrt_d + (gplane - (long long)a.data_k0 * a.J) * n * n;
     float2* uo = a.u_out ? a.u_out + (long long)lp * n * n : nullptr;
     float lsum = 0.f;
 #pragma unroll
@@ -482,7 +489,7 @@ __global__ void __launch_bounds__(ColCfg<P>::NT) k_pass_b_split(PassArgs a) {
         const float2 b = sb[rr * C + g];
         u.x = fmaf(a.ext, b.x, u.x);
         u.y = fmaf(a.ext, b.y, u.y);
-        const float dat = __ldg(ad + e);
+        const float dat = dats[c];
         const float i2 = fmaf(u.x, u.x, u.y * u.y);
         float diff, s;
         if (a.functional) {
