@@ -39,6 +39,11 @@
  *     arguments are rejected before any device work (HOLO_ERR_ARG); CUDA failures return
  *     HOLO_ERR_CUDA (details in holo_last_error).  Calls in the wrong order (e.g. a
  *     gradient before holo_set_probe) return HOLO_ERR_STATE.
+ *   - Device waits are bounded.  Where the column pass stages its input tiles by TMA
+ *     (P >= 1024, even n), a tile that does not arrive within the bound makes the kernel
+ *     return early and set a device error word; the next call that reads a loss (any call
+ *     returning a loss, holo_read_loss) returns HOLO_ERR_TIMEOUT, clears the word, and the
+ *     results of the evaluations since the previous loss read are invalid.
  */
 #ifndef HOLO_H
 #define HOLO_H

@@ -9,6 +9,8 @@
 #include <string>
 #include <vector>
 
+#include <cuda.h>
+
 #include "holo.h"
 #include "holo_internal.h"
 
@@ -64,6 +66,10 @@ using holo::PlaneDesc;
 constexpr int kHostParts = 8;
 constexpr int kHostMinPart = 2;
 constexpr int kHostWeights[kHostParts] = {1, 2, 3, 3, 3, 3, 3, 2};
+
+// d_red: kRed doubles; word kErrWord holds the device-wait error flag (as 64-bit integer).
+constexpr int kRed = 10;
+constexpr int kErrWord = 8;
 
 struct holo_ctx {
   holo_geometry geo{};
@@ -123,8 +129,12 @@ struct holo_ctx {
   double* d_dot3 = nullptr;     // partial sums of holo_dy_dots: 3 x (8 x SM count)
   float2* d_tpart = nullptr;    // pass B (plane-split form): partial residual sums
   size_t tpart_bytes = 0;
-  double* d_red = nullptr;      // 8 doubles: loss, reference term, dot, running loss, DY dots
-  double* h_red = nullptr;      // pinned, 8 doubles
+  double* d_red = nullptr;      // kRed doubles: loss, reference term, dot, running loss, DY
+                                // dots, call loss; word kErrWord: device-wait error flag
+  double* h_red = nullptr;      // pinned, kRed doubles
+  // pass B's Y stage: TMA tensor map over ybuf (device, 128 bytes), used when ystage
+  void* d_ymap = nullptr;
+  bool ystage = false;
   // host-buffer staging
   float2* s_psi = nullptr;
   float2* s_gpsi = nullptr;
@@ -190,6 +200,52 @@ void dfree(holo_ctx* c, void* p, size_t bytes) {
 }
 
 bool is_pow2(int x) { return x > 0 && (x & (x - 1)) == 0; }
+
+// Pass B's Y stage: a TMA tensor map over ybuf viewed as a row-major [planes * maxbys][2n]
+// float matrix, boxes of 2C floats x kStageBox rows.  Used only where the driver provides
+// the encoder, n is even (16-byte row pitch) and the stage leaves pass B's resident blocks
+// per SM unchanged; otherwise pass B loads Y directly.
+using EncodeTiledFn = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*,
+                                   const cuuint64_t*, const cuuint64_t*, const cuuint32_t*,
+                                   const cuuint32_t*, CUtensorMapInterleave, CUtensorMapSwizzle,
+                                   CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+EncodeTiledFn encode_tiled() {
+  static EncodeTiledFn fn = [] {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault,
+                                         &q) != cudaSuccess ||
+        q != cudaDriverEntryPointSuccess) {
+      cudaGetLastError();
+      p = nullptr;
+    }
+    return reinterpret_cast<EncodeTiledFn>(p);
+  }();
+  return fn;
+}
+
+holo_status encode_ystage(holo_ctx* c, int maxbys) {
+  c->ystage = false;
+  const int n = c->n, C = c->ops->pass_b_cols;
+  if (n % 2 || !c->ops->pass_b_stage_ok(n, maxbys)) return HOLO_OK;
+  EncodeTiledFn enc = encode_tiled();
+  if (!enc) return HOLO_OK;
+  const long long rows = (long long)c->chunk * c->J * (c->ystride / n);
+  CUtensorMap m;
+  const cuuint64_t dims[2] = {(cuuint64_t)2 * n, (cuuint64_t)rows};
+  const cuuint64_t strides[1] = {(cuuint64_t)n * sizeof(float2)};
+  const cuuint32_t box[2] = {(cuuint32_t)(2 * C), (cuuint32_t)holo::kStageBox};
+  const cuuint32_t estr[2] = {1, 1};
+  if (enc(&m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, c->ybuf, dims, strides, box, estr,
+          CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+          CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+    return HOLO_OK;
+  HOLO_CK(c, cudaMemcpyAsync(c->d_ymap, &m, sizeof(m), cudaMemcpyHostToDevice, c->stream));
+  HOLO_CK(c, cudaStreamSynchronize(c->stream));
+  c->ystage = true;
+  return HOLO_OK;
+}
 
 // Scoped event pair around a group of launches of one pass (no-op unless timing is on).
 struct PassTimer {
@@ -438,6 +494,9 @@ PassArgs pass_args(holo_ctx* c, int k0, int nk, const void* psi) {
   a.line0 = c->rowstart[(size_t)k0 * c->J];
   a.nlines = c->rowstart[(size_t)(k0 + nk) * c->J] - a.line0;
   a.pass_b_items = c->ops->pass_b_groups(c->n);
+  a.ymap = c->ystage ? c->d_ymap : nullptr;
+  a.yrows = (int)(c->ystride / c->n);
+  a.err = reinterpret_cast<unsigned long long*>(c->d_red + kErrWord);
   return a;
 }
 
@@ -455,7 +514,7 @@ PassArgs pass_args(holo_ctx* c, int k0, int nk, const void* psi) {
 // tslots slots of [n][C] per block.
 holo_status pass_b_grid(holo_ctx* c, PassArgs& a, bool gradient, int* nblocks) {
   const int groups = a.pass_b_items;
-  const int full = c->ops->pass_b_blocks(1 << 30, c->n, a.max_box_rows);
+  const int full = c->ops->pass_b_blocks(1 << 30, c->n, a.ymap ? a.max_box_rows : 0);
   a.pb_split = groups % full != 0 && groups / full < 3;
   a.tslots = 0;
   if (!a.pb_split) {
@@ -484,7 +543,7 @@ holo_status pass_b_grid(holo_ctx* c, PassArgs& a, bool gradient, int* nblocks) {
 
 holo_status eval_begin(holo_ctx* c, PassArgs& a) {
   PassTimer tm_red(c, HOLO_T_REDUCE);
-  const int nbx = c->ops->pass_b_blocks(a.pass_b_items, c->n, a.max_box_rows);
+  const int nbx = c->ops->pass_b_blocks(a.pass_b_items, c->n, a.ymap ? a.max_box_rows : 0);
   const long long n2 = (long long)c->n * c->n;
   if (a.k0 == 0 && c->wref != 0.0) {
     // reference residual first: pass B folds w_ref r_ref into the grad_q source
@@ -572,10 +631,21 @@ holo_status run_eval(holo_ctx* c, PassArgs& a, bool gradient, float2* grad_q, un
   return eval_qgrad(c, a, grad_q, acc);
 }
 
+// A bounded device wait that gave up (the error word) is reported, and the word cleared,
+// by the next call that reads a loss.
+holo_status check_err_word(holo_ctx* c) {
+  unsigned long long w;
+  std::memcpy(&w, c->h_red + kErrWord, sizeof(w));
+  if (!w) return HOLO_OK;
+  HOLO_CK(c, cudaMemsetAsync(c->d_red + kErrWord, 0, sizeof(double), c->stream));
+  return fail(c, HOLO_ERR_TIMEOUT, "pass B: Y-tile wait gave up; results of the call are invalid");
+}
+
 holo_status read_loss(holo_ctx* c, double* loss, unsigned flags) {
-  HOLO_CK(c, cudaMemcpyAsync(c->h_red + 7, c->d_red + 7, sizeof(double), cudaMemcpyDeviceToHost,
-                             c->stream));
+  HOLO_CK(c, cudaMemcpyAsync(c->h_red + 7, c->d_red + 7, 2 * sizeof(double),
+                             cudaMemcpyDeviceToHost, c->stream));
   HOLO_CK(c, cudaStreamSynchronize(c->stream));
+  if (holo_status st = check_err_word(c)) return st;
   const double l = c->h_red[7];
   if (loss) *loss = (flags & (HOLO_ACCUMULATE | HOLO_ACCUMULATE_Q)) ? *loss + l : l;
   if (!std::isfinite(l)) return fail(c, HOLO_ERR_NUMERIC, "non-finite loss");
@@ -693,9 +763,14 @@ holo_status holo_create(const holo_geometry* geo, void* stream, holo_ctx** out) 
       (st = dalloc(c, (void**)&c->d_Gp, cP * P)) ||
       (st = dalloc(c, (void**)&c->d_T, sizeof(float2) * (size_t)n * n)) ||
       (st = dalloc(c, (void**)&c->d_rref, sizeof(float2) * (size_t)n * n)) ||
-      (st = dalloc(c, (void**)&c->d_red, 8 * sizeof(double))))
+      (st = dalloc(c, (void**)&c->d_red, kRed * sizeof(double))) ||
+      (st = dalloc(c, &c->d_ymap, sizeof(CUtensorMap))))
     return bail(st);
-  if (cudaMallocHost((void**)&c->h_red, 8 * sizeof(double)) != cudaSuccess) {
+  if (cudaMemset(c->d_red, 0, kRed * sizeof(double)) != cudaSuccess) {
+    cudaGetLastError();
+    return bail(HOLO_ERR_CUDA);
+  }
+  if (cudaMallocHost((void**)&c->h_red, kRed * sizeof(double)) != cudaSuccess) {
     cudaGetLastError();
     return bail(HOLO_ERR_OOM);
   }
@@ -724,7 +799,7 @@ holo_status holo_destroy(holo_ctx* c) {
                   c->d_red,   c->d_dot3,       c->d_tpart,       c->s_psi,         c->s_gpsi,
                   c->s_data,
                   c->s_q,     c->s_gq,         c->d_xtap,        c->d_ytap,
-                  c->d_xadj,  c->d_yadj,       c->d_lines};
+                  c->d_xadj,  c->d_yadj,       c->d_lines,       c->d_ymap};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   if (c->h_red) cudaFreeHost(c->h_red);
@@ -814,7 +889,7 @@ holo_status holo_set_shifts(holo_ctx* c, const float* t) {
   const long long np = (long long)c->chunk * J;
   const size_t ybytes = sizeof(float2) * (size_t)(np * ystride);
   const size_t gbytes = sizeof(float2) * (size_t)(np * gkstride);
-  const long long parts = (long long)c->ops->pass_b_blocks(1 << 30, n, maxbys) + kRefBlocks + 1024;
+  const long long parts = (long long)c->ops->pass_b_blocks(1 << 30, n, 0) + kRefBlocks + 1024;
   if (ystride > c->ystride || gkstride > c->gkstride || !c->ybuf) {
     dfree(c, c->ybuf, sizeof(float2) * (size_t)(np * c->ystride));
     dfree(c, c->gkbuf, sizeof(float2) * (size_t)(np * c->gkstride));
@@ -824,6 +899,7 @@ holo_status holo_set_shifts(holo_ctx* c, const float* t) {
     if ((st = dalloc(c, (void**)&c->ybuf, ybytes)) || (st = dalloc(c, (void**)&c->gkbuf, gbytes)))
       return st;
   }
+  if ((st = encode_ystage(c, maxbys))) return st;
   if (parts > c->part_cap) {
     dfree(c, c->d_part, sizeof(double) * (size_t)c->part_cap);
     c->d_part = nullptr;
@@ -1163,9 +1239,10 @@ holo_status holo_set_stream(holo_ctx* c, void* stream) {
 
 holo_status holo_read_loss(holo_ctx* c, double* loss) {
   if (!c || !loss) return fail(c, HOLO_ERR_ARG, "null argument");
-  HOLO_CK(c, cudaMemcpyAsync(c->h_red + 3, c->d_red + 3, sizeof(double), cudaMemcpyDeviceToHost,
-                             c->stream));
+  HOLO_CK(c, cudaMemcpyAsync(c->h_red + 3, c->d_red + 3, (kErrWord - 2) * sizeof(double),
+                             cudaMemcpyDeviceToHost, c->stream));
   HOLO_CK(c, cudaStreamSynchronize(c->stream));
+  if (holo_status st = check_err_word(c)) return st;
   *loss = c->h_red[3];
   if (!std::isfinite(*loss)) return fail(c, HOLO_ERR_NUMERIC, "non-finite loss");
   return HOLO_OK;

@@ -92,7 +92,16 @@ struct PassArgs {
   const int2* lines;           // [total box rows of all planes]
   int line0, nlines;           // the chunk's lines: [line0, line0 + nlines)
   int pass_b_items;            // column groups of pass B
+  // pass B stages each plane's Y tile [box rows][C columns] into shared memory by TMA
+  // while the previous plane computes: tensor map over ybuf as a [planes * yrows][2n] float
+  // matrix (box 2C x kStageBox), or null for plain loads
+  const void* ymap;
+  int yrows;                   // rows per plane in ybuf (ystride / n)
+  unsigned long long* err;     // device word, set when a bounded device wait gave up
 };
+
+// Rows of one TMA box of pass B's Y stage (the tensor-map box limit is 256).
+constexpr int kStageBox = 256;
 
 // Entry points implemented once per supported line length P.
 struct Ops {
@@ -105,6 +114,7 @@ struct Ops {
   int (*pass_b_groups)(int n);              // column groups of pass B for side n
   int (*pass_b_blocks)(int items, int n, int rows);  // persistent grid of pass B
   int (*pass_b_blocks_split)(long long items, int n);  // ... of its plane-split form
+  int (*pass_b_stage_ok)(int n, int rows);  // 1: pass B may stage Y tiles of `rows` rows
   int twiddle_count;
   int pass_b_cols;                          // columns per pass-B group (C)
 };

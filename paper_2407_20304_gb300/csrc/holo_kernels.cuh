@@ -26,6 +26,7 @@
 
 #include "holo_fft.cuh"
 #include "holo_internal.h"
+#include "holo_tma.cuh"
 
 namespace holo {
 
@@ -269,12 +270,35 @@ __global__ void __launch_bounds__(RowCfg<P>::NT, RowCfg<P>::MINB) k_pass_a(PassA
 
 // ------------------------------------------------------------------ pass B
 
-// Shared memory of pass B: head, C exchange lines, the reference field slice b[n][C] and
-// the residual sum S[n][C] of the block's column group.
+// Y stage of pass B: whole TMA boxes covering `rows` box rows of C columns.
 template <int P>
-size_t pass_b_smem(int n) {
-  return (size_t)(SmemHead<P>::WORDS + ColCfg<P>::C * ColCfg<P>::LS + 2 * n * ColCfg<P>::C) *
-         sizeof(float2);
+size_t pass_b_stage_bytes(int rows) {
+  return (size_t)((rows + kStageBox - 1) / kStageBox) * kStageBox * ColCfg<P>::C * sizeof(float2);
+}
+
+// Shared memory of pass B: head, C exchange lines, the reference field slice b[n][C] and
+// the residual sum S[n][C] of the block's column group; with srows > 0 also the Y stage
+// for planes of up to srows box rows (128-byte aligned).
+template <int P>
+size_t pass_b_smem(int n, int srows = 0) {
+  const size_t base =
+      (size_t)(SmemHead<P>::WORDS + ColCfg<P>::C * ColCfg<P>::LS + 2 * n * ColCfg<P>::C) *
+      sizeof(float2);
+  return srows > 0 ? base + 128 + pass_b_stage_bytes<P>(srows) : base;
+}
+
+// Pass B's Y stage: thread 0 arms the barrier and loads the tile of plane (kl, j) for
+// column group cg (every box of the plane's box rows; rows past them are not read).
+template <int P>
+__device__ __forceinline__ void stage_y(const PassArgs& a, float2* stg, uint64_t* bar, int cg,
+                                        int j, int kl) {
+  constexpr int C = ColCfg<P>::C;
+  const int bys = a.planes[(long long)(a.k0 + kl) * a.J + j].bys;
+  const int nb = (bys + kStageBox - 1) / kStageBox;
+  const int row0 = (kl * a.J + j) * a.yrows;
+  mbar_expect_tx(bar, (uint32_t)(nb * kStageBox * C * sizeof(float2)));
+  for (int b = 0; b < nb; ++b)
+    tma_load_2d(stg + b * kStageBox * C, a.ymap, 2 * C * cg, row0 + b * kStageBox, bar);
 }
 
 // Each block owns whole column groups (C adjacent detector columns) and walks every plane
@@ -290,6 +314,7 @@ __global__ void __launch_bounds__(ColCfg<P>::NT) k_pass_b(PassArgs a) {
   constexpr int C = Cc::C;
   extern __shared__ float2 smem[];
   __shared__ double red[32];
+  __shared__ uint64_t ybar;
   float2* roots = smem;
   float2* chs = smem + H::ROOTS;
   const int g = threadIdx.x % C, t = threadIdx.x / C;
@@ -302,6 +327,16 @@ __global__ void __launch_bounds__(ColCfg<P>::NT) k_pass_b(PassArgs a) {
   const int ngroups = (n + C - 1) / C;
   double dsum = 0.0;
   int jcur = -1;
+  // Y stage: the tile of the block's next plane is in flight while the current one computes
+  const bool staged = a.ymap != nullptr;
+  float2* stg = reinterpret_cast<float2*>((reinterpret_cast<uintptr_t>(sS + n * C) + 127) &
+                                          ~static_cast<uintptr_t>(127));
+  uint32_t yphase = 0;
+  if (staged) {
+    if (threadIdx.x == 0) mbar_init(&ybar);
+    __syncthreads();
+    if (threadIdx.x == 0 && (int)blockIdx.x < ngroups) stage_y<P>(a, stg, &ybar, blockIdx.x, 0, 0);
+  }
   for (int cg = blockIdx.x; cg < ngroups; cg += gridDim.x) {
     const int col = cg * C + g;
     const bool valid = col < n;
@@ -322,13 +357,40 @@ __global__ void __launch_bounds__(ColCfg<P>::NT) k_pass_b(PassArgs a) {
         const PlaneDesc d = a.planes[gplane];
         float2* yb = a.ybuf + (long long)lp * a.ystride;
         float2 v[16];
+        if (staged) {
+          const bool ok = mbar_wait(&ybar, yphase);
+          yphase ^= 1;
 #pragma unroll
-        for (int c = 0; c < 16; ++c) {
-          const int rel = F::pos(t, c) - d.by0;
-          v[c] = (valid && (unsigned)rel < (unsigned)d.bys) ? yb[(long long)rel * n + col]
-                                                             : make_float2(0.f, 0.f);
+          for (int c = 0; c < 16; ++c) {
+            const int rel = F::pos(t, c) - d.by0;
+            v[c] = (valid && (unsigned)rel < (unsigned)d.bys) ? stg[rel * C + g]
+                                                               : make_float2(0.f, 0.f);
+          }
+          // every thread has its tile entries: the stage is free for the next plane
+          if (__syncthreads_or(!ok)) {
+            if (threadIdx.x == 0) atomicOr(a.err, 1ull);
+            return;
+          }
+          if (threadIdx.x == 0) {
+            int nkl = kl + 1, nj = j, ncg = cg;
+            if (nkl == a.nk) {
+              nkl = 0;
+              if (++nj == a.J) {
+                nj = 0;
+                ncg += gridDim.x;
+              }
+            }
+            if (ncg < ngroups) stage_y<P>(a, stg, &ybar, ncg, nj, nkl);
+          }
+        } else {
+#pragma unroll
+          for (int c = 0; c < 16; ++c) {
+            const int rel = F::pos(t, c) - d.by0;
+            v[c] = (valid && (unsigned)rel < (unsigned)d.bys) ? yb[(long long)rel * n + col]
+                                                               : make_float2(0.f, 0.f);
+          }
+          __syncthreads();
         }
-        __syncthreads();
         fft_fwd_with<P>(v, sm, tw, t, SyncBlock());
         // the data of the crop rows are fetched now, so the inverse transform hides their latency
         const float* ad = a.sqrt_d + (gplane - (long long)a.data_k0 * a.J) * n * n;
@@ -780,13 +842,35 @@ inline int max_dynamic_smem() {
   return v;
 }
 
+// rows: box rows of the Y stage (0: plain loads)
 template <int P>
 int pass_b_blocks(int items, int n, int rows) {
   using Cc = ColCfg<P>;
-  (void)rows;
-  const size_t sm = pass_b_smem<P>(n);
+  const size_t sm = pass_b_smem<P>(n, rows);
+  if (sm > (size_t)max_dynamic_smem()) return 0;
   cudaFuncSetAttribute(k_pass_b<P, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
   return persistent_blocks(k_pass_b<P, true>, Cc::NT, sm, items);
+}
+
+// The Y stage is used where the box is at most 2C x kStageBox floats wide (P >= 1024), the
+// shared memory fits and pass B keeps its resident blocks per SM.
+template <int P>
+int pass_b_stage_ok(int n, int rows) {
+  using Cc = ColCfg<P>;
+  if (P < 1024 || rows <= 0 || 2 * Cc::C > kStageBox) return 0;
+  const size_t s0 = pass_b_smem<P>(n), s1 = pass_b_smem<P>(n, rows);
+  if (s1 > (size_t)max_dynamic_smem()) return 0;
+  int b0 = 0, b1 = 0;
+  if (cudaFuncSetAttribute(k_pass_b<P, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)s1) != cudaSuccess ||
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b0, k_pass_b<P, true>, Cc::NT, s0) !=
+          cudaSuccess ||
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b1, k_pass_b<P, true>, Cc::NT, s1) !=
+          cudaSuccess) {
+    cudaGetLastError();
+    return 0;
+  }
+  return b1 >= 1 && b1 == b0 ? 1 : 0;
 }
 
 template <int P>
@@ -817,10 +901,14 @@ cudaError_t launch_pass_b_split(const PassArgs& a, int nblocks, size_t sm, cudaS
 template <int P>
 cudaError_t launch_pass_b(const PassArgs& a, int adj, int nblocks, cudaStream_t s) {
   using Cc = ColCfg<P>;
-  const size_t sm = pass_b_smem<P>(a.n);
-  if (a.pb_split)
-    return adj ? launch_pass_b_split<P, true>(a, nblocks, sm, s)
-               : launch_pass_b_split<P, false>(a, nblocks, sm, s);
+  if (a.pb_split) {
+    PassArgs b = a;
+    b.ymap = nullptr;
+    const size_t sm = pass_b_smem<P>(a.n);
+    return adj ? launch_pass_b_split<P, true>(b, nblocks, sm, s)
+               : launch_pass_b_split<P, false>(b, nblocks, sm, s);
+  }
+  const size_t sm = pass_b_smem<P>(a.n, a.ymap ? a.max_box_rows : 0);
   cudaError_t e;
   if (adj) {
     e = cudaFuncSetAttribute(k_pass_b<P, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -859,6 +947,7 @@ const Ops* make_ops() {
                           pass_b_groups<P>,
                           pass_b_blocks<P>,
                           pass_b_blocks_split<P>,
+                          pass_b_stage_ok<P>,
                           Fft<P>::TW,
                           ColCfg<P>::C};
   return &ops;

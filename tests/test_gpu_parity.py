@@ -114,6 +114,9 @@ def test_forward_fields_and_loss(n, P, K, ext):
     # line lengths 3 * 2^k (radix-3 step)
     (24, 48, 2, 4, 1.0, 1.0), (48, 96, 3, 4, 1.0, 1.0), (96, 192, 2, 3, 1.0, 0.0),
     (192, 384, 2, 4, 0.0, 0.0), (384, 768, 2, 4, 1.0, 1.0), (700, 1536, 1, 2, 1.0, 1.0),
+    # pass B with TMA-staged Y tiles (whole column-group rounds); n = 1826 leaves the last
+    # group of 4 columns half outside the detector
+    (1216, 2048, 1, 3, 1.0, 1.0), (1826, 2048, 2, 2, 1.0, 1.0),
 ])
 def test_gradient_matches_oracle(n, P, K, J, ext, w_ref):
     pr = make_problem(n, P, K, J=J, ext=ext, w_ref=w_ref, seed=3 * n + J)
