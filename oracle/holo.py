@@ -21,7 +21,15 @@ R4  (R psi)(x) = ext + sum_taps bilinear weight * (psi - ext) at psi-coordinate
     M_m f(x) = f(x/m) (Sec. 2, after Eq. fwd_model_cone) and S_t moves content by +t.
     ext = 1 is free space (transmittance 1); ext = 0 is a test mode in which R is
     linear.  The gradient uses the exact transpose R0^T of the linear part.
-R5  Probe shifts s_kj are zero (they can be moved onto psi and the data, Sec. 2).
+R5  Probe shifts s_kj (the S_{s_kj}(q) inside D_{omega_j} of Eq. min2 / Eq. min1) are zero
+    unless given.  When given, the model is evaluated in the form the paper points to
+    after Eq. min2: shifts commute with the other operators, so the shift can leave the
+    probe and act on psi and the detector field instead,
+        D_zhat( D_omega(S_s q) * M_{1/m~} S_t psi ) = S_s D_zhat( p * M_{1/m~} S_{t - m~ s} psi ),
+    with S_s the band-limited (Fourier phase ramp) shift of the P x P grid, so the probe
+    is never interpolated (Sec. 2).  For integer s this is exactly the literal expression
+    with q rolled by s; for fractional s the two differ only in how the bilinear object
+    field is shifted.
 R6  r = u - a u/|u| with u/|u| := 0 where |u| = 0.
 R8  z_j are the focus-to-sample distances; m~_j = z_j/z_0, omega_j = (z_j-z_0)/m~_j,
     zeta_j = z_j (Z - z_j)/Z (Sec. 2 after Eq. fwd_model_cone3; Theorem t3).
@@ -109,6 +117,27 @@ def embed(y, P):
     out = np.zeros(y.shape[:-2] + (P, P), dtype=np.complex128)
     out[..., o:o + n, o:o + n] = y
     return out
+
+
+def shift(x, s):
+    """S_s: shift of a P x P field by s = (s_y, s_x) pixels, content moving by +s (Eq. min2
+    operator S_s; reading R5).  Evaluated as the phase ramp exp(-2 pi i (k_y s_y + k_x s_x)/P)
+    on the DFT with k in [-P/2, P/2): a periodic index shift for integer s, band-limited
+    interpolation otherwise.  S_s is unitary, S_s* = S_{-s}, and it commutes with D_z."""
+    x = np.asarray(x, dtype=np.complex128)
+    P = x.shape[-1]
+    k = np.arange(P, dtype=np.float64)
+    k[k >= P // 2] -= P
+    ramp_y = np.exp(-2j * np.pi * k * s[0] / P)
+    ramp_x = np.exp(-2j * np.pi * k * s[1] / P)
+    return sfft.ifft2(sfft.fft2(x, workers=-1) * np.outer(ramp_y, ramp_x), workers=-1)
+
+
+def moved_object_shift(t, mt, s):
+    """The object shift that carries the probe shift s of plane j (reading R5):
+    S_{-s} M_{1/m~} S_t psi = M_{1/m~} S_{t - m~ s} psi, since (M_{1/m~} S_t psi)(x) =
+    psi(m~ x - t)."""
+    return (t[0] - mt * s[0], t[1] - mt * s[1])
 
 
 def _bilinear_axis(mt, t, n, P):
@@ -222,11 +251,21 @@ def initial_probe(sqrt_dref, geo):
     return propagate(ext, -d["zeta"][0], geo.wavelength, geo.pixel)
 
 
-def forward(psi, q, shifts, geo):
-    """Detector wavefields u_kj = C D_{zeta_j/m~_j^2}( D_{omega_j}(q) * M_{1/m~_j} S_{t_kj} psi_k ).
+def _plane_shifts(shifts, probe_shifts, mt, k, j):
+    """(object shift, probe shift or None) of plane (k, j) under reading R5."""
+    if probe_shifts is None:
+        return shifts[k][j], None
+    s = probe_shifts[k][j]
+    return moved_object_shift(shifts[k][j], mt, s), s
 
-    Eq. fwd_model_cone3 with the shifts of Eq. min1 (probe shifts zero, reading R5).
-    psi: [K][n][n] complex, q: [P][P] complex, shifts: [K][J][2] (t_y, t_x) pixels.
+
+def forward(psi, q, shifts, geo, probe_shifts=None):
+    """Detector wavefields
+    u_kj = C D_{zeta_j/m~_j^2}( D_{omega_j}(S_{s_kj} q) * M_{1/m~_j} S_{t_kj} psi_k ).
+
+    Eq. fwd_model_cone3 with the shifts of Eq. min1.  psi: [K][n][n] complex, q: [P][P]
+    complex, shifts: [K][J][2] (t_y, t_x) pixels; probe_shifts: [K][J][2] (s_y, s_x) or None
+    (zero), evaluated as C S_s D_zhat( p_j * M_{1/m~_j} S_{t - m~_j s} psi_k ) (reading R5).
     Returns u: [K][J][n][n] complex128.
     """
     psi = np.asarray(psi, dtype=np.complex128)
@@ -236,8 +275,12 @@ def forward(psi, q, shifts, geo):
     u = np.empty((K, J, geo.n, geo.n), dtype=np.complex128)
     for k in range(K):
         for j in range(J):
-            x = p[j] * resample(psi[k], d["mt"][j], shifts[k][j], geo.P, geo.ext)
-            u[k, j] = crop(propagate(x, d["zhat"][j], geo.wavelength, geo.pixel), geo.n)
+            t, s = _plane_shifts(shifts, probe_shifts, d["mt"][j], k, j)
+            x = p[j] * resample(psi[k], d["mt"][j], t, geo.P, geo.ext)
+            y = propagate(x, d["zhat"][j], geo.wavelength, geo.pixel)
+            if s is not None:
+                y = shift(y, s)
+            u[k, j] = crop(y, geo.n)
     return u
 
 
@@ -265,9 +308,9 @@ def _plane_loss_f1(u, d):
     return float(np.sum((np.abs(u) ** 2 - d) ** 2))
 
 
-def functional(psi, q, shifts, sqrt_d, sqrt_dref, geo):
+def functional(psi, q, shifts, sqrt_d, sqrt_dref, geo, probe_shifts=None):
     """F2 of Eq. min1: sum_kj || |u_kj| - sqrt(d~_kj) ||^2 + w_ref || |D_{zeta_0} q| - sqrt(d~^r) ||^2."""
-    u = forward(psi, q, shifts, geo)
+    u = forward(psi, q, shifts, geo, probe_shifts)
     F = float(np.sum((np.abs(u) - sqrt_d) ** 2))
     if geo.w_ref != 0.0:
         uref = reference_field(q, geo)
@@ -275,10 +318,10 @@ def functional(psi, q, shifts, sqrt_d, sqrt_dref, geo):
     return F
 
 
-def functional_f1(psi, q, shifts, d, d_ref, geo):
+def functional_f1(psi, q, shifts, d, d_ref, geo, probe_shifts=None):
     """F1 of Eq. min2: sum_kj || |u_kj|^2 - d~_kj ||^2 + w_ref || |D_{zeta_0} q|^2 - d~^r ||^2
     (d are intensities; the paper's reference term has weight 1)."""
-    u = forward(psi, q, shifts, geo)
+    u = forward(psi, q, shifts, geo, probe_shifts)
     F = float(np.sum((np.abs(u) ** 2 - d) ** 2))
     if geo.w_ref != 0.0:
         uref = reference_field(q, geo)
@@ -286,11 +329,13 @@ def functional_f1(psi, q, shifts, d, d_ref, geo):
     return F
 
 
-def _gradients(psi, q, shifts, data, data_ref, geo, plane_loss, residual):
+def _gradients(psi, q, shifts, data, data_ref, geo, plane_loss, residual, probe_shifts=None):
     """Loss and real gradients for a per-pixel loss of u whose real gradient is 2 residual(u):
     grad_psi_k = 2 sum_j R0_kj^T( conj(p_j) * D_{-zhat_j}(C* r_kj) ),
     grad_q     = 2 [ sum_j D_{-omega_j}( sum_k conj(R_kj psi_k) * D_{-zhat_j}(C* r_kj) )
-                     + w_ref D_{-zeta_0}(C* r_ref) ]."""
+                     + w_ref D_{-zeta_0}(C* r_ref) ].
+    With probe shifts (reading R5), R_kj carries the object shift t - m~_j s_kj and
+    D_{-zhat_j} C* r becomes D_{-zhat_j} S_{-s} C* r, the adjoint of C S_s D_{zhat_j}."""
     psi = np.asarray(psi, dtype=np.complex128)
     d = derived_geometry(geo.z, geo.Z)
     lam, dx, n, P = geo.wavelength, geo.pixel, geo.n, geo.P
@@ -301,12 +346,15 @@ def _gradients(psi, q, shifts, data, data_ref, geo, plane_loss, residual):
     G = np.zeros((J, P, P), dtype=np.complex128)
     for k in range(K):
         for j in range(J):
-            Rpsi = resample(psi[k], d["mt"][j], shifts[k][j], P, geo.ext)
-            u = crop(propagate(p[j] * Rpsi, d["zhat"][j], lam, dx), n)
+            t, s = _plane_shifts(shifts, probe_shifts, d["mt"][j], k, j)
+            Rpsi = resample(psi[k], d["mt"][j], t, P, geo.ext)
+            y = propagate(p[j] * Rpsi, d["zhat"][j], lam, dx)
+            u = crop(y if s is None else shift(y, s), n)
             F += plane_loss(u, data[k][j])
             r = residual(u, data[k][j])
-            v = propagate(embed(r, P), -d["zhat"][j], lam, dx)
-            gpsi[k] += 2.0 * resample_adjoint(np.conj(p[j]) * v, d["mt"][j], shifts[k][j], n)
+            e = embed(r, P)
+            v = propagate(e if s is None else shift(e, (-s[0], -s[1])), -d["zhat"][j], lam, dx)
+            gpsi[k] += 2.0 * resample_adjoint(np.conj(p[j]) * v, d["mt"][j], t, n)
             G[j] += np.conj(Rpsi) * v
     gq = np.zeros((P, P), dtype=np.complex128)
     for j in range(J):
@@ -319,7 +367,7 @@ def _gradients(psi, q, shifts, data, data_ref, geo, plane_loss, residual):
     return F, gpsi, gq
 
 
-def gradients(psi, q, shifts, sqrt_d, sqrt_dref, geo):
+def gradients(psi, q, shifts, sqrt_d, sqrt_dref, geo, probe_shifts=None):
     """F2 and its gradients (Eq. gradpsi and the probe gradient after it).
 
     grad_psi_k = 2 sum_j R0_kj^T( conj(p_j) * D_{-zhat_j}(C* r_kj) )
@@ -327,15 +375,18 @@ def gradients(psi, q, shifts, sqrt_d, sqrt_dref, geo):
                      + w_ref D_{-zeta_0}(C* r_ref) ]
     with r = u - sqrt(d~) u/|u|.  These are real gradients for <a,b> = Re sum conj(a) b:
     dF(x; h) = Re <grad, h>.
+    Probe shifts (reading R5) are optional, as in ``forward``.
     Returns (F, grad_psi [K][n][n], grad_q [P][P]).
     """
-    return _gradients(psi, q, shifts, sqrt_d, sqrt_dref, geo, _plane_loss_f2, amplitude_residual)
+    return _gradients(psi, q, shifts, sqrt_d, sqrt_dref, geo, _plane_loss_f2, amplitude_residual,
+                      probe_shifts)
 
 
-def gradients_f1(psi, q, shifts, d, d_ref, geo):
+def gradients_f1(psi, q, shifts, d, d_ref, geo, probe_shifts=None):
     """F1 (Eq. min2) and its gradients: the chain of ``gradients`` with r replaced by
     r1 = 2 (|u|^2 - d~) u and intensities d~ as data."""
-    return _gradients(psi, q, shifts, d, d_ref, geo, _plane_loss_f1, intensity_residual)
+    return _gradients(psi, q, shifts, d, d_ref, geo, _plane_loss_f1, intensity_residual,
+                      probe_shifts)
 
 
 def plane_gradient(psi_k, q, t_kj, sqrt_d_kj, geo, j):

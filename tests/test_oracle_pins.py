@@ -577,3 +577,137 @@ def test_reconstruction_is_monotone():
     F = np.array(out["hist"]["F"])
     assert np.all(np.diff(F) <= 0.0)
     assert F[-1] < F[0]
+
+
+# ---------------------------------------------------------------- probe shifts (reading R5)
+
+def test_shift_is_index_roll_for_integers_and_moves_a_gaussian():
+    """S_s moves content by +s: an integer s is a periodic index roll, and a fractional s
+    moves a band-limited Gaussian to its samples at x - s (sign and scale of the ramp)."""
+    rng = _rng(21)
+    P = 32
+    x = _crandn(rng, P, P)
+    for s in [(1, 0), (0, -3), (2, 5), (-7, 4)]:
+        np.testing.assert_allclose(holo.shift(x, s), np.roll(x, s, axis=(0, 1)), atol=1e-13)
+    P, sig = 64, 3.0
+    c = np.arange(P) - P // 2
+    g = lambda y0, x0: np.exp(-((c[:, None] - y0) ** 2 + (c[None, :] - x0) ** 2) / (2 * sig**2))
+    s = (0.37, -1.61)
+    np.testing.assert_allclose(holo.shift(g(0, 0), s), g(*s), atol=1e-12)
+    assert np.abs(holo.shift(g(0, 0), (-s[0], -s[1])) - g(*s)).max() > 0.1
+
+
+def test_shift_group_unitary_adjoint_and_commutes_with_propagation():
+    rng = _rng(22)
+    P = 32
+    x, y = _crandn(rng, P, P), _crandn(rng, P, P)
+    a, b = (0.3, -1.2), (1.45, 0.7)
+    np.testing.assert_allclose(holo.shift(holo.shift(x, a), b),
+                               holo.shift(x, (a[0] + b[0], a[1] + b[1])), atol=1e-12)
+    assert np.linalg.norm(holo.shift(x, a)) == pytest.approx(np.linalg.norm(x), rel=1e-13)
+    lhs = np.vdot(holo.shift(x, a), y)
+    rhs = np.vdot(x, holo.shift(y, (-a[0], -a[1])))
+    assert abs(lhs - rhs) <= 1e-12 * abs(lhs)
+    z = 4.6e-4
+    np.testing.assert_allclose(holo.shift(holo.propagate(x, z, LAM, DX), a),
+                               holo.propagate(holo.shift(x, a), z, LAM, DX), atol=1e-12)
+
+
+def _literal_forward_rolled_probe(psi, q, t, s, geo):
+    """Eq. min1's field with the probe shift applied literally, S_s q = np.roll(q, s) for
+    integer s, written without the moved form."""
+    d = holo.derived_geometry(geo.z, geo.Z)
+    K, J = psi.shape[0], geo.n_dist
+    u = np.empty((K, J, geo.n, geo.n), complex)
+    for k in range(K):
+        for j in range(J):
+            qs = np.roll(q, (int(s[k][j][0]), int(s[k][j][1])), axis=(0, 1))
+            pj = holo.propagate(qs, d["omega"][j], LAM, DX)
+            x = pj * holo.resample(psi[k], d["mt"][j], t[k][j], geo.P, geo.ext)
+            u[k, j] = holo.crop(holo.propagate(x, d["zhat"][j], LAM, DX), geo.n)
+    return u
+
+
+@pytest.mark.parametrize("ext", [1.0, 0.0])
+def test_probe_shift_integer_equals_rolled_probe(ext):
+    """The moved form (reading R5) is the literal D_omega(S_s q) of Eq. min1 exactly when s
+    is an integer shift: S_s q is then q rolled by s."""
+    geo, psi, q, t, _, _ = _small_problem(ext=ext)
+    rng = _rng(23)
+    s = rng.integers(-3, 4, (psi.shape[0], geo.n_dist, 2)).astype(float)
+    u = holo.forward(psi, q, t, geo, probe_shifts=s)
+    np.testing.assert_allclose(u, _literal_forward_rolled_probe(psi, q, t, s, geo), atol=1e-12)
+    # the object shift must carry -m~ s: without it the fields differ at O(1)
+    d = holo.derived_geometry(geo.z, geo.Z)
+    assert np.abs(u - holo.forward(psi, q, t, geo)).max() > 1e-2
+    assert d["mt"][3] > 1.5
+
+
+def test_probe_shift_zero_and_psi_one():
+    """Zero probe shifts give the unshifted model; psi = 1 gives C S_s D_{zeta_0} q on every
+    plane (Theorem t3 with the shift commuted out of the propagations)."""
+    geo, psi, q, t, _, _ = _small_problem()
+    K, J = psi.shape[0], geo.n_dist
+    zero = np.zeros((K, J, 2))
+    np.testing.assert_allclose(holo.forward(psi, q, t, geo, probe_shifts=zero),
+                               holo.forward(psi, q, t, geo), atol=1e-13)
+    s = _rng(24).integers(-2, 3, (K, J, 2)).astype(float)
+    u = holo.forward(np.ones_like(psi), q, t, geo, probe_shifts=s)
+    d = holo.derived_geometry(geo.z, geo.Z)
+    b = holo.propagate(q, d["zeta"][0], LAM, DX)
+    for k in range(K):
+        for j in range(J):
+            ref = holo.crop(np.roll(b, (int(s[k, j, 0]), int(s[k, j, 1])), axis=(0, 1)), geo.n)
+            np.testing.assert_allclose(u[k, j], ref, atol=1e-12)
+
+
+def test_probe_shift_fractional_close_to_band_limited_probe_shift():
+    """For fractional s the moved form differs from D_omega(S_s q) * R_t psi only in how the
+    bilinear object field is shifted: on a smooth object the two fields agree to a small
+    fraction of the object's contribution, and far worse with the object shift's sign
+    flipped."""
+    n, P = 32, 64
+    geo = _geo(n, P)
+    d = holo.derived_geometry(geo.z, geo.Z)
+    c = np.arange(n) - n // 2
+    phase = -0.8 * np.exp(-(c[:, None] ** 2 + c[None, :] ** 2) / (2 * 5.0 ** 2))
+    psi = hs.transmittance(phase)[None]
+    q = hs.striped_probe(P, 0.3 * n, _rng(25))
+    t = np.array([[[0.6, -1.1]] * 4])
+    s = np.array([[[0.45, -0.3], [1.3, 0.2], [-0.7, 0.55], [0.25, 1.6]]])
+    u = holo.forward(psi, q, t, geo, probe_shifts=s)
+    obj = np.abs(u - holo.forward(np.ones_like(psi), q, t, geo, probe_shifts=s))
+    lit = np.empty_like(u)
+    wrong = np.empty_like(u)
+    for j in range(4):
+        pj = holo.propagate(holo.shift(q, s[0, j]), d["omega"][j], LAM, DX)
+        x = pj * holo.resample(psi[0], d["mt"][j], t[0, j], P, 1.0)
+        lit[0, j] = holo.crop(holo.propagate(x, d["zhat"][j], LAM, DX), n)
+        tw = (t[0, j, 0] + d["mt"][j] * s[0, j, 0], t[0, j, 1] + d["mt"][j] * s[0, j, 1])
+        y = holo.propagate(holo.probe_at_planes(q, geo)[j] *
+                           holo.resample(psi[0], d["mt"][j], tw, P, 1.0), d["zhat"][j], LAM, DX)
+        wrong[0, j] = holo.crop(holo.shift(y, s[0, j]), n)
+    err = np.linalg.norm(u - lit) / np.linalg.norm(obj)
+    assert err < 0.01
+    assert np.linalg.norm(wrong - lit) / np.linalg.norm(obj) > 10 * err
+
+
+@pytest.mark.parametrize("ext,w_ref,f1", [(1.0, 1.0, False), (0.0, 0.0, False), (1.0, 1.0, True)])
+def test_probe_shift_gradients_central_finite_differences(ext, w_ref, f1):
+    """With fractional probe shifts, central differences of F2 (and F1) equal Re<grad, h>:
+    pins the adjoint D_{-zhat} S_{-s} C* and the moved object shift in both gradients."""
+    geo, psi, q, t, sqrt_d, sqrt_dref = _small_problem(ext=ext, w_ref=w_ref)
+    s = _rng(26).uniform(-2, 2, (psi.shape[0], geo.n_dist, 2))
+    fun, grad = ((holo.functional_f1, holo.gradients_f1) if f1 else
+                 (holo.functional, holo.gradients))
+    data, dref = (sqrt_d ** 2, sqrt_dref ** 2) if f1 else (sqrt_d, sqrt_dref)
+    F, gpsi, gq = grad(psi, q, t, data, dref, geo, probe_shifts=s)
+    assert F == pytest.approx(fun(psi, q, t, data, dref, geo, probe_shifts=s), rel=1e-13)
+    rng = _rng(27)
+    for _ in range(4):
+        hpsi, hq = _crandn(rng, *psi.shape), _crandn(rng, *q.shape)
+        eps = 1e-6
+        fp = fun(psi + eps * hpsi, q + eps * hq, t, data, dref, geo, probe_shifts=s)
+        fm = fun(psi - eps * hpsi, q - eps * hq, t, data, dref, geo, probe_shifts=s)
+        an = cg.re_inner(gpsi, hpsi) + cg.re_inner(gq, hq)
+        assert (fp - fm) / (2 * eps) == pytest.approx(an, rel=1e-7)
