@@ -118,9 +118,22 @@ holo_status holo_destroy(holo_ctx* ctx);
 
 /* Sample shifts t_kj of Eq. min1 (S_{t_kj} psi_k), host float [n_angles][n_dist][2] as
  * (t_y, t_x) in psi pixels, copied.  Sizes the per-plane workspace; must precede
- * holo_forward / holo_gradient.  Probe shifts s_kj are zero (Sec. 2: they can be moved
- * onto psi and the data). */
+ * holo_forward / holo_gradient.  Probe shifts s_kj are zero unless
+ * holo_set_probe_shifts sets them. */
 holo_status holo_set_shifts(holo_ctx* ctx, const float* t_host);
+
+/* Probe shifts s_kj of Eq. min1 / Eq. min2 (the S_{s_kj} q inside D_{omega_j}), host float
+ * [n_angles][n_dist][2] as (s_y, s_x) in pixels of the padded grid, copied; NULL clears
+ * them.  |s| <= n/2 per component, else HOLO_ERR_ARG.  The shift is moved off the probe as
+ * Sec. 2 remarks after Eq. min2 (shifts commute with the other operators), so q is never
+ * interpolated:
+ *   u_kj = C S_s D_{zhat_j}( p_j * M_{1/m~_j} S_{t_kj - m~_j s_kj} psi_k ),
+ * with S_s the band-limited shift (phase ramp exp(-2 pi i k s / P) on the DFT, k in
+ * [-P/2, P/2)); for integer s this is exactly Eq. min1 with q rolled by s.  The ext-part of
+ * every plane then moves with s, so the per-plane box becomes the whole P x P grid: more
+ * row transforms per plane and a per-plane workspace of P x n + P x P complex64 per plane
+ * slot.  May be called before or after holo_set_shifts (the planes are rebuilt). */
+holo_status holo_set_probe_shifts(holo_ctx* ctx, const float* s_host);
 
 /* Register the data: sqrt_d (dev float [n_angles][n_dist][n][n]) holds sqrt(d~_kj), the
  * amplitudes of the data rescaled to the plane-0 grid (d~ = m0^2 M_{1/m0} d, Sec. 2);

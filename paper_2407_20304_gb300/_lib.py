@@ -20,7 +20,8 @@ STATUS = {0: "HOLO_OK", 1: "HOLO_ERR_ARG", 2: "HOLO_ERR_CUDA", 3: "HOLO_ERR_OOM"
           7: "HOLO_ERR_UNSUPPORTED"}
 
 # Every symbol declared in include/holo.h.
-EXPORTS = ("holo_create", "holo_destroy", "holo_set_shifts", "holo_set_data", "holo_set_probe",
+EXPORTS = ("holo_create", "holo_destroy", "holo_set_shifts", "holo_set_probe_shifts",
+           "holo_set_data", "holo_set_probe",
            "holo_forward", "holo_gradient", "holo_gradient_host", "holo_propagate", "holo_dot",
            "holo_step", "holo_direction", "holo_dy_dots", "holo_direction_step", "holo_set_functional",
            "holo_initial_probe", "holo_bin_amplitudes", "holo_upsample2", "holo_set_timing",
@@ -66,6 +67,7 @@ def load():
         "holo_create": [ctypes.POINTER(HoloGeometry), P, ctypes.POINTER(P)],
         "holo_destroy": [P],
         "holo_set_shifts": [P, P],
+        "holo_set_probe_shifts": [P, P],
         "holo_set_data": [P, P, P],
         "holo_set_probe": [P, P],
         "holo_forward": [P, I, I, P, P, ctypes.POINTER(D)],

@@ -95,6 +95,14 @@ struct holo_ctx {
   std::vector<PlaneDesc> planes;
   PlaneDesc* d_planes = nullptr;
   bool have_shifts = false;
+  std::vector<float> t_host;       // sample shifts t [K][J][2] as given
+  // probe shifts s [K][J][2] (holo_set_probe_shifts): the planes then use the full-grid box,
+  // object shifts t - m~_j s and the per-plane phase ramps below
+  bool probe_shift = false;
+  std::vector<float> s_host;
+  float2* d_ramp_x = nullptr;      // [K * J][P]: exp(-2 pi i k s_x / P)
+  float2* d_ramp_y = nullptr;      // [K * J][P]: exp(-2 pi i k s_y / P)
+  size_t ramp_bytes = 0;
   int maxbys = 0, maxbxs = 0;
   // FP64-built bilinear tap tables and the flat row list of all planes
   holo::Tap* d_xtap = nullptr;
@@ -497,6 +505,11 @@ PassArgs pass_args(holo_ctx* c, int k0, int nk, const void* psi) {
   a.ymap = c->ystage ? c->d_ymap : nullptr;
   a.yrows = (int)(c->ystride / c->n);
   a.err = reinterpret_cast<unsigned long long*>(c->d_red + kErrWord);
+  if (c->probe_shift) {
+    a.ramp_x = c->d_ramp_x;
+    a.ramp_y = c->d_ramp_y;
+    a.ymap = nullptr;
+  }
   return a;
 }
 
@@ -572,7 +585,11 @@ holo_status eval_planes(holo_ctx* c, PassArgs& a, bool gradient, bool first, int
   }
   {
     PassTimer tm(c, HOLO_T_PASS_B);
-    HOLO_LAUNCH(c, c->ops->pass_b(a, gradient ? 1 : 0, nbx, c->stream));
+    // with probe shifts the ext-part is inside the full-grid rows: no b term in pass B, and
+    // T carries only the reference residual
+    PassArgs ab = a;
+    if (c->probe_shift) ab.ext = 0.f;
+    HOLO_LAUNCH(c, c->ops->pass_b(ab, gradient ? 1 : 0, nbx, c->stream));
     // the last round's combine kernel of the plane-split form
     if (gradient && a.pb_split && a.pass_b_items % nbx) c->launches++;
   }
@@ -799,7 +816,8 @@ holo_status holo_destroy(holo_ctx* c) {
                   c->d_red,   c->d_dot3,       c->d_tpart,       c->s_psi,         c->s_gpsi,
                   c->s_data,
                   c->s_q,     c->s_gq,         c->d_xtap,        c->d_ytap,
-                  c->d_xadj,  c->d_yadj,       c->d_lines,       c->d_ymap};
+                  c->d_xadj,  c->d_yadj,       c->d_lines,       c->d_ymap,
+                  c->d_ramp_x, c->d_ramp_y};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   if (c->h_red) cudaFreeHost(c->h_red);
@@ -820,21 +838,39 @@ holo_status holo_destroy(holo_ctx* c) {
   return HOLO_OK;
 }
 
-holo_status holo_set_shifts(holo_ctx* c, const float* t) {
-  if (!c || !t) return fail(c, HOLO_ERR_ARG, "null argument");
+}  // extern "C"
+
+namespace {
+
+// Plane descriptors, bilinear tap tables, the flat row list and the per-plane workspace for
+// the sample shifts t (and probe shifts, when set).  Without probe shifts each plane's box
+// is the support of R0(psi - ext); with them the box is the whole P x P grid and the taps
+// use the object shift t - m~_j s (FP64).
+holo_status build_planes(holo_ctx* c) {
   const int n = c->n, P = c->P, J = c->J, K = c->K;
-  for (long long i = 0; i < 2LL * K * J; ++i)
-    if (!std::isfinite(t[i]) || std::fabs(t[i]) > n) return fail(c, HOLO_ERR_ARG, "bad shift");
+  const float* t = c->t_host.data();
   c->planes.assign((size_t)K * J, PlaneDesc{});
+  std::vector<double> teff((size_t)K * J * 2);
   int maxbys = 1, maxbxs = 1;
   for (int k = 0; k < K; ++k)
     for (int j = 0; j < J; ++j) {
-      PlaneDesc& d = c->planes[(size_t)k * J + j];
+      const size_t p = (size_t)k * J + j;
+      PlaneDesc& d = c->planes[p];
       split_mt(c->mt[j], P, &d.mt_hi, &d.mt_lo);
-      d.ty = t[((size_t)k * J + j) * 2 + 0];
-      d.tx = t[((size_t)k * J + j) * 2 + 1];
-      axis_box(c->mt[j], d.ty, n, P, &d.by0, &d.bys);
-      axis_box(c->mt[j], d.tx, n, P, &d.bx0, &d.bxs);
+      double ty = t[p * 2 + 0], tx = t[p * 2 + 1];
+      if (c->probe_shift) {
+        ty -= c->mt[j] * (double)c->s_host[p * 2 + 0];
+        tx -= c->mt[j] * (double)c->s_host[p * 2 + 1];
+        d.by0 = d.bx0 = 0;
+        d.bys = d.bxs = P;
+      } else {
+        axis_box(c->mt[j], ty, n, P, &d.by0, &d.bys);
+        axis_box(c->mt[j], tx, n, P, &d.bx0, &d.bxs);
+      }
+      teff[p * 2 + 0] = ty;
+      teff[p * 2 + 1] = tx;
+      d.ty = (float)ty;
+      d.tx = (float)tx;
       maxbys = std::max(maxbys, d.bys);
       maxbxs = std::max(maxbxs, d.bxs);
     }
@@ -847,8 +883,8 @@ holo_status holo_set_shifts(holo_ctx* c, const float* t) {
   for (size_t p = 0; p < np_all; ++p) {
     const PlaneDesc& d = c->planes[p];
     const double mt = c->mt[p % J];
-    axis_taps(mt, d.tx, n, P, d.bx0, d.bxs, &xt[p * stride], &xa[p * n]);
-    axis_taps(mt, d.ty, n, P, d.by0, d.bys, &yt[p * stride], &ya[p * n]);
+    axis_taps(mt, teff[p * 2 + 1], n, P, d.bx0, d.bxs, &xt[p * stride], &xa[p * n]);
+    axis_taps(mt, teff[p * 2 + 0], n, P, d.by0, d.bys, &yt[p * stride], &ya[p * n]);
     c->rowstart[p + 1] = c->rowstart[p] + d.bys;
   }
   std::vector<int2> lines((size_t)c->rowstart[np_all]);
@@ -911,6 +947,67 @@ holo_status holo_set_shifts(holo_ctx* c, const float* t) {
   c->maxbxs = maxbxs;
   c->have_shifts = true;
   return HOLO_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+holo_status holo_set_shifts(holo_ctx* c, const float* t) {
+  if (!c || !t) return fail(c, HOLO_ERR_ARG, "null argument");
+  const int n = c->n;
+  const long long cnt = 2LL * c->K * c->J;
+  for (long long i = 0; i < cnt; ++i)
+    if (!std::isfinite(t[i]) || std::fabs(t[i]) > n) return fail(c, HOLO_ERR_ARG, "bad shift");
+  c->t_host.assign(t, t + cnt);
+  return build_planes(c);
+}
+
+holo_status holo_set_probe_shifts(holo_ctx* c, const float* s) {
+  if (!c) return HOLO_ERR_ARG;
+  const int n = c->n, P = c->P;
+  const long long np = (long long)c->K * c->J;
+  if (!s) {
+    c->probe_shift = false;
+    c->s_host.clear();
+    dfree(c, c->d_ramp_x, c->ramp_bytes);
+    dfree(c, c->d_ramp_y, c->ramp_bytes);
+    c->d_ramp_x = c->d_ramp_y = nullptr;
+    c->ramp_bytes = 0;
+    return c->have_shifts ? build_planes(c) : HOLO_OK;
+  }
+  for (long long i = 0; i < 2 * np; ++i)
+    if (!std::isfinite(s[i]) || std::fabs(s[i]) > n / 2)
+      return fail(c, HOLO_ERR_ARG, "bad probe shift (|s| must be at most n/2)");
+  // phase ramps of S_s on the DFT, k in [-P/2, P/2) (FP64)
+  const double kPi = 3.14159265358979323846;
+  const size_t bytes = sizeof(float2) * (size_t)np * P;
+  std::vector<float2> rx((size_t)np * P), ry((size_t)np * P);
+  for (long long p = 0; p < np; ++p)
+    for (int f = 0; f < P; ++f) {
+      const double k = f < P / 2 ? f : f - P;
+      const double ay = -2.0 * kPi * k * (double)s[p * 2 + 0] / P;
+      const double ax = -2.0 * kPi * k * (double)s[p * 2 + 1] / P;
+      ry[(size_t)p * P + f] = make_float2((float)std::cos(ay), (float)std::sin(ay));
+      rx[(size_t)p * P + f] = make_float2((float)std::cos(ax), (float)std::sin(ax));
+    }
+  holo_status st;
+  if (bytes != c->ramp_bytes) {
+    dfree(c, c->d_ramp_x, c->ramp_bytes);
+    dfree(c, c->d_ramp_y, c->ramp_bytes);
+    c->d_ramp_x = c->d_ramp_y = nullptr;
+    c->ramp_bytes = 0;
+    if ((st = dalloc(c, (void**)&c->d_ramp_x, bytes)) ||
+        (st = dalloc(c, (void**)&c->d_ramp_y, bytes)))
+      return st;
+    c->ramp_bytes = bytes;
+  }
+  if ((st = upload(c, c->d_ramp_x, rx.data(), bytes)) ||
+      (st = upload(c, c->d_ramp_y, ry.data(), bytes)))
+    return st;
+  c->s_host.assign(s, s + 2 * np);
+  c->probe_shift = true;
+  return c->have_shifts ? build_planes(c) : HOLO_OK;
 }
 
 holo_status holo_set_data(holo_ctx* c, const float* sqrt_d, const float* sqrt_dref) {

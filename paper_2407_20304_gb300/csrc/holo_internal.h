@@ -98,6 +98,11 @@ struct PassArgs {
   const void* ymap;
   int yrows;                   // rows per plane in ybuf (ystride / n)
   unsigned long long* err;     // device word, set when a bounded device wait gave up
+  // probe shifts (SHIFT forms of passes A-C): per global plane the phase ramps
+  // exp(-2 pi i k s / P) of the row (x) and column (y) frequencies k, [planes][P] each;
+  // null without probe shifts
+  const float2* ramp_x;
+  const float2* ramp_y;
 };
 
 // Rows of one TMA box of pass B's Y stage (the tensor-map box limit is 256).

@@ -21,6 +21,14 @@
 //
 // All passes run persistent blocks (a grid that fills the GPU once) that load the FFT
 // twiddles into shared memory once and then walk a flat list of work items.
+//
+// Probe shifts s_kj (Eq. min1) use the SHIFT forms of passes A, B and C.  The shift is moved
+// off the probe, u_kj = C S_s D_{zhat_j}(p_j * R'_kj psi_k) with R' the resample at object
+// shift t - m~_j s, and S_s D_{zhat_j} is one separable Fourier multiplier: the chirp times
+// the per-plane phase ramps exp(-2 pi i k s / P) of each axis (ramp_x in the row passes,
+// ramp_y in the column pass; conjugated in the adjoints).  The ext-part of the field is then
+// shifted per plane as well, so the box is the whole P x P grid, w holds R' psi itself
+// (ext added back in pass A) and pass B runs with ext = 0 (no b term, T = w_ref r_ref).
 
 #pragma once
 
@@ -204,7 +212,7 @@ __device__ __forceinline__ void ensure_chirp(float2* chs, const float2* __restri
 
 // ------------------------------------------------------------------ pass A
 
-template <int P>
+template <int P, bool SHIFT>
 __global__ void __launch_bounds__(RowCfg<P>::NT, RowCfg<P>::MINB) k_pass_a(PassArgs a) {
   using F = Fft<P>;
   using R = RowCfg<P>;
@@ -242,7 +250,8 @@ __global__ void __launch_bounds__(RowCfg<P>::NT, RowCfg<P>::MINB) k_pass_a(PassA
       const int X = F::pos(t, c), rel = X - d.bx0;
       float2 x = make_float2(0.f, 0.f);
       if (valid && (unsigned)rel < (unsigned)d.bxs) {
-        const float2 w = resample_w(psi, n, a.ext, yt.i0, yt.f, xt[rel]);
+        float2 w = resample_w(psi, n, a.ext, yt.i0, yt.f, xt[rel]);
+        if (SHIFT) w.x += a.ext;  // full-grid form: w = R' psi
         wrow[rel] = w;
         x = cmul(__ldg(prow + X), w);
       }
@@ -253,10 +262,12 @@ __global__ void __launch_bounds__(RowCfg<P>::NT, RowCfg<P>::MINB) k_pass_a(PassA
     fft_fwd_with<P>(v, sm, tw, t, SyncBlock());
     const bool own = R::G == 1 || j == jcur;
     const float2* chg = a.chirp_zhat + (long long)j * P;
+    const float2* rmp = SHIFT ? a.ramp_x + (long long)gp * P : nullptr;
 #pragma unroll
     for (int c = 0; c < 16; ++c) {
       const int f = F::fpos(t, c);
       v[c] = cmul(v[c], own ? chirp_half<P>(chs, f) : __ldg(chg + f));
+      if (SHIFT) v[c] = cmul(v[c], __ldg(rmp + f));
     }
     fft_inv_with<P>(v, sm, tw, t, SyncBlock());
     float2* yrow = a.ybuf + (long long)lp * a.ystride + (long long)i * n;
@@ -306,7 +317,7 @@ __device__ __forceinline__ void stage_y(const PassArgs& a, float2* stg, uint64_t
 // and S = sum_kj r_kj is accumulated in shared memory in a fixed order and written once
 // (with the reference residual) as the source of the ext-part of grad_q.  Every S / b slot
 // is owned by one thread (its crop rows of its column), so no barrier guards them.
-template <int P, bool ADJ>
+template <int P, bool ADJ, bool SHIFT>
 __global__ void __launch_bounds__(ColCfg<P>::NT) k_pass_b(PassArgs a) {
   using F = Fft<P>;
   using Cc = ColCfg<P>;
@@ -400,8 +411,12 @@ __global__ void __launch_bounds__(ColCfg<P>::NT) k_pass_b(PassArgs a) {
           const int rr = F::pos(t, c) - lo;
           dats[c] = (valid && (unsigned)rr < (unsigned)n) ? __ldg(ad + (long long)rr * n + col) : 0.f;
         }
+        const float2* rmp = SHIFT ? a.ramp_y + gplane * P : nullptr;
 #pragma unroll
-        for (int c = 0; c < 16; ++c) v[c] = cmul(v[c], chirp_half<P>(chs, F::fpos(t, c)));
+        for (int c = 0; c < 16; ++c) {
+          v[c] = cmul(v[c], chirp_half<P>(chs, F::fpos(t, c)));
+          if (SHIFT) v[c] = cmul(v[c], __ldg(rmp + F::fpos(t, c)));
+        }
         fft_inv_with<P>(v, sm, tw, t, SyncBlock());
         float2* uo = a.u_out ? a.u_out + (long long)lp * n * n : nullptr;
         float lsum = 0.f;
@@ -441,7 +456,10 @@ __global__ void __launch_bounds__(ColCfg<P>::NT) k_pass_b(PassArgs a) {
         if constexpr (ADJ) {
           fft_fwd_with<P>(v, sm, tw, t, SyncBlock());
 #pragma unroll
-          for (int c = 0; c < 16; ++c) v[c] = cmulc(v[c], chirp_half<P>(chs, F::fpos(t, c)));
+          for (int c = 0; c < 16; ++c) {
+            v[c] = cmulc(v[c], chirp_half<P>(chs, F::fpos(t, c)));
+            if (SHIFT) v[c] = cmulc(v[c], __ldg(rmp + F::fpos(t, c)));
+          }
           fft_inv_with<P>(v, sm, tw, t, SyncBlock());
 #pragma unroll
           for (int c = 0; c < 16; ++c) {
@@ -478,7 +496,7 @@ __global__ void __launch_bounds__(ColCfg<P>::NT) k_pass_b(PassArgs a) {
 // partial round split evenly over all blocks in (group, distance, angle) order.  Each block
 // leaves S of every group it touched in its own slot; k_pass_b_tail adds the slots in block
 // order (a fixed order) into T.  The item body is k_pass_b's.
-template <int P, bool ADJ>
+template <int P, bool ADJ, bool SHIFT>
 __global__ void __launch_bounds__(ColCfg<P>::NT) k_pass_b_split(PassArgs a) {
   using F = Fft<P>;
   using Cc = ColCfg<P>;
@@ -536,8 +554,12 @@ __global__ void __launch_bounds__(ColCfg<P>::NT) k_pass_b_split(PassArgs a) {
       const int rr = F::pos(t, c) - lo;
       dats[c] = (valid && (unsigned)rr < (unsigned)n) ? __ldg(ad + (long long)rr * n + col) : 0.f;
     }
+    const float2* rmp = SHIFT ? a.ramp_y + gplane * P : nullptr;
 #pragma unroll
-    for (int c = 0; c < 16; ++c) v[c] = cmul(v[c], chirp_half<P>(chs, F::fpos(t, c)));
+    for (int c = 0; c < 16; ++c) {
+      v[c] = cmul(v[c], chirp_half<P>(chs, F::fpos(t, c)));
+      if (SHIFT) v[c] = cmul(v[c], __ldg(rmp + F::fpos(t, c)));
+    }
     fft_inv_with<P>(v, sm, tw, t, SyncBlock());
     float2* uo = a.u_out ? a.u_out + (long long)lp * n * n : nullptr;
     float lsum = 0.f;
@@ -575,7 +597,10 @@ __global__ void __launch_bounds__(ColCfg<P>::NT) k_pass_b_split(PassArgs a) {
     if constexpr (ADJ) {
       fft_fwd_with<P>(v, sm, tw, t, SyncBlock());
 #pragma unroll
-      for (int c = 0; c < 16; ++c) v[c] = cmulc(v[c], chirp_half<P>(chs, F::fpos(t, c)));
+      for (int c = 0; c < 16; ++c) {
+        v[c] = cmulc(v[c], chirp_half<P>(chs, F::fpos(t, c)));
+        if (SHIFT) v[c] = cmulc(v[c], __ldg(rmp + F::fpos(t, c)));
+      }
       fft_inv_with<P>(v, sm, tw, t, SyncBlock());
 #pragma unroll
       for (int c = 0; c < 16; ++c) {
@@ -683,7 +708,7 @@ __global__ void k_pass_b_tail(PassArgs a, int nblocks) {
 
 // ------------------------------------------------------------------ pass C
 
-template <int P>
+template <int P, bool SHIFT>
 __global__ void __launch_bounds__(RowCfg<P>::NT, RowCfg<P>::MINB) k_pass_c(PassArgs a) {
   using F = Fft<P>;
   using R = RowCfg<P>;
@@ -718,14 +743,17 @@ __global__ void __launch_bounds__(RowCfg<P>::NT, RowCfg<P>::MINB) k_pass_c(PassA
     fft_fwd_with<P>(v, sm, tw, t, SyncBlock());
     const bool own = R::G == 1 || j == jcur;
     const float2* chg = a.chirp_zhat + (long long)j * P;
+    const float2* rmp = SHIFT ? a.ramp_x + (long long)gp * P : nullptr;
 #pragma unroll
     for (int c = 0; c < 16; ++c) {
       const int f = F::fpos(t, c);
       v[c] = cmulc(v[c], own ? chirp_half<P>(chs, f) : __ldg(chg + f));
+      if (SHIFT) v[c] = cmulc(v[c], __ldg(rmp + f));
     }
     fft_inv_with<P>(v, sm, tw, t, SyncBlock());
     // v holds the adjoint field on this P-grid row; the exchange buffer is free.
-    // The box holds w = R0(psi - ext) written by pass A; replace it by conj(w) v.
+    // The box holds w = R0(psi - ext) (R' psi in the SHIFT form) written by pass A; replace
+    // it by conj(w) v.
     const PlaneDesc d = a.planes[gp];
     const float2* prow = a.pj + ((long long)j * P + d.by0 + i) * P;
     float2* gk = a.gkbuf + (long long)lp * a.gkstride + (long long)i * d.bxs;
@@ -814,16 +842,23 @@ cudaError_t launch_cols(const LineArgs& a, const float2* tw, cudaStream_t s) {
   return launch_lines<P, true>(a, tw, s);
 }
 
-template <int P>
-cudaError_t launch_pass_a(const PassArgs& a, cudaStream_t s) {
+template <int P, bool SHIFT>
+cudaError_t launch_pass_a_form(const PassArgs& a, cudaStream_t s) {
   using R = RowCfg<P>;
   if (a.nlines <= 0) return cudaSuccess;
-  cudaError_t e = cudaFuncSetAttribute(k_pass_a<P>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+  cudaError_t e = cudaFuncSetAttribute(k_pass_a<P, SHIFT>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)R::SMEM_BYTES);
   if (e != cudaSuccess) return e;
-  const int nb = persistent_blocks(k_pass_a<P>, R::NT, R::SMEM_BYTES, (a.nlines + R::G - 1) / R::G);
-  k_pass_a<P><<<nb, R::NT, R::SMEM_BYTES, s>>>(a);
+  const int nb = persistent_blocks(k_pass_a<P, SHIFT>, R::NT, R::SMEM_BYTES,
+                                   (a.nlines + R::G - 1) / R::G);
+  k_pass_a<P, SHIFT><<<nb, R::NT, R::SMEM_BYTES, s>>>(a);
   return cudaGetLastError();
+}
+
+template <int P>
+cudaError_t launch_pass_a(const PassArgs& a, cudaStream_t s) {
+  return a.ramp_x ? launch_pass_a_form<P, true>(a, s) : launch_pass_a_form<P, false>(a, s);
 }
 
 template <int P>
@@ -848,8 +883,8 @@ int pass_b_blocks(int items, int n, int rows) {
   using Cc = ColCfg<P>;
   const size_t sm = pass_b_smem<P>(n, rows);
   if (sm > (size_t)max_dynamic_smem()) return 0;
-  cudaFuncSetAttribute(k_pass_b<P, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-  return persistent_blocks(k_pass_b<P, true>, Cc::NT, sm, items);
+  cudaFuncSetAttribute(k_pass_b<P, true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  return persistent_blocks(k_pass_b<P, true, false>, Cc::NT, sm, items);
 }
 
 // The Y stage is used where the box is at most 2C x kStageBox floats wide (P >= 1024), the
@@ -861,11 +896,11 @@ int pass_b_stage_ok(int n, int rows) {
   const size_t s0 = pass_b_smem<P>(n), s1 = pass_b_smem<P>(n, rows);
   if (s1 > (size_t)max_dynamic_smem()) return 0;
   int b0 = 0, b1 = 0;
-  if (cudaFuncSetAttribute(k_pass_b<P, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+  if (cudaFuncSetAttribute(k_pass_b<P, true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                            (int)s1) != cudaSuccess ||
-      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b0, k_pass_b<P, true>, Cc::NT, s0) !=
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b0, k_pass_b<P, true, false>, Cc::NT, s0) !=
           cudaSuccess ||
-      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b1, k_pass_b<P, true>, Cc::NT, s1) !=
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b1, k_pass_b<P, true, false>, Cc::NT, s1) !=
           cudaSuccess) {
     cudaGetLastError();
     return 0;
@@ -877,18 +912,18 @@ template <int P>
 int pass_b_blocks_split(long long items, int n) {
   using Cc = ColCfg<P>;
   const size_t sm = pass_b_smem<P>(n);
-  cudaFuncSetAttribute(k_pass_b_split<P, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+  cudaFuncSetAttribute(k_pass_b_split<P, true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                        (int)sm);
-  return persistent_blocks(k_pass_b_split<P, true>, Cc::NT, sm, items);
+  return persistent_blocks(k_pass_b_split<P, true, false>, Cc::NT, sm, items);
 }
 
-template <int P, bool ADJ>
+template <int P, bool ADJ, bool SHIFT>
 cudaError_t launch_pass_b_split(const PassArgs& a, int nblocks, size_t sm, cudaStream_t s) {
   using Cc = ColCfg<P>;
-  cudaError_t e = cudaFuncSetAttribute(k_pass_b_split<P, ADJ>,
+  cudaError_t e = cudaFuncSetAttribute(k_pass_b_split<P, ADJ, SHIFT>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
   if (e != cudaSuccess) return e;
-  k_pass_b_split<P, ADJ><<<nblocks, Cc::NT, sm, s>>>(a);
+  k_pass_b_split<P, ADJ, SHIFT><<<nblocks, Cc::NT, sm, s>>>(a);
   const int ngroups = (a.n + Cc::C - 1) / Cc::C, tail = ngroups - (ngroups / nblocks) * nblocks;
   if (ADJ && tail > 0) {
     e = cudaGetLastError();
@@ -898,42 +933,52 @@ cudaError_t launch_pass_b_split(const PassArgs& a, int nblocks, size_t sm, cudaS
   return cudaGetLastError();
 }
 
-template <int P>
-cudaError_t launch_pass_b(const PassArgs& a, int adj, int nblocks, cudaStream_t s) {
+template <int P, bool ADJ, bool SHIFT>
+cudaError_t launch_pass_b_form(const PassArgs& a, int nblocks, cudaStream_t s) {
   using Cc = ColCfg<P>;
   if (a.pb_split) {
     PassArgs b = a;
     b.ymap = nullptr;
-    const size_t sm = pass_b_smem<P>(a.n);
-    return adj ? launch_pass_b_split<P, true>(b, nblocks, sm, s)
-               : launch_pass_b_split<P, false>(b, nblocks, sm, s);
+    return launch_pass_b_split<P, ADJ, SHIFT>(b, nblocks, pass_b_smem<P>(a.n), s);
   }
   const size_t sm = pass_b_smem<P>(a.n, a.ymap ? a.max_box_rows : 0);
-  cudaError_t e;
-  if (adj) {
-    e = cudaFuncSetAttribute(k_pass_b<P, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)sm);
-    if (e != cudaSuccess) return e;
-    k_pass_b<P, true><<<nblocks, Cc::NT, sm, s>>>(a);
-  } else {
-    e = cudaFuncSetAttribute(k_pass_b<P, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)sm);
-    if (e != cudaSuccess) return e;
-    k_pass_b<P, false><<<nblocks, Cc::NT, sm, s>>>(a);
+  cudaError_t e = cudaFuncSetAttribute(k_pass_b<P, ADJ, SHIFT>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  if (e != cudaSuccess) return e;
+  k_pass_b<P, ADJ, SHIFT><<<nblocks, Cc::NT, sm, s>>>(a);
+  return cudaGetLastError();
+}
+
+// The SHIFT form (probe shifts) runs without the Y stage: its box is the whole grid.
+template <int P>
+cudaError_t launch_pass_b(const PassArgs& a, int adj, int nblocks, cudaStream_t s) {
+  if (a.ramp_y) {
+    PassArgs b = a;
+    b.ymap = nullptr;
+    return adj ? launch_pass_b_form<P, true, true>(b, nblocks, s)
+               : launch_pass_b_form<P, false, true>(b, nblocks, s);
   }
+  return adj ? launch_pass_b_form<P, true, false>(a, nblocks, s)
+             : launch_pass_b_form<P, false, false>(a, nblocks, s);
+}
+
+template <int P, bool SHIFT>
+cudaError_t launch_pass_c_form(const PassArgs& a, cudaStream_t s) {
+  using R = RowCfg<P>;
+  if (a.nlines <= 0) return cudaSuccess;
+  cudaError_t e = cudaFuncSetAttribute(k_pass_c<P, SHIFT>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)R::SMEM_BYTES);
+  if (e != cudaSuccess) return e;
+  const int nb = persistent_blocks(k_pass_c<P, SHIFT>, R::NT, R::SMEM_BYTES,
+                                   (a.nlines + R::G - 1) / R::G);
+  k_pass_c<P, SHIFT><<<nb, R::NT, R::SMEM_BYTES, s>>>(a);
   return cudaGetLastError();
 }
 
 template <int P>
 cudaError_t launch_pass_c(const PassArgs& a, cudaStream_t s) {
-  using R = RowCfg<P>;
-  if (a.nlines <= 0) return cudaSuccess;
-  cudaError_t e = cudaFuncSetAttribute(k_pass_c<P>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)R::SMEM_BYTES);
-  if (e != cudaSuccess) return e;
-  const int nb = persistent_blocks(k_pass_c<P>, R::NT, R::SMEM_BYTES, (a.nlines + R::G - 1) / R::G);
-  k_pass_c<P><<<nb, R::NT, R::SMEM_BYTES, s>>>(a);
-  return cudaGetLastError();
+  return a.ramp_x ? launch_pass_c_form<P, true>(a, s) : launch_pass_c_form<P, false>(a, s);
 }
 
 template <int P>

@@ -153,6 +153,17 @@ class Holo:
         p = _host_ptr(t, np.float32, (self.n_angles, self.n_dist, 2), "shifts")
         _check(self.lib, self.ctx, self.lib.holo_set_shifts(self.ctx, p), "holo_set_shifts")
 
+    def set_probe_shifts(self, s):
+        """Probe shifts s_kj (y, x) in pixels: float32 [n_angles][n_dist][2] (numpy, host), or
+        None to clear them (holo_set_probe_shifts)."""
+        if s is None:
+            p = ctypes.c_void_p(None)
+        else:
+            s = np.ascontiguousarray(s, dtype=np.float32)
+            p = _host_ptr(s, np.float32, (self.n_angles, self.n_dist, 2), "probe shifts")
+        _check(self.lib, self.ctx, self.lib.holo_set_probe_shifts(self.ctx, p),
+               "holo_set_probe_shifts")
+
     def set_data(self, sqrt_d, sqrt_dref=None):
         """sqrt(d~_kj): float32 cuda [n_angles][n_dist][n][n]; sqrt(d~^r): [n][n] or None."""
         import torch
