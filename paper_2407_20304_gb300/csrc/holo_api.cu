@@ -845,10 +845,13 @@ namespace {
 // Plane descriptors, bilinear tap tables, the flat row list and the per-plane workspace for
 // the sample shifts t (and probe shifts, when set).  Without probe shifts each plane's box
 // is the support of R0(psi - ext); with them the box is the whole P x P grid and the taps
-// use the object shift t - m~_j s (FP64).
+// use the object shift t - m~_j s (FP64).  Until it succeeds the context has no valid
+// planes (evaluations return HOLO_ERR_STATE), so a failed rebuild never leaves stale or
+// freed tables in use.
 holo_status build_planes(holo_ctx* c) {
   const int n = c->n, P = c->P, J = c->J, K = c->K;
   const float* t = c->t_host.data();
+  c->have_shifts = false;
   c->planes.assign((size_t)K * J, PlaneDesc{});
   std::vector<double> teff((size_t)K * J * 2);
   int maxbys = 1, maxbxs = 1;
@@ -906,7 +909,6 @@ holo_status build_planes(holo_ctx* c) {
         (st = dalloc(c, (void**)&c->d_lines, rb)))
       return st;
     c->tap_bytes = 2 * tb + 2 * ab + rb;
-    c->bytes -= 0;
     if ((st = upload(c, c->d_xtap, xt.data(), tb)) || (st = upload(c, c->d_ytap, yt.data(), tb)) ||
         (st = upload(c, c->d_xadj, xa.data(), ab)) || (st = upload(c, c->d_yadj, ya.data(), ab)) ||
         (st = upload(c, c->d_lines, lines.data(), rb)))
@@ -992,19 +994,30 @@ holo_status holo_set_probe_shifts(holo_ctx* c, const float* s) {
       rx[(size_t)p * P + f] = make_float2((float)std::cos(ax), (float)std::sin(ax));
     }
   holo_status st;
+  // on a failure below the context drops its probe shifts and its planes (evaluations then
+  // return HOLO_ERR_STATE until holo_set_shifts succeeds again)
+  auto drop = [&](holo_status e) {
+    c->probe_shift = false;
+    c->s_host.clear();
+    c->have_shifts = false;
+    return e;
+  };
   if (bytes != c->ramp_bytes) {
     dfree(c, c->d_ramp_x, c->ramp_bytes);
     dfree(c, c->d_ramp_y, c->ramp_bytes);
     c->d_ramp_x = c->d_ramp_y = nullptr;
     c->ramp_bytes = 0;
     if ((st = dalloc(c, (void**)&c->d_ramp_x, bytes)) ||
-        (st = dalloc(c, (void**)&c->d_ramp_y, bytes)))
-      return st;
+        (st = dalloc(c, (void**)&c->d_ramp_y, bytes))) {
+      dfree(c, c->d_ramp_x, bytes);
+      c->d_ramp_x = nullptr;
+      return drop(st);
+    }
     c->ramp_bytes = bytes;
   }
   if ((st = upload(c, c->d_ramp_x, rx.data(), bytes)) ||
       (st = upload(c, c->d_ramp_y, ry.data(), bytes)))
-    return st;
+    return drop(st);
   c->s_host.assign(s, s + 2 * np);
   c->probe_shift = true;
   return c->have_shifts ? build_planes(c) : HOLO_OK;
