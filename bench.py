@@ -833,10 +833,13 @@ def run_hier(args):
 
 # ---------------------------------------------------------------- batch of reconstructions
 
-def batch_specs(seed, count=64, budget_gb=160.0):
+def batch_specs(seed, count=64, budget_gb=280.0):
     """Seeded uneven batch: side n in {256, 384, 512, 1024, 2048}, 1-4 distances, 16-128
-    angles, P = 2n (768 for n = 384: one radix-3 step), 16-angle chunks.  Instances are dropped from the
-    largest down if the planned device memory exceeds the budget."""
+    angles, P = 2n (768 for n = 384: one radix-3 step), 16-angle chunks.  Planned device
+    memory per instance: psi and grad_psi, data, q / grad_q / two P x P scratch fields, p_j,
+    the per-plane slots of a chunk (box rows x n for Y and box rows x box columns for w, the
+    box at most n + 16 per axis) and the plane tables.  Instances are dropped from the largest
+    down if the plan exceeds the budget (280 GB of the GPU's 298 GB)."""
     rng = hs.rng_for(seed, 77)
     specs = []
     for i in range(count):
@@ -846,7 +849,8 @@ def batch_specs(seed, count=64, budget_gb=160.0):
         P = 2 * n
         chunk = min(K, 16)
         mem = (2 * K * n * n * 8 + K * J * n * n * 4 + 4 * P * P * 8 + J * P * P * 8
-               + chunk * J * 3 * (n + 16) ** 2 * 8 + K * J * (2 * (n + 16) * 8 + 2 * n * 16))
+               + chunk * J * 2 * (n + 16) ** 2 * 8 + K * J * (2 * (n + 16) * 8 + 2 * n * 16)
+               + 3 * n * n * 8)
         specs.append({"n": n, "P": P, "J": J, "K": K, "chunk": chunk, "mem": mem, "seed": i})
     kept = sorted(specs, key=lambda d: d["mem"])
     while sum(d["mem"] for d in kept) > budget_gb * 1e9:
@@ -894,6 +898,9 @@ def run_batch(args):
                         q_true.clone())
         inst.data = (sqrt_d, sqrt_dref)
         insts.append(inst)
+        # the data-generation temporaries go back to the device before the next context
+        # allocates its workspace
+        torch.cuda.empty_cache()
     b = HoloBatch(insts)
     loop_ms = b.time_loop(reps=2)
     best_ms, sched, cost = b.autotune(candidates=(1, 2, 4, 8), reps=2)
