@@ -107,18 +107,21 @@ def backtrack(f, f0, x, eta, gamma0, max_halvings):
 
 
 def reconstruct(psi0, q0, shifts, sqrt_d, sqrt_dref, geo, iters, gamma0=1.0,
-                max_halvings=20, update_q=True, rule="dai-yuan", line_search="backtracking"):
+                max_halvings=20, update_q=True, rule="dai-yuan", line_search="backtracking",
+                probe_shifts=None):
     """Joint psi / q reconstruction by nonlinear conjugate gradients (Sec. 2).
 
     rule: the direction formula ('dai-yuan' of Eq. DaiYuan2, 'fletcher-reeves',
     'polak-ribiere'); line_search: 'backtracking' (first decrease of F, reading R7) or
     'armijo' (sufficient decrease with c = 1e-4).  Returns a dict with the final psi, q and
     per-iteration F, gamma_psi, gamma_q, beta_psi, beta_q.  The initial trial step of each
-    block is twice its last accepted step (gamma0 at the first iteration).
+    block is twice its last accepted step (gamma0 at the first iteration).  probe_shifts:
+    the s_kj of Eq. min1 (reading R5 of oracle.holo), or None.
     """
+    ps = probe_shifts
     psi = np.array(psi0, dtype=np.complex128)
     q = np.array(q0, dtype=np.complex128)
-    F, gpsi, gq = holo.gradients(psi, q, shifts, sqrt_d, sqrt_dref, geo)
+    F, gpsi, gq = holo.gradients(psi, q, shifts, sqrt_d, sqrt_dref, geo, ps)
     eta_psi, eta_q = -gpsi, -gq
     trial_psi = trial_q = gamma0
     hist = {"F": [F], "gamma_psi": [], "gamma_q": [], "beta_psi": [], "beta_q": [],
@@ -131,21 +134,21 @@ def reconstruct(psi0, q0, shifts, sqrt_d, sqrt_dref, geo, iters, gamma0=1.0,
 
     for _ in range(iters):
         def f_psi(x):
-            return holo.functional(x, q, shifts, sqrt_d, sqrt_dref, geo)
+            return holo.functional(x, q, shifts, sqrt_d, sqrt_dref, geo, ps)
         gam_psi, F = search(f_psi, F, gpsi, psi, eta_psi, trial_psi)
         psi = psi + gam_psi * eta_psi
         hist["F_after_psi"].append(F)
         gam_q = 0.0
         if update_q:
             def f_q(x):
-                return holo.functional(psi, x, shifts, sqrt_d, sqrt_dref, geo)
+                return holo.functional(psi, x, shifts, sqrt_d, sqrt_dref, geo, ps)
             # the q gradient at the updated psi is not evaluated; the slope of the Armijo
             # test uses the gradient of the last evaluation
             gam_q, F = search(f_q, F, gq, q, eta_q, trial_q)
             q = q + gam_q * eta_q
         trial_psi = 2.0 * gam_psi if gam_psi > 0 else trial_psi
         trial_q = 2.0 * gam_q if gam_q > 0 else trial_q
-        F_new, gpsi_new, gq_new = holo.gradients(psi, q, shifts, sqrt_d, sqrt_dref, geo)
+        F_new, gpsi_new, gq_new = holo.gradients(psi, q, shifts, sqrt_d, sqrt_dref, geo, ps)
         eta_psi, b_psi = direction(gpsi_new, gpsi, eta_psi, rule)
         eta_q, b_q = direction(gq_new, gq, eta_q, rule)
         gpsi, gq, F = gpsi_new, gq_new, F_new
@@ -157,12 +160,14 @@ def reconstruct(psi0, q0, shifts, sqrt_d, sqrt_dref, geo, iters, gamma0=1.0,
     return {"psi": psi, "q": q, "hist": hist}
 
 
-def reconstruct_hierarchical(sqrt_d, sqrt_dref, shifts, geo, levels, q0=None, **kw):
+def reconstruct_hierarchical(sqrt_d, sqrt_dref, shifts, geo, levels, q0=None,
+                             probe_shifts=None, **kw):
     """Hierarchical reconstruction (Sec. 3, on speeding up): for each (b, iters) of `levels`,
     from the coarsest binning b to b = 1, run `reconstruct` on data binned by b (pixel b dx,
-    side n/b on a P/b grid, shifts t/b), starting from psi = 1 and the initial probe of the
-    binned reference image at the first level and from the previous level's psi and q
-    upsampled twice as dense afterwards.  Returns the list of per-level results."""
+    side n/b on a P/b grid, shifts t/b and probe shifts s/b), starting from psi = 1 and the
+    initial probe of the binned reference image at the first level and from the previous
+    level's psi and q upsampled twice as dense afterwards.  Returns the list of per-level
+    results."""
     import dataclasses
     out = []
     psi = q = None
@@ -171,6 +176,7 @@ def reconstruct_hierarchical(sqrt_d, sqrt_dref, shifts, geo, levels, q0=None, **
         d = holo.bin_amplitudes(sqrt_d, b)
         dr = holo.bin_amplitudes(sqrt_dref, b) if sqrt_dref is not None else None
         t = np.asarray(shifts, np.float64) / b
+        s = None if probe_shifts is None else np.asarray(probe_shifts, np.float64) / b
         if i == 0:
             psi = np.ones((d.shape[0], g.n, g.n), np.complex128)
             q = holo.initial_probe(dr, g) if q0 is None else q0
@@ -179,7 +185,7 @@ def reconstruct_hierarchical(sqrt_d, sqrt_dref, shifts, geo, levels, q0=None, **
             while factor > 1:
                 psi, q = holo.upsample2(psi), holo.upsample2(q)
                 factor //= 2
-        res = reconstruct(psi, q, t, d, dr, g, iters, **kw)
+        res = reconstruct(psi, q, t, d, dr, g, iters, probe_shifts=s, **kw)
         psi, q = res["psi"], res["q"]
         out.append({"b": b, "psi": psi, "q": q, "hist": res["hist"]})
     return out

@@ -3,7 +3,8 @@ data, then the recovered object and probe extrapolated to a grid twice as dense 
 of the next, less binned level, ending without binning.
 
 Level (b, iters): data binned by b (amplitudes sqrt of the b x b mean intensity,
-holo_bin_amplitudes), pixel b dx, psi side n/b on a P/b grid, shifts t/b, `iters` iterations
+holo_bin_amplitudes), pixel b dx, psi side n/b on a P/b grid, shifts t/b (and probe shifts
+s/b when given), `iters` iterations
 of the joint psi / q driver (cg.Reconstruction).  The first level starts from psi = 1 and the
 paper's initial probe (the binned reference image propagated back to plane 0); later levels
 start from the previous level's psi and q upsampled (holo_upsample2).  The FP64 oracle's
@@ -18,7 +19,7 @@ from .holo import Holo, bin_amplitudes, upsample2
 
 class Hierarchy:
     def __init__(self, n, n_angles, n_dist, wavelength, pixel, Z, z, shifts, pad=0,
-                 levels=((8, 1000), (4, 500), (2, 250), (1, 125)), **driver):
+                 levels=((8, 1000), (4, 500), (2, 250), (1, 125)), probe_shifts=None, **driver):
         P = pad or 2 * n
         bs = [b for b, _ in levels]
         if bs[-1] != 1 or any(bs[i] != 2 * bs[i + 1] for i in range(len(bs) - 1)):
@@ -28,6 +29,7 @@ class Hierarchy:
         self.geo = dict(n=n, P=P, n_angles=n_angles, n_dist=n_dist, wavelength=wavelength,
                         pixel=pixel, Z=Z, z=tuple(z))
         self.shifts = np.asarray(shifts, np.float32)
+        self.probe_shifts = None if probe_shifts is None else np.asarray(probe_shifts, np.float32)
         self.levels = tuple(levels)
         self.driver = driver
         self.results = []
@@ -42,6 +44,8 @@ class Hierarchy:
             nb, Pb = g["n"] // b, g["P"] // b
             h = Holo(nb, g["n_angles"], g["n_dist"], g["wavelength"], g["pixel"] * b, g["Z"],
                      g["z"], pad=Pb)
+            if self.probe_shifts is not None:
+                h.set_probe_shifts(np.ascontiguousarray(self.probe_shifts / b))
             h.set_shifts(np.ascontiguousarray(self.shifts / b))
             d = bin_amplitudes(sqrt_d, b) if b > 1 else sqrt_d
             dr = bin_amplitudes(sqrt_dref, b) if b > 1 else sqrt_dref

@@ -175,3 +175,21 @@ def test_probe_shift_argument_errors():
         h.set_probe_shifts(bad)
     with pytest.raises(ValueError):
         h.set_probe_shifts(np.zeros((2, 3, 2), np.float32))
+
+
+@pytest.mark.parametrize("recompute", [False, True])
+def test_probe_shift_autograd(recompute):
+    """The autograd Function on a context with probe shifts: loss and .grad against the
+    oracle (both stored-gradient and recompute modes)."""
+    from paper_2407_20304_gb300.autograd import holo_loss
+    pr = make_problem(64, 128, 2, seed=9)
+    h = make_holo(pr)
+    psi = dev(pr["psi"], torch.complex64).requires_grad_(True)
+    q = dev(pr["q"], torch.complex64).requires_grad_(True)
+    loss = holo_loss(psi, q, h, recompute=recompute)
+    loss.backward()
+    F, gp_ref, gq_ref = oh.gradients(pr["psi"], pr["q"], pr["t"], pr["sqrt_d"], pr["sqrt_dref"],
+                                     pr["geo"], probe_shifts=pr["s"])
+    assert abs(float(loss) - F) / F < LOSS_TOL
+    assert rel(psi.grad.cpu().numpy(), gp_ref) < GRAD_TOL
+    assert rel(q.grad.cpu().numpy(), gq_ref) < GRAD_TOL

@@ -711,3 +711,26 @@ def test_probe_shift_gradients_central_finite_differences(ext, w_ref, f1):
         fm = fun(psi - eps * hpsi, q - eps * hq, t, data, dref, geo, probe_shifts=s)
         an = cg.re_inner(gpsi, hpsi) + cg.re_inner(gq, hq)
         assert (fp - fm) / (2 * eps) == pytest.approx(an, rel=1e-7)
+
+
+def test_drivers_with_probe_shifts():
+    """The joint driver and the hierarchy carry probe shifts: zero shifts reproduce the
+    unshifted F history, F decreases monotonically with fractional shifts, and one level
+    without binning is the plain driver from psi = 1 and the initial probe."""
+    geo, psi, q, t, _, _ = _small_problem(n=32, P=64, K=2, noiseless=True, seed=8)
+    s = _rng(31).uniform(-2, 2, (2, geo.n_dist, 2))
+    sqrt_d = np.abs(holo.forward(psi, q, t, geo, probe_shifts=s))
+    sqrt_dref = np.abs(holo.reference_field(q, geo))
+    q0 = holo.initial_probe(sqrt_dref, geo)
+    plain = cg.reconstruct(np.ones_like(psi), q0, t, sqrt_d, sqrt_dref, geo, 3)
+    zero = cg.reconstruct(np.ones_like(psi), q0, t, sqrt_d, sqrt_dref, geo, 3,
+                          probe_shifts=np.zeros_like(s))
+    np.testing.assert_allclose(zero["hist"]["F"], plain["hist"]["F"], rtol=1e-12)
+    shifted = cg.reconstruct(np.ones_like(psi), q0, t, sqrt_d, sqrt_dref, geo, 4, probe_shifts=s)
+    F = np.array(shifted["hist"]["F"])
+    assert np.all(np.diff(F) <= 0.0) and F[-1] < F[0]
+    one = cg.reconstruct_hierarchical(sqrt_d, sqrt_dref, t, geo, [(1, 4)], probe_shifts=s)
+    np.testing.assert_allclose(one[0]["hist"]["F"], F, rtol=1e-13)
+    lev = cg.reconstruct_hierarchical(sqrt_d, sqrt_dref, t, geo, [(2, 2), (1, 2)], probe_shifts=s)
+    for r in lev:
+        assert np.all(np.diff(r["hist"]["F"]) <= 0.0)
