@@ -734,3 +734,40 @@ def test_drivers_with_probe_shifts():
     lev = cg.reconstruct_hierarchical(sqrt_d, sqrt_dref, t, geo, [(2, 2), (1, 2)], probe_shifts=s)
     for r in lev:
         assert np.all(np.diff(r["hist"]["F"]) <= 0.0)
+
+
+def test_dense_matrix_adjoint_and_gradient_with_probe_shifts():
+    """Brute force at P = 8, n = 4 (ext = 0) with fractional probe shifts: the columns of
+    L_kj and Q_kj built from unit vectors reproduce the fields, and the oracle gradients equal
+    2 A^H r, which pins D_{-zhat} S_{-s} C* as the exact adjoint of C S_s D_{zhat}."""
+    n, P = 4, 8
+    rng = _rng(41)
+    geo = _geo(n, P, ext=0.0, w_ref=0.0)
+    psi = _crandn(rng, 1, n, n)
+    q = _crandn(rng, P, P)
+    t = rng.uniform(-1, 1, (1, 4, 2))
+    s = rng.uniform(-1.5, 1.5, (1, 4, 2))
+    a = rng.uniform(0.1, 1.0, (1, 4, n, n))
+    F, gpsi, gq = holo.gradients(psi, q, t, a, None, geo, probe_shifts=s)
+    u = holo.forward(psi, q, t, geo, probe_shifts=s)
+    r = holo.amplitude_residual(u, a)
+    gpsi_ref = np.zeros(n * n, complex)
+    gq_ref = np.zeros(P * P, complex)
+    for j in range(4):
+        Lp = np.zeros((n * n, n * n), complex)
+        for c in range(n * n):
+            e = np.zeros(n * n, complex)
+            e[c] = 1.0
+            Lp[:, c] = holo.forward(e.reshape(1, n, n), q, t, geo, probe_shifts=s)[0, j].ravel()
+        Lq = np.zeros((n * n, P * P), complex)
+        for c in range(P * P):
+            e = np.zeros(P * P, complex)
+            e[c] = 1.0
+            Lq[:, c] = holo.forward(psi, e.reshape(P, P), t, geo, probe_shifts=s)[0, j].ravel()
+        np.testing.assert_allclose(Lp @ psi[0].ravel(), u[0, j].ravel(), atol=1e-12)
+        np.testing.assert_allclose(Lq @ q.ravel(), u[0, j].ravel(), atol=1e-12)
+        gpsi_ref += 2 * Lp.conj().T @ r[0, j].ravel()
+        gq_ref += 2 * Lq.conj().T @ r[0, j].ravel()
+    assert F == pytest.approx(np.sum((np.abs(u) - a) ** 2), rel=1e-13)
+    np.testing.assert_allclose(gpsi[0].ravel(), gpsi_ref, atol=1e-11)
+    np.testing.assert_allclose(gq.ravel(), gq_ref, atol=1e-11)
