@@ -5,8 +5,10 @@
  * with simultaneous probe retrieval of Nikitin et al., "X-ray nano-holotomography
  * reconstruction with simultaneous probe retrieval" (Sec. 2), and its gradients:
  *
- *   u_kj  = L_kj(psi_k) = C D_{zeta_j/m~_j^2}( D_{omega_j}(q) * M_{1/m~_j}(S_{t_kj} psi_k) )
- *                                                   (Eq. fwd_model_cone3 with the shifts of Eq. min1)
+ *   u_kj  = L_kj(psi_k) = C D_{zeta_j/m~_j^2}( D_{omega_j}(S_{s_kj} q) * M_{1/m~_j}(S_{t_kj} psi_k) )
+ *                                                   (Eq. fwd_model_cone3 with the shifts of Eq. min1;
+ *                                                    probe shifts s_kj are zero unless
+ *                                                    holo_set_probe_shifts sets them)
  *   F2    = sum_kj || |u_kj| - sqrt(d~_kj) ||^2 + w_ref || |C D_{zeta_0} q| - sqrt(d~^r) ||^2
  *                                                   (Eq. min1)
  *   grad_psi_k F2 = 2 sum_j L*_kj( u - sqrt(d~) u/|u| )        (Eq. gradpsi)
