@@ -48,3 +48,22 @@ def test_poisson_amplitude_mean_counts():
     amp = hs.poisson_amplitude(inten, 1e4, rng)
     assert abs(np.mean(amp ** 2) - 0.25) < 1e-3
     np.testing.assert_array_equal(hs.poisson_amplitude(inten, 0, rng), 0.5)
+
+
+def test_workloads_have_the_stated_shapes():
+    """psi side, padded grid, angles, distances, chunk, probe sigma (40 px at n = 128, scaled
+    with n) and Poisson counts of the synthetic workloads."""
+    w = hs.workloads()
+    expect = {"tiny": (128, 256, 8, 4, 8, 0.0, "ellipses"),
+              "medium": (512, 1024, 180, 4, 180, 1e4, "layers"),
+              "autograd": (1024, 2048, 90, 4, 90, 1e4, "layers"),
+              "large": (2048, 4096, 900, 4, 60, 1e4, "layers")}
+    for name, (n, P, K, J, chunk, counts, phantom) in expect.items():
+        x = w[name]
+        assert (x.n, x.P, x.n_angles, x.n_dist, x.chunk, x.counts, x.phantom) == \
+            (n, P, K, J, chunk, counts, phantom)
+        assert x.probe_sigma == 40.0 * n / 128
+    assert len({x.seed for x in w.values()}) == len(w)
+    g = hs.WORKLOAD_GEOMETRY
+    assert g["wavelength"] == 3.72e-11 and g["pixel"] == 10e-9
+    assert tuple(g["z"]) == (4.6e-4, 5.1e-4, 6.2e-4, 8.3e-4)
