@@ -51,19 +51,12 @@ class HoloError(RuntimeError):
 _lib = None
 
 
-def load():
-    """Load libholo.so once; raise if it has not been built."""
-    global _lib
-    if _lib is not None:
-        return _lib
-    if not os.path.exists(LIB_PATH):
-        raise RuntimeError(f"{LIB_PATH} is missing: build it with "
-                           "`python -c 'import __graft_entry__ as g; g.build()'`")
-    lib = ctypes.CDLL(LIB_PATH)
+def _signatures():
+    """ctypes parameter types of every status-returning entry point of include/holo.h."""
     P = ctypes.c_void_p
     I, LL, D = ctypes.c_int, ctypes.c_longlong, ctypes.c_double
     U = ctypes.c_uint
-    sigs = {
+    return {
         "holo_create": [ctypes.POINTER(HoloGeometry), P, ctypes.POINTER(P)],
         "holo_destroy": [P],
         "holo_set_shifts": [P, P],
@@ -91,13 +84,25 @@ def load():
         "holo_workspace_bytes": [P, ctypes.POINTER(LL)],
         "holo_launch_count": [P, ctypes.POINTER(LL)],
     }
+
+
+def load():
+    """Load libholo.so once; raise if it has not been built."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise RuntimeError(f"{LIB_PATH} is missing: build it with "
+                           "`python -c 'import __graft_entry__ as g; g.build()'`")
+    lib = ctypes.CDLL(LIB_PATH)
+    sigs = _signatures()
     for name, args in sigs.items():
         fn = getattr(lib, name)
         fn.argtypes = args
         fn.restype = ctypes.c_int
     lib.holo_status_string.argtypes = [ctypes.c_int]
     lib.holo_status_string.restype = ctypes.c_char_p
-    lib.holo_last_error.argtypes = [P]
+    lib.holo_last_error.argtypes = [ctypes.c_void_p]
     lib.holo_last_error.restype = ctypes.c_char_p
     _lib = lib
     return lib

@@ -74,3 +74,37 @@ def test_null_arguments(lib):
     assert lib.holo_gradient(None, 0, 1, None, None, None, None, 0) == 1
     assert lib.holo_dot(None, None, None, 0, ctypes.byref(d)) == 1
     assert lib.holo_step(None, None, None, 1.0, 0) == 1
+
+
+def _prototypes():
+    """{name: [parameter type strings]} of the function declarations in include/holo.h."""
+    src = open(os.path.join(ROOT, "include", "holo.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    out = {}
+    for ret, name, params in re.findall(r"([A-Za-z_][\w ]*?[\s\*]+)(holo_[a-z_0-9]+)\s*\(([^)]*)\)\s*;",
+                                        src):
+        ps = [p.strip() for p in params.split(",") if p.strip() and p.strip() != "void"]
+        out[name] = ps
+    return out
+
+
+def test_binding_prototypes_match_the_header():
+    """Every ctypes prototype of the binding has the header's parameter count, and pointer
+    parameters are bound as pointers, integers as integers and doubles as doubles."""
+    from paper_2407_20304_gb300 import _lib
+    protos = _prototypes()
+    assert sorted(protos) == sorted(_lib.EXPORTS)
+    sigs = _lib._signatures()
+    assert sorted(sigs) == sorted(set(protos) - {"holo_status_string", "holo_last_error"})
+    for name, params in protos.items():
+        if name not in sigs:
+            continue
+        args = sigs[name]
+        assert len(args) == len(params), (name, params, args)
+        for p, a in zip(params, args):
+            if "*" in p:
+                assert a is ctypes.c_void_p or issubclass(a, ctypes._Pointer), (name, p, a)
+            elif p.startswith("double"):
+                assert a is ctypes.c_double, (name, p, a)
+            elif p.startswith(("int", "long long", "unsigned", "holo_status")):
+                assert a in (ctypes.c_int, ctypes.c_longlong, ctypes.c_uint), (name, p, a)
