@@ -39,8 +39,6 @@ UNIT = "plane-grads/s"
 KERNEL_SOURCES = ("paper_2407_20304_gb300/csrc/holo_kernels.cuh",
                   "paper_2407_20304_gb300/csrc/holo_fft.cuh")
 FP32_LANES_PER_SM = 128
-SMS = 152
-MAX_SM_GHZ = 2.07
 
 
 def parse():
@@ -149,6 +147,30 @@ def algorithmic_costs(n, P, box, ref=True):
         out["pass_d"]["bytes"] += 8 * n * n
     out["pass_b"]["bytes"] += (24 if ref else 16) * n * n
     return out
+
+
+def survey_bytes(n, B):
+    """Algorithmic bytes per plane of the full-grid three-pass schedule (P = 2n): pass A
+    56 n^2, pass B 36 n^2, pass C 72 n^2 + 64 n^2 / B (G_j read-modify-write once per B
+    angles), total B_alg = 164 n^2 + 64 n^2 / B."""
+    a, b, c = 56.0 * n * n, 36.0 * n * n, 72.0 * n * n + 64.0 * n * n / B
+    return {"pass_a": a, "pass_b": b, "pass_c": c, "total": a + b + c}
+
+
+def fp32_units(dev, clocks):
+    """(SM count, SM clock in GHz, source) for the nominal FP32 peak: the SM count from the
+    device properties; the maximum SM clock from the clocks sampled during the timed region,
+    else from MEASURED_PEAKS.json, else 2.07 GHz."""
+    import torch
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    if clocks.get("sm_max_mhz"):
+        return sms, clocks["sm_max_mhz"] / 1e3, "max SM clock sampled by nvidia-smi"
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        mhz = json.load(open(path)).get("sm_max_mhz")
+        if mhz:
+            return sms, float(mhz) / 1e3, "sm_max_mhz of MEASURED_PEAKS.json"
+    return sms, 2.07, "nominal maximum SM clock"
 
 
 # ---------------------------------------------------------------- clocks
@@ -345,29 +367,40 @@ def run_ours(args, w, rank, world, local_rank):
     gbs = costs[top]["bytes"] / (top_ms / 1e3) / 1e9
     tfl = costs[top]["flops"] / (top_ms / 1e3) / 1e12
     clocks = clk.summary()
-    fp32_peak = SMS * FP32_LANES_PER_SM * 2 * MAX_SM_GHZ / 1e3
+    sms, sm_ghz, clock_src = fp32_units(dev, clocks)
+    fp32_peak = sms * FP32_LANES_PER_SM * 2 * sm_ghz / 1e3
     hbm_frac, alu_frac = gbs / pk["hbm_gbs"], tfl / fp32_peak
     traffic = None if args.probe_shifts else recorded_traffic(top, n, K * J)
+    # the same kernel and the whole step against the survey's full-grid three-pass byte model
+    sv = survey_bytes(n, K)
+    top_sv_frac = sv[top] * K * J / (top_ms / 1e3) / 1e9 / pk["hbm_gbs"] if top in sv else None
+    step_balg = sv["total"] * value / 1e9
+    common = {"kernel": top, "traffic": traffic,
+              "frac_survey_bytes": None if top_sv_frac is None else round(top_sv_frac, 4),
+              "step_balg_gbs": round(step_balg, 1),
+              "step_frac_balg": round(step_balg / pk["hbm_gbs"], 4),
+              "balg_bytes_per_plane": round(sv["total"]),
+              "flop_convention": "5 N log2 N per complex FFT of length N plus pointwise flops; "
+                                 "nominal, above a radix-16 FFT's real operation count",
+              "peak_source": f"FP32: {sms} SMs x {FP32_LANES_PER_SM} lanes x 2 x {sm_ghz:.3f} GHz "
+                             f"({clock_src}); HBM {pk['source']} {pk['hbm_gbs']} GB/s"}
     if alu_frac >= hbm_frac:
         roof = {"bound": "alu", "achieved": round(tfl, 2), "peak": round(fp32_peak, 1),
-                "unit": "TFLOP/s", "frac": round(alu_frac, 4), "traffic": traffic,
-                "kernel": top, "hbm_gbs": round(gbs, 1), "hbm_frac": round(hbm_frac, 4),
-                "peak_source": f"FP32: {SMS} SMs x {FP32_LANES_PER_SM} lanes x 2 x "
-                               f"{MAX_SM_GHZ} GHz; HBM {pk['source']} {pk['hbm_gbs']} GB/s"}
+                "unit": "TFLOP/s", "frac": round(alu_frac, 4), "hbm_gbs": round(gbs, 1),
+                "hbm_frac": round(hbm_frac, 4), **common}
     else:
         roof = {"bound": "hbm", "achieved": round(gbs, 1), "peak": pk["hbm_gbs"], "unit": "GB/s",
-                "frac": round(hbm_frac, 4), "traffic": traffic, "kernel": top,
-                "alu_tflops": round(tfl, 2), "alu_frac": round(alu_frac, 4),
-                "peak_source": f"HBM {pk['source']}"}
+                "frac": round(hbm_frac, 4), "alu_tflops": round(tfl, 2),
+                "alu_frac": round(alu_frac, 4), **common}
     per_pass = {p: {"ms_per_step": round(timing[p][0] / args.steps, 3),
                     "launches_per_step": timing[p][1] / args.steps}
                 for p in hs_timers()}
 
     unfused = None
     if not args.no_unfused:
-        shifts_np = shifts.astype(np.float64)
-        unfused = run_unfused_sample(w, torch.ones_like(psi), torch.from_numpy(q0).to(dev),
-                                     shifts_np, sqrt_d, sqrt_dref)
+        unfused = run_unfused_sample(w, psi, q, shifts.astype(np.float64), sqrt_d, sqrt_dref,
+                                     pk["hbm_gbs"])
+        unfused["fused_over_unfused"] = round(value / unfused["value"], 2)
     result = {
         "metric": METRIC + (" (F1 intensity functional)" if f1 else "")
                   + (" (probe shifts)" if args.probe_shifts else ""), "value": round(value, 1),
@@ -402,7 +435,11 @@ def hs_timers():
 
 def run_e2e(h, args, w, psi, q, sqrt_d, dev, planes, dist):
     """Same metric through holo_gradient_host: inputs copied from pinned host memory and
-    results read back inside the timed region, every step."""
+    results read back inside the timed region, every step.  Also recorded, to show which
+    resource binds the host call: the copies alone (the step's inputs host->device, then its
+    results device->host, on one stream), the device-only gradient of the same chunk, and the
+    fraction of the shorter of the two that the host call hides,
+    overlap = (copy + compute - host call) / min(copy, compute)."""
     import torch
     K, J, n, P = w.chunk, w.n_dist, w.n, w.P
     pin = dict(pin_memory=True)
@@ -414,6 +451,7 @@ def run_e2e(h, args, w, psi, q, sqrt_d, dev, planes, dist):
     q_h.copy_(q)
     gp_h = torch.empty((K, n, n), dtype=torch.complex64, **pin)
     gq_h = torch.empty((P, P), dtype=torch.complex64, **pin)
+    pinned = all(x.is_pinned() for x in (psi_h, d_h, q_h, gp_h, gq_h))
     a = [x.numpy() for x in (psi_h, d_h, q_h, gp_h, gq_h)]
     h.gradient_host(a[0], sqrt_d=a[1], q=a[2], grad_psi=a[3], grad_q=a[4])
     steps = max(3, min(args.steps, 10))
@@ -432,27 +470,71 @@ def run_e2e(h, args, w, psi, q, sqrt_d, dev, planes, dist):
         dt = float(t.item())
     h2d = psi_h.numel() * 8 + d_h.numel() * 4 + q_h.numel() * 8
     d2h = gp_h.numel() * 8 + gq_h.numel() * 8 + 16
+    # the parts: copies alone, device gradient alone
+    s = torch.cuda.Stream(dev)
+    bufs = [torch.empty_like(x, device=dev) for x in (psi_h, d_h, q_h)]
+    outs = [torch.empty_like(x, device=dev) for x in (gp_h, gq_h)]
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+    with torch.cuda.stream(s):
+        for rep in range(2):
+            ev[0].record(s)
+            for dst, src in zip(bufs, (psi_h, d_h, q_h)):
+                dst.copy_(src, non_blocking=True)
+            ev[1].record(s)
+            for dst, src in zip((gp_h, gq_h), outs):
+                dst.copy_(src, non_blocking=True)
+            ev[2].record(s)
+    torch.cuda.synchronize()
+    h2d_ms, d2h_ms = ev[0].elapsed_time(ev[1]), ev[1].elapsed_time(ev[2])
+    del bufs, outs
+    gpsi, gq = torch.empty_like(psi), torch.empty_like(q)
+    h.set_probe(q)
+    h.gradient(psi, grad_psi=gpsi, grad_q=gq)
+    torch.cuda.synchronize()
+    c0, c1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    st = torch.cuda.current_stream(dev)
+    c0.record(st)
+    for _ in range(3):
+        h.set_probe(q)
+        h.gradient(psi, grad_psi=gpsi, grad_q=gq, want_loss=False)
+    c1.record(st)
+    torch.cuda.synchronize()
+    compute_ms = c0.elapsed_time(c1) / 3
+    call_ms = dt / steps * 1e3
+    copy_ms = h2d_ms + d2h_ms
+    overlap = (copy_ms + compute_ms - call_ms) / min(copy_ms, compute_ms)
     return {"value": round(planes * steps / dt, 1), "unit": UNIT, "steps": steps,
             "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
-            "api": "holo_gradient_host (psi, data, q host -> grad_psi, grad_q, loss host)"}
+            "api": "holo_gradient_host (psi, data, q host -> grad_psi, grad_q, loss host)",
+            "host_buffers_pinned": pinned, "call_ms": round(call_ms, 2),
+            "h2d_ms": round(h2d_ms, 2), "d2h_ms": round(d2h_ms, 2),
+            "h2d_gbs": round(h2d / h2d_ms / 1e6, 1), "d2h_gbs": round(d2h / d2h_ms / 1e6, 1),
+            "compute_ms": round(compute_ms, 2), "overlap": round(overlap, 3)}
 
 
 # ---------------------------------------------------------------- unfused comparison
 
 class Unfused:
-    """The same F2 and gradients in the plain unfused per-plane form: cuFFT 2D transforms
-    (torch.fft) on the full P x P grid and separate elementwise kernels (resample by
-    separable gathers, chirp products, crop, residual, zero embedding, adjoint resample by
-    index_add_, G_j accumulation).  A timed comparison only; not part of the library."""
+    """The same F2 and gradients in the plain unfused form: cuFFT 2D transforms (torch.fft)
+    on the full P x P grid, batched over groups of planes of one distance, and separate
+    elementwise / gather / scatter kernels (resample by separable gathers, probe product,
+    chirp products, crop, residual, zero embedding, adjoint resample by scatter-adds, G_j
+    accumulation).  Taps and transfer functions are built once; the loss accumulates on the
+    device, so a whole evaluation issues no host synchronisation.  A timed comparison only;
+    not part of the library.
 
-    def __init__(self, n, P, geom, shifts, sqrt_d, sqrt_dref, ext=1.0, w_ref=1.0, device="cuda"):
+    `bytes` tallies, per evaluation, the bytes every issued operation reads and writes (its
+    input and output tensors; a 2-D FFT of P x P counted as two passes over the array, as
+    cuFFT takes at least two at these sizes): the unfused form's own algorithmic traffic."""
+
+    def __init__(self, n, P, geom, shifts, sqrt_d, sqrt_dref, ext=1.0, w_ref=1.0, device="cuda",
+                 group=8):
         import torch
         self.t = torch
-        self.n, self.P, self.ext, self.w_ref = n, P, ext, w_ref
+        self.n, self.P, self.ext, self.w_ref, self.group = n, P, ext, w_ref, group
         z = np.asarray(geom["z"], float)
         Z, lam, dx = geom["Z"], geom["wavelength"], geom["pixel"]
         mt = z / z[0]
-        self.mt = mt
         omega, zeta = (z - z[0]) / mt, z * (Z - z) / Z
         zhat = zeta / mt ** 2
         k = np.arange(P, dtype=float)
@@ -465,104 +547,169 @@ class Unfused:
         self.Hz = [H(d) for d in zhat]
         self.Ho = [H(d) for d in omega]
         self.Hr = H(zeta[0])
-        self.shifts = shifts
-        self.sqrt_d = sqrt_d            # [K][J][n][n] torch cuda
+        self.sqrt_d = sqrt_d            # [K][J][n][n] torch
         self.sqrt_dref = sqrt_dref
         self.dev = device
         self.J = len(z)
+        # bilinear taps of every plane, both axes: index (clamped) and weight (0 outside psi)
+        sh = torch.as_tensor(np.asarray(shifts, np.float64), device=device)       # [K][J][2]
+        X = torch.arange(P, device=device, dtype=torch.float64) - P // 2
+        mtt = torch.as_tensor(mt, device=device)
+        self.taps = []
+        for ax in (0, 1):
+            xi = mtt[None, :, None] * X[None, None, :] - sh[:, :, ax, None] + n // 2  # [K][J][P]
+            i0 = torch.floor(xi)
+            f = (xi - i0).float()
+            i0 = i0.long()
+            axis = []
+            for di, wt in ((0, 1 - f), (1, f)):
+                idx = i0 + di
+                m = (idx >= 0) & (idx < n)
+                axis.append((idx.clamp(0, n - 1), wt * m.float()))
+            self.taps.append(axis)
+        self.bytes = 0.0
 
-    def _taps(self, mtj, tj):
+    def _io(self, *ts):
+        self.bytes += sum(x.numel() * x.element_size() for x in ts)
+
+    def _fft(self, x, H):
+        """ifft2(fft2(x) * H) over the last two axes, batched over the first."""
         t = self.t
-        X = t.arange(self.P, device=self.dev, dtype=t.float64) - self.P // 2
-        xi = mtj * X - tj + self.n // 2
-        i0 = t.floor(xi)
-        f = (xi - i0).float()
-        i0 = i0.long()
-        return i0, f
+        X = t.fft.fft2(x)
+        self._io(x, X, x, X)
+        Y = X * H
+        self._io(X, H, Y)
+        y = t.fft.ifft2(Y)
+        self._io(Y, y, Y, y)
+        return y
 
-    def _axis(self, i0, f):
-        """taps (index, weight*mask) for the two neighbours along one axis."""
-        n = self.n
-        out = []
-        for di, w in ((0, 1 - f), (1, f)):
-            idx = i0 + di
-            m = (idx >= 0) & (idx < n)
-            out.append((idx.clamp(0, n - 1), w * m.float()))
-        return out
-
-    def resample(self, psi, ky, kx):
-        """ext + R0(psi - ext) on the P x P grid (separable bilinear)."""
+    def resample(self, psi, j, ks):
+        """ext + R0(psi - ext) on the P x P grid for angles ks at distance j (separable)."""
+        t = self.t
+        G, n, P = len(ks), self.n, self.P
         d = psi - self.ext
-        rows = sum(w[:, None] * d.index_select(0, idx) for idx, w in ky)          # [P][n]
-        full = sum(w[None, :] * rows.index_select(1, idx) for idx, w in kx)       # [P][P]
-        return full + self.ext
-
-    def resample_T(self, g, ky, kx):
-        t = self.t
-        n = self.n
-        cols = t.zeros((self.P, n), dtype=g.dtype, device=self.dev)
-        for idx, w in kx:
-            cols.index_add_(1, idx, g * w[None, :])
-        out = t.zeros((n, n), dtype=g.dtype, device=self.dev)
-        for idx, w in ky:
-            out.index_add_(0, idx, cols * w[:, None])
+        self._io(psi, d)
+        rows = None
+        for idx, w in self.taps[0]:
+            ii, ww = idx[ks, j], w[ks, j]                                             # [G][P]
+            g = t.gather(d, 1, ii[:, :, None].expand(G, P, n))
+            term = ww[:, :, None] * g
+            self._io(d, g, g, ww, term)
+            rows = term if rows is None else rows + term
+        self._io(rows, rows, rows)
+        full = None
+        for idx, w in self.taps[1]:
+            ii, ww = idx[ks, j], w[ks, j]
+            g = t.gather(rows, 2, ii[:, None, :].expand(G, P, P))
+            term = ww[:, None, :] * g
+            self._io(rows, g, g, ww, term)
+            full = term if full is None else full + term
+        out = full + self.ext
+        self._io(full, full, full, full, out)
         return out
+
+    def resample_T(self, g, j, ks):
+        """Exact transpose of R0 for angles ks at distance j: [G][P][P] -> [G][n][n]."""
+        t = self.t
+        G, n, P = len(ks), self.n, self.P
+        gr = t.view_as_real(g)                                                        # [G][P][P][2]
+        cols = t.zeros((G, P, n, 2), dtype=gr.dtype, device=self.dev)
+        for idx, w in self.taps[1]:
+            ii, ww = idx[ks, j], w[ks, j]
+            src = gr * ww[:, None, :, None]
+            cols.scatter_add_(2, ii[:, None, :, None].expand(G, P, P, 2), src)
+            self._io(gr, src, src, cols, cols)
+        out = t.zeros((G, n, n, 2), dtype=gr.dtype, device=self.dev)
+        for idx, w in self.taps[0]:
+            ii, ww = idx[ks, j], w[ks, j]
+            src = cols * ww[:, :, None, None]
+            out.scatter_add_(1, ii[:, :, None, None].expand(G, P, n, 2), src)
+            self._io(cols, src, src, out, out)
+        return t.view_as_complex(out)
 
     def gradient(self, psi, q):
+        """F2 (a device FP64 scalar), grad_psi and grad_q of all angles of psi."""
         t = self.t
-        n, P, J = self.n, self.P, self.J
+        n, P, J, K = self.n, self.P, self.J, psi.shape[0]
         lo = P // 2 - n // 2
-        fft2, ifft2 = t.fft.fft2, t.fft.ifft2
-        p = [q] + [ifft2(fft2(q) * self.Ho[j]) for j in range(1, J)]
+        c = slice(lo, lo + n)
+        p = [q] + [self._fft(q[None], self.Ho[j])[0] for j in range(1, J)]
         gpsi = t.zeros_like(psi)
         G = [t.zeros((P, P), dtype=t.complex64, device=self.dev) for _ in range(J)]
-        loss = 0.0
-        for k in range(psi.shape[0]):
-            for j in range(J):
-                ty, tx = float(self.shifts[k, j, 0]), float(self.shifts[k, j, 1])
-                ky = self._axis(*self._taps(float(self.mt[j]), ty))
-                kx = self._axis(*self._taps(float(self.mt[j]), tx))
-                Rpsi = self.resample(psi[k], ky, kx)
-                u = ifft2(fft2(p[j] * Rpsi) * self.Hz[j])[lo:lo + n, lo:lo + n]
-                a = self.sqrt_d[k, j]
+        loss = t.zeros((), dtype=t.float64, device=self.dev)
+        for j in range(J):
+            for k0 in range(0, K, self.group):
+                ks = list(range(k0, min(K, k0 + self.group)))
+                Rpsi = self.resample(psi[ks[0]:ks[-1] + 1], j, ks)
+                x = p[j][None] * Rpsi
+                self._io(Rpsi, p[j], x)
+                u = self._fft(x, self.Hz[j])[:, c, c]
+                a = self.sqrt_d[ks[0]:ks[-1] + 1, j]
                 mag = u.abs()
-                loss += float(((mag - a) ** 2).sum(dtype=t.float64))
-                r = u * t.where(mag > 0, 1 - a / mag, t.zeros_like(mag))
-                e = t.zeros((P, P), dtype=t.complex64, device=self.dev)
-                e[lo:lo + n, lo:lo + n] = r
-                v = ifft2(fft2(e) * t.conj(self.Hz[j]))
-                gpsi[k] += 2 * self.resample_T(t.conj(p[j]) * v, ky, kx)
-                G[j] += t.conj(Rpsi) * v
-        gq = sum(2 * ifft2(fft2(G[j]) * t.conj(self.Ho[j])) for j in range(J))
+                dd = mag - a
+                loss += (dd * dd).sum(dtype=t.float64)
+                s_ = t.where(mag > 0, 1 - a / t.where(mag > 0, mag, t.ones_like(mag)),
+                             t.zeros_like(mag))
+                r = u * s_
+                self._io(u, mag, mag, a, dd, dd, dd, mag, a, s_, u, s_, r)
+                e = t.zeros((len(ks), P, P), dtype=t.complex64, device=self.dev)
+                e[:, c, c] = r
+                self._io(e, r, r)
+                v = self._fft(e, t.conj(self.Hz[j]))
+                z = t.conj(p[j])[None] * v
+                self._io(v, p[j], z)
+                gpsi[ks[0]:ks[-1] + 1] += 2 * self.resample_T(z, j, ks)
+                self._io(gpsi[ks[0]:ks[-1] + 1], gpsi[ks[0]:ks[-1] + 1])
+                Gc = (t.conj(Rpsi) * v).sum(0)
+                G[j] += Gc
+                self._io(Rpsi, v, Gc, G[j], G[j])
+        gq = t.zeros((P, P), dtype=t.complex64, device=self.dev)
+        for j in range(J):
+            gq += 2 * self._fft(G[j][None], t.conj(self.Ho[j]))[0]
+            self._io(gq, gq)
         if self.w_ref:
-            b = ifft2(fft2(q) * self.Hr)[lo:lo + n, lo:lo + n]
+            b = self._fft(q[None], self.Hr)[0][c, c]
             mag = b.abs()
-            loss += self.w_ref * float(((mag - self.sqrt_dref) ** 2).sum(dtype=t.float64))
-            rr = b * t.where(mag > 0, 1 - self.sqrt_dref / mag, t.zeros_like(mag))
+            loss += self.w_ref * ((mag - self.sqrt_dref) ** 2).sum(dtype=t.float64)
+            rr = b * t.where(mag > 0, 1 - self.sqrt_dref / t.where(mag > 0, mag, t.ones_like(mag)),
+                             t.zeros_like(mag))
             e = t.zeros((P, P), dtype=t.complex64, device=self.dev)
-            e[lo:lo + n, lo:lo + n] = rr
-            gq = gq + 2 * self.w_ref * ifft2(fft2(e) * t.conj(self.Hr))
+            e[c, c] = rr
+            gq += 2 * self.w_ref * self._fft(e[None], t.conj(self.Hr))[0]
         return loss, gpsi, gq
 
 
-def run_unfused_sample(w, psi, q, shifts, sqrt_d, sqrt_dref, angles=4):
-    """Plane-gradients/s of the unfused cuFFT form on `angles` angles of the workload."""
+def run_unfused_sample(w, psi, q, shifts, sqrt_d, sqrt_dref, hbm_gbs):
+    """Plane-gradients/s of the unfused cuFFT form over the whole chunk (all angles and
+    distances of one evaluation, probe propagation and grad_q included), batched over groups
+    of 8 angles of one distance, with the loss read once at the end; one warm-up evaluation
+    on the first group first (cuFFT plans, allocator)."""
     import torch
     g = hs.WORKLOAD_GEOMETRY
-    u = Unfused(w.n, w.P, g, shifts[:angles], sqrt_d[:angles], sqrt_dref)
-    u.gradient(psi[:1], q)          # warm-up (plans, allocator)
+    K = psi.shape[0]
+    u = Unfused(w.n, w.P, g, shifts, sqrt_d, sqrt_dref)
+    loss, _, _ = u.gradient(psi[:u.group], q)
+    float(loss)
     torch.cuda.synchronize()
+    u.bytes = 0.0
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record()
-    u.gradient(psi[:angles], q)
+    loss, gp, gq = u.gradient(psi, q)
     e1.record()
     torch.cuda.synchronize()
+    float(loss)
     ms = e0.elapsed_time(e1)
-    return {"value": round(angles * w.n_dist / (ms / 1e3), 1), "unit": UNIT,
-            "sample": f"{angles} angles x {w.n_dist} distances, one gradient evaluation incl. "
-                      f"probe propagation and grad_q",
-            "impl": "torch.fft (cuFFT) 2D transforms on the P x P grid + separate elementwise "
-                    "kernels, FP32"}
+    planes = K * w.n_dist
+    gbs = u.bytes / (ms / 1e3) / 1e9
+    del gp, gq
+    return {"value": round(planes / (ms / 1e3), 1), "unit": UNIT,
+            "sample": f"one gradient evaluation of the whole {K}-angle x {w.n_dist}-distance "
+                      f"chunk ({planes} planes) incl. probe propagation and grad_q",
+            "bytes_per_plane": round(u.bytes / planes),
+            "hbm_gbs": round(gbs, 1), "hbm_frac": round(gbs / hbm_gbs, 4),
+            "impl": "torch.fft (cuFFT) 2D transforms on the P x P grid batched over 8 planes of "
+                    "one distance + separate elementwise / gather / scatter kernels, FP32, loss "
+                    "on the device"}
 
 
 # ---------------------------------------------------------------- oracle (CPU)
@@ -618,44 +765,86 @@ def cpu_baseline(w, budget_s):
                       f"scipy.fft on all host cores"}, err
 
 
-def precision_report(w):
-    """Part of the CPU leg: relative L2 error of the FP32 GPU loss and gradients against the
-    FP64 oracle on one angle (all distances, reference term included) of the workload at the
-    start point psi = 1, q = the true probe: the oracle's own noiseless data, inputs rounded
-    to the GPU's types and given to both sides.  Also returns the oracle's time for that
-    evaluation."""
+def _gpu_vs_oracle(psi, q, shifts, sqrt_d, sqrt_dref, geo):
+    """Relative L2 errors of the GPU loss and gradients against the FP64 oracle at one
+    evaluation point (inputs already rounded to the GPU's types), and the oracle's time."""
     import torch
     from oracle import holo as oh
     from paper_2407_20304_gb300 import Holo
-    psi0, q, shifts, sqrt_d, geo = oracle_setup(w)
-    q = q.astype(np.complex64).astype(np.complex128)
-    sqrt_d = sqrt_d.astype(np.float32).astype(np.float64)
-    sqrt_dref = np.abs(oh.reference_field(q, geo)).astype(np.float32).astype(np.float64)
-    J, n, P = geo.n_dist, geo.n, geo.P
+    K, J, n, P = psi.shape[0], geo.n_dist, geo.n, geo.P
     t0 = time.perf_counter()
-    F, gp_ref, gq_ref = oh.gradients(psi0[None], q, shifts, sqrt_d[None], sqrt_dref, geo)
+    F, gp_ref, gq_ref = oh.gradients(psi, q, shifts, sqrt_d, sqrt_dref, geo)
     t_oracle = time.perf_counter() - t0
-    g = hs.WORKLOAD_GEOMETRY
-    h = Holo(n, 1, J, g["wavelength"], g["pixel"], g["Z"], g["z"][:J], pad=P)
+    h = Holo(n, K, J, geo.wavelength, geo.pixel, geo.Z, geo.z, pad=P)
     dev = torch.device("cuda", torch.cuda.current_device())
     h.set_shifts(shifts.astype(np.float32))
-    d_sd = torch.tensor(sqrt_d[None], dtype=torch.float32, device=dev)
-    d_ref = torch.tensor(sqrt_dref, dtype=torch.float32, device=dev)
-    h.set_data(d_sd, d_ref)
+    h.set_data(torch.tensor(sqrt_d, dtype=torch.float32, device=dev),
+               torch.tensor(sqrt_dref, dtype=torch.float32, device=dev))
     h.set_probe(torch.tensor(q, dtype=torch.complex64, device=dev))
-    loss, gp, gq = h.gradient(torch.tensor(psi0[None], dtype=torch.complex64, device=dev))
+    loss, gp, gq = h.gradient(torch.tensor(psi, dtype=torch.complex64, device=dev))
     torch.cuda.synchronize()
     h.close()
 
     def rel(a, b):
         return float(np.linalg.norm(a - b) / np.linalg.norm(b))
 
-    return {"loss": abs(loss - F) / abs(F), "grad_psi": rel(gp.cpu().numpy(), gp_ref[0]),
-            "grad_q": rel(gq.cpu().numpy(), gq_ref), "oracle_s": round(t_oracle, 2),
-            "sample": f"angle 0 x {J} distances of the {w.name} workload (n={n}, P={P}) with the "
-                      "reference term, at psi = 1 and the true probe, oracle-made noiseless "
-                      "data; relative L2 against the FP64 oracle (targets: loss 1e-5, "
-                      "gradients 1e-4)"}
+    return {"loss": abs(loss - F) / abs(F), "grad_psi": rel(gp.cpu().numpy(), gp_ref),
+            "grad_q": rel(gq.cpu().numpy(), gq_ref), "oracle_s": round(t_oracle, 2)}
+
+
+def precision_report(w):
+    """Part of the CPU leg: relative L2 error of the FP32 GPU loss and gradients against the
+    FP64 oracle (targets: loss 1e-5, gradients 1e-4), inputs rounded to the GPU's types and
+    given to both sides, at three evaluation points:
+      start:    angle 0 x all distances of the workload at psi = 1 and the true probe, with
+                the oracle's noiseless data (the object field R0(psi - 1) is zero there);
+      object:   the same plane set at the true object times 1 + 0.05 complex noise and the
+                perturbed probe, Poisson data at the workload's counts;
+      iterated: 2 angles x 4 distances of the tiny workload (psi 128^2 on 256^2) after 5
+                iterations of the oracle's CG driver from psi = 1 and the perturbed probe."""
+    from oracle import cg as ocg
+    from oracle import holo as oh
+
+    def c64(x):
+        return np.asarray(x).astype(np.complex64).astype(np.complex128)
+
+    def f32(x):
+        return np.asarray(x).astype(np.float32).astype(np.float64)
+
+    psi0, q, shifts, sqrt_d, geo = oracle_setup(w)
+    q = c64(q)
+    sqrt_dref = np.abs(oh.reference_field(q, geo))
+    out = {"start": _gpu_vs_oracle(psi0[None], q, shifts, f32(sqrt_d)[None], f32(sqrt_dref), geo)}
+    # the perturbed true object, Poisson data
+    rng = hs.rng_for(w.seed, 101)
+    psi_true = hs.object_stack(w, range(1), rng)
+    q_true = hs.striped_probe(w.P, w.probe_sigma, rng)
+    d = np.abs(oh.forward(psi_true, q_true, shifts, geo))
+    d = hs.poisson_amplitude(d ** 2, w.counts, rng)
+    dr = hs.poisson_amplitude(np.abs(oh.reference_field(q_true, geo)) ** 2, w.counts, rng)
+    psi_o = c64(hs.perturbed_probe(psi_true, rng, 0.05))
+    q_o = c64(hs.perturbed_probe(q_true, rng))
+    out["object"] = _gpu_vs_oracle(psi_o, q_o, shifts, f32(d), f32(dr), geo)
+    del psi_true, q_true, d, psi_o
+    # the tiny workload after 5 oracle CG iterations
+    tw = hs.workloads()["tiny"]
+    g = hs.WORKLOAD_GEOMETRY
+    rng = hs.rng_for(tw.seed, 102)
+    geo_t = oh.Geometry(g["wavelength"], g["pixel"], g["Z"], tuple(g["z"][:tw.n_dist]), tw.n, tw.P)
+    psi_true = hs.object_stack(tw, range(2), rng)
+    q_true = hs.striped_probe(tw.P, tw.probe_sigma, rng)
+    t_t = hs.sample_shifts(2, tw.n_dist, rng).astype(np.float32).astype(np.float64)
+    d = f32(np.abs(oh.forward(psi_true, q_true, t_t, geo_t)))
+    dr = f32(np.abs(oh.reference_field(q_true, geo_t)))
+    r = ocg.reconstruct(np.ones((2, tw.n, tw.n), np.complex128), c64(hs.perturbed_probe(q_true, rng)),
+                        t_t, d, dr, geo_t, 5, max_halvings=8)
+    out["iterated"] = _gpu_vs_oracle(c64(r["psi"]), c64(r["q"]), t_t, d, dr, geo_t)
+    out["sample"] = (f"start / object: angle 0 x {geo.n_dist} distances of the {w.name} workload "
+                     f"(n={geo.n}, P={geo.P}) with the reference term; iterated: 2 angles x "
+                     f"{tw.n_dist} distances of the tiny workload (n={tw.n}, P={tw.P}) after 5 "
+                     "oracle CG iterations; relative L2 against the FP64 oracle (targets: loss "
+                     "1e-5, gradients 1e-4)")
+    return out
 
 
 def run_reference(args, w):

@@ -257,14 +257,16 @@ holo_status holo_get_timing(holo_ctx* ctx, double* ms, long long* launches);
 
 /* Re <a, b> like holo_dot, for callers that cannot allocate device memory: no context is
  * needed and nothing is allocated (the paper has no counterpart; this is an interface
- * for embedders).  a, b: dev complex64 [n_c64]; re_out: host, written after the call
- * synchronises `stream` (a cudaStream_t, NULL for the legacy default stream).  The
- * per-block partial sums live in a fixed 512 KiB device array inside the library (held
- * on every GPU that loads it until the process exits), so n_c64 may be at most
- * 268435456 (2^28); longer inputs return HOLO_ERR_UNSUPPORTED before any device work.
- * The first call on a device looks up that array's device address (with the device
- * current); make it before any stream capture.  All calls share the array: calls that
- * overlap on the GPU race. */
+ * for embedders).  a, b: dev complex64 [n_c64] on the CURRENT device (device or managed
+ * memory; anything else, e.g. host memory or another device's memory, returns HOLO_ERR_ARG
+ * before any device work); re_out: host, written after the call synchronises `stream` (a
+ * cudaStream_t of the current device, NULL for the legacy default stream).  The per-block
+ * partial sums live in a fixed 512 KiB device array inside the library (held on every GPU
+ * that loads it until the process exits), so n_c64 may be at most 268435456 (2^28);
+ * longer inputs return HOLO_ERR_UNSUPPORTED before any device work.  The first call on a
+ * device looks up that array's device address (with the device current); make it before
+ * any stream capture.  All calls share the array: calls that overlap on the GPU race.
+ * There is no context to hold error text: HOLO_ERR_CUDA comes without details. */
 holo_status holo_dot_noalloc(const void* a, const void* b, long long n_c64, double* re_out,
                              void* stream);
 

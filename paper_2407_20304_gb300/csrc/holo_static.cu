@@ -62,6 +62,17 @@ __global__ void k_dot_final(const double* __restrict__ part, int count, double* 
   if (threadIdx.x == 0) *out = t;
 }
 
+// True when p is device (or managed) memory that kernels on device `dev` may read.
+bool on_device(const void* p, int dev) {
+  cudaPointerAttributes at;
+  if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  if (at.type == cudaMemoryTypeManaged) return true;
+  return at.type == cudaMemoryTypeDevice && at.device == dev;
+}
+
 // Device address of g_dot_scratch on the current device (set up once per device).
 holo_status scratch_for_current_device(double** out) {
   int dev = -1;
@@ -88,6 +99,14 @@ extern "C" holo_status holo_dot_noalloc(const void* a, const void* b, long long 
                                         double* re_out, void* stream) {
   if (!a || !b || !re_out || n_c64 < 0) return HOLO_ERR_ARG;
   if (n_c64 > (long long)kScratchDoubles * kElemsPerBlock) return HOLO_ERR_UNSUPPORTED;
+  // both inputs must live on the current device, whose copy of the scratch array the kernels
+  // use (checked before any device work)
+  int dev = -1;
+  if (cudaGetDevice(&dev) != cudaSuccess) {
+    cudaGetLastError();
+    return HOLO_ERR_CUDA;
+  }
+  if (!on_device(a, dev) || !on_device(b, dev)) return HOLO_ERR_ARG;
   double* scratch = nullptr;
   holo_status st = scratch_for_current_device(&scratch);
   if (st != HOLO_OK) return st;

@@ -58,9 +58,15 @@ def dot_noalloc(a, b, stream=None):
         raise ValueError(f"dot_noalloc handles at most {_lib.NOALLOC_MAX_ELEMENTS} elements")
     pa = _ptr(a, torch.complex64, None, "a")
     pb = _ptr(b, torch.complex64, None, "b")
-    s = stream if stream is not None else torch.cuda.current_stream(a.device)
-    out = ct.c_double(0.0)
-    st = lib.holo_dot_noalloc(pa, pb, a.numel(), ct.byref(out), ct.c_void_p(s.cuda_stream))
+    if b.device != a.device:
+        raise ValueError(f"a and b must be on one device, got {a.device} and {b.device}")
+    # the library uses the scratch array of the current device: make a's device current
+    with torch.cuda.device(a.device):
+        s = stream if stream is not None else torch.cuda.current_stream(a.device)
+        if s.device != a.device:
+            raise ValueError(f"stream of {s.device} for tensors on {a.device}")
+        out = ct.c_double(0.0)
+        st = lib.holo_dot_noalloc(pa, pb, a.numel(), ct.byref(out), ct.c_void_p(s.cuda_stream))
     _check(lib, None, st, "holo_dot_noalloc")
     return out.value
 

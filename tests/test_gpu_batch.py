@@ -1,9 +1,12 @@
 """Batched evaluation of uneven reconstructions: the captured graph (any schedule) gives
-exactly the per-instance loop's results, and those match the FP64 oracle."""
+exactly the per-instance loop's results, and those match the FP64 oracle.  The instances mix
+sides 32 .. 2048 (P = 64 .. 4096, including the radix-3 lengths 96 and 768) and evaluation
+points: psi = 1 and the perturbed true object (where the object field is not zero)."""
 
 import numpy as np
 import pytest
 
+import evalpoints as ep
 import holo_synth as hs
 from oracle import holo as oh
 
@@ -25,7 +28,8 @@ def batch():
     from paper_2407_20304_gb300 import Holo
     from paper_2407_20304_gb300.batch import HoloBatch, Instance
     rng = hs.rng_for(hs.SEED_BASE + 3000, 0)
-    specs = [(32, 3, 2), (48, 2, 4), (64, 5, 1), (32, 4, 3), (48, 3, 2), (64, 2, 4)]
+    specs = [(32, 3, 2), (48, 2, 4), (64, 5, 1), (32, 4, 3), (48, 3, 2), (64, 2, 4),
+             (384, 1, 2), (2048, 1, 1)]
     insts, refs = [], []
     for i, (n, K, J) in enumerate(specs):
         P = pad_of(n)
@@ -37,7 +41,8 @@ def batch():
         t = hs.sample_shifts(K, J, rng).astype(np.float32).astype(np.float64)
         sqrt_d = np.abs(oh.forward(psi_true, q_true, t, geo)).astype(np.float32)
         sqrt_dref = np.abs(oh.reference_field(q_true, geo)).astype(np.float32)
-        psi0 = np.ones((K, n, n), np.complex64)
+        psi0 = (np.ones((K, n, n), np.complex128) if i % 2 == 0 and n < 256 else
+                ep.object_point(psi_true, rng)).astype(np.complex64)
         q0 = hs.perturbed_probe(q_true, rng).astype(np.complex64)
         h = Holo(n, K, J, G["wavelength"], G["pixel"], G["Z"], z, pad=P, chunk=2)
         h.set_shifts(t.astype(np.float32))

@@ -5,6 +5,10 @@ gradients grad_psi_k of four sampled angles are compared with the oracle's per-p
 (grad_psi_k depends only on the planes of angle k).  The loss and grad_q, which sum over
 every plane of a chunk, are compared on a 4-angle chunk of the same problem.  Relative L2
 errors are printed (the precision report of FP32 wavefields with FP64 reductions).
+
+Two evaluation points: the start point psi = 1 (where the object field R0(psi - 1) is zero)
+and the layered phantom times a small perturbation (where pass A's gather of the object at
+P = 4096 and the conj(w) v term of grad_q are exercised).
 """
 
 import time
@@ -12,6 +16,7 @@ import time
 import numpy as np
 import pytest
 
+import evalpoints as ep
 import holo_synth as hs
 from oracle import holo as oh
 
@@ -51,16 +56,22 @@ def problem():
         sqrt_d[k] = amp[s]
     sqrt_dref = hs.poisson_amplitude(np.abs(oh.reference_field(q_true, geo)) ** 2, w.counts,
                                      rng).astype(np.float32)
-    psi0 = np.ones((K, n, n), np.complex64)
-    # oracle per-plane terms at the start point psi = 1, q = q0
-    terms = {}
+    psis = {"start": np.ones((K, n, n), np.complex64),
+            "object": psi_true.astype(np.complex64)}
     for k in SAMPLED:
-        for j in range(J):
-            terms[(k, j)] = oh.plane_gradient(psi0[k].astype(np.complex128), q0, t[k][j],
-                                              sqrt_d[k, j].astype(np.float64), geo, j)
+        psis["object"][k] = ep.object_point(psi_true[k], rng)
+    del psi_true
+    # oracle per-plane terms of the sampled angles at both points (q = q0)
+    terms = {}
+    for point, psi in psis.items():
+        for k in SAMPLED:
+            for j in range(J):
+                terms[(point, k, j)] = oh.plane_gradient(
+                    psi[k].astype(np.complex128), q0, t[k][j], sqrt_d[k, j].astype(np.float64),
+                    geo, j)
     print(f"\noracle set-up {time.time() - t0:.0f} s")
     return dict(w=w, g=g, n=n, P=P, K=K, J=J, t=t, q0=q0, sqrt_d=sqrt_d, sqrt_dref=sqrt_dref,
-                psi0=psi0, terms=terms, geo=geo)
+                psis=psis, terms=terms, geo=geo)
 
 
 def _holo(pr, K, sqrt_d):
@@ -72,32 +83,34 @@ def _holo(pr, K, sqrt_d):
     return h
 
 
-def test_grad_psi_of_sampled_angles_in_the_benchmark_chunk(problem):
+@pytest.mark.parametrize("point", ["start", "object"])
+def test_grad_psi_of_sampled_angles_in_the_benchmark_chunk(problem, point):
     pr = problem
     h = _holo(pr, pr["K"], pr["sqrt_d"])
     h.set_shifts(pr["t"].astype(np.float32))
-    _, gp, _ = h.gradient(torch.from_numpy(pr["psi0"]).cuda())
+    _, gp, _ = h.gradient(torch.from_numpy(pr["psis"][point]).cuda())
     gp = gp.cpu().numpy()
     for k in SAMPLED:
-        ref = sum(pr["terms"][(k, j)][1] for j in range(pr["J"]))
+        ref = sum(pr["terms"][(point, k, j)][1] for j in range(pr["J"]))
         e = rel(gp[k].astype(np.complex128), ref)
-        print(f"angle {k}: grad_psi relative L2 error {e:.2e}")
+        print(f"{point}, angle {k}: grad_psi relative L2 error {e:.2e}")
         assert e < GRAD_TOL
     h.close()
 
 
-def test_loss_and_grad_q_on_a_four_angle_chunk(problem):
+@pytest.mark.parametrize("point", ["start", "object"])
+def test_loss_and_grad_q_on_a_four_angle_chunk(problem, point):
     pr = problem
     ks = list(SAMPLED)
     h = _holo(pr, 4, np.ascontiguousarray(pr["sqrt_d"][ks]))
     h.set_shifts(pr["t"][ks].astype(np.float32))
-    loss, gp, gq = h.gradient(torch.from_numpy(np.ascontiguousarray(pr["psi0"][ks])).cuda())
+    loss, gp, gq = h.gradient(torch.from_numpy(np.ascontiguousarray(pr["psis"][point][ks])).cuda())
     geo, J = pr["geo"], pr["J"]
     d = oh.derived_geometry(geo.z, geo.Z)
-    F = sum(pr["terms"][(k, j)][0] for k in ks for j in range(J))
+    F = sum(pr["terms"][(point, k, j)][0] for k in ks for j in range(J))
     gq_ref = np.zeros((pr["P"], pr["P"]), np.complex128)
     for j in range(J):
-        G = sum(pr["terms"][(k, j)][2] for k in ks)
+        G = sum(pr["terms"][(point, k, j)][2] for k in ks)
         gq_ref += 2 * oh.propagate(G, -d["omega"][j], geo.wavelength, geo.pixel)
     uref = oh.reference_field(pr["q0"], geo)
     aref = pr["sqrt_dref"].astype(np.float64)
@@ -107,8 +120,8 @@ def test_loss_and_grad_q_on_a_four_angle_chunk(problem):
     e_l = abs(loss - F) / F
     e_q = rel(gq.cpu().numpy().astype(np.complex128), gq_ref)
     e_p = max(rel(gp.cpu().numpy()[s].astype(np.complex128),
-                  sum(pr["terms"][(k, j)][1] for j in range(J))) for s, k in enumerate(ks))
-    print(f"4-angle chunk: loss {e_l:.2e}, grad_q {e_q:.2e}, grad_psi (max over angles) {e_p:.2e}")
+                  sum(pr["terms"][(point, k, j)][1] for j in range(J))) for s, k in enumerate(ks))
+    print(f"{point}, 4-angle chunk: loss {e_l:.2e}, grad_q {e_q:.2e}, grad_psi (max over angles) {e_p:.2e}")
     assert e_l < LOSS_TOL and e_q < GRAD_TOL and e_p < GRAD_TOL
     h.close()
 
@@ -124,7 +137,7 @@ def test_intensity_functional_on_a_four_angle_chunk(problem):
     h.set_functional("intensity")
     h.set_data(torch.from_numpy(d.astype(np.float32)).cuda(), torch.from_numpy(dref.astype(np.float32)).cuda())
     h.set_shifts(pr["t"][ks].astype(np.float32))
-    psi = np.ascontiguousarray(pr["psi0"][ks])
+    psi = np.ascontiguousarray(pr["psis"]["object"][ks])
     loss, gp, gq = h.gradient(torch.from_numpy(psi).cuda())
     F, gp_ref, gq_ref = oh.gradients_f1(psi.astype(np.complex128), pr["q0"], pr["t"][ks],
                                         d.astype(np.float32).astype(np.float64),

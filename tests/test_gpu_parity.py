@@ -8,6 +8,7 @@ Inputs come from holo_synth; data are made by the oracle, never by the CUDA path
 import numpy as np
 import pytest
 
+import evalpoints as ep
 import holo_synth as hs
 from oracle import holo as oh
 
@@ -34,7 +35,12 @@ def dev(a, dtype):
     return torch.tensor(np.ascontiguousarray(a), dtype=dtype, device="cuda")
 
 
-def make_problem(n, P, K, J=4, ext=1.0, w_ref=1.0, seed=0, noiseless=False, z=None):
+def make_problem(n, P, K, J=4, ext=1.0, w_ref=1.0, seed=0, noiseless=False, z=None,
+                 point="start"):
+    """A seeded problem with oracle-made data.  point: "start" (psi = 1 in production mode
+    ext = 1, a random transmittance for ext = 0, and the perturbed probe), "iterated" (after 5
+    iterations of the oracle's CG driver from the start point) or "object" (the true object
+    times a small perturbation, with the perturbed probe)."""
     rng = hs.rng_for(hs.SEED_BASE + 7, seed)
     z = tuple(z or G["z"][:J])
     geo = oh.Geometry(G["wavelength"], G["pixel"], G["Z"], z, n, P, ext=ext, w_ref=w_ref)
@@ -55,6 +61,10 @@ def make_problem(n, P, K, J=4, ext=1.0, w_ref=1.0, seed=0, noiseless=False, z=No
     q0 = q0.astype(np.complex64).astype(np.complex128)
     sqrt_d = sqrt_d.astype(np.float32).astype(np.float64)
     sqrt_dref = sqrt_dref.astype(np.float32).astype(np.float64)
+    if point == "iterated":
+        psi0, q0 = ep.iterated_point(psi0, q0, t, sqrt_d, sqrt_dref, geo)
+    elif point == "object":
+        psi0 = ep.object_point(psi_true, rng)
     return dict(geo=geo, psi=psi0, q=q0, t=t, sqrt_d=sqrt_d, sqrt_dref=sqrt_dref,
                 psi_true=psi_true, q_true=q_true)
 
@@ -129,14 +139,60 @@ def test_gradient_matches_oracle(n, P, K, J, ext, w_ref):
     assert rel(gq.cpu().numpy(), gq_ref) < GRAD_TOL
 
 
-@pytest.mark.parametrize("n,P,K,J,ext,w_ref", [
-    (16, 32, 2, 4, 1.0, 1.0), (64, 128, 3, 4, 1.0, 1.0), (48, 96, 2, 3, 0.0, 0.0),
-    (128, 256, 2, 4, 1.0, 1.0), (256, 512, 2, 2, 1.0, 0.0),
+# Production mode (ext = 1) away from psi = 1, where the object field w = R0(psi - 1) is not
+# zero: every line-length class, the row passes' 3-blocks-per-SM forms (P = 768 .. 4096), the
+# plane-split (n <= 1024) and whole-round (n = 1826, 2048) forms of pass B, and the
+# group-local last exchange of P = 4096.  Small problems are evaluated after 5 oracle CG
+# iterations, large ones at the perturbed true object.
+AWAY = [(16, 32, 2, 4, "iterated"), (32, 64, 2, 4, "iterated"), (64, 128, 2, 4, "iterated"),
+        (128, 256, 2, 4, "iterated"), (256, 512, 1, 4, "iterated"), (24, 48, 2, 4, "iterated"),
+        (48, 96, 2, 4, "iterated"), (96, 192, 2, 3, "iterated"), (192, 384, 1, 4, "iterated"),
+        (384, 768, 2, 4, "object"), (512, 1024, 2, 4, "object"), (700, 1536, 1, 2, "object"),
+        (1024, 2048, 1, 4, "object"), (1826, 2048, 2, 2, "object"),
+        (1536, 3072, 1, 2, "object"), (2048, 4096, 1, 2, "object")]
+
+
+@pytest.mark.parametrize("n,P,K,J,point", AWAY)
+def test_gradient_away_from_start_matches_oracle(n, P, K, J, point):
+    pr = make_problem(n, P, K, J=J, seed=11 * n + J, point=point)
+    # the object field is far from zero at this point
+    assert np.abs(pr["psi"] - 1).mean() > 1e-2
+    h = make_holo(pr)
+    psi = dev(pr["psi"], torch.complex64)
+    loss_f = h.forward(psi)
+    loss, gp, gq = h.gradient(psi)
+    F, gp_ref, gq_ref = oh.gradients(pr["psi"], pr["q"], pr["t"], pr["sqrt_d"], pr["sqrt_dref"],
+                                     pr["geo"])
+    e = (abs(loss - F) / F, rel(gp.cpu().numpy(), gp_ref), rel(gq.cpu().numpy(), gq_ref))
+    print(f"n={n} P={P} {point}: loss {e[0]:.2e}, grad_psi {e[1]:.2e}, grad_q {e[2]:.2e}")
+    assert abs(loss_f - F) / F < LOSS_TOL
+    assert e[0] < LOSS_TOL and e[1] < GRAD_TOL and e[2] < GRAD_TOL
+
+
+@pytest.mark.parametrize("n,P,K,point", [(64, 128, 2, "iterated"), (96, 192, 2, "iterated"),
+                                         (1024, 2048, 1, "object")])
+def test_forward_fields_away_from_start(n, P, K, point):
+    pr = make_problem(n, P, K, seed=13 * n, point=point)
+    h = make_holo(pr)
+    u = torch.empty((K, 4, n, n), dtype=torch.complex64, device="cuda")
+    loss = h.forward(dev(pr["psi"], torch.complex64), u_out=u)
+    u_ref = oh.forward(pr["psi"], pr["q"], pr["t"], pr["geo"])
+    F_ref = oh.functional(pr["psi"], pr["q"], pr["t"], pr["sqrt_d"], pr["sqrt_dref"], pr["geo"])
+    assert rel(u.cpu().numpy(), u_ref) < FIELD_TOL
+    assert abs(loss - F_ref) / F_ref < LOSS_TOL
+
+
+@pytest.mark.parametrize("n,P,K,J,ext,w_ref,point", [
+    (16, 32, 2, 4, 1.0, 1.0, "start"), (64, 128, 3, 4, 1.0, 1.0, "start"),
+    (48, 96, 2, 3, 0.0, 0.0, "start"),
+    (64, 128, 2, 4, 1.0, 1.0, "object"), (384, 768, 1, 4, 1.0, 1.0, "object"),
+    (1024, 2048, 1, 2, 1.0, 1.0, "object"),
+    (128, 256, 2, 4, 1.0, 1.0, "start"), (256, 512, 2, 2, 1.0, 0.0, "start"),
 ])
-def test_intensity_functional_matches_oracle(n, P, K, J, ext, w_ref):
+def test_intensity_functional_matches_oracle(n, P, K, J, ext, w_ref, point):
     """F1 (Eq. min2): intensities as data, r = 2 (|u|^2 - d) u; forward loss and gradients
     against the oracle's functional_f1 / gradients_f1."""
-    pr = make_problem(n, P, K, J=J, ext=ext, w_ref=w_ref, seed=5 * n + J)
+    pr = make_problem(n, P, K, J=J, ext=ext, w_ref=w_ref, seed=5 * n + J, point=point)
     d = pr["sqrt_d"] ** 2
     dref = pr["sqrt_dref"] ** 2 if w_ref else None
     h = make_holo(pr)

@@ -9,6 +9,7 @@ Data are made by the oracle, never by the CUDA path.
 import numpy as np
 import pytest
 
+import evalpoints as ep
 import holo_synth as hs
 from oracle import holo as oh
 
@@ -35,7 +36,9 @@ def dev(a, dtype):
     return torch.tensor(np.ascontiguousarray(a), dtype=dtype, device="cuda")
 
 
-def make_problem(n, P, K, J=4, ext=1.0, w_ref=1.0, seed=0, smax=2.0):
+def make_problem(n, P, K, J=4, ext=1.0, w_ref=1.0, seed=0, smax=2.0, point="start"):
+    """point: "start" (psi = 1 for ext = 1), "iterated" (5 oracle CG iterations from the
+    start point, probe shifts included) or "object" (the perturbed true object)."""
     rng = hs.rng_for(hs.SEED_BASE + 11, seed)
     geo = oh.Geometry(G["wavelength"], G["pixel"], G["Z"], tuple(G["z"][:J]), n, P, ext=ext,
                       w_ref=w_ref)
@@ -51,6 +54,10 @@ def make_problem(n, P, K, J=4, ext=1.0, w_ref=1.0, seed=0, smax=2.0):
     psi0 = np.ones((K, n, n), np.complex128) if ext == 1.0 else hs.transmittance(
         -0.5 * rng.uniform(0, 1, (K, n, n))).astype(np.complex64).astype(np.complex128)
     q0 = hs.perturbed_probe(q_true, rng).astype(np.complex64).astype(np.complex128)
+    if point == "iterated":
+        psi0, q0 = ep.iterated_point(psi0, q0, t, sqrt_d, sqrt_dref, geo, probe_shifts=s)
+    elif point == "object":
+        psi0 = ep.object_point(psi_true, rng)
     return dict(geo=geo, psi=psi0, q=q0, t=t, s=s, sqrt_d=sqrt_d, sqrt_dref=sqrt_dref)
 
 
@@ -82,6 +89,28 @@ def make_holo(pr, chunk=0, probe_shifts=True, functional="amplitude"):
 ])
 def test_probe_shift_gradient_matches_oracle(n, P, K, J, ext, w_ref):
     pr = make_problem(n, P, K, J=J, ext=ext, w_ref=w_ref, seed=7 * n + J)
+    h = make_holo(pr)
+    psi = dev(pr["psi"], torch.complex64)
+    loss_f = h.forward(psi)
+    loss, gp, gq = h.gradient(psi)
+    F, gp_ref, gq_ref = oh.gradients(pr["psi"], pr["q"], pr["t"], pr["sqrt_d"], pr["sqrt_dref"],
+                                     pr["geo"], probe_shifts=pr["s"])
+    assert abs(loss_f - F) / F < LOSS_TOL
+    assert abs(loss - F) / F < LOSS_TOL
+    assert rel(gp.cpu().numpy(), gp_ref) < GRAD_TOL
+    assert rel(gq.cpu().numpy(), gq_ref) < GRAD_TOL
+
+
+@pytest.mark.parametrize("n,P,K,J,point", [
+    (32, 64, 2, 4, "iterated"), (48, 96, 2, 4, "iterated"), (128, 256, 2, 4, "iterated"),
+    (384, 768, 1, 4, "object"), (512, 1024, 2, 4, "object"), (1826, 2048, 1, 2, "object"),
+    (2048, 4096, 1, 2, "object"),
+])
+def test_probe_shift_gradient_away_from_start(n, P, K, J, point):
+    """Production mode (ext = 1) with probe shifts away from psi = 1: the full-grid gather of
+    R' psi at the object shift t - m~ s and the conj(R' psi) v term of the probe gradient."""
+    pr = make_problem(n, P, K, J=J, seed=17 * n + J, point=point)
+    assert np.abs(pr["psi"] - 1).mean() > 1e-2
     h = make_holo(pr)
     psi = dev(pr["psi"], torch.complex64)
     loss_f = h.forward(psi)
