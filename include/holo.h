@@ -282,6 +282,17 @@ holo_status holo_set_stream(holo_ctx* ctx, void* stream);
  * inside a captured CUDA graph. */
 holo_status holo_read_loss(holo_ctx* ctx, double* loss);
 
+/* Fault injection for tests (no counterpart in the paper; nothing faults on the GPU).
+ * holo_set_device_error writes `word` into the context's device error word, the word a
+ * bounded device wait sets when it gives up (see the conventions above), as if such a wait
+ * had expired: the next call that reads a loss returns HOLO_ERR_TIMEOUT and clears it
+ * (word 0 clears it now).  Synchronises the context's stream.
+ * The environment variable HOLO_FAULT (a comma-separated list, read at every check)
+ * injects host-side failures: "alloc" fails every workspace allocation (HOLO_ERR_OOM, before
+ * cudaMalloc), "arg" rejects every forward / gradient call (HOLO_ERR_ARG, before device
+ * work), "nan" makes every loss read report a non-finite loss (HOLO_ERR_NUMERIC). */
+holo_status holo_set_device_error(holo_ctx* ctx, unsigned long long word);
+
 /* Bytes of device workspace currently held by the context. */
 holo_status holo_workspace_bytes(const holo_ctx* ctx, long long* bytes);
 

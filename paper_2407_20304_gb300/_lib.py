@@ -26,7 +26,7 @@ EXPORTS = ("holo_create", "holo_destroy", "holo_set_shifts", "holo_set_probe_shi
            "holo_step", "holo_direction", "holo_dy_dots", "holo_direction_step", "holo_set_functional",
            "holo_initial_probe", "holo_bin_amplitudes", "holo_upsample2", "holo_set_timing",
            "holo_get_timing", "holo_dot_noalloc",
-           "holo_set_stream", "holo_read_loss",
+           "holo_set_stream", "holo_read_loss", "holo_set_device_error",
            "holo_workspace_bytes", "holo_launch_count", "holo_status_string", "holo_last_error")
 
 # Pass ids of holo_get_timing (HOLO_T_* in include/holo.h).
@@ -79,6 +79,7 @@ def _signatures():
         "holo_dot_noalloc": [P, P, LL, ctypes.POINTER(D), P],
         "holo_set_stream": [P, P],
         "holo_read_loss": [P, ctypes.POINTER(D)],
+        "holo_set_device_error": [P, ctypes.c_ulonglong],
         "holo_set_timing": [P, I],
         "holo_get_timing": [P, P, P],
         "holo_workspace_bytes": [P, ctypes.POINTER(LL)],

@@ -18,8 +18,20 @@ propagated back to plane 0) is Holo.initial_probe.
 
 Angles are processed in chunks of holo.chunk (the paper's independent angle chunks,
 Sec. 4); the loss and grad_q are summed over chunks with the library's accumulate flag.
+
+Shared probe over several processes (`group`, a torch.distributed process group, or the
+default group when `group=True`): each rank holds its own slice of the angles (psi and its
+context cover only those angles) and one copy of q.  F2 and grad_q are sums over all planes
+(Eq. min1 and the probe gradient after Eq. gradpsi), so every gradient and every line-search
+trial loss is summed over the ranks by an all-reduce, as are the psi block's inner products
+(sums over the angles); grad_q is then the same on every rank, so the q block's products
+need no exchange.  Every rank takes the same steps.  The reference-image term must be
+counted once: only the rank that owns angle 0 creates its context with w_ref != 0.
 """
 
+import json
+
+import numpy as np
 import torch
 
 
@@ -31,9 +43,10 @@ class Reconstruction:
     ARMIJO_C = 1e-4
 
     def __init__(self, holo, psi, q, gamma0=1.0, max_halvings=20, update_q=True,
-                 rule="dai-yuan", line_search="backtracking"):
+                 rule="dai-yuan", line_search="backtracking", group=None):
         if rule not in self.RULES or line_search not in self.SEARCHES:
             raise ValueError(f"rule in {self.RULES}, line_search in {self.SEARCHES}")
+        self.group = group
         self.h = holo
         self.psi = psi
         self.q = q
@@ -51,6 +64,28 @@ class Reconstruction:
         self.history = {"F": [], "gamma_psi": [], "gamma_q": [], "beta_psi": [], "beta_q": [],
                         "F_after_psi": []}
 
+    # ------------------------------------------------------------------ reductions over ranks
+    def _allreduce(self, vals):
+        """Sum a list of floats over the ranks (FP64); unchanged without a group."""
+        if self.group is None:
+            return list(vals)
+        import torch.distributed as dist
+        grp = None if self.group is True else self.group
+        t = torch.tensor(list(vals), dtype=torch.float64, device=self.psi.device)
+        dist.all_reduce(t, group=grp)
+        return t.tolist()
+
+    def _allreduce_tensor(self, x):
+        if self.group is not None:
+            import torch.distributed as dist
+            dist.all_reduce(x, group=None if self.group is True else self.group)
+        return x
+
+    def _dots(self, b, *pairs):
+        """Re <a, c> for each pair; summed over the ranks for the psi block (b = 0)."""
+        vals = [self.h.dot(a, c) for a, c in pairs]
+        return self._allreduce(vals) if b == 0 else vals
+
     # ------------------------------------------------------------------ evaluations
     def _chunks(self):
         K, c = self.h.n_angles, self.h.chunk
@@ -60,7 +95,8 @@ class Reconstruction:
         """F2 at (psi, q); q = None keeps the probe last set (its propagations are reused)."""
         if q is not None:
             self.h.set_probe(q)
-        return sum(self.h.forward(psi[k0:k0 + nk], k0=k0) for k0, nk in self._chunks())
+        F = sum(self.h.forward(psi[k0:k0 + nk], k0=k0) for k0, nk in self._chunks())
+        return self._allreduce([F])[0]
 
     def gradient(self, psi, q, gpsi, gq):
         self.h.set_probe(q)
@@ -68,7 +104,8 @@ class Reconstruction:
         for i, (k0, nk) in enumerate(self._chunks()):
             loss, _, _ = self.h.gradient(psi[k0:k0 + nk], grad_psi=gpsi[k0:k0 + nk], grad_q=gq,
                                          k0=k0, accumulate_q=i > 0, loss_in=loss)
-        return loss
+        self._allreduce_tensor(gq)
+        return self._allreduce([loss])[0]
 
     # ------------------------------------------------------------------ iteration
     def _backtrack(self, f, x, eta, gamma, F0, scratch, slope):
@@ -90,6 +127,8 @@ class Reconstruction:
         Re <g_new, eta_new> from the same inner products."""
         g_old, eta = self.g[b], self.eta[b]
         num, d_new, d_old = self.h.dy_dots(g_new, g_old, eta)
+        if b == 0:
+            num, d_new, d_old = self._allreduce([num, d_new, d_old])
         beta = None
         if self.rule == "dai-yuan":
             den = d_new - d_old
@@ -100,7 +139,7 @@ class Reconstruction:
                 if self.rule == "fletcher-reeves":
                     beta = num / oo
                 else:
-                    beta = (num - self.h.dot(g_new, g_old)) / oo
+                    beta = (num - self._dots(b, (g_new, g_old))[0]) / oo
             if beta is not None and not (-num + beta * d_new) < 0.0:
                 beta = None
         beta = 0.0 if beta is None else beta
@@ -118,7 +157,7 @@ class Reconstruction:
             self.eta = [torch.zeros_like(psi), torch.zeros_like(q)]
             for b in range(2):
                 self.h.direction(self.eta[b], self.g[b], 0.0)
-                self.gg[b] = self.h.dot(self.g[b], self.g[b])
+                self.gg[b] = self._dots(b, (self.g[b], self.g[b]))[0]
                 self.slope[b] = -self.gg[b]
             self.history["F"].append(self.F)
         scratch_psi, scratch_q = torch.empty_like(psi), torch.empty_like(q)
@@ -143,3 +182,43 @@ class Reconstruction:
                              ("beta_psi", betas[0]), ("beta_q", betas[1])):
                 self.history[key].append(val)
         return self.history
+
+    # ------------------------------------------------------------------ checkpoint / resume
+    def save(self, path):
+        """Write the driver state to an .npz file: psi, q, both blocks' gradients and
+        directions, the next trial steps, ||g||^2 and the slopes of both blocks, F, and the
+        history.  With a process group each rank saves its own psi slice (its own path)."""
+        if self.g is None:
+            raise RuntimeError("no state before the first gradient (run at least 0 iterations)")
+        arrs = {"psi": self.psi, "q": self.q, "g_psi": self.g[0], "g_q": self.g[1],
+                "eta_psi": self.eta[0], "eta_q": self.eta[1]}
+        scal = np.array(self.trial + self.gg + self.slope + [self.F], np.float64)
+        meta = json.dumps({"history": self.history, "rule": self.rule,
+                           "line_search": self.line_search, "update_q": self.update_q,
+                           "max_halvings": self.max_halvings, "gamma0": self.gamma0})
+        np.savez(path, scalars=scal, meta=np.array(meta),
+                 **{k: v.detach().cpu().numpy() for k, v in arrs.items()})
+
+    def load(self, path):
+        """Restore a state written by `save` into this driver: psi and q are overwritten in
+        place (same shapes), the other tensors are allocated on psi's device.  The next `run`
+        continues exactly where the saved one stopped."""
+        with np.load(path) as f:
+            meta = json.loads(str(f["meta"]))
+            for k in ("rule", "line_search", "update_q", "max_halvings"):
+                if meta[k] != getattr(self, k):
+                    raise ValueError(f"checkpoint has {k}={meta[k]!r}, driver {getattr(self, k)!r}")
+            arr = {k: torch.from_numpy(f[k]) for k in
+                   ("psi", "q", "g_psi", "g_q", "eta_psi", "eta_q")}
+            scal = f["scalars"].tolist()
+        if arr["psi"].shape != self.psi.shape or arr["q"].shape != self.q.shape:
+            raise ValueError("checkpoint shapes differ from this driver's psi / q")
+        self.psi.copy_(arr["psi"])
+        self.q.copy_(arr["q"])
+        dev = self.psi.device
+        self.g = [arr["g_psi"].to(dev), arr["g_q"].to(dev)]
+        self.eta = [arr["eta_psi"].to(dev), arr["eta_q"].to(dev)]
+        self.trial, self.gg, self.slope = scal[0:2], scal[2:4], scal[4:6]
+        self.F = scal[6]
+        self.gamma0 = meta["gamma0"]
+        self.history = meta["history"]

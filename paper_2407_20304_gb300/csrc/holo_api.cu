@@ -5,6 +5,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <string>
 #include <vector>
@@ -186,9 +187,24 @@ holo_status fail(holo_ctx* c, holo_status s, const std::string& msg) {
     (ctx)->launches++;           \
   } while (0)
 
+// Host-side fault injection for tests (nothing faults on the GPU): the environment variable
+// HOLO_FAULT holds a comma-separated list of kinds, read at every check.
+//   alloc  every workspace allocation fails (HOLO_ERR_OOM) before cudaMalloc is called;
+//   arg    every forward / gradient call is rejected as an invalid argument (HOLO_ERR_ARG)
+//          before any device work;
+//   nan    every loss read reports a non-finite loss (HOLO_ERR_NUMERIC).
+bool fault_on(const char* kind) {
+  const char* e = std::getenv("HOLO_FAULT");
+  if (!e || !*e) return false;
+  const std::string list = std::string(",") + e + ",";
+  return list.find(std::string(",") + kind + ",") != std::string::npos;
+}
+
 holo_status dalloc(holo_ctx* c, void** p, size_t bytes) {
   *p = nullptr;
   if (bytes == 0) return HOLO_OK;
+  if (fault_on("alloc"))
+    return fail(c, HOLO_ERR_OOM, "allocation failure injected by HOLO_FAULT=alloc");
   cudaError_t e = cudaMalloc(p, bytes);
   if (e != cudaSuccess) {
     *p = nullptr;
@@ -455,6 +471,7 @@ holo_status dstep2d(holo_ctx* c, const float2* in, int r_lo, int rows, int c_lo,
 
 holo_status check_chunk(holo_ctx* c, int k0, int nk) {
   if (!c) return HOLO_ERR_ARG;
+  if (fault_on("arg")) return fail(c, HOLO_ERR_ARG, "argument error injected by HOLO_FAULT=arg");
   if (nk < 1 || nk > c->chunk || k0 < 0 || k0 + nk > c->K)
     return fail(c, HOLO_ERR_ARG, "chunk [k0, k0+nk) outside [0, n_angles) or nk > chunk");
   if (!c->have_shifts) return fail(c, HOLO_ERR_STATE, "holo_set_shifts not called");
@@ -663,7 +680,7 @@ holo_status read_loss(holo_ctx* c, double* loss, unsigned flags) {
                              cudaMemcpyDeviceToHost, c->stream));
   HOLO_CK(c, cudaStreamSynchronize(c->stream));
   if (holo_status st = check_err_word(c)) return st;
-  const double l = c->h_red[7];
+  const double l = fault_on("nan") ? std::nan("") : c->h_red[7];
   if (loss) *loss = (flags & (HOLO_ACCUMULATE | HOLO_ACCUMULATE_Q)) ? *loss + l : l;
   if (!std::isfinite(l)) return fail(c, HOLO_ERR_NUMERIC, "non-finite loss");
   return HOLO_OK;
@@ -1353,8 +1370,16 @@ holo_status holo_read_loss(holo_ctx* c, double* loss) {
                              cudaMemcpyDeviceToHost, c->stream));
   HOLO_CK(c, cudaStreamSynchronize(c->stream));
   if (holo_status st = check_err_word(c)) return st;
-  *loss = c->h_red[3];
+  *loss = fault_on("nan") ? std::nan("") : c->h_red[3];
   if (!std::isfinite(*loss)) return fail(c, HOLO_ERR_NUMERIC, "non-finite loss");
+  return HOLO_OK;
+}
+
+holo_status holo_set_device_error(holo_ctx* c, unsigned long long word) {
+  if (!c) return HOLO_ERR_ARG;
+  HOLO_CK(c, cudaMemcpyAsync(c->d_red + kErrWord, &word, sizeof(word), cudaMemcpyHostToDevice,
+                             c->stream));
+  HOLO_CK(c, cudaStreamSynchronize(c->stream));
   return HOLO_OK;
 }
 

@@ -358,6 +358,12 @@ class Holo:
         _check(self.lib, self.ctx, self.lib.holo_get_timing(self.ctx, ms, nl), "holo_get_timing")
         return {name: (ms[i], nl[i]) for i, name in enumerate(_lib.TIMERS)}
 
+    def set_device_error(self, word=1):
+        """Test hook (holo_set_device_error): set the device error word as if a bounded
+        device wait had given up; the next loss read raises HOLO_ERR_TIMEOUT and clears it."""
+        st = self.lib.holo_set_device_error(self.ctx, ctypes.c_ulonglong(word))
+        _check(self.lib, self.ctx, st, "holo_set_device_error")
+
     def workspace_bytes(self):
         v = ctypes.c_longlong(0)
         _check(self.lib, self.ctx, self.lib.holo_workspace_bytes(self.ctx, ctypes.byref(v)),

@@ -76,6 +76,23 @@ def test_null_arguments(lib):
     assert lib.holo_step(None, None, None, 1.0, 0) == 1
 
 
+def test_injected_allocation_failure_needs_no_gpu(lib, monkeypatch):
+    """HOLO_FAULT=alloc fails the first workspace allocation of holo_create before cudaMalloc
+    (HOLO_ERR_OOM) and returns no context; the check runs on the host only."""
+    monkeypatch.setenv("HOLO_FAULT", "alloc")
+    g = _geo()
+    out = ctypes.c_void_p(123)
+    assert lib.holo_create(ctypes.byref(g), None, ctypes.byref(out)) == 3
+    assert out.value is None
+    # an invalid geometry is still reported as such (validation comes first)
+    g = _geo(n=63)
+    assert lib.holo_create(ctypes.byref(g), None, ctypes.byref(out)) == 1
+
+
+def test_device_error_hook_rejects_a_null_context(lib):
+    assert lib.holo_set_device_error(None, 1) == 1
+
+
 def _prototypes():
     """{name: [parameter type strings]} of the function declarations in include/holo.h."""
     src = open(os.path.join(ROOT, "include", "holo.h")).read()
@@ -107,4 +124,5 @@ def test_binding_prototypes_match_the_header():
             elif p.startswith("double"):
                 assert a is ctypes.c_double, (name, p, a)
             elif p.startswith(("int", "long long", "unsigned", "holo_status")):
-                assert a in (ctypes.c_int, ctypes.c_longlong, ctypes.c_uint), (name, p, a)
+                assert a in (ctypes.c_int, ctypes.c_longlong, ctypes.c_uint,
+                             ctypes.c_ulonglong), (name, p, a)

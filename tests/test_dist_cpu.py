@@ -86,3 +86,133 @@ def test_two_rank_shared_probe_gradient_equals_full(probe_shifts):
     np.testing.assert_allclose(gq_all, gq, atol=1e-12 * np.abs(gq).max())
     for k0, nk, g in parts:
         np.testing.assert_allclose(g, gp[k0:k0 + nk], atol=1e-12 * np.abs(gp).max())
+
+
+class _OracleHolo:
+    """The library's evaluation calls, computed by the FP64 oracle on CPU tensors, so the
+    GPU driver's sharded logic runs on gloo ranks without a GPU.  Covers the angles
+    [k0g, k0g + K) of the problem; the reference term only if w_ref is set."""
+
+    def __init__(self, geo, t, sqrt_d, sqrt_dref):
+        self.geo, self.t, self.sqrt_d, self.sqrt_dref = geo, t, sqrt_d, sqrt_dref
+        self.n_angles = self.chunk = t.shape[0]
+        self.q = None
+
+    def set_probe(self, q):
+        self.q = q.numpy()
+
+    def forward(self, psi, k0=0):
+        nk = psi.shape[0]
+        return oh.functional(psi.numpy(), self.q, self.t[k0:k0 + nk], self.sqrt_d[k0:k0 + nk],
+                             self.sqrt_dref, self.geo)
+
+    def gradient(self, psi, grad_psi, grad_q, k0=0, accumulate_q=False, loss_in=0.0):
+        nk = psi.shape[0]
+        F, gp, gq = oh.gradients(psi.numpy(), self.q, self.t[k0:k0 + nk],
+                                 self.sqrt_d[k0:k0 + nk], self.sqrt_dref, self.geo)
+        grad_psi.copy_(torch.from_numpy(gp))
+        if accumulate_q:
+            grad_q.add_(torch.from_numpy(gq))
+            F += loss_in
+        else:
+            grad_q.copy_(torch.from_numpy(gq))
+        return F, grad_psi, grad_q
+
+    @staticmethod
+    def dot(a, b):
+        return float(np.real(np.vdot(a.numpy(), b.numpy())))
+
+    def dy_dots(self, g, g_prev, eta):
+        return self.dot(g, g), self.dot(g, eta), self.dot(g_prev, eta)
+
+    @staticmethod
+    def direction(eta, g, beta):
+        eta.mul_(beta).sub_(g)
+
+    @staticmethod
+    def step(x, eta, gamma):
+        x.add_(eta * gamma)
+
+
+ITERS = 3
+
+
+def _driver_worker(rank, world, port, out):
+    import dataclasses
+
+    import torch.distributed as dist
+    from paper_2407_20304_gb300.cg import Reconstruction
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    geo, psi, q, t, _, sqrt_d, sqrt_dref = _problem(False)
+    k0, nk = shard(psi.shape[0], world, rank)
+    geo_r = dataclasses.replace(geo, w_ref=geo.w_ref if k0 == 0 else 0.0)
+    h = _OracleHolo(geo_r, t[k0:k0 + nk], sqrt_d[k0:k0 + nk], sqrt_dref)
+    r = Reconstruction(h, torch.from_numpy(psi[k0:k0 + nk].copy()), torch.from_numpy(q.copy()),
+                       group=True)
+    hist = r.run(ITERS)
+    parts = [None] * world
+    dist.all_gather_object(parts, (k0, nk, r.psi.numpy()))
+    if rank == 0:
+        out.put((hist, r.q.numpy(), parts))
+    dist.barrier()
+    dist.destroy_process_group()
+
+
+def test_two_rank_sharded_driver_follows_the_single_process_oracle_driver():
+    """Reconstruction with a process group over 2 gloo ranks, the oracle standing in for
+    each rank's evaluations: every loss, trial loss, grad_q and psi-block inner product is
+    summed over the ranks, so the sharded run takes the single-process oracle driver's steps
+    (same accepted step lengths, F history and iterates to rounding)."""
+    from oracle import cg as ocg
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = _free_port()
+    procs = [ctx.Process(target=_driver_worker, args=(r, 2, port, q)) for r in range(2)]
+    for p in procs:
+        p.start()
+    hist, q_fin, parts = q.get(timeout=600)
+    for p in procs:
+        p.join(timeout=60)
+        assert p.exitcode == 0
+    geo, psi, qq, t, _, sqrt_d, sqrt_dref = _problem(False)
+    ref = ocg.reconstruct(psi, qq, t, sqrt_d, sqrt_dref, geo, ITERS)
+    assert hist["gamma_psi"] == ref["hist"]["gamma_psi"]
+    assert hist["gamma_q"] == ref["hist"]["gamma_q"]
+    np.testing.assert_allclose(hist["F"], ref["hist"]["F"], rtol=1e-10)
+    np.testing.assert_allclose(hist["beta_psi"], ref["hist"]["beta_psi"], rtol=1e-8, atol=1e-14)
+    np.testing.assert_allclose(q_fin, ref["q"], rtol=0, atol=1e-10 * np.abs(ref["q"]).max())
+    for k0, nk, x in parts:
+        np.testing.assert_allclose(x, ref["psi"][k0:k0 + nk], rtol=0,
+                                   atol=1e-10 * np.abs(ref["psi"]).max())
+    # the sharded run really moved both blocks
+    assert any(g > 0 for g in hist["gamma_psi"]) and any(g > 0 for g in hist["gamma_q"])
+
+
+def test_checkpoint_resume_is_bit_exact(tmp_path):
+    """Driver state saved after 2 iterations and restored into a fresh driver continues
+    exactly as an uninterrupted 4-iteration run (the oracle standing in for the library's
+    evaluations, on CPU)."""
+    from paper_2407_20304_gb300.cg import Reconstruction
+    geo, psi, q, t, _, sqrt_d, sqrt_dref = _problem(False)
+
+    def fresh(p0=psi, q0=q):
+        h = _OracleHolo(geo, t, sqrt_d, sqrt_dref)
+        return Reconstruction(h, torch.from_numpy(p0.copy()), torch.from_numpy(q0.copy()))
+
+    full = fresh()
+    full.run(4)
+    part = fresh()
+    part.run(2)
+    path = tmp_path / "state.npz"
+    part.save(path)
+    res = fresh(np.zeros_like(psi), np.zeros_like(q))
+    res.load(path)
+    res.run(2)
+    assert res.history == full.history
+    assert torch.equal(res.psi, full.psi) and torch.equal(res.q, full.q)
+    assert torch.equal(res.eta[0], full.eta[0]) and torch.equal(res.g[1], full.g[1])
+    with pytest.raises(ValueError):
+        Reconstruction(_OracleHolo(geo, t, sqrt_d, sqrt_dref), torch.from_numpy(psi.copy()),
+                       torch.from_numpy(q.copy()), rule="polak-ribiere").load(path)
