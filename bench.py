@@ -470,6 +470,12 @@ def run_e2e(h, args, w, psi, q, sqrt_d, dev, planes, dist):
         dt = float(t.item())
     h2d = psi_h.numel() * 8 + d_h.numel() * 4 + q_h.numel() * 8
     d2h = gp_h.numel() * 8 + gq_h.numel() * 8 + 16
+    # device time of the library's kernels inside one host call (events around each pass on
+    # the context's stream; waits for copies are outside them)
+    h.set_timing(True)
+    h.gradient_host(a[0], sqrt_d=a[1], q=a[2], grad_psi=a[3], grad_q=a[4])
+    kernels_in_call = sum(v[0] for v in h.get_timing().values())
+    h.set_timing(False)
     # the parts: copies alone, device gradient alone
     s = torch.cuda.Stream(dev)
     bufs = [torch.empty_like(x, device=dev) for x in (psi_h, d_h, q_h)]
@@ -509,7 +515,8 @@ def run_e2e(h, args, w, psi, q, sqrt_d, dev, planes, dist):
             "host_buffers_pinned": pinned, "call_ms": round(call_ms, 2),
             "h2d_ms": round(h2d_ms, 2), "d2h_ms": round(d2h_ms, 2),
             "h2d_gbs": round(h2d / h2d_ms / 1e6, 1), "d2h_gbs": round(d2h / d2h_ms / 1e6, 1),
-            "compute_ms": round(compute_ms, 2), "overlap": round(overlap, 3)}
+            "compute_ms": round(compute_ms, 2), "overlap": round(overlap, 3),
+            "kernels_in_call_ms": round(kernels_in_call, 2)}
 
 
 # ---------------------------------------------------------------- unfused comparison

@@ -54,6 +54,16 @@ struct SmemHead {
   static constexpr int WORDS = ROOTS + CHIRP;
 };
 
+// Shared memory head of pass B: the full per-stage twiddle table (Fft<P>::TW entries, one
+// shared load per twiddle instead of a product tree of powers; pass B runs one block per SM
+// and has the room) and the half chirp table.
+template <int P>
+struct PassBHead {
+  static constexpr int TWF = (Fft<P>::TW + 1) & ~1;
+  static constexpr int CHIRP = SmemHead<P>::CHIRP;
+  static constexpr int WORDS = TWF + CHIRP;
+};
+
 // Lines per row block: about 256 threads, whole warps.
 __host__ __device__ constexpr int row_lines(int T, int g = 0) {
   return T >= 256 ? 1 : (g == 0 ? row_lines(T, 256 / T) : ((g * T) % 32 ? row_lines(T, g - 1) : g));
@@ -257,6 +267,21 @@ __global__ void __launch_bounds__(RowCfg<P>::NT, RowCfg<P>::MINB) k_pass_a(PassA
       }
       v[c] = x;
     }
+    // the next line of this thread group: its probe row and its two object rows go to L2 now
+    // (one bulk request each, issued by the line's first thread)
+    if (t == 0 && li + (int)gridDim.x * R::G < a.nlines) {
+      const int2 NL = __ldg(a.lines + a.line0 + li + gridDim.x * R::G);
+      const int nlp = NL.x - p_lo;
+      const PlaneDesc nd = a.planes[NL.x];
+      const Tap nyt = a.ytap[(long long)NL.x * a.tap_stride + NL.y];
+      l2_prefetch_bulk(a.pj + ((long long)(nlp % a.J) * P + nd.by0 + NL.y) * P + nd.bx0,
+                       nd.bxs * (uint32_t)sizeof(float2));
+      const float2* npsi = a.psi + (long long)(nlp / a.J) * n * n;
+      if ((unsigned)nyt.i0 < (unsigned)n)
+        l2_prefetch_bulk(npsi + (long long)nyt.i0 * n, n * (uint32_t)sizeof(float2));
+      if ((unsigned)(nyt.i0 + 1) < (unsigned)n)
+        l2_prefetch_bulk(npsi + (long long)(nyt.i0 + 1) * n, n * (uint32_t)sizeof(float2));
+    }
     ensure_chirp<P>(chs, a.chirp_zhat, R::G == 1 ? j : jb, jcur);
     __syncthreads();
     fft_fwd_with<P>(v, sm, tw, t, SyncBlock());
@@ -293,7 +318,7 @@ size_t pass_b_stage_bytes(int rows) {
 template <int P>
 size_t pass_b_smem(int n, int srows = 0) {
   const size_t base =
-      (size_t)(SmemHead<P>::WORDS + ColCfg<P>::C * ColCfg<P>::LS + 2 * n * ColCfg<P>::C) *
+      (size_t)(PassBHead<P>::WORDS + ColCfg<P>::C * ColCfg<P>::LS + 2 * n * ColCfg<P>::C) *
       sizeof(float2);
   return srows > 0 ? base + 128 + pass_b_stage_bytes<P>(srows) : base;
 }
@@ -321,20 +346,20 @@ template <int P, bool ADJ, bool SHIFT>
 __global__ void __launch_bounds__(ColCfg<P>::NT) k_pass_b(PassArgs a) {
   using F = Fft<P>;
   using Cc = ColCfg<P>;
-  using H = SmemHead<P>;
+  using H = PassBHead<P>;
   constexpr int C = Cc::C;
   extern __shared__ float2 smem[];
   __shared__ double red[32];
   __shared__ uint64_t ybar;
-  float2* roots = smem;
-  float2* chs = smem + H::ROOTS;
+  float2* tws = smem;
+  float2* chs = smem + H::TWF;
   const int g = threadIdx.x % C, t = threadIdx.x / C;
   float2* sm = smem + H::WORDS + g * Cc::LS;
   const int n = a.n, lo = P / 2 - n / 2;
   float2* sb = smem + H::WORDS + C * Cc::LS;
   float2* sS = sb + n * C;
-  load_roots<P>(roots, a.twiddles);
-  const TwRoots tw{roots};
+  load_twiddles<P>(tws, a.twiddles);
+  const TwTable tw{tws};
   const int ngroups = (n + C - 1) / C;
   double dsum = 0.0;
   int jcur = -1;
@@ -410,6 +435,27 @@ __global__ void __launch_bounds__(ColCfg<P>::NT) k_pass_b(PassArgs a) {
         for (int c = 0; c < 16; ++c) {
           const int rr = F::pos(t, c) - lo;
           dats[c] = (valid && (unsigned)rr < (unsigned)n) ? __ldg(ad + (long long)rr * n + col) : 0.f;
+        }
+        // ... and the next item's data rows are prefetched into L2 (the group's columns share
+        // a sector per row; the rows are spread over the C threads of each position)
+        {
+          int nkl = kl + 1, nj = j, ncg = cg;
+          if (nkl == a.nk) {
+            nkl = 0;
+            if (++nj == a.J) {
+              nj = 0;
+              ncg += gridDim.x;
+            }
+          }
+          if (ncg < ngroups) {
+            const float* adn =
+                a.sqrt_d + ((long long)(a.k0 + nkl - a.data_k0) * a.J + nj) * n * n + ncg * C;
+#pragma unroll
+            for (int c = 0; c < 16; ++c) {
+              const int rr = F::pos(t, c) - lo;
+              if (c % C == g && (unsigned)rr < (unsigned)n) l2_prefetch(adn + (long long)rr * n);
+            }
+          }
         }
         const float2* rmp = SHIFT ? a.ramp_y + gplane * P : nullptr;
 #pragma unroll
@@ -500,19 +546,19 @@ template <int P, bool ADJ, bool SHIFT>
 __global__ void __launch_bounds__(ColCfg<P>::NT) k_pass_b_split(PassArgs a) {
   using F = Fft<P>;
   using Cc = ColCfg<P>;
-  using H = SmemHead<P>;
+  using H = PassBHead<P>;
   constexpr int C = Cc::C;
   extern __shared__ float2 smem[];
   __shared__ double red[32];
-  float2* roots = smem;
-  float2* chs = smem + H::ROOTS;
+  float2* tws = smem;
+  float2* chs = smem + H::TWF;
   const int g = threadIdx.x % C, t = threadIdx.x / C;
   float2* sm = smem + H::WORDS + g * Cc::LS;
   const int n = a.n, lo = P / 2 - n / 2;
   float2* sb = smem + H::WORDS + C * Cc::LS;
   float2* sS = sb + n * C;
-  load_roots<P>(roots, a.twiddles);
-  const TwRoots tw{roots};
+  load_twiddles<P>(tws, a.twiddles);
+  const TwTable tw{tws};
   const int ngroups = (n + C - 1) / C;
   double dsum = 0.0;
   int jcur = -1;
@@ -737,6 +783,19 @@ __global__ void __launch_bounds__(RowCfg<P>::NT, RowCfg<P>::MINB) k_pass_c(PassA
     for (int c = 0; c < 16; ++c) {
       const int rel = F::pos(t, c) - lo;
       v[c] = (valid && (unsigned)rel < (unsigned)n) ? yrow[rel] : make_float2(0.f, 0.f);
+    }
+    // the next line of this thread group: its adjoint-field row, probe row and conj(w) v row go
+    // to L2 now (one bulk request each, issued by the line's first thread)
+    if (t == 0 && li + (int)gridDim.x * R::G < a.nlines) {
+      const int2 NL = __ldg(a.lines + a.line0 + li + gridDim.x * R::G);
+      const int nlp = NL.x - p_lo;
+      const PlaneDesc nd = a.planes[NL.x];
+      l2_prefetch_bulk(a.ybuf + (long long)nlp * a.ystride + (long long)NL.y * n,
+                       n * (uint32_t)sizeof(float2));
+      l2_prefetch_bulk(a.pj + ((long long)(nlp % a.J) * P + nd.by0 + NL.y) * P + nd.bx0,
+                       nd.bxs * (uint32_t)sizeof(float2));
+      l2_prefetch_bulk(a.gkbuf + (long long)nlp * a.gkstride + (long long)NL.y * nd.bxs,
+                       nd.bxs * (uint32_t)sizeof(float2));
     }
     ensure_chirp<P>(chs, a.chirp_zhat, R::G == 1 ? j : jb, jcur);
     __syncthreads();

@@ -154,6 +154,64 @@ def test_cg_driver_follows_the_oracle_driver(rule, line_search):
         assert change < 1e-4
 
 
+@pytest.mark.parametrize("rule,line_search", [("dai-yuan", "backtracking"),
+                                              ("fletcher-reeves", "armijo"),
+                                              ("polak-ribiere", "backtracking"),
+                                              ("dai-yuan", "armijo")])
+def test_every_cg_iteration_matches_an_fp64_step_from_the_same_state(rule, line_search):
+    """Pins every iteration, not only those before the first difference: before each GPU
+    iteration the driver's state (psi, q, directions, gradients, trial steps) is handed to
+    the FP64 oracle, which takes one iteration from it with the oracle's functional, line
+    search and direction rule.  The accepted step lengths must be the GPU's, unless the
+    oracle's accepted trial changed F by less than FP32 resolves (a near-tie, relative change
+    < 1e-4); the new directions' beta must agree to 1e-4 relative."""
+    from paper_2407_20304_gb300.cg import Reconstruction
+    geo, t, sqrt_d, sqrt_dref, psi0, q0 = small_problem(K=4, seed=4)
+    h = make_holo(geo, 4, t, sqrt_d, sqrt_dref, chunk=3)
+    rec = Reconstruction(h, torch.from_numpy(psi0).cuda(), torch.from_numpy(q0).cuda(),
+                         rule=rule, line_search=line_search)
+    d64, r64 = sqrt_d.astype(np.float64), sqrt_dref.astype(np.float64)
+    c = lambda x: x.detach().cpu().numpy().astype(np.complex128)
+    rec.run(0)
+    ties = 0
+    for it in range(6):
+        psi, q = c(rec.psi), c(rec.q)
+        eta, g = [c(e) for e in rec.eta], [c(x) for x in rec.g]
+        trial = list(rec.trial)
+        F0 = oh.functional(psi, q, t, d64, r64, geo)
+
+        def search(f, F, gb, x, e, tr):
+            if line_search == "armijo":
+                return ocg.armijo(f, F, ocg.re_inner(gb, e), x, e, tr, rec.max_halvings)
+            return ocg.backtrack(f, F, x, e, tr, rec.max_halvings)
+
+        gp_o, Fp = search(lambda x: oh.functional(x, q, t, d64, r64, geo), F0, g[0], psi, eta[0],
+                          trial[0])
+        psi_o = psi + gp_o * eta[0]
+        gq_o, Fq = search(lambda x: oh.functional(psi_o, x, t, d64, r64, geo), Fp, g[1], q,
+                          eta[1], trial[1])
+        rec.run(1)
+        hist = rec.history
+        for name, mine, theirs, before, after in (("psi", hist["gamma_psi"][-1], gp_o, F0, Fp),
+                                                  ("q", hist["gamma_q"][-1], gq_o, Fp, Fq)):
+            if mine != theirs:
+                change = abs(before - after) / before
+                print(f"iteration {it}: {name} step {mine} (gpu) vs {theirs} (fp64), "
+                      f"relative F change of the fp64 step {change:.1e}")
+                assert change < 1e-4
+                ties += 1
+        if hist["gamma_psi"][-1] != gp_o or hist["gamma_q"][-1] != gq_o:
+            continue
+        # the direction update from the GPU's new gradients, in FP64
+        g_new = [c(x) for x in rec.g]
+        for b, key in ((0, "beta_psi"), (1, "beta_q")):
+            _, beta_o = ocg.direction(g_new[b], g[b], eta[b], rule)
+            beta = hist[key][-1]
+            assert abs(beta - beta_o) <= 1e-4 * max(abs(beta_o), 1e-12) or \
+                (beta == 0.0) == (beta_o == 0.0) == True, (it, key, beta, beta_o)
+    assert ties <= 2
+
+
 @pytest.mark.parametrize("n,P", [(64, 128), (48, 96), (256, 512)])
 def test_initial_probe_matches_oracle(n, P):
     """The paper's initial probe (reference image propagated back to plane 0) against the

@@ -44,7 +44,7 @@ def batch():
         psi0 = (np.ones((K, n, n), np.complex128) if i % 2 == 0 and n < 256 else
                 ep.object_point(psi_true, rng)).astype(np.complex64)
         q0 = hs.perturbed_probe(q_true, rng).astype(np.complex64)
-        h = Holo(n, K, J, G["wavelength"], G["pixel"], G["Z"], z, pad=P, chunk=2)
+        h = Holo(n, K, J, G["wavelength"], G["pixel"], G["Z"], z, pad=P, chunk=min(2, K))
         h.set_shifts(t.astype(np.float32))
         d, dr = torch.from_numpy(sqrt_d).cuda(), torch.from_numpy(sqrt_dref).cuda()
         h.set_data(d, dr)
