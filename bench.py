@@ -1076,7 +1076,7 @@ def run_batch(args):
         t = hs.sample_shifts(K, J, rng).astype(np.float32)
         h = Holo(n, K, J, g["wavelength"], g["pixel"], g["Z"], g["z"][:J], pad=P, chunk=chunk)
         h.set_shifts(t)
-        sqrt_d = torch.empty((K, J, n, n), dtype=torch.float32, device="cuda")
+        sqrt_d = torch.zeros((K, J, n, n), dtype=torch.float32, device="cuda")
         ones_ref = torch.ones((n, n), dtype=torch.float32, device="cuda")
         h.set_data(sqrt_d, ones_ref)
         h.set_probe(q_true)
@@ -1094,9 +1094,11 @@ def run_batch(args):
         bref = h.propagate(q_true, zeta[0])[lo:lo + n, lo:lo + n]
         sqrt_dref = bref.abs().contiguous()
         h.set_data(sqrt_d, sqrt_dref)
+        # the library keeps its own (column-blocked) copy of the amplitudes
+        del sqrt_d
         inst = Instance(h, torch.ones((K, n, n), dtype=torch.complex64, device="cuda"),
                         q_true.clone())
-        inst.data = (sqrt_d, sqrt_dref)
+        inst.data = sqrt_dref
         insts.append(inst)
         # the data-generation temporaries go back to the device before the next context
         # allocates its workspace

@@ -139,9 +139,12 @@ holo_status holo_set_probe_shifts(holo_ctx* ctx, const float* s_host);
 
 /* Register the data: sqrt_d (dev float [n_angles][n_dist][n][n]) holds sqrt(d~_kj), the
  * amplitudes of the data rescaled to the plane-0 grid (d~ = m0^2 M_{1/m0} d, Sec. 2);
- * sqrt_dref (dev float [n][n], may be NULL when w_ref = 0) holds sqrt(d~^r).  Not
- * copied: both must stay valid while used.  sqrt_d may be NULL when every evaluation
- * passes its chunk's data through holo_gradient_host (only the reference is kept). */
+ * sqrt_dref (dev float [n][n], may be NULL when w_ref = 0) holds sqrt(d~^r).  sqrt_d is
+ * copied into the workspace (in the column-blocked layout the column pass reads: the columns
+ * of one column group contiguous per row) and the stream is synchronised, so the caller may
+ * reuse or free it when the call returns; sqrt_dref is not copied and must stay valid while
+ * used.  sqrt_d may be NULL when every evaluation passes its chunk's data through
+ * holo_gradient_host (only the reference is kept). */
 holo_status holo_set_data(holo_ctx* ctx, const float* sqrt_d, const float* sqrt_dref);
 
 /* Set the probe q (dev complex64 [P][P]) and compute its propagations p_j = D_{omega_j} q

@@ -114,8 +114,10 @@ struct holo_ctx {
   std::vector<int> rowstart;    // first line of each plane (host)
   int tap_stride = 0;
   size_t tap_bytes = 0;
-  // data
-  const float* sqrt_d = nullptr;
+  // data: the amplitudes of holo_set_data copied into pass B's column-blocked layout
+  // [n_angles][J][groups][n][C]; the reference image is used in place
+  float* d_dblk = nullptr;
+  size_t dblk_bytes = 0;
   const float* sqrt_dref = nullptr;
   bool have_data = false;
   // probe
@@ -148,6 +150,7 @@ struct holo_ctx {
   float2* s_psi = nullptr;
   float2* s_gpsi = nullptr;
   float* s_data = nullptr;
+  float* s_dblk = nullptr;      // the chunk's data of the host call, column-blocked
   float2* s_q = nullptr;
   float2* s_gq = nullptr;
   long long bytes = 0;
@@ -493,7 +496,8 @@ PassArgs pass_args(holo_ctx* c, int k0, int nk, const void* psi) {
   a.psi = (const float2*)psi;
   a.pj = c->d_pj;
   a.bref = c->d_b;
-  a.sqrt_d = c->sqrt_d;
+  a.dblk = c->d_dblk;
+  a.dgroups = c->ops->pass_b_groups(c->n);
   a.data_k0 = 0;
   a.chirp_zhat = c->d_chirp_zhat;
   a.ybuf = c->ybuf;
@@ -831,7 +835,7 @@ holo_status holo_destroy(holo_ctx* c) {
                   c->ybuf,    c->gkbuf,        c->d_scratch,
                   c->d_Gp,    c->d_T,          c->d_rref,        c->d_part,
                   c->d_red,   c->d_dot3,       c->d_tpart,       c->s_psi,         c->s_gpsi,
-                  c->s_data,
+                  c->s_data,       c->s_dblk,       c->d_dblk,
                   c->s_q,     c->s_gq,         c->d_xtap,        c->d_ytap,
                   c->d_xadj,  c->d_yadj,       c->d_lines,       c->d_ymap,
                   c->d_ramp_x, c->d_ramp_y};
@@ -1044,8 +1048,25 @@ holo_status holo_set_data(holo_ctx* c, const float* sqrt_d, const float* sqrt_dr
   if (!c) return HOLO_ERR_ARG;
   if (!sqrt_d && !sqrt_dref) return fail(c, HOLO_ERR_ARG, "null data");
   if (c->wref != 0.0 && !sqrt_dref) return fail(c, HOLO_ERR_ARG, "w_ref != 0 needs sqrt_dref");
-  c->sqrt_d = sqrt_d;
   c->sqrt_dref = sqrt_dref;
+  if (sqrt_d) {
+    // copy into pass B's column-blocked layout, then synchronise so the caller may reuse or
+    // free its buffer as soon as the call returns
+    const int C = c->ops->pass_b_cols, groups = c->ops->pass_b_groups(c->n);
+    const long long planes = (long long)c->K * c->J;
+    const size_t need = sizeof(float) * (size_t)planes * groups * c->n * C;
+    if (need != c->dblk_bytes) {
+      dfree(c, c->d_dblk, c->dblk_bytes);
+      c->d_dblk = nullptr;
+      c->dblk_bytes = 0;
+      c->have_data = false;
+      holo_status st = dalloc(c, (void**)&c->d_dblk, need);
+      if (st) return st;
+      c->dblk_bytes = need;
+    }
+    HOLO_LAUNCH(c, holo::launch_block_data(sqrt_d, planes, c->n, C, c->d_dblk, c->stream));
+    HOLO_CK(c, cudaStreamSynchronize(c->stream));
+  }
   c->have_data = sqrt_d != nullptr;
   return HOLO_OK;
 }
@@ -1105,6 +1126,7 @@ static holo_status gradient_host_parts(holo_ctx* c, int k0, int nk, int parts, c
                                 void* grad_psi_host, void* grad_q_host, unsigned flags) {
   const int n = c->n, P = c->P, J = c->J;
   const size_t n2 = (size_t)n * n;
+  const size_t dplane = (size_t)c->ops->pass_b_groups(n) * n * c->ops->pass_b_cols;
   holo_status st;
   if (!c->cs_in) {
     if (cudaStreamCreateWithFlags(&c->cs_in, cudaStreamNonBlocking) != cudaSuccess ||
@@ -1153,7 +1175,10 @@ static holo_status gradient_host_parts(holo_ctx* c, int k0, int nk, int parts, c
     HOLO_CK(c, cudaStreamWaitEvent(c->stream, c->ev_in[p], 0));
     PassArgs a = pass_args(c, k0 + b0, m, c->s_psi + b0 * n2);
     if (sqrt_d_host) {
-      a.sqrt_d = c->s_data + (size_t)b0 * J * n2;
+      float* blk = c->s_dblk + (size_t)b0 * J * dplane;
+      HOLO_LAUNCH(c, holo::launch_block_data(c->s_data + (size_t)b0 * J * n2, (long long)m * J, n,
+                                             c->ops->pass_b_cols, blk, c->stream));
+      a.dblk = blk;
       a.data_k0 = k0 + b0;
     }
     a.grad_psi = c->s_gpsi + b0 * n2;
@@ -1216,7 +1241,12 @@ static holo_status gradient_host_impl(holo_ctx* c, int k0, int nk, const void* p
                     (st = dalloc(c, (void**)&c->s_q, q_bytes)) ||
                     (st = dalloc(c, (void**)&c->s_gq, q_bytes))))
     return st;
-  if (sqrt_d_host && !c->s_data && (st = dalloc(c, (void**)&c->s_data, data_bytes))) return st;
+  const size_t dblk_bytes =
+      sizeof(float) * (size_t)c->chunk * J * c->ops->pass_b_groups(n) * n * c->ops->pass_b_cols;
+  if (sqrt_d_host && !c->s_data &&
+      ((st = dalloc(c, (void**)&c->s_data, data_bytes)) ||
+       (st = dalloc(c, (void**)&c->s_dblk, dblk_bytes))))
+    return st;
   const int parts = nk >= 2 * kHostMinPart ? std::min(kHostParts, nk / kHostMinPart) : 1;
   if (parts > 1)
     return gradient_host_parts(c, k0, nk, parts, psi_host, sqrt_d_host, q_host, loss,
@@ -1232,7 +1262,9 @@ static holo_status gradient_host_impl(holo_ctx* c, int k0, int nk, const void* p
   }
   PassArgs a = pass_args(c, k0, nk, c->s_psi);
   if (sqrt_d_host) {
-    a.sqrt_d = c->s_data;
+    HOLO_LAUNCH(c, holo::launch_block_data(c->s_data, (long long)nk * J, n, c->ops->pass_b_cols,
+                                           c->s_dblk, c->stream));
+    a.dblk = c->s_dblk;
     a.data_k0 = k0;
   }
   a.grad_psi = c->s_gpsi;

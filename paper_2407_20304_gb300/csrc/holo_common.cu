@@ -114,6 +114,31 @@ __global__ void __launch_bounds__(256) k_reduce_g(PassArgs a, float2* Gp, int j,
   }
 }
 
+// Column-blocked copy of amplitude images for pass B: out[p][gr][r][c] = in[p][r][gr C + c]
+// (zero where gr C + c >= n), so the C columns of a pass-B column group are contiguous per
+// row.  A block moves a tile of 32 rows x W columns (W a multiple of C) of one image through
+// shared memory: the rows are read and the groups' runs of 32 x C values written contiguously.
+constexpr int kBlkRows = 32;
+__global__ void __launch_bounds__(256) k_block_data(const float* __restrict__ in, int n, int C,
+                                                    int W, float* __restrict__ out) {
+  extern __shared__ float tile[];  // [kBlkRows][W + 1]
+  const long long p = blockIdx.z;
+  const int r0 = blockIdx.x * kBlkRows, c0 = blockIdx.y * W;
+  const int groups = (n + C - 1) / C;
+  const float* src = in + p * n * (long long)n;
+  for (int e = threadIdx.x; e < kBlkRows * W; e += blockDim.x) {
+    const int rr = e / W, cc = e % W, r = r0 + rr, col = c0 + cc;
+    tile[rr * (W + 1) + cc] = (r < n && col < n) ? __ldg(src + (long long)r * n + col) : 0.f;
+  }
+  __syncthreads();
+  const int g0 = c0 / C, ng = min(W / C, groups - g0), rows = min(kBlkRows, n - r0);
+  float* dst = out + (p * groups + g0) * (long long)n * C;
+  for (int e = threadIdx.x; e < ng * rows * C; e += blockDim.x) {
+    const int gl = e / (rows * C), rem = e % (rows * C), rr = rem / C, cc = rem % C;
+    dst[((long long)gl * n + r0 + rr) * C + cc] = tile[rr * (W + 1) + gl * C + cc];
+  }
+}
+
 // Reference-image term (Eq. min1, second norm): r_ref = b - a b/|b|, loss partials.
 __global__ void k_ref_residual(const float2* __restrict__ b, const float* __restrict__ aref,
                                long long n2, float2* __restrict__ rref, double* part,
@@ -354,6 +379,22 @@ cudaError_t launch_ref_residual(const float2* bref, const float* sqrt_dref, long
 
 cudaError_t launch_embed_edge(const float* a, int n, int P, float2* q, cudaStream_t s) {
   k_embed_edge<<<grid_for((long long)P * P), kThreads, 0, s>>>(a, n, P, q);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_block_data(const float* in, long long planes, int n, int C, float* out,
+                              cudaStream_t s) {
+  if (planes <= 0) return cudaSuccess;
+  const int W = C >= 64 ? C : 64;  // a multiple of C (C is 2^k or a power of two below 64)
+  const int groups = (n + C - 1) / C;
+  const dim3 grid((n + kBlkRows - 1) / kBlkRows, (groups * C + W - 1) / W, (unsigned)planes);
+  const size_t sm = (size_t)kBlkRows * (W + 1) * sizeof(float);
+  if (sm > 48 * 1024) {
+    cudaError_t e = cudaFuncSetAttribute(k_block_data, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)sm);
+    if (e != cudaSuccess) return e;
+  }
+  k_block_data<<<grid, kThreads, sm, s>>>(in, n, C, W, out);
   return cudaGetLastError();
 }
 

@@ -60,7 +60,11 @@ struct PassArgs {
   const float2* psi;           // [nk][n][n]
   const float2* pj;            // [J][P][P]  probe at the sample planes
   const float2* bref;          // [n][n]    C D_{zeta_0}(q)
-  const float* sqrt_d;         // [.][J][n][n], angle k stored at index k - data_k0
+  // data amplitudes in pass B's column-blocked layout [.][J][dgroups][n][C] (C = the pass-B
+  // column-group width): the C columns of a group are contiguous per row, so a warp's loads of
+  // consecutive rows of a group are one contiguous run.  Angle k is stored at index k - data_k0.
+  const float* dblk;
+  int dgroups;
   int data_k0;
   const float2* chirp_zhat;    // [J][P]
   float2* ybuf;                // per local plane: [ystride] (box rows x n)
@@ -134,6 +138,8 @@ cudaError_t launch_ref_residual(const float2* bref, const float* sqrt_dref, long
                                 float2* rref, double* part, int nblocks, int functional,
                                 cudaStream_t s);
 cudaError_t launch_embed_edge(const float* a, int n, int P, float2* q, cudaStream_t s);
+cudaError_t launch_block_data(const float* in, long long planes, int n, int C, float* out,
+                              cudaStream_t s);
 cudaError_t launch_bin_amplitudes(const float* in, long long count, int n, int b, float* out,
                                   cudaStream_t s);
 cudaError_t launch_upsample2(const float2* in, long long count, int N, float2* out,

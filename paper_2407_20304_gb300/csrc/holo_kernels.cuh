@@ -54,16 +54,6 @@ struct SmemHead {
   static constexpr int WORDS = ROOTS + CHIRP;
 };
 
-// Shared memory head of pass B: the full per-stage twiddle table (Fft<P>::TW entries, one
-// shared load per twiddle instead of a product tree of powers; pass B runs one block per SM
-// and has the room) and the half chirp table.
-template <int P>
-struct PassBHead {
-  static constexpr int TWF = (Fft<P>::TW + 1) & ~1;
-  static constexpr int CHIRP = SmemHead<P>::CHIRP;
-  static constexpr int WORDS = TWF + CHIRP;
-};
-
 // Lines per row block: about 256 threads, whole warps.
 __host__ __device__ constexpr int row_lines(int T, int g = 0) {
   return T >= 256 ? 1 : (g == 0 ? row_lines(T, 256 / T) : ((g * T) % 32 ? row_lines(T, g - 1) : g));
@@ -95,37 +85,6 @@ struct ColCfg {
   static constexpr size_t SMEM_BYTES = (size_t)(SmemHead<P>::WORDS + C * LS) * sizeof(float2);
   static constexpr size_t PASS_B_SMEM = SMEM_BYTES;
 };
-
-// w = R0(psi - ext) at one P-grid position from its row tap (iy0, fy) and column tap:
-// bilinear interpolation of psi - ext with taps outside the n x n domain dropped.
-__device__ __forceinline__ float2 resample_w(const float2* __restrict__ psi, int n, float ext,
-                                             int iy0, float fy, Tap xt) {
-  const int ix0 = xt.i0;
-  const float fx = xt.f;
-  const bool c0 = (unsigned)ix0 < (unsigned)n, c1 = (unsigned)(ix0 + 1) < (unsigned)n;
-  float2 w = make_float2(0.f, 0.f);
-#pragma unroll
-  for (int a = 0; a < 2; ++a) {
-    const int iy = iy0 + a;
-    if ((unsigned)iy >= (unsigned)n) continue;
-    const float wy = a ? fy : 1.f - fy;
-    const float2* row = psi + (long long)iy * n;
-    float2 s = make_float2(0.f, 0.f);
-    if (c0) {
-      const float2 p0 = __ldg(row + ix0);
-      s.x = fmaf(1.f - fx, p0.x - ext, s.x);
-      s.y = fmaf(1.f - fx, p0.y, s.y);
-    }
-    if (c1) {
-      const float2 p1 = __ldg(row + ix0 + 1);
-      s.x = fmaf(fx, p1.x - ext, s.x);
-      s.y = fmaf(fx, p1.y, s.y);
-    }
-    w.x = fmaf(wy, s.x, w.x);
-    w.y = fmaf(wy, s.y, w.y);
-  }
-  return w;
-}
 
 // Sum of per-thread FP64 values over the block; result valid in thread 0.
 __device__ __forceinline__ double block_sum_f64(double v, double* red) {
@@ -232,9 +191,10 @@ __global__ void __launch_bounds__(RowCfg<P>::NT, RowCfg<P>::MINB) k_pass_a(PassA
   float2* chs = smem + H::ROOTS;
   const int g = threadIdx.x / F::T, t = threadIdx.x % F::T;
   float2* sm = smem + H::WORDS + g * R::LS;
+  const int n = a.n, lo = P / 2 - n / 2;
+  float2* rmix = smem + H::WORDS + R::G * R::LS + g * n;  // [n] per line group
   load_roots<P>(roots, a.twiddles);
   const TwRoots tw{roots};
-  const int n = a.n, lo = P / 2 - n / 2;
   const int p_lo = a.k0 * a.J;
   int jcur = -1;
   for (int base = blockIdx.x * R::G; base < a.nlines; base += gridDim.x * R::G) {
@@ -254,13 +214,49 @@ __global__ void __launch_bounds__(RowCfg<P>::NT, RowCfg<P>::MINB) k_pass_a(PassA
     // table then follows the distance of the block's first line (block-uniform) and the
     // other lines read the chirp from global memory.
     const int jb = (__ldg(a.lines + a.line0 + base).x - p_lo) % a.J;
+    // the line's two object rows mixed with its row tap, into shared memory:
+    //   r[ix] = (1 - fy) (psi[iy0][ix] - ext) + fy (psi[iy0 + 1][ix] - ext)
+    // (rows outside psi dropped); the x-interpolation below reads r, so each object pixel
+    // costs two coalesced, independent loads instead of four dependent gathers per position
+    if (valid) {
+      const bool r0 = (unsigned)yt.i0 < (unsigned)n, r1 = (unsigned)(yt.i0 + 1) < (unsigned)n;
+      const float wy0 = 1.f - yt.f, wy1 = yt.f;
+      const float2* p0 = psi + (long long)(r0 ? yt.i0 : 0) * n;
+      const float2* p1 = psi + (long long)(r1 ? yt.i0 + 1 : 0) * n;
+      for (int ix = t; ix < n; ix += F::T) {
+        float2 r = make_float2(0.f, 0.f);
+        if (r0) {
+          const float2 q = __ldg(p0 + ix);
+          r.x = wy0 * (q.x - a.ext);
+          r.y = wy0 * q.y;
+        }
+        if (r1) {
+          const float2 q = __ldg(p1 + ix);
+          r.x = fmaf(wy1, q.x - a.ext, r.x);
+          r.y = fmaf(wy1, q.y, r.y);
+        }
+        rmix[ix] = r;
+      }
+    }
+    __syncthreads();
     float2 v[16];
 #pragma unroll
     for (int c = 0; c < 16; ++c) {
       const int X = F::pos(t, c), rel = X - d.bx0;
       float2 x = make_float2(0.f, 0.f);
       if (valid && (unsigned)rel < (unsigned)d.bxs) {
-        float2 w = resample_w(psi, n, a.ext, yt.i0, yt.f, xt[rel]);
+        const Tap xtp = xt[rel];
+        float2 w = make_float2(0.f, 0.f);
+        if ((unsigned)xtp.i0 < (unsigned)n) {
+          const float2 r = rmix[xtp.i0];
+          w.x = (1.f - xtp.f) * r.x;
+          w.y = (1.f - xtp.f) * r.y;
+        }
+        if ((unsigned)(xtp.i0 + 1) < (unsigned)n) {
+          const float2 r = rmix[xtp.i0 + 1];
+          w.x = fmaf(xtp.f, r.x, w.x);
+          w.y = fmaf(xtp.f, r.y, w.y);
+        }
         if (SHIFT) w.x += a.ext;  // full-grid form: w = R' psi
         wrow[rel] = w;
         x = cmul(__ldg(prow + X), w);
@@ -318,7 +314,7 @@ size_t pass_b_stage_bytes(int rows) {
 template <int P>
 size_t pass_b_smem(int n, int srows = 0) {
   const size_t base =
-      (size_t)(PassBHead<P>::WORDS + ColCfg<P>::C * ColCfg<P>::LS + 2 * n * ColCfg<P>::C) *
+      (size_t)(SmemHead<P>::WORDS + ColCfg<P>::C * ColCfg<P>::LS + 2 * n * ColCfg<P>::C) *
       sizeof(float2);
   return srows > 0 ? base + 128 + pass_b_stage_bytes<P>(srows) : base;
 }
@@ -346,20 +342,20 @@ template <int P, bool ADJ, bool SHIFT>
 __global__ void __launch_bounds__(ColCfg<P>::NT) k_pass_b(PassArgs a) {
   using F = Fft<P>;
   using Cc = ColCfg<P>;
-  using H = PassBHead<P>;
+  using H = SmemHead<P>;
   constexpr int C = Cc::C;
   extern __shared__ float2 smem[];
   __shared__ double red[32];
   __shared__ uint64_t ybar;
-  float2* tws = smem;
-  float2* chs = smem + H::TWF;
+  float2* roots = smem;
+  float2* chs = smem + H::ROOTS;
   const int g = threadIdx.x % C, t = threadIdx.x / C;
   float2* sm = smem + H::WORDS + g * Cc::LS;
   const int n = a.n, lo = P / 2 - n / 2;
   float2* sb = smem + H::WORDS + C * Cc::LS;
   float2* sS = sb + n * C;
-  load_twiddles<P>(tws, a.twiddles);
-  const TwTable tw{tws};
+  load_roots<P>(roots, a.twiddles);
+  const TwRoots tw{roots};
   const int ngroups = (n + C - 1) / C;
   double dsum = 0.0;
   int jcur = -1;
@@ -429,33 +425,13 @@ __global__ void __launch_bounds__(ColCfg<P>::NT) k_pass_b(PassArgs a) {
         }
         fft_fwd_with<P>(v, sm, tw, t, SyncBlock());
         // the data of the crop rows are fetched now, so the inverse transform hides their latency
-        const float* ad = a.sqrt_d + (gplane - (long long)a.data_k0 * a.J) * n * n;
+        const float* ad =
+            a.dblk + ((gplane - (long long)a.data_k0 * a.J) * a.dgroups + cg) * (long long)n * C;
         float dats[16];
 #pragma unroll
         for (int c = 0; c < 16; ++c) {
           const int rr = F::pos(t, c) - lo;
-          dats[c] = (valid && (unsigned)rr < (unsigned)n) ? __ldg(ad + (long long)rr * n + col) : 0.f;
-        }
-        // ... and the next item's data rows are prefetched into L2 (the group's columns share
-        // a sector per row; the rows are spread over the C threads of each position)
-        {
-          int nkl = kl + 1, nj = j, ncg = cg;
-          if (nkl == a.nk) {
-            nkl = 0;
-            if (++nj == a.J) {
-              nj = 0;
-              ncg += gridDim.x;
-            }
-          }
-          if (ncg < ngroups) {
-            const float* adn =
-                a.sqrt_d + ((long long)(a.k0 + nkl - a.data_k0) * a.J + nj) * n * n + ncg * C;
-#pragma unroll
-            for (int c = 0; c < 16; ++c) {
-              const int rr = F::pos(t, c) - lo;
-              if (c % C == g && (unsigned)rr < (unsigned)n) l2_prefetch(adn + (long long)rr * n);
-            }
-          }
+          dats[c] = (valid && (unsigned)rr < (unsigned)n) ? __ldg(ad + rr * C + g) : 0.f;
         }
         const float2* rmp = SHIFT ? a.ramp_y + gplane * P : nullptr;
 #pragma unroll
@@ -546,19 +522,19 @@ template <int P, bool ADJ, bool SHIFT>
 __global__ void __launch_bounds__(ColCfg<P>::NT) k_pass_b_split(PassArgs a) {
   using F = Fft<P>;
   using Cc = ColCfg<P>;
-  using H = PassBHead<P>;
+  using H = SmemHead<P>;
   constexpr int C = Cc::C;
   extern __shared__ float2 smem[];
   __shared__ double red[32];
-  float2* tws = smem;
-  float2* chs = smem + H::TWF;
+  float2* roots = smem;
+  float2* chs = smem + H::ROOTS;
   const int g = threadIdx.x % C, t = threadIdx.x / C;
   float2* sm = smem + H::WORDS + g * Cc::LS;
   const int n = a.n, lo = P / 2 - n / 2;
   float2* sb = smem + H::WORDS + C * Cc::LS;
   float2* sS = sb + n * C;
-  load_twiddles<P>(tws, a.twiddles);
-  const TwTable tw{tws};
+  load_roots<P>(roots, a.twiddles);
+  const TwRoots tw{roots};
   const int ngroups = (n + C - 1) / C;
   double dsum = 0.0;
   int jcur = -1;
@@ -593,12 +569,13 @@ __global__ void __launch_bounds__(ColCfg<P>::NT) k_pass_b_split(PassArgs a) {
     __syncthreads();
     fft_fwd_with<P>(v, sm, tw, t, SyncBlock());
     // the data of the crop rows are fetched now, so the inverse transform hides their latency
-    const float* ad = a.sqrt_d + (gplane - (long long)a.data_k0 * a.J) * n * n;
+    const float* ad =
+        a.dblk + ((gplane - (long long)a.data_k0 * a.J) * a.dgroups + cg) * (long long)n * C;
     float dats[16];
 #pragma unroll
     for (int c = 0; c < 16; ++c) {
       const int rr = F::pos(t, c) - lo;
-      dats[c] = (valid && (unsigned)rr < (unsigned)n) ? __ldg(ad + (long long)rr * n + col) : 0.f;
+      dats[c] = (valid && (unsigned)rr < (unsigned)n) ? __ldg(ad + rr * C + g) : 0.f;
     }
     const float2* rmp = SHIFT ? a.ramp_y + gplane * P : nullptr;
 #pragma unroll
@@ -901,17 +878,22 @@ cudaError_t launch_cols(const LineArgs& a, const float2* tw, cudaStream_t s) {
   return launch_lines<P, true>(a, tw, s);
 }
 
+// Pass A's shared memory: the row pass layout plus one mixed object row [n] per line.
+template <int P>
+size_t pass_a_smem(int n) {
+  return RowCfg<P>::SMEM_BYTES + (size_t)RowCfg<P>::G * n * sizeof(float2);
+}
+
 template <int P, bool SHIFT>
 cudaError_t launch_pass_a_form(const PassArgs& a, cudaStream_t s) {
   using R = RowCfg<P>;
   if (a.nlines <= 0) return cudaSuccess;
+  const size_t sm = pass_a_smem<P>(a.n);
   cudaError_t e = cudaFuncSetAttribute(k_pass_a<P, SHIFT>,
-                                       cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)R::SMEM_BYTES);
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
   if (e != cudaSuccess) return e;
-  const int nb = persistent_blocks(k_pass_a<P, SHIFT>, R::NT, R::SMEM_BYTES,
-                                   (a.nlines + R::G - 1) / R::G);
-  k_pass_a<P, SHIFT><<<nb, R::NT, R::SMEM_BYTES, s>>>(a);
+  const int nb = persistent_blocks(k_pass_a<P, SHIFT>, R::NT, sm, (a.nlines + R::G - 1) / R::G);
+  k_pass_a<P, SHIFT><<<nb, R::NT, sm, s>>>(a);
   return cudaGetLastError();
 }
 

@@ -60,7 +60,7 @@ __device__ __forceinline__ void tma_load_2d(void* dst, const void* map, int x, i
       : "memory");
 }
 
-// L2 prefetches (hints: nothing is written to shared memory and nothing waits on them).
+// L2 prefetch (a hint: nothing is written to shared memory and nothing waits on it):
 // l2_prefetch_bulk fetches the 16-byte-aligned hull of [p, p + bytes) with one bulk request;
 // the hull must lie inside one allocation (every buffer here starts 256-byte aligned and
 // has a size that is a multiple of 16 bytes).
@@ -70,10 +70,6 @@ __device__ __forceinline__ void l2_prefetch_bulk(const void* p, uint32_t bytes) 
       (reinterpret_cast<uintptr_t>(p) + bytes + 15) & ~static_cast<uintptr_t>(15);
   asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(a0), "r"((uint32_t)(a1 - a0))
                : "memory");
-}
-
-__device__ __forceinline__ void l2_prefetch(const void* p) {
-  asm volatile("prefetch.global.L2 [%0];" ::"l"(p));
 }
 
 }  // namespace holo

@@ -181,7 +181,8 @@ class Holo:
         if sqrt_dref is not None:
             pr = _ptr(sqrt_dref, torch.float32, (n, n), "sqrt_dref")
         _check(self.lib, self.ctx, self.lib.holo_set_data(self.ctx, pd, pr), "holo_set_data")
-        self._keep["data"] = (sqrt_d, sqrt_dref)
+        # the amplitudes are copied by the library; the reference image is used in place
+        self._keep["data"] = sqrt_dref
 
     def set_probe(self, q):
         """q: complex64 cuda [P][P]; computes p_j = D_{omega_j} q and C D_{zeta_0} q."""

@@ -71,8 +71,10 @@ def test_autograd_function_matches_oracle(recompute):
     assert rel(q.grad.cpu().numpy() / 3.0, gq) < 1e-4
 
 
-def test_autograd_finite_differences_at_differentiation_size():
-    from paper_2407_20304_gb300.autograd import holo_loss
+@pytest.fixture(scope="module")
+def diff_problem():
+    """The differentiation workload: psi 1024^2 (layered phantom) on 2048^2, 90 angles x 4
+    distances, striped probe, positive Poisson amplitudes of the workload's counts."""
     w = hs.workloads()["autograd"]
     n, P, K, J = w.n, w.P, w.n_angles, w.n_dist
     rng = hs.rng_for(w.seed, 0)
@@ -83,9 +85,56 @@ def test_autograd_finite_differences_at_differentiation_size():
     sqrt_d = hs.poisson_amplitude(sqrt_d.astype(np.float64) ** 2, w.counts, rng).astype(np.float32)
     sqrt_dref = base
     geo = oh.Geometry(G["wavelength"], G["pixel"], G["Z"], G["z"], n, P)
-    h = make_holo(geo, K, t, sqrt_d, sqrt_dref)
-    psi = torch.from_numpy(hs.object_stack(w, range(K), rng).astype(np.complex64)).cuda()
-    q = torch.from_numpy(hs.striped_probe(P, w.probe_sigma, rng).astype(np.complex64)).cuda()
+    psi = hs.object_stack(w, range(K), rng).astype(np.complex64)
+    q = hs.striped_probe(P, w.probe_sigma, rng).astype(np.complex64)
+    return dict(w=w, t=t, sqrt_d=sqrt_d, sqrt_dref=sqrt_dref, geo=geo, psi=psi, q=q)
+
+
+def test_autograd_matches_oracle_at_differentiation_size(diff_problem):
+    """HoloLoss at the differentiation workload's size against the FP64 oracle: psi.grad of
+    three sampled angles of the 90-angle evaluation against the oracle's per-plane terms (an
+    angle's gradient depends only on its own planes), and F2, psi.grad and q.grad of a 2-angle
+    problem (reference term included) against the oracle's full gradients."""
+    from paper_2407_20304_gb300.autograd import holo_loss
+    pr = diff_problem
+    geo, t, d, dr = pr["geo"], pr["t"], pr["sqrt_d"], pr["sqrt_dref"]
+    t64, d64, dr64 = t.astype(np.float64), d.astype(np.float64), dr.astype(np.float64)
+    q64 = pr["q"].astype(np.complex128)
+    K = pr["psi"].shape[0]
+    h = make_holo(geo, K, t, d, dr)
+    psi = torch.from_numpy(pr["psi"]).cuda().requires_grad_(True)
+    q = torch.from_numpy(pr["q"]).cuda().requires_grad_(True)
+    holo_loss(psi, q, h).backward()
+    gp = psi.grad.cpu().numpy()
+    h.close()
+    for k in (0, 45, 89):
+        ref = sum(oh.plane_gradient(pr["psi"][k].astype(np.complex128), q64, t64[k][j], d64[k, j],
+                                    geo, j)[1] for j in range(4))
+        e = rel(gp[k].astype(np.complex128), ref)
+        print(f"angle {k}: grad_psi relative L2 error {e:.2e}")
+        assert e < 1e-4
+    ks = [0, 45]
+    h2 = make_holo(geo, 2, np.ascontiguousarray(t[ks]), np.ascontiguousarray(d[ks]), dr)
+    psi2 = torch.from_numpy(np.ascontiguousarray(pr["psi"][ks])).cuda().requires_grad_(True)
+    q2 = torch.from_numpy(pr["q"]).cuda().requires_grad_(True)
+    loss = holo_loss(psi2, q2, h2, recompute=True)
+    loss.backward()
+    F, gp_ref, gq_ref = oh.gradients(pr["psi"][ks].astype(np.complex128), q64, t64[ks], d64[ks],
+                                     dr64, geo)
+    e = (abs(loss.item() - F) / F, rel(psi2.grad.cpu().numpy(), gp_ref),
+         rel(q2.grad.cpu().numpy(), gq_ref))
+    print(f"2-angle problem: loss {e[0]:.2e}, grad_psi {e[1]:.2e}, grad_q {e[2]:.2e}")
+    assert e[0] < 1e-5 and e[1] < 1e-4 and e[2] < 1e-4
+    h2.close()
+
+
+def test_autograd_finite_differences_at_differentiation_size(diff_problem):
+    from paper_2407_20304_gb300.autograd import holo_loss
+    pr = diff_problem
+    K = pr["psi"].shape[0]
+    h = make_holo(pr["geo"], K, pr["t"], pr["sqrt_d"], pr["sqrt_dref"])
+    psi = torch.from_numpy(pr["psi"]).cuda()
+    q = torch.from_numpy(pr["q"]).cuda()
     psi.requires_grad_(True)
     q.requires_grad_(True)
     loss = holo_loss(psi, q, h)

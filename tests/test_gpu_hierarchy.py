@@ -46,9 +46,10 @@ def test_upsampling_matches_oracle(n, count):
 
 
 def test_hierarchy_follows_the_oracle():
-    """Three levels (bin 4, 2, 1) of 3 iterations each: the first level's F history matches the
-    FP64 driver's, every level is monotone, and the final F agrees to a few per cent (FP32
-    line-search decisions may part from FP64 ones at near-ties and the levels compound)."""
+    """Three levels (bin 4, 2, 1) of 3 iterations each: every level is monotone and its whole F
+    history matches the FP64 driver's to 1e-4 relative, i.e. the FP32 driver takes the same
+    line-search decisions on every level (FP32 wavefields put F within about 1e-5 of the FP64
+    value on this seeded problem, far from any near-tie), and the final F agrees to 1e-4."""
     from paper_2407_20304_gb300.hierarchy import Hierarchy
     n, P, K, J = 64, 128, 2, 4
     rng = hs.rng_for(hs.SEED_BASE + 11, 0)
@@ -69,10 +70,9 @@ def test_hierarchy_follows_the_oracle():
         F, Fo = np.array(mine["history"]["F"]), np.array(theirs["hist"]["F"])
         print(f"level b={mine['b']}: F gpu {F} oracle {Fo}")
         assert np.all(np.diff(F) <= 0)
-        if lvl == 0:
-            np.testing.assert_allclose(F[:2], Fo[:2], rtol=1e-4)
+        np.testing.assert_allclose(F, Fo, rtol=1e-4)
     Fl, Fol = hier.results[-1]["history"]["F"][-1], ref[-1]["hist"]["F"][-1]
-    assert abs(Fl - Fol) / Fol < 5e-2
+    assert abs(Fl - Fol) / Fol < 1e-4
 
 
 def test_hierarchy_with_probe_shifts_follows_the_oracle():
@@ -97,6 +97,7 @@ def test_hierarchy_with_probe_shifts_follows_the_oracle():
                                        t, geo, levels, probe_shifts=s)
     for lvl, (mine, theirs) in enumerate(zip(hier.results, ref)):
         F, Fo = np.array(mine["history"]["F"]), np.array(theirs["hist"]["F"])
+        print(f"probe shifts, level b={mine['b']}: F gpu {F} oracle {Fo}")
         assert np.all(np.diff(F) <= 0)
         if lvl == 0:
             np.testing.assert_allclose(F[:2], Fo[:2], rtol=1e-4)

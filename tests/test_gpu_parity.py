@@ -384,3 +384,18 @@ def test_state_and_argument_errors():
     assert h.lib.holo_set_functional(h.ctx, 7) == 1      # HOLO_ERR_ARG
     with pytest.raises(KeyError):
         h.set_functional("phase")
+
+
+def test_set_data_copies_the_amplitudes():
+    """holo_set_data copies the amplitudes (into the column pass's blocked layout): the
+    caller may overwrite its buffer after the call without changing the results."""
+    pr = make_problem(96, 192, 2, seed=23, point="object")
+    h = make_holo(pr)
+    psi = dev(pr["psi"], torch.complex64)
+    ref = h.gradient(psi)
+    d = dev(pr["sqrt_d"], torch.float32)
+    h.set_data(d, dev(pr["sqrt_dref"], torch.float32))
+    d.fill_(7.0)
+    again = h.gradient(psi)
+    assert again[0] == ref[0]
+    assert torch.equal(again[1], ref[1]) and torch.equal(again[2], ref[2])
