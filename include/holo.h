@@ -278,6 +278,50 @@ holo_status holo_dot_noalloc(const void* a, const void* b, long long n_c64, doub
  * captured CUDA graph.  The caller orders it against work already issued. */
 holo_status holo_set_stream(holo_ctx* ctx, void* stream);
 
+/* Schedule of the context's passes (an autotuner's knobs; results do not depend on the first
+ * two, the third changes only the summation order of grad_q's residual sum and the loss):
+ *   row_blocks_per_sm  resident blocks per SM of the row passes A and C (0: as many as fit);
+ *   pass_b_stage       pass B's TMA staging of its input tiles: -1 where it fits (default),
+ *                      0 off (plain loads), 1 same as -1;
+ *   pass_b_split       pass B's plane-split form for small problems: -1 automatic (default),
+ *                      0 never (whole column groups per block), 1 whenever the last round of
+ *                      column groups is partial.
+ * HOLO_ERR_ARG for values outside these ranges. */
+holo_status holo_set_schedule(holo_ctx* ctx, int row_blocks_per_sm, int pass_b_stage,
+                              int pass_b_split);
+
+/* Batched evaluation of independent problems (Sec. 4: independent angle chunks; here problems
+ * of uneven sizes on one GPU), each an existing context with shifts and data set.  One batch
+ * gradient evaluates, for every problem, the probe propagation and F2, grad_psi and grad_q
+ * over all its angles (in chunks of the context's chunk size, summed like holo_gradient with
+ * HOLO_ACCUMULATE_Q).  Passes A-D of the chunks of all problems run as persistent launches
+ * that walk device work lists of (problem, work item) entries, one launch per pass and line
+ * length (pass D: one for all); the reductions and the grad_q propagations run per problem.
+ * Every problem's results equal bit for bit those of its own holo_set_probe + holo_gradient
+ * calls with the same schedule (holo_batch_prepare sets pass_b_split = 0 on every context:
+ * the batched column pass works on whole column groups).
+ *   holo_batch_create   keeps the array of `count` contexts (not owned; they must outlive
+ *                       the batch);
+ *   holo_batch_set_problem  the device buffers of problem i: psi [n_angles][n][n], q [P][P]
+ *                       (complex64, read), grad_psi [n_angles][n][n] and grad_q [P][P]
+ *                       (written);
+ *   holo_batch_prepare  builds and uploads the work lists (allocates; synchronous); again
+ *                       after any set_problem, holo_set_schedule or holo_set_shifts;
+ *   holo_batch_gradient issues one evaluation of every problem on `stream` (a cudaStream_t,
+ *                       NULL: the legacy stream; every context is switched to it).  Nothing
+ *                       is allocated and the host does not wait, so the call can be captured
+ *                       into a CUDA graph.  Losses: holo_read_loss of each context afterwards.
+ *                       HOLO_ERR_STATE before prepare.  A bounded wait that gives up sets
+ *                       every problem's error word (reported by its next loss read).
+ *   holo_batch_destroy  frees the work lists (NULL accepted). */
+typedef struct holo_batch holo_batch;
+holo_status holo_batch_create(holo_ctx* const* ctxs, int count, holo_batch** out);
+holo_status holo_batch_set_problem(holo_batch* b, int i, const void* psi, const void* q,
+                                   void* grad_psi, void* grad_q);
+holo_status holo_batch_prepare(holo_batch* b);
+holo_status holo_batch_gradient(holo_batch* b, void* stream);
+holo_status holo_batch_destroy(holo_batch* b);
+
 /* F2 accumulated on the device: the loss of the last forward / gradient evaluation
  * (including the reference term when it had k0 == 0), plus the earlier ones since the
  * last evaluation issued without HOLO_ACCUMULATE / HOLO_ACCUMULATE_Q.  Read after

@@ -27,7 +27,9 @@ EXPORTS = ("holo_create", "holo_destroy", "holo_set_shifts", "holo_set_probe_shi
            "holo_initial_probe", "holo_bin_amplitudes", "holo_upsample2", "holo_set_timing",
            "holo_get_timing", "holo_dot_noalloc",
            "holo_set_stream", "holo_read_loss", "holo_set_device_error",
-           "holo_workspace_bytes", "holo_launch_count", "holo_status_string", "holo_last_error")
+           "holo_workspace_bytes", "holo_launch_count", "holo_status_string", "holo_last_error",
+           "holo_set_schedule", "holo_batch_create", "holo_batch_set_problem",
+           "holo_batch_prepare", "holo_batch_gradient", "holo_batch_destroy")
 
 # Pass ids of holo_get_timing (HOLO_T_* in include/holo.h).
 TIMERS = ("probe", "pass_a", "pass_b", "pass_c", "pass_d", "qgrad", "reduce", "vector")
@@ -84,6 +86,12 @@ def _signatures():
         "holo_get_timing": [P, P, P],
         "holo_workspace_bytes": [P, ctypes.POINTER(LL)],
         "holo_launch_count": [P, ctypes.POINTER(LL)],
+        "holo_set_schedule": [P, I, I, I],
+        "holo_batch_create": [ctypes.POINTER(P), I, ctypes.POINTER(P)],
+        "holo_batch_set_problem": [P, I, P, P, P, P],
+        "holo_batch_prepare": [P],
+        "holo_batch_gradient": [P, P],
+        "holo_batch_destroy": [P],
     }
 
 

@@ -1,5 +1,17 @@
 """Many independent reconstructions of uneven sizes evaluated by one CUDA-graph launch.
 
+Two ways of issuing a batch evaluation are kept side by side:
+* the persistent form (`prepare_persistent`, `capture_persistent`): the library's batch
+  object (holo_batch_*) runs passes A-D of every round of chunks of all problems as persistent
+  launches that walk device work lists of (problem, item) entries, one launch per pass and
+  line length, captured once into a CUDA graph; `autotune_persistent` picks, per line length,
+  the row passes' resident blocks per SM and pass B's TMA staging (coordinate descent, each
+  candidate timed by graph replays);
+* the per-problem form below: each problem's own launches, as a loop on one stream or
+  captured into a graph whose branches run problems concurrently.
+Both give every problem exactly the results of its own calls with the same schedule.
+
+
 Each instance is its own problem (geometry, angles, distances, data, psi, q) with its own
 library context; one evaluation of an instance is the probe propagation and the gradient
 of F2 over all its angles (in chunks of the context's chunk size, the chunks summing
@@ -15,9 +27,12 @@ and keeps the fastest.  Results do not depend on the schedule (every kernel is
 deterministic and instances share no buffers).
 """
 
+import ctypes
 import time
 
 import torch
+
+from . import _lib
 
 
 class Instance:
@@ -54,6 +69,9 @@ class HoloBatch:
         self.graph = None
         self.schedule = None
         self.tuning = {}
+        self._pb = None          # holo_batch handle of the persistent form
+        self.pgraph = None
+        self.ptuning = {}
 
     @property
     def planes(self):
@@ -150,3 +168,81 @@ class HoloBatch:
                 best = (ms, sched)
         self.capture(best[1])
         return best[0], best[1], cost
+
+    # ------------------------------------------------------------------ persistent form
+    def _check(self, st, where):
+        if st != 0:
+            raise _lib.HoloError(st, where, _lib.load().holo_last_error(self.inst[0].h.ctx).decode())
+
+    def prepare_persistent(self):
+        """Create (once) the library's batch over every instance, register the instances'
+        buffers and build the work lists (this sets pass_b_split = 0 on every context, so the
+        per-problem loop gives the same results)."""
+        lib = _lib.load()
+        if self._pb is None:
+            arr = (ctypes.c_void_p * len(self.inst))(*[it.h.ctx.value for it in self.inst])
+            out = ctypes.c_void_p()
+            self._check(lib.holo_batch_create(arr, len(self.inst), ctypes.byref(out)),
+                        "holo_batch_create")
+            self._pb = out
+        for i, it in enumerate(self.inst):
+            self._check(lib.holo_batch_set_problem(
+                self._pb, i, ctypes.c_void_p(it.psi.data_ptr()), ctypes.c_void_p(it.q.data_ptr()),
+                ctypes.c_void_p(it.grad_psi.data_ptr()), ctypes.c_void_p(it.grad_q.data_ptr())),
+                "holo_batch_set_problem")
+        self._check(lib.holo_batch_prepare(self._pb), "holo_batch_prepare")
+
+    def issue_persistent(self):
+        """Issue one persistent-form evaluation of the whole batch on the current stream."""
+        st = _lib.load().holo_batch_gradient(
+            self._pb, ctypes.c_void_p(torch.cuda.current_stream().cuda_stream))
+        self._check(st, "holo_batch_gradient")
+
+    def capture_persistent(self):
+        torch.cuda.synchronize()
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g, stream=self.main):
+            self.issue_persistent()
+        self.pgraph = g
+        return g
+
+    def replay_persistent(self):
+        with torch.cuda.stream(self.main):
+            self.pgraph.replay()
+
+    def line_lengths(self):
+        return sorted({it.h.P for it in self.inst}, reverse=True)
+
+    def autotune_persistent(self, candidates=((0, -1), (2, -1), (0, 0), (2, 0)), reps=2):
+        """Per line length, the (row blocks per SM, pass-B stage) schedule whose captured
+        persistent graph evaluates the whole batch fastest, by coordinate descent from the
+        first candidate (line lengths in decreasing order).  Returns (ms, {P: schedule})."""
+        chosen = {P: candidates[0] for P in self.line_lengths()}
+
+        def apply(sched):
+            for it in self.inst:
+                rb, stage = sched[it.h.P]
+                it.h.set_schedule(rb, stage, 0)
+            self.prepare_persistent()
+            self.capture_persistent()
+            self.replay_persistent()
+            return self._time(self.replay_persistent, reps)
+
+        best = apply(chosen)
+        self.ptuning = {"start": best}
+        for P in self.line_lengths():
+            for cand in candidates[1:]:
+                trial = dict(chosen)
+                trial[P] = cand
+                ms = apply(trial)
+                self.ptuning[f"P={P} {cand}"] = ms
+                if ms < best:
+                    best, chosen = ms, trial
+        apply(chosen)
+        return best, chosen
+
+    def close(self):
+        if self._pb is not None:
+            _lib.load().holo_batch_destroy(self._pb)
+            self._pb = None
+

@@ -78,6 +78,9 @@ struct holo_ctx {
   float ext = 1.f;
   double wref = 0.0;
   int functional = HOLO_F2_AMPLITUDE;
+  // schedule (holo_set_schedule): row-pass blocks per SM (0: as many as fit), pass-B Y stage
+  // and plane-split form (-1: automatic, 0: off, 1: on where applicable)
+  int sched_row_per_sm = 0, sched_stage = -1, sched_split = -1;
   cudaStream_t stream = nullptr;
   // holo_gradient_host in parts: copy streams and their events (created on first use)
   cudaStream_t cs_in = nullptr, cs_out = nullptr;
@@ -523,7 +526,8 @@ PassArgs pass_args(holo_ctx* c, int k0, int nk, const void* psi) {
   a.line0 = c->rowstart[(size_t)k0 * c->J];
   a.nlines = c->rowstart[(size_t)(k0 + nk) * c->J] - a.line0;
   a.pass_b_items = c->ops->pass_b_groups(c->n);
-  a.ymap = c->ystage ? c->d_ymap : nullptr;
+  a.ymap = c->ystage && c->sched_stage != 0 ? c->d_ymap : nullptr;
+  a.row_per_sm = c->sched_row_per_sm;
   a.yrows = (int)(c->ystride / c->n);
   a.err = reinterpret_cast<unsigned long long*>(c->d_red + kErrWord);
   if (c->probe_shift) {
@@ -549,7 +553,8 @@ PassArgs pass_args(holo_ctx* c, int k0, int nk, const void* psi) {
 holo_status pass_b_grid(holo_ctx* c, PassArgs& a, bool gradient, int* nblocks) {
   const int groups = a.pass_b_items;
   const int full = c->ops->pass_b_blocks(1 << 30, c->n, a.ymap ? a.max_box_rows : 0);
-  a.pb_split = groups % full != 0 && groups / full < 3;
+  a.pb_split = c->sched_split < 0 ? (groups % full != 0 && groups / full < 3)
+                                  : (c->sched_split > 0 && groups % full != 0);
   a.tslots = 0;
   if (!a.pb_split) {
     *nblocks = std::min(full, groups);
@@ -1390,6 +1395,17 @@ holo_status holo_set_functional(holo_ctx* c, int functional) {
   return HOLO_OK;
 }
 
+holo_status holo_set_schedule(holo_ctx* c, int row_blocks_per_sm, int pass_b_stage,
+                              int pass_b_split) {
+  if (!c || row_blocks_per_sm < 0 || pass_b_stage < -1 || pass_b_stage > 1 || pass_b_split < -1 ||
+      pass_b_split > 1)
+    return fail(c, HOLO_ERR_ARG, "schedule: blocks per SM >= 0, stage and split in {-1, 0, 1}");
+  c->sched_row_per_sm = row_blocks_per_sm;
+  c->sched_stage = pass_b_stage;
+  c->sched_split = pass_b_split;
+  return HOLO_OK;
+}
+
 holo_status holo_set_stream(holo_ctx* c, void* stream) {
   if (!c) return HOLO_ERR_ARG;
   c->stream = (cudaStream_t)stream;
@@ -1428,3 +1444,221 @@ holo_status holo_launch_count(const holo_ctx* c, long long* count) {
 }
 
 }  // extern "C"
+
+// ------------------------------------------------------------------ batched evaluation
+
+// Work lists of one round of a batch: the r-th chunk of every problem that has one.  Problems
+// of one line length (and probe-shift form) share the launches of passes A, B and C; pass D
+// has one launch for all.  Items are {index into the round's PassArgs, work index}.
+struct BatchGroup {
+  const holo::Ops* ops = nullptr;
+  int shift = 0, max_n = 0, max_rows = 0, per_sm = 0;
+  std::vector<int2> rows, cols;  // pass A / C: {arg, first line}; pass B: {arg, block}
+  size_t off_rows = 0, off_cols = 0;
+};
+
+struct BatchRound {
+  std::vector<int> prob;          // problem of each PassArgs
+  std::vector<PassArgs> args;     // host copies (also used for the per-problem launches)
+  std::vector<int> nbx;           // pass-B grid of each
+  std::vector<BatchGroup> groups;
+  std::vector<int2> dits;         // pass D: {arg, kl * n + i}
+  size_t off_args = 0, off_dits = 0;
+};
+
+struct holo_batch {
+  std::vector<holo_ctx*> ctx;
+  struct Buffers {
+    const float2* psi = nullptr;
+    const float2* q = nullptr;
+    float2* gpsi = nullptr;
+    float2* gq = nullptr;
+  };
+  std::vector<Buffers> buf;
+  std::vector<BatchRound> rounds;
+  void* dmem = nullptr;           // every round's PassArgs and items, one allocation
+  size_t dbytes = 0;
+  bool prepared = false;
+};
+
+namespace {
+
+size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
+
+}  // namespace
+
+extern "C" {
+
+holo_status holo_batch_create(holo_ctx* const* ctxs, int count, holo_batch** out) {
+  if (!out) return HOLO_ERR_ARG;
+  *out = nullptr;
+  if (!ctxs || count < 1) return HOLO_ERR_ARG;
+  for (int i = 0; i < count; ++i)
+    if (!ctxs[i]) return HOLO_ERR_ARG;
+  holo_batch* b = new holo_batch();
+  b->ctx.assign(ctxs, ctxs + count);
+  b->buf.resize(count);
+  *out = b;
+  return HOLO_OK;
+}
+
+holo_status holo_batch_set_problem(holo_batch* b, int i, const void* psi, const void* q,
+                                   void* grad_psi, void* grad_q) {
+  if (!b || i < 0 || i >= (int)b->ctx.size() || !psi || !q || !grad_psi || !grad_q)
+    return HOLO_ERR_ARG;
+  b->buf[i] = {static_cast<const float2*>(psi), static_cast<const float2*>(q),
+               static_cast<float2*>(grad_psi), static_cast<float2*>(grad_q)};
+  b->prepared = false;
+  return HOLO_OK;
+}
+
+holo_status holo_batch_destroy(holo_batch* b) {
+  if (!b) return HOLO_OK;
+  if (b->dmem) cudaFree(b->dmem);
+  delete b;
+  return HOLO_OK;
+}
+
+holo_status holo_batch_prepare(holo_batch* b) {
+  if (!b) return HOLO_ERR_ARG;
+  holo_ctx* c0 = b->ctx[0];
+  b->prepared = false;
+  b->rounds.clear();
+  int nround = 0;
+  for (size_t i = 0; i < b->ctx.size(); ++i) {
+    holo_ctx* c = b->ctx[i];
+    if (!b->buf[i].psi) return fail(c0, HOLO_ERR_STATE, "batch: problem buffers not set");
+    if (!c->have_shifts || !c->have_data)
+      return fail(c0, HOLO_ERR_STATE, "batch: a problem has no shifts or data");
+    c->sched_split = 0;  // the batched column pass works on whole column groups
+    nround = std::max(nround, (c->K + c->chunk - 1) / c->chunk);
+  }
+  size_t off = 0;
+  b->rounds.resize(nround);
+  for (int r = 0; r < nround; ++r) {
+    BatchRound& R = b->rounds[r];
+    for (size_t i = 0; i < b->ctx.size(); ++i) {
+      holo_ctx* c = b->ctx[i];
+      const int k0 = r * c->chunk;
+      if (k0 >= c->K) continue;
+      const int nk = std::min(c->chunk, c->K - k0);
+      const size_t n2 = (size_t)c->n * c->n;
+      PassArgs a = pass_args(c, k0, nk, b->buf[i].psi + (size_t)k0 * n2);
+      a.grad_psi = b->buf[i].gpsi + (size_t)k0 * n2;
+      a.accumulate = 0;
+      if (k0 == 0 && c->wref != 0.0) a.rref = c->d_rref;
+      int nbx = 0;
+      holo_status st = pass_b_grid(c, a, true, &nbx);
+      if (st) return st;
+      a.pb_blocks = nbx;
+      const int ai = (int)R.args.size();
+      R.prob.push_back((int)i);
+      R.args.push_back(a);
+      R.nbx.push_back(nbx);
+      const int shift = a.ramp_x != nullptr;
+      BatchGroup* g = nullptr;
+      for (auto& x : R.groups)
+        if (x.ops == c->ops && x.shift == shift) g = &x;
+      if (!g) {
+        R.groups.emplace_back();
+        g = &R.groups.back();
+        g->ops = c->ops;
+        g->shift = shift;
+        g->per_sm = c->sched_row_per_sm;
+      }
+      g->max_n = std::max(g->max_n, c->n);
+      if (a.ymap) g->max_rows = std::max(g->max_rows, a.max_box_rows);
+      for (int base = 0; base < a.nlines; base += c->ops->row_lines) g->rows.push_back({ai, base});
+      for (int blk = 0; blk < nbx; ++blk) g->cols.push_back({ai, blk});
+      for (int e = 0; e < nk * c->n; ++e) R.dits.push_back({ai, e});
+    }
+    R.off_args = off = align_up(off, 256);
+    off += sizeof(PassArgs) * R.args.size();
+    for (auto& g : R.groups) {
+      g.off_rows = off = align_up(off, 256);
+      off += sizeof(int2) * g.rows.size();
+      g.off_cols = off = align_up(off, 256);
+      off += sizeof(int2) * g.cols.size();
+    }
+    R.off_dits = off = align_up(off, 256);
+    off += sizeof(int2) * R.dits.size();
+  }
+  std::vector<char> host(off);
+  for (auto& R : b->rounds) {
+    std::memcpy(host.data() + R.off_args, R.args.data(), sizeof(PassArgs) * R.args.size());
+    for (auto& g : R.groups) {
+      std::memcpy(host.data() + g.off_rows, g.rows.data(), sizeof(int2) * g.rows.size());
+      std::memcpy(host.data() + g.off_cols, g.cols.data(), sizeof(int2) * g.cols.size());
+    }
+    std::memcpy(host.data() + R.off_dits, R.dits.data(), sizeof(int2) * R.dits.size());
+  }
+  if (off > b->dbytes) {
+    if (b->dmem) cudaFree(b->dmem);
+    b->dmem = nullptr;
+    b->dbytes = 0;
+    if (cudaMalloc(&b->dmem, off) != cudaSuccess) {
+      cudaGetLastError();
+      return fail(c0, HOLO_ERR_OOM, "batch work lists");
+    }
+    b->dbytes = off;
+  }
+  HOLO_CK(c0, cudaMemcpy(b->dmem, host.data(), off, cudaMemcpyHostToDevice));
+  b->prepared = true;
+  return HOLO_OK;
+}
+
+}  // extern "C"
+
+extern "C" holo_status holo_batch_gradient(holo_batch* b, void* stream) {
+  if (!b) return HOLO_ERR_ARG;
+  holo_ctx* c0 = b->ctx[0];
+  if (!b->prepared) return fail(c0, HOLO_ERR_STATE, "batch: holo_batch_prepare not called");
+  const cudaStream_t s = static_cast<cudaStream_t>(stream);
+  holo_status st;
+  for (size_t i = 0; i < b->ctx.size(); ++i) {
+    b->ctx[i]->stream = s;
+    if ((st = holo_set_probe(b->ctx[i], b->buf[i].q))) return st;
+  }
+  static int sms = 0;
+  if (!sms) {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
+      cudaGetLastError();
+      sms = 1;
+    }
+  }
+  char* dm = static_cast<char*>(b->dmem);
+  for (size_t r = 0; r < b->rounds.size(); ++r) {
+    BatchRound& R = b->rounds[r];
+    const PassArgs* dargs = reinterpret_cast<const PassArgs*>(dm + R.off_args);
+    const int acc = r > 0 ? 1 : 0;
+    const int na = (int)R.args.size();
+    for (int ai = 0; ai < na; ++ai) {
+      PassArgs a = R.args[ai];
+      if ((st = eval_begin(b->ctx[R.prob[ai]], a))) return st;
+    }
+    for (auto& g : R.groups)
+      HOLO_CK(c0, g.ops->rows_multi(0, dargs, reinterpret_cast<const int2*>(dm + g.off_rows),
+                                    (int)g.rows.size(), g.shift, g.max_n, g.per_sm, s));
+    for (auto& g : R.groups)
+      HOLO_CK(c0, g.ops->pass_b_multi(dargs, reinterpret_cast<const int2*>(dm + g.off_cols),
+                                      (int)g.cols.size(), na, 1, g.shift, g.max_n, g.max_rows, 0,
+                                      s));
+    for (int ai = 0; ai < na; ++ai) {
+      holo_ctx* c = b->ctx[R.prob[ai]];
+      HOLO_LAUNCH(c, holo::launch_sum_f64(c->d_part, R.nbx[ai], c->d_red, 0, s));
+      HOLO_LAUNCH(c, holo::launch_loss_total(c->d_red, c->wref, acc, 1, s));
+    }
+    for (auto& g : R.groups)
+      HOLO_CK(c0, g.ops->rows_multi(1, dargs, reinterpret_cast<const int2*>(dm + g.off_rows),
+                                    (int)g.rows.size(), g.shift, g.max_n, g.per_sm, s));
+    HOLO_CK(c0, holo::launch_pass_d_multi(dargs, reinterpret_cast<const int2*>(dm + R.off_dits),
+                                          (int)R.dits.size(), 16 * sms, s));
+    for (int ai = 0; ai < na; ++ai) {
+      const int i = R.prob[ai];
+      if ((st = eval_qgrad(b->ctx[i], R.args[ai], b->buf[i].gq, acc))) return st;
+    }
+  }
+  return HOLO_OK;
+}

@@ -17,8 +17,9 @@ constexpr int kThreads = 256;
 // One block per (psi row i, angle kl): the transposed row taps of every distance are read
 // once into shared memory, then each thread sums its column pairs over j with all the
 // 16-byte loads of one pair issued together.  h rows start on 16-byte boundaries (n even).
-__global__ void __launch_bounds__(256) k_pass_d(PassArgs a) {
-  const int n = a.n, i = blockIdx.x, kl = blockIdx.y;
+// (One psi row of one angle; the block-shared row table is filled, synchronised and read.)
+__device__ __forceinline__ void pass_d_row(const PassArgs& a, int i, int kl) {
+  const int n = a.n;
   __shared__ const float4* row[HOLO_MAX_DIST];
   __shared__ float w0s[HOLO_MAX_DIST], w1s[HOLO_MAX_DIST];
   if (threadIdx.x < a.J) {
@@ -64,6 +65,21 @@ __global__ void __launch_bounds__(256) k_pass_d(PassArgs a) {
     }
     out[2 * p] = r0;
     out[2 * p + 1] = r1;
+  }
+}
+
+__global__ void __launch_bounds__(256) k_pass_d(const __grid_constant__ PassArgs a) {
+  pass_d_row(a, blockIdx.x, blockIdx.y);
+}
+
+// Pass D of several problems in one persistent launch: items {problem, kl * n + i}.
+__global__ void __launch_bounds__(256) k_pass_d_multi(const PassArgs* __restrict__ args,
+                                                      const int2* __restrict__ items, int nitems) {
+  for (int it = blockIdx.x; it < nitems; it += gridDim.x) {
+    const int2 item = items[it];
+    const PassArgs& a = args[item.x];
+    __syncthreads();  // the previous item's row table has been read
+    pass_d_row(a, item.y % a.n, item.y / a.n);
   }
 }
 
@@ -358,6 +374,13 @@ int grid_for(long long n) {
 cudaError_t launch_pass_d(const PassArgs& a, cudaStream_t s) {
   dim3 grid(a.n, a.nk);
   k_pass_d<<<grid, 256, 0, s>>>(a);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_pass_d_multi(const PassArgs* args, const int2* items, int nitems, int nblocks,
+                                cudaStream_t s) {
+  if (nitems <= 0) return cudaSuccess;
+  k_pass_d_multi<<<nblocks < nitems ? nblocks : nitems, 256, 0, s>>>(args, items, nitems);
   return cudaGetLastError();
 }
 

@@ -96,6 +96,8 @@ struct PassArgs {
   const int2* lines;           // [total box rows of all planes]
   int line0, nlines;           // the chunk's lines: [line0, line0 + nlines)
   int pass_b_items;            // column groups of pass B
+  int pb_blocks;               // pass-B grid of this problem (items of k_pass_b_multi)
+  int row_per_sm;              // row passes: resident blocks per SM (0: as many as fit)
   // pass B stages each plane's Y tile [box rows][C columns] into shared memory by TMA
   // while the previous plane computes: tensor map over ybuf as a [planes * yrows][2n] float
   // matrix (box 2C x kStageBox), or null for plain loads
@@ -126,12 +128,24 @@ struct Ops {
   int (*pass_b_stage_ok)(int n, int rows);  // 1: pass B may stage Y tiles of `rows` rows
   int twiddle_count;
   int pass_b_cols;                          // columns per pass-B group (C)
+  int row_lines;                            // lines per block of the row passes (G)
+  // several problems of this line length in one persistent launch (args, items in device
+  // memory; see k_pass_a_multi / k_pass_b_multi / k_pass_c_multi).  per_sm caps the resident
+  // blocks per SM (0: as many as fit); max_n / max_rows size the shared memory for the
+  // largest problem.
+  cudaError_t (*rows_multi)(int pass_c, const PassArgs* args, const int2* items, int nitems,
+                            int shift, int max_n, int per_sm, cudaStream_t);
+  cudaError_t (*pass_b_multi)(const PassArgs* args, const int2* items, int nitems, int nprob,
+                              int adj, int shift, int max_n, int max_rows, int per_sm,
+                              cudaStream_t);
 };
 
 const Ops* ops_for(int P);
 
 // Line-length independent kernels (holo_common.cu).
 cudaError_t launch_pass_d(const PassArgs& a, cudaStream_t s);
+cudaError_t launch_pass_d_multi(const PassArgs* args, const int2* items, int nitems, int nblocks,
+                                cudaStream_t s);
 cudaError_t launch_reduce_g(const PassArgs& a, float2* Gp, int j, int row0, int nrows, int col0,
                             int ncols, cudaStream_t s);
 cudaError_t launch_ref_residual(const float2* bref, const float* sqrt_dref, long long n2,

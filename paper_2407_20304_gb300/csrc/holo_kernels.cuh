@@ -181,23 +181,36 @@ __device__ __forceinline__ void ensure_chirp(float2* chs, const float2* __restri
 
 // ------------------------------------------------------------------ pass A
 
-template <int P, bool SHIFT>
-__global__ void __launch_bounds__(RowCfg<P>::NT, RowCfg<P>::MINB) k_pass_a(PassArgs a) {
+// Chirp table of distance j of problem `key` resident in shared memory: loaded unless the
+// block's resident table already is that one (block-uniform arguments).
+template <int P>
+__device__ __forceinline__ void ensure_chirp_key(float2* chs, const float2* __restrict__ tables,
+                                                 int j, int key, int& cur) {
+  if (key != cur) {
+    __syncthreads();
+    load_chirp_half<P>(chs, tables + (long long)j * P);
+    cur = key;
+  }
+}
+
+// One block-step of pass A: the lines [base, base + G) of the problem `a` (indices relative
+// to a.line0; lines past a.nlines are idle), one line per thread group.  `next` is the base of
+// the block's next step in the same problem (its lines are prefetched into L2), or -1.  The
+// resident chirp table is identified by pkey * 16 + distance (pkey: the problem's index in a
+// batch, 0 for a single problem).
+template <int P, bool SHIFT, class Args>
+__device__ __forceinline__ void pass_a_step(const Args& a, int base, int next, float2* smem,
+                                            const TwRoots& tw, int pkey, int& jcur) {
   using F = Fft<P>;
   using R = RowCfg<P>;
   using H = SmemHead<P>;
-  extern __shared__ float2 smem[];
-  float2* roots = smem;
   float2* chs = smem + H::ROOTS;
   const int g = threadIdx.x / F::T, t = threadIdx.x % F::T;
   float2* sm = smem + H::WORDS + g * R::LS;
   const int n = a.n, lo = P / 2 - n / 2;
   float2* rmix = smem + H::WORDS + R::G * R::LS + g * n;  // [n] per line group
-  load_roots<P>(roots, a.twiddles);
-  const TwRoots tw{roots};
   const int p_lo = a.k0 * a.J;
-  int jcur = -1;
-  for (int base = blockIdx.x * R::G; base < a.nlines; base += gridDim.x * R::G) {
+  {
     const int li = base + g;
     const bool valid = li < a.nlines;
     const int line = a.line0 + (valid ? li : 0);
@@ -265,8 +278,8 @@ __global__ void __launch_bounds__(RowCfg<P>::NT, RowCfg<P>::MINB) k_pass_a(PassA
     }
     // the next line of this thread group: its probe row and its two object rows go to L2 now
     // (one bulk request each, issued by the line's first thread)
-    if (t == 0 && li + (int)gridDim.x * R::G < a.nlines) {
-      const int2 NL = __ldg(a.lines + a.line0 + li + gridDim.x * R::G);
+    if (t == 0 && next >= 0 && next + g < a.nlines) {
+      const int2 NL = __ldg(a.lines + a.line0 + next + g);
       const int nlp = NL.x - p_lo;
       const PlaneDesc nd = a.planes[NL.x];
       const Tap nyt = a.ytap[(long long)NL.x * a.tap_stride + NL.y];
@@ -278,10 +291,11 @@ __global__ void __launch_bounds__(RowCfg<P>::NT, RowCfg<P>::MINB) k_pass_a(PassA
       if ((unsigned)(nyt.i0 + 1) < (unsigned)n)
         l2_prefetch_bulk(npsi + (long long)(nyt.i0 + 1) * n, n * (uint32_t)sizeof(float2));
     }
-    ensure_chirp<P>(chs, a.chirp_zhat, R::G == 1 ? j : jb, jcur);
+    ensure_chirp_key<P>(chs, a.chirp_zhat, R::G == 1 ? j : jb, pkey * 16 + (R::G == 1 ? j : jb),
+                        jcur);
     __syncthreads();
     fft_fwd_with<P>(v, sm, tw, t, SyncBlock());
-    const bool own = R::G == 1 || j == jcur;
+    const bool own = R::G == 1 || pkey * 16 + j == jcur;
     const float2* chg = a.chirp_zhat + (long long)j * P;
     const float2* rmp = SHIFT ? a.ramp_x + (long long)gp * P : nullptr;
 #pragma unroll
@@ -297,6 +311,39 @@ __global__ void __launch_bounds__(RowCfg<P>::NT, RowCfg<P>::MINB) k_pass_a(PassA
       const int rel = F::pos(t, c) - lo;
       if (valid && (unsigned)rel < (unsigned)n) yrow[rel] = v[c];
     }
+  }
+}
+
+template <int P, bool SHIFT>
+__global__ void __launch_bounds__(RowCfg<P>::NT, RowCfg<P>::MINB)
+k_pass_a(const __grid_constant__ PassArgs a) {
+  extern __shared__ float2 smem[];
+  load_roots<P>(smem, a.twiddles);
+  const TwRoots tw{smem};
+  int jcur = -1;
+  const int step = gridDim.x * RowCfg<P>::G;
+  for (int base = blockIdx.x * RowCfg<P>::G; base < a.nlines; base += step)
+    pass_a_step<P, SHIFT>(a, base, base + step < a.nlines ? base + step : -1, smem, tw, 0, jcur);
+}
+
+// Pass A of several problems of line length P in one persistent launch: items {problem,
+// base} of G lines each, walked by the blocks in a grid-stride loop (args: one PassArgs per
+// problem, in device memory).
+template <int P, bool SHIFT>
+__global__ void __launch_bounds__(RowCfg<P>::NT, RowCfg<P>::MINB)
+k_pass_a_multi(const PassArgs* __restrict__ args, const int2* __restrict__ items, int nitems) {
+  extern __shared__ float2 smem[];
+  load_roots<P>(smem, args[0].twiddles);
+  const TwRoots tw{smem};
+  int jcur = -1;
+  for (int it = blockIdx.x; it < nitems; it += gridDim.x) {
+    const int2 item = items[it];
+    int next = -1;
+    if (it + (int)gridDim.x < nitems) {
+      const int2 ni = items[it + gridDim.x];
+      if (ni.x == item.x) next = ni.y;
+    }
+    pass_a_step<P, SHIFT>(args[item.x], item.y, next, smem, tw, item.x, jcur);
   }
 }
 
@@ -338,38 +385,33 @@ __device__ __forceinline__ void stage_y(const PassArgs& a, float2* stg, uint64_t
 // and S = sum_kj r_kj is accumulated in shared memory in a fixed order and written once
 // (with the reference residual) as the source of the ext-part of grad_q.  Every S / b slot
 // is owned by one thread (its crop rows of its column), so no barrier guards them.
+// The work of block `bid` of a pass-B grid of `nblk` blocks for the problem `a`: column groups
+// bid, bid + nblk, ...; its FP64 loss partial goes to a.loss_part[bid].  The caller has loaded
+// the twiddle roots at the head of shared memory and, for a staged problem, initialised the
+// Y-stage barrier.  The resident chirp table is identified by pkey * 16 + distance.  Returns
+// false when a bounded Y-stage wait gave up (the problem's error word is then set).
 template <int P, bool ADJ, bool SHIFT>
-__global__ void __launch_bounds__(ColCfg<P>::NT) k_pass_b(PassArgs a) {
+__device__ __forceinline__ bool pass_b_run(const PassArgs& a, int bid, int nblk, float2* smem,
+                                           const TwRoots& tw, double* red, uint64_t* ybarp,
+                                           uint32_t& yphase, int pkey, int& jcur) {
   using F = Fft<P>;
   using Cc = ColCfg<P>;
   using H = SmemHead<P>;
   constexpr int C = Cc::C;
-  extern __shared__ float2 smem[];
-  __shared__ double red[32];
-  __shared__ uint64_t ybar;
-  float2* roots = smem;
   float2* chs = smem + H::ROOTS;
   const int g = threadIdx.x % C, t = threadIdx.x / C;
   float2* sm = smem + H::WORDS + g * Cc::LS;
   const int n = a.n, lo = P / 2 - n / 2;
   float2* sb = smem + H::WORDS + C * Cc::LS;
   float2* sS = sb + n * C;
-  load_roots<P>(roots, a.twiddles);
-  const TwRoots tw{roots};
   const int ngroups = (n + C - 1) / C;
   double dsum = 0.0;
-  int jcur = -1;
   // Y stage: the tile of the block's next plane is in flight while the current one computes
   const bool staged = a.ymap != nullptr;
   float2* stg = reinterpret_cast<float2*>((reinterpret_cast<uintptr_t>(sS + n * C) + 127) &
                                           ~static_cast<uintptr_t>(127));
-  uint32_t yphase = 0;
-  if (staged) {
-    if (threadIdx.x == 0) mbar_init(&ybar);
-    __syncthreads();
-    if (threadIdx.x == 0 && (int)blockIdx.x < ngroups) stage_y<P>(a, stg, &ybar, blockIdx.x, 0, 0);
-  }
-  for (int cg = blockIdx.x; cg < ngroups; cg += gridDim.x) {
+  if (staged && threadIdx.x == 0 && bid < ngroups) stage_y<P>(a, stg, ybarp, bid, 0, 0);
+  for (int cg = bid; cg < ngroups; cg += nblk) {
     const int col = cg * C + g;
     const bool valid = col < n;
 #pragma unroll
@@ -382,7 +424,7 @@ __global__ void __launch_bounds__(ColCfg<P>::NT) k_pass_b(PassArgs a) {
       }
     }
     for (int j = 0; j < a.J; ++j) {
-      ensure_chirp<P>(chs, a.chirp_zhat, j, jcur);
+      ensure_chirp_key<P>(chs, a.chirp_zhat, j, pkey * 16 + j, jcur);
       for (int kl = 0; kl < a.nk; ++kl) {
         const int lp = kl * a.J + j;
         const long long gplane = (long long)(a.k0 + kl) * a.J + j;
@@ -390,7 +432,7 @@ __global__ void __launch_bounds__(ColCfg<P>::NT) k_pass_b(PassArgs a) {
         float2* yb = a.ybuf + (long long)lp * a.ystride;
         float2 v[16];
         if (staged) {
-          const bool ok = mbar_wait(&ybar, yphase);
+          const bool ok = mbar_wait(ybarp, yphase);
           yphase ^= 1;
 #pragma unroll
           for (int c = 0; c < 16; ++c) {
@@ -401,7 +443,7 @@ __global__ void __launch_bounds__(ColCfg<P>::NT) k_pass_b(PassArgs a) {
           // every thread has its tile entries: the stage is free for the next plane
           if (__syncthreads_or(!ok)) {
             if (threadIdx.x == 0) atomicOr(a.err, 1ull);
-            return;
+            return false;
           }
           if (threadIdx.x == 0) {
             int nkl = kl + 1, nj = j, ncg = cg;
@@ -409,10 +451,10 @@ __global__ void __launch_bounds__(ColCfg<P>::NT) k_pass_b(PassArgs a) {
               nkl = 0;
               if (++nj == a.J) {
                 nj = 0;
-                ncg += gridDim.x;
+                ncg += nblk;
               }
             }
-            if (ncg < ngroups) stage_y<P>(a, stg, &ybar, ncg, nj, nkl);
+            if (ncg < ngroups) stage_y<P>(a, stg, ybarp, ncg, nj, nkl);
           }
         } else {
 #pragma unroll
@@ -510,7 +552,53 @@ __global__ void __launch_bounds__(ColCfg<P>::NT) k_pass_b(PassArgs a) {
     }
   }
   const double s = block_sum_f64(dsum, red);
-  if (threadIdx.x == 0) a.loss_part[blockIdx.x] = s;
+  if (threadIdx.x == 0) a.loss_part[bid] = s;
+  return true;
+}
+
+template <int P, bool ADJ, bool SHIFT>
+__global__ void __launch_bounds__(ColCfg<P>::NT) k_pass_b(const __grid_constant__ PassArgs a) {
+  extern __shared__ float2 smem[];
+  __shared__ double red[32];
+  __shared__ uint64_t ybar;
+  load_roots<P>(smem, a.twiddles);
+  const TwRoots tw{smem};
+  if (a.ymap != nullptr) {
+    if (threadIdx.x == 0) mbar_init(&ybar);
+    __syncthreads();
+  }
+  uint32_t yphase = 0;
+  int jcur = -1;
+  pass_b_run<P, ADJ, SHIFT>(a, blockIdx.x, gridDim.x, smem, tw, red, &ybar, yphase, 0, jcur);
+}
+
+// Pass B of several problems of line length P in one persistent launch: items {problem, b},
+// b < the problem's own pass-B grid (a.pb_blocks), each the work of block b of that grid, so
+// every problem's results (loss partials included) are those of its own launch bit for bit.
+// A Y-stage wait that gives up sets the error word of every problem of the launch.
+template <int P, bool ADJ, bool SHIFT>
+__global__ void __launch_bounds__(ColCfg<P>::NT)
+k_pass_b_multi(const PassArgs* __restrict__ args, const int2* __restrict__ items, int nitems,
+               int nprob) {
+  extern __shared__ float2 smem[];
+  __shared__ double red[32];
+  __shared__ uint64_t ybar;
+  load_roots<P>(smem, args[0].twiddles);
+  const TwRoots tw{smem};
+  if (threadIdx.x == 0) mbar_init(&ybar);
+  __syncthreads();
+  uint32_t yphase = 0;
+  int jcur = -1;
+  for (int it = blockIdx.x; it < nitems; it += gridDim.x) {
+    const int2 item = items[it];
+    const PassArgs& a = args[item.x];
+    if (!pass_b_run<P, ADJ, SHIFT>(a, item.y, a.pb_blocks, smem, tw, red, &ybar, yphase, item.x,
+                                   jcur)) {
+      if (threadIdx.x == 0)
+        for (int p = 0; p < nprob; ++p) atomicOr(args[p].err, 1ull);
+      return;
+    }
+  }
 }
 
 // Pass B when the column groups do not fill the GPU a few times over (fewer than three full
@@ -731,22 +819,40 @@ __global__ void k_pass_b_tail(PassArgs a, int nblocks) {
 
 // ------------------------------------------------------------------ pass C
 
-template <int P, bool SHIFT>
-__global__ void __launch_bounds__(RowCfg<P>::NT, RowCfg<P>::MINB) k_pass_c(PassArgs a) {
+// Pass C over block-steps of G lines: MULTI = false walks the lines of the single problem
+// `one` grid-stride; MULTI = true walks items {problem, base} of several problems (args in
+// device memory), one block-step per item.  The resident chirp table is identified by
+// problem * 16 + distance.
+template <int P, bool SHIFT, bool MULTI>
+__device__ __forceinline__ void pass_c_run(const PassArgs& one, const PassArgs* __restrict__ args,
+                                           const int2* __restrict__ items, int nitems) {
   using F = Fft<P>;
   using R = RowCfg<P>;
   using H = SmemHead<P>;
   extern __shared__ float2 smem[];
-  float2* roots = smem;
+  load_roots<P>(smem, MULTI ? args[0].twiddles : one.twiddles);
+  const TwRoots tw{smem};
   float2* chs = smem + H::ROOTS;
   const int g = threadIdx.x / F::T, t = threadIdx.x % F::T;
   float2* sm = smem + H::WORDS + g * R::LS;
-  load_roots<P>(roots, a.twiddles);
-  const TwRoots tw{roots};
-  const int n = a.n, lo = P / 2 - n / 2;
-  const int p_lo = a.k0 * a.J;
   int jcur = -1;
-  for (int base = blockIdx.x * R::G; base < a.nlines; base += gridDim.x * R::G) {
+  const int nsteps = MULTI ? nitems : (one.nlines + R::G - 1) / R::G;
+  for (int it = blockIdx.x; it < nsteps; it += gridDim.x) {
+    int pkey = 0, base = it * R::G, next = -1;
+    if constexpr (MULTI) {
+      const int2 item = items[it];
+      pkey = item.x;
+      base = item.y;
+      if (it + (int)gridDim.x < nitems) {
+        const int2 ni = items[it + gridDim.x];
+        if (ni.x == item.x) next = ni.y;
+      }
+    } else {
+      next = base + gridDim.x * R::G;  // the prefetch checks it against nlines
+    }
+    const PassArgs& a = MULTI ? args[pkey] : one;
+    const int n = a.n, lo = P / 2 - n / 2;
+    const int p_lo = a.k0 * a.J;
     const int li = base + g;
     const bool valid = li < a.nlines;
     const int line = a.line0 + (valid ? li : 0);
@@ -763,8 +869,8 @@ __global__ void __launch_bounds__(RowCfg<P>::NT, RowCfg<P>::MINB) k_pass_c(PassA
     }
     // the next line of this thread group: its adjoint-field row, probe row and conj(w) v row go
     // to L2 now (one bulk request each, issued by the line's first thread)
-    if (t == 0 && li + (int)gridDim.x * R::G < a.nlines) {
-      const int2 NL = __ldg(a.lines + a.line0 + li + gridDim.x * R::G);
+    if (t == 0 && next >= 0 && next + g < a.nlines) {
+      const int2 NL = __ldg(a.lines + a.line0 + next + g);
       const int nlp = NL.x - p_lo;
       const PlaneDesc nd = a.planes[NL.x];
       l2_prefetch_bulk(a.ybuf + (long long)nlp * a.ystride + (long long)NL.y * n,
@@ -774,10 +880,11 @@ __global__ void __launch_bounds__(RowCfg<P>::NT, RowCfg<P>::MINB) k_pass_c(PassA
       l2_prefetch_bulk(a.gkbuf + (long long)nlp * a.gkstride + (long long)NL.y * nd.bxs,
                        nd.bxs * (uint32_t)sizeof(float2));
     }
-    ensure_chirp<P>(chs, a.chirp_zhat, R::G == 1 ? j : jb, jcur);
+    ensure_chirp_key<P>(chs, a.chirp_zhat, R::G == 1 ? j : jb, pkey * 16 + (R::G == 1 ? j : jb),
+                        jcur);
     __syncthreads();
     fft_fwd_with<P>(v, sm, tw, t, SyncBlock());
-    const bool own = R::G == 1 || j == jcur;
+    const bool own = R::G == 1 || pkey * 16 + j == jcur;
     const float2* chg = a.chirp_zhat + (long long)j * P;
     const float2* rmp = SHIFT ? a.ramp_x + (long long)gp * P : nullptr;
 #pragma unroll
@@ -828,6 +935,20 @@ __global__ void __launch_bounds__(RowCfg<P>::NT, RowCfg<P>::MINB) k_pass_c(PassA
   }
 }
 
+template <int P, bool SHIFT>
+__global__ void __launch_bounds__(RowCfg<P>::NT, RowCfg<P>::MINB)
+k_pass_c(const __grid_constant__ PassArgs a) {
+  pass_c_run<P, SHIFT, false>(a, nullptr, nullptr, 0);
+}
+
+// Pass C of several problems of line length P in one persistent launch (items as
+// k_pass_a_multi).
+template <int P, bool SHIFT>
+__global__ void __launch_bounds__(RowCfg<P>::NT, RowCfg<P>::MINB)
+k_pass_c_multi(const PassArgs* __restrict__ args, const int2* __restrict__ items, int nitems) {
+  pass_c_run<P, SHIFT, true>(args[0], args, items, nitems);
+}
+
 // ------------------------------------------------------------------ launchers
 
 inline int sm_count() {
@@ -853,6 +974,20 @@ int persistent_blocks(K kernel, int threads, size_t smem, long long items) {
   long long b = (long long)per_sm * sm_count();
   if (items < b) b = items;
   return (int)(b < 1 ? 1 : b);
+}
+
+// Persistent grid of a multi-problem launch: per_sm (or as many as fit) blocks per SM,
+// capped by the items.
+template <class K>
+int multi_blocks(K kernel, int threads, size_t smem, int nitems, int per_sm) {
+  int fit = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&fit, kernel, threads, smem) != cudaSuccess ||
+      fit < 1) {
+    cudaGetLastError();
+    fit = 1;
+  }
+  const int b = (per_sm > 0 && per_sm < fit ? per_sm : fit) * sm_count();
+  return b < nitems ? b : (nitems > 0 ? nitems : 1);
 }
 
 template <int P, bool COLS>
@@ -892,7 +1027,8 @@ cudaError_t launch_pass_a_form(const PassArgs& a, cudaStream_t s) {
   cudaError_t e = cudaFuncSetAttribute(k_pass_a<P, SHIFT>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
   if (e != cudaSuccess) return e;
-  const int nb = persistent_blocks(k_pass_a<P, SHIFT>, R::NT, sm, (a.nlines + R::G - 1) / R::G);
+  const int nb = multi_blocks(k_pass_a<P, SHIFT>, R::NT, sm, (a.nlines + R::G - 1) / R::G,
+                              a.row_per_sm);
   k_pass_a<P, SHIFT><<<nb, R::NT, sm, s>>>(a);
   return cudaGetLastError();
 }
@@ -1011,8 +1147,8 @@ cudaError_t launch_pass_c_form(const PassArgs& a, cudaStream_t s) {
                                        cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)R::SMEM_BYTES);
   if (e != cudaSuccess) return e;
-  const int nb = persistent_blocks(k_pass_c<P, SHIFT>, R::NT, R::SMEM_BYTES,
-                                   (a.nlines + R::G - 1) / R::G);
+  const int nb = multi_blocks(k_pass_c<P, SHIFT>, R::NT, R::SMEM_BYTES,
+                              (a.nlines + R::G - 1) / R::G, a.row_per_sm);
   k_pass_c<P, SHIFT><<<nb, R::NT, R::SMEM_BYTES, s>>>(a);
   return cudaGetLastError();
 }
@@ -1020,6 +1156,53 @@ cudaError_t launch_pass_c_form(const PassArgs& a, cudaStream_t s) {
 template <int P>
 cudaError_t launch_pass_c(const PassArgs& a, cudaStream_t s) {
   return a.ramp_x ? launch_pass_c_form<P, true>(a, s) : launch_pass_c_form<P, false>(a, s);
+}
+
+template <int P, bool SHIFT>
+cudaError_t launch_rows_multi_form(int pass_c, const PassArgs* args, const int2* items,
+                                   int nitems, int max_n, int per_sm, cudaStream_t s) {
+  using R = RowCfg<P>;
+  if (nitems <= 0) return cudaSuccess;
+  const size_t sm = pass_c ? R::SMEM_BYTES : pass_a_smem<P>(max_n);
+  auto kern = pass_c ? k_pass_c_multi<P, SHIFT> : k_pass_a_multi<P, SHIFT>;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  if (e != cudaSuccess) return e;
+  const int nb = multi_blocks(kern, R::NT, sm, nitems, per_sm);
+  kern<<<nb, R::NT, sm, s>>>(args, items, nitems);
+  return cudaGetLastError();
+}
+
+template <int P>
+cudaError_t launch_rows_multi(int pass_c, const PassArgs* args, const int2* items, int nitems,
+                              int shift, int max_n, int per_sm, cudaStream_t s) {
+  return shift ? launch_rows_multi_form<P, true>(pass_c, args, items, nitems, max_n, per_sm, s)
+               : launch_rows_multi_form<P, false>(pass_c, args, items, nitems, max_n, per_sm, s);
+}
+
+template <int P, bool ADJ, bool SHIFT>
+cudaError_t launch_pass_b_multi_form(const PassArgs* args, const int2* items, int nitems,
+                                     int nprob, int max_n, int max_rows, int per_sm,
+                                     cudaStream_t s) {
+  using Cc = ColCfg<P>;
+  if (nitems <= 0) return cudaSuccess;
+  const size_t sm = pass_b_smem<P>(max_n, max_rows);
+  auto kern = k_pass_b_multi<P, ADJ, SHIFT>;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  if (e != cudaSuccess) return e;
+  const int nb = multi_blocks(kern, Cc::NT, sm, nitems, per_sm);
+  kern<<<nb, Cc::NT, sm, s>>>(args, items, nitems, nprob);
+  return cudaGetLastError();
+}
+
+template <int P>
+cudaError_t launch_pass_b_multi(const PassArgs* args, const int2* items, int nitems, int nprob,
+                                int adj, int shift, int max_n, int max_rows, int per_sm,
+                                cudaStream_t s) {
+  if (shift)
+    return adj ? launch_pass_b_multi_form<P, true, true>(args, items, nitems, nprob, max_n, 0, per_sm, s)
+               : launch_pass_b_multi_form<P, false, true>(args, items, nitems, nprob, max_n, 0, per_sm, s);
+  return adj ? launch_pass_b_multi_form<P, true, false>(args, items, nitems, nprob, max_n, max_rows, per_sm, s)
+             : launch_pass_b_multi_form<P, false, false>(args, items, nitems, nprob, max_n, max_rows, per_sm, s);
 }
 
 template <int P>
@@ -1035,7 +1218,10 @@ const Ops* make_ops() {
                           pass_b_blocks_split<P>,
                           pass_b_stage_ok<P>,
                           Fft<P>::TW,
-                          ColCfg<P>::C};
+                          ColCfg<P>::C,
+                          RowCfg<P>::G,
+                          launch_rows_multi<P>,
+                          launch_pass_b_multi<P>};
   return &ops;
 }
 

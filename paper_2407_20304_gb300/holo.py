@@ -359,6 +359,13 @@ class Holo:
         _check(self.lib, self.ctx, self.lib.holo_get_timing(self.ctx, ms, nl), "holo_get_timing")
         return {name: (ms[i], nl[i]) for i, name in enumerate(_lib.TIMERS)}
 
+    def set_schedule(self, row_blocks_per_sm=0, pass_b_stage=-1, pass_b_split=-1):
+        """holo_set_schedule: resident row-pass blocks per SM (0: as many as fit), pass B's
+        TMA stage (-1 auto, 0 off) and plane-split form (-1 auto, 0 never, 1 when partial)."""
+        st = self.lib.holo_set_schedule(self.ctx, row_blocks_per_sm, pass_b_stage, pass_b_split)
+        _check(self.lib, self.ctx, st, "holo_set_schedule")
+        self.schedule = (row_blocks_per_sm, pass_b_stage, pass_b_split)
+
     def set_device_error(self, word=1):
         """Test hook (holo_set_device_error): set the device error word as if a bounded
         device wait had given up; the next loss read raises HOLO_ERR_TIMEOUT and clears it."""

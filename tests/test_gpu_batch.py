@@ -89,3 +89,51 @@ def test_autotune_picks_a_schedule(batch):
     ms, sched, cost = b.autotune(candidates=(1, 2, 4), reps=1)
     assert sorted(i for g in sched for i in g) == list(range(len(b.inst)))
     assert ms > 0 and len(b.tuning) >= 2
+
+
+def _snapshot(b):
+    torch.cuda.synchronize()
+    return [(it.h.read_loss(), it.grad_psi.clone(), it.grad_q.clone()) for it in b.inst]
+
+
+def _clear(b):
+    for it in b.inst:
+        it.grad_psi.fill_(float("nan"))
+        it.grad_q.fill_(float("nan"))
+
+
+def test_persistent_graph_equals_loop_and_oracle(batch):
+    """The persistent form (passes A-D of all problems as multi-problem launches walking work
+    lists, captured once, replayed twice) gives every problem the per-problem loop's loss,
+    grad_psi and grad_q bit for bit (same schedule), and those match the FP64 oracle, at
+    sides 32 .. 2048 including the radix-3 lengths."""
+    b, refs = batch
+    b.prepare_persistent()
+    b.run_loop()
+    ref = _snapshot(b)
+    _clear(b)
+    b.capture_persistent()
+    b.replay_persistent()
+    b.replay_persistent()
+    got = _snapshot(b)
+    for (F, gp, gq), (F2, gp2, gq2), (Fo, gpo, gqo) in zip(ref, got, refs):
+        assert F2 == F
+        assert torch.equal(gp2, gp) and torch.equal(gq2, gq)
+        assert abs(F2 - Fo) / Fo < 1e-5
+        assert np.linalg.norm(gp2.cpu().numpy() - gpo) / np.linalg.norm(gpo) < 1e-4
+        assert np.linalg.norm(gq2.cpu().numpy() - gqo) / np.linalg.norm(gqo) < 1e-4
+
+
+def test_persistent_autotune_keeps_the_results(batch):
+    """The schedule autotuner changes only launch shapes: after it, the replayed persistent
+    graph still equals the per-problem loop run with the chosen schedule."""
+    b, _ = batch
+    ms, chosen = b.autotune_persistent(reps=1)
+    assert ms > 0 and set(chosen) == set(b.line_lengths()) and len(b.ptuning) >= 2
+    b.run_loop()
+    ref = _snapshot(b)
+    _clear(b)
+    b.replay_persistent()
+    got = _snapshot(b)
+    for (F, gp, gq), (F2, gp2, gq2) in zip(ref, got):
+        assert F2 == F and torch.equal(gp2, gp) and torch.equal(gq2, gq)
