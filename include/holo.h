@@ -77,6 +77,9 @@ typedef enum {
 #define HOLO_ACCUMULATE 1u   /* add to grad_psi, grad_q and *loss instead of overwriting */
 #define HOLO_ACCUMULATE_Q 2u /* add to grad_q and *loss only; grad_psi is overwritten (chunks
                                 of one problem own disjoint psi slices but share q) */
+#define HOLO_DEFER_Q 4u      /* holo_gradient: keep the chunk's probe-gradient sources in the
+                                context instead of propagating them into grad_q (see
+                                holo_finish_q); grad_q may be NULL */
 
 /*
  * Instrument geometry and discretisation (Table 1 lists the paper's instrument).
@@ -168,6 +171,20 @@ holo_status holo_forward(holo_ctx* ctx, int k0, int nk, const void* psi, void* u
  * one problem); otherwise all are overwritten. */
 holo_status holo_gradient(holo_ctx* ctx, int k0, int nk, const void* psi, double* loss,
                           void* grad_psi, void* grad_q, unsigned flags);
+
+/* Deferred probe gradient.  grad_q is linear in two sources per chunk: the residual sum
+ * T = ext sum_kj r_kj + w_ref r_ref and, per distance j, G'_j = sum_k conj(w_kj) v_kj; each
+ * chunk's share is propagated by J + 1 P x P Fresnel steps.  A gradient call with
+ * HOLO_DEFER_Q instead adds its sources to the context's accumulators (held on the union of
+ * every plane's box of distance j), starting them afresh unless HOLO_ACCUMULATE or
+ * HOLO_ACCUMULATE_Q is set, and leaves grad_q alone; holo_finish_q then writes (or with
+ * HOLO_ACCUMULATE_Q adds) grad_q = 2 [D_{-zeta_0}(C* T) + sum_j D_{-omega_j}(G'_j)] once for
+ * all the deferred chunks.  The loss and grad_psi are not deferred.  A gradient call without
+ * HOLO_DEFER_Q discards pending sources; holo_finish_q without pending sources returns
+ * HOLO_ERR_STATE.  The accumulators (about J (n + 16)^2 complex64) are allocated by the first
+ * deferred call.  Summing the sources before propagating rounds differently from summing the
+ * propagated chunks (equal to rounding).  holo_gradient_host does not take HOLO_DEFER_Q. */
+holo_status holo_finish_q(holo_ctx* ctx, void* grad_q, unsigned flags);
 
 /* holo_gradient with host buffers: copies psi_host ([nk][n][n]) and, when not NULL,
  * sqrt_d_host (float [nk][n_dist][n][n], the chunk's data, used instead of the data
@@ -297,9 +314,11 @@ holo_status holo_set_schedule(holo_ctx* ctx, int row_blocks_per_sm, int pass_b_s
  * HOLO_ACCUMULATE_Q).  Passes A-D of the chunks of all problems run as persistent launches
  * that walk device work lists of (problem, work item) entries, one launch per pass and line
  * length (pass D: one for all); the reductions and the grad_q propagations run per problem.
- * Every problem's results equal bit for bit those of its own holo_set_probe + holo_gradient
- * calls with the same schedule (holo_batch_prepare sets pass_b_split = 0 on every context:
- * the batched column pass works on whole column groups).
+ * The probe gradient's sources are summed over a problem's chunks and propagated once (as
+ * holo_gradient with HOLO_DEFER_Q and holo_finish_q).  Every problem's results equal bit for
+ * bit those of its own holo_set_probe, holo_gradient (HOLO_DEFER_Q, HOLO_ACCUMULATE_Q after
+ * the first chunk) and holo_finish_q calls with the same schedule (holo_batch_prepare sets
+ * pass_b_split = 0 on every context: the batched column pass works on whole column groups).
  *   holo_batch_create   keeps the array of `count` contexts (not owned; they must outlive
  *                       the batch);
  *   holo_batch_set_problem  the device buffers of problem i: psi [n_angles][n][n], q [P][P]

@@ -13,6 +13,7 @@ MAX_DIST = 8
 F2_AMPLITUDE, F1_INTENSITY = 0, 1   # holo_set_functional
 ACCUMULATE = 1
 ACCUMULATE_Q = 2
+DEFER_Q = 4
 NOALLOC_MAX_ELEMENTS = 1 << 28   # holo_dot_noalloc: capacity of its static partial-sum array
 
 STATUS = {0: "HOLO_OK", 1: "HOLO_ERR_ARG", 2: "HOLO_ERR_CUDA", 3: "HOLO_ERR_OOM",
@@ -28,7 +29,7 @@ EXPORTS = ("holo_create", "holo_destroy", "holo_set_shifts", "holo_set_probe_shi
            "holo_get_timing", "holo_dot_noalloc",
            "holo_set_stream", "holo_read_loss", "holo_set_device_error",
            "holo_workspace_bytes", "holo_launch_count", "holo_status_string", "holo_last_error",
-           "holo_set_schedule", "holo_batch_create", "holo_batch_set_problem",
+           "holo_set_schedule", "holo_finish_q", "holo_batch_create", "holo_batch_set_problem",
            "holo_batch_prepare", "holo_batch_gradient", "holo_batch_destroy")
 
 # Pass ids of holo_get_timing (HOLO_T_* in include/holo.h).
@@ -87,6 +88,7 @@ def _signatures():
         "holo_workspace_bytes": [P, ctypes.POINTER(LL)],
         "holo_launch_count": [P, ctypes.POINTER(LL)],
         "holo_set_schedule": [P, I, I, I],
+        "holo_finish_q": [P, P, U],
         "holo_batch_create": [ctypes.POINTER(P), I, ctypes.POINTER(P)],
         "holo_batch_set_problem": [P, I, P, P, P, P],
         "holo_batch_prepare": [P],

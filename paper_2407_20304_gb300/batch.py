@@ -50,11 +50,13 @@ class Instance:
         return [(k0, min(c, K - k0)) for k0 in range(0, K, c)]
 
     def issue(self):
-        """Issue one evaluation on the context's stream (no host synchronisation)."""
+        """Issue one evaluation on the context's stream (no host synchronisation): the chunks'
+        probe-gradient sources are summed and propagated once (deferred grad_q)."""
         self.h.set_probe(self.q)
         for i, (k0, nk) in enumerate(self.chunks()):
-            self.h.gradient(self.psi[k0:k0 + nk], grad_psi=self.grad_psi[k0:k0 + nk],
-                            grad_q=self.grad_q, k0=k0, want_loss=False, accumulate_q=i > 0)
+            self.h.gradient(self.psi[k0:k0 + nk], grad_psi=self.grad_psi[k0:k0 + nk], k0=k0,
+                            want_loss=False, accumulate_q=i > 0, defer_q=True)
+        self.h.finish_q(self.grad_q)
 
     @property
     def planes(self):

@@ -137,6 +137,13 @@ struct holo_ctx {
   float2* d_scratch = nullptr;  // P*P
   float2* d_Gp = nullptr;       // P*P
   float2* d_T = nullptr;        // n*n
+  // deferred probe gradient (HOLO_DEFER_Q): per distance the union box {row0, rows, col0, cols}
+  // of every plane's box, and G'_j accumulated on it (offset gacc_off[j] in d_gacc)
+  int qbox[HOLO_MAX_DIST][4] = {};
+  float2* d_gacc = nullptr;
+  size_t gacc_bytes = 0;
+  size_t gacc_off[HOLO_MAX_DIST] = {};
+  bool q_pending = false;
   float2* d_rref = nullptr;     // n*n
   double* d_part = nullptr;
   long long part_cap = 0;
@@ -657,7 +664,8 @@ holo_status eval_qgrad(holo_ctx* c, const PassArgs& a, float2* grad_q, int acc) 
       c1 = std::max(c1, d.bx0 + d.bxs);
     }
     if (r1 <= r0 || c1 <= c0) continue;
-    HOLO_LAUNCH(c, holo::launch_reduce_g(a, c->d_Gp, j, r0, r1 - r0, c0, c1 - c0, c->stream));
+    HOLO_LAUNCH(c, holo::launch_reduce_g(a, c->d_Gp, j, r0, r1 - r0, c0, c1 - c0, c1 - c0, r0, c0,
+                                         0, c->stream));
     st = dstep2d(c, c->d_Gp, r0, r1 - r0, c0, c1 - c0, grad_q, 0, P, 0, P,
                  c->d_chirp_omega + (size_t)j * P, 1, 2.f, 1);
     if (st != HOLO_OK) return st;
@@ -665,12 +673,65 @@ holo_status eval_qgrad(holo_ctx* c, const PassArgs& a, float2* grad_q, int acc) 
   return HOLO_OK;
 }
 
+// Deferred probe gradient: the chunk's G'_j added (acc) or written into the accumulators on
+// the union boxes; T was written or accumulated by pass B (a.tq_accumulate).
+holo_status eval_qsources(holo_ctx* c, const PassArgs& a, int acc) {
+  PassTimer tm_q(c, HOLO_T_QGRAD);
+  size_t need = 0, off[HOLO_MAX_DIST];
+  for (int j = 0; j < c->J; ++j) {
+    off[j] = need;
+    need += sizeof(float2) * (size_t)c->qbox[j][1] * c->qbox[j][3];
+  }
+  if (need != c->gacc_bytes) {
+    dfree(c, c->d_gacc, c->gacc_bytes);
+    c->d_gacc = nullptr;
+    c->gacc_bytes = 0;
+    holo_status st = dalloc(c, (void**)&c->d_gacc, need);
+    if (st) return st;
+    c->gacc_bytes = need;
+    acc = 0;
+  }
+  for (int j = 0; j < c->J; ++j) {
+    c->gacc_off[j] = off[j] / sizeof(float2);
+    const int* qb = c->qbox[j];
+    if (qb[1] <= 0 || qb[3] <= 0) continue;
+    HOLO_LAUNCH(c, holo::launch_reduce_g(a, c->d_gacc + c->gacc_off[j], j, qb[0], qb[1], qb[2],
+                                         qb[3], qb[3], qb[0], qb[2], acc, c->stream));
+  }
+  c->q_pending = true;
+  return HOLO_OK;
+}
+
+// grad_q (= or +=) 2 [ D_{-zeta_0}(C* T) + sum_j D_{-omega_j}(G'_j) ] from the accumulators.
+holo_status eval_qfinish(holo_ctx* c, float2* grad_q, int acc) {
+  PassTimer tm_q(c, HOLO_T_QGRAD);
+  const int P = c->P, n = c->n, lo = P / 2 - n / 2;
+  holo_status st = dstep2d(c, c->d_T, lo, n, lo, n, grad_q, 0, P, 0, P, c->d_chirp_zeta0, 1, 2.f,
+                           acc);
+  if (st != HOLO_OK) return st;
+  for (int j = 0; j < c->J; ++j) {
+    const int* qb = c->qbox[j];
+    if (qb[1] <= 0 || qb[3] <= 0) continue;
+    st = dstep2d(c, c->d_gacc + c->gacc_off[j], qb[0], qb[1], qb[2], qb[3], grad_q, 0, P, 0, P,
+                 c->d_chirp_omega + (size_t)j * P, 1, 2.f, 1);
+    if (st != HOLO_OK) return st;
+  }
+  c->q_pending = false;
+  return HOLO_OK;
+}
+
 // The whole evaluation of one chunk in one pass over its planes.
 holo_status run_eval(holo_ctx* c, PassArgs& a, bool gradient, float2* grad_q, unsigned flags) {
   const int acc = (flags & (HOLO_ACCUMULATE | HOLO_ACCUMULATE_Q)) ? 1 : 0;
+  // deferred probe gradient: the sources accumulate onto pending ones when asked to
+  const bool defer = gradient && (flags & HOLO_DEFER_Q);
+  const int srcacc = defer && acc && c->q_pending ? 1 : 0;
+  if (defer) a.tq_accumulate = srcacc;
   holo_status st;
   if ((st = eval_begin(c, a)) || (st = eval_planes(c, a, gradient, true, acc))) return st;
   if (!gradient) return HOLO_OK;
+  if (defer) return eval_qsources(c, a, srcacc);
+  c->q_pending = false;
   return eval_qgrad(c, a, grad_q, acc);
 }
 
@@ -840,7 +901,7 @@ holo_status holo_destroy(holo_ctx* c) {
                   c->ybuf,    c->gkbuf,        c->d_scratch,
                   c->d_Gp,    c->d_T,          c->d_rref,        c->d_part,
                   c->d_red,   c->d_dot3,       c->d_tpart,       c->s_psi,         c->s_gpsi,
-                  c->s_data,       c->s_dblk,       c->d_dblk,
+                  c->s_data,       c->s_dblk,       c->d_dblk,        c->d_gacc,
                   c->s_q,     c->s_gq,         c->d_xtap,        c->d_ytap,
                   c->d_xadj,  c->d_yadj,       c->d_lines,       c->d_ymap,
                   c->d_ramp_x, c->d_ramp_y};
@@ -898,6 +959,19 @@ holo_status build_planes(holo_ctx* c) {
       }
       teff[p * 2 + 0] = ty;
       teff[p * 2 + 1] = tx;
+      int* qb = c->qbox[j];
+      if (k == 0) {
+        qb[0] = d.by0;
+        qb[1] = d.bys;
+        qb[2] = d.bx0;
+        qb[3] = d.bxs;
+      } else {
+        const int r1 = std::max(qb[0] + qb[1], d.by0 + d.bys), c1 = std::max(qb[2] + qb[3], d.bx0 + d.bxs);
+        qb[0] = std::min(qb[0], d.by0);
+        qb[2] = std::min(qb[2], d.bx0);
+        qb[1] = r1 - qb[0];
+        qb[3] = c1 - qb[2];
+      }
       d.ty = (float)ty;
       d.tx = (float)tx;
       maxbys = std::max(maxbys, d.bys);
@@ -973,6 +1047,7 @@ holo_status build_planes(holo_ctx* c) {
   }
   c->maxbys = maxbys;
   c->maxbxs = maxbxs;
+  c->q_pending = false;
   c->have_shifts = true;
   return HOLO_OK;
 }
@@ -1111,7 +1186,8 @@ holo_status holo_gradient(holo_ctx* c, int k0, int nk, const void* psi, double* 
                           void* grad_psi, void* grad_q, unsigned flags) {
   holo_status st = check_chunk(c, k0, nk);
   if (st != HOLO_OK) return st;
-  if (!psi || !grad_psi || !grad_q) return fail(c, HOLO_ERR_ARG, "null pointer");
+  if (!psi || !grad_psi || (!grad_q && !(flags & HOLO_DEFER_Q)))
+    return fail(c, HOLO_ERR_ARG, "null pointer");
   PassArgs a = pass_args(c, k0, nk, psi);
   a.grad_psi = (float2*)grad_psi;
   a.accumulate = (flags & HOLO_ACCUMULATE) ? 1 : 0;
@@ -1228,6 +1304,8 @@ static holo_status gradient_host_impl(holo_ctx* c, int k0, int nk, const void* p
                                      const float* sqrt_d_host, const void* q_host, double* loss,
                                      void* grad_psi_host, void* grad_q_host, unsigned flags) {
   if (!c) return HOLO_ERR_ARG;
+  if (flags & HOLO_DEFER_Q) return fail(c, HOLO_ERR_ARG, "the host call does not defer grad_q");
+  c->q_pending = false;
   if (!psi_host || !grad_psi_host || !grad_q_host) return fail(c, HOLO_ERR_ARG, "null pointer");
   if (nk < 1 || nk > c->chunk || k0 < 0 || k0 + nk > c->K)
     return fail(c, HOLO_ERR_ARG, "chunk [k0, k0+nk) outside [0, n_angles) or nk > chunk");
@@ -1277,6 +1355,13 @@ static holo_status gradient_host_impl(holo_ctx* c, int k0, int nk, const void* p
   HOLO_CK(c, cudaMemcpyAsync(grad_psi_host, c->s_gpsi, nb, cudaMemcpyDeviceToHost, c->stream));
   HOLO_CK(c, cudaMemcpyAsync(grad_q_host, c->s_gq, q_bytes, cudaMemcpyDeviceToHost, c->stream));
   return read_loss(c, loss, flags);
+}
+
+holo_status holo_finish_q(holo_ctx* c, void* grad_q, unsigned flags) {
+  if (!c || !grad_q) return fail(c, HOLO_ERR_ARG, "null argument");
+  if (!c->q_pending) return fail(c, HOLO_ERR_STATE, "no deferred probe-gradient sources");
+  return eval_qfinish(c, static_cast<float2*>(grad_q),
+                      (flags & (HOLO_ACCUMULATE | HOLO_ACCUMULATE_Q)) ? 1 : 0);
 }
 
 holo_status holo_propagate(holo_ctx* c, const void* in, void* out, double z) {
@@ -1546,6 +1631,7 @@ holo_status holo_batch_prepare(holo_batch* b) {
       PassArgs a = pass_args(c, k0, nk, b->buf[i].psi + (size_t)k0 * n2);
       a.grad_psi = b->buf[i].gpsi + (size_t)k0 * n2;
       a.accumulate = 0;
+      a.tq_accumulate = r > 0 ? 1 : 0;  // probe-gradient sources summed over the rounds
       if (k0 == 0 && c->wref != 0.0) a.rref = c->d_rref;
       int nbx = 0;
       holo_status st = pass_b_grid(c, a, true, &nbx);
@@ -1655,9 +1741,15 @@ extern "C" holo_status holo_batch_gradient(holo_batch* b, void* stream) {
                                     (int)g.rows.size(), g.shift, g.max_n, g.per_sm, s));
     HOLO_CK(c0, holo::launch_pass_d_multi(dargs, reinterpret_cast<const int2*>(dm + R.off_dits),
                                           (int)R.dits.size(), 16 * sms, s));
+    // the probe gradient's sources are summed over the rounds and propagated once, in the
+    // problem's last round (as its own calls with HOLO_DEFER_Q and holo_finish_q)
     for (int ai = 0; ai < na; ++ai) {
       const int i = R.prob[ai];
-      if ((st = eval_qgrad(b->ctx[i], R.args[ai], b->buf[i].gq, acc))) return st;
+      holo_ctx* c = b->ctx[i];
+      if ((st = eval_qsources(c, R.args[ai], acc))) return st;
+      if ((int)r == (c->K + c->chunk - 1) / c->chunk - 1 &&
+          (st = eval_qfinish(c, b->buf[i].gq, 0)))
+        return st;
     }
   }
   return HOLO_OK;

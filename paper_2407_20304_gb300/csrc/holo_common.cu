@@ -90,7 +90,8 @@ __global__ void __launch_bounds__(256) k_pass_d_multi(const PassArgs* __restrict
 constexpr int kReduceEpt = 4;
 constexpr int kReduceTile = 128;
 __global__ void __launch_bounds__(256) k_reduce_g(PassArgs a, float2* Gp, int j, int row0, int nrows,
-                                                  int col0, int ncols) {
+                                                  int col0, int ncols, int opitch, int orow0,
+                                                  int ocol0, int accumulate) {
   __shared__ int4 box[kReduceTile];
   const long long total = (long long)nrows * ncols;
   const long long base = (long long)blockIdx.x * blockDim.x * kReduceEpt + threadIdx.x;
@@ -126,7 +127,10 @@ __global__ void __launch_bounds__(256) k_reduce_g(PassArgs a, float2* Gp, int j,
 #pragma unroll
   for (int e = 0; e < kReduceEpt; ++e) {
     const long long idx = base + (long long)e * blockDim.x;
-    if (idx < total) Gp[idx] = acc[e];
+    if (idx < total) {
+      float2* o = Gp + (long long)(Y[e] - orow0) * opitch + (X[e] - ocol0);
+      *o = accumulate ? cadd(*o, acc[e]) : acc[e];
+    }
   }
 }
 
@@ -384,12 +388,15 @@ cudaError_t launch_pass_d_multi(const PassArgs* args, const int2* items, int nit
   return cudaGetLastError();
 }
 
-cudaError_t launch_reduce_g(const PassArgs& a, float2* Gp, int j, int row0, int nrows, int col0,
-                            int ncols, cudaStream_t s) {
+cudaError_t launch_reduce_g(const PassArgs& a, float2* out, int j, int row0, int nrows, int col0,
+                            int ncols, int opitch, int orow0, int ocol0, int accumulate,
+                            cudaStream_t s) {
   const long long total = (long long)nrows * ncols;
   if (total <= 0) return cudaSuccess;
   const long long per = 256LL * kReduceEpt;
-  k_reduce_g<<<(unsigned)((total + per - 1) / per), 256, 0, s>>>(a, Gp, j, row0, nrows, col0, ncols);
+  k_reduce_g<<<(unsigned)((total + per - 1) / per), 256, 0, s>>>(a, out, j, row0, nrows, col0,
+                                                                 ncols, opitch, orow0, ocol0,
+                                                                 accumulate);
   return cudaGetLastError();
 }
 

@@ -146,8 +146,11 @@ const Ops* ops_for(int P);
 cudaError_t launch_pass_d(const PassArgs& a, cudaStream_t s);
 cudaError_t launch_pass_d_multi(const PassArgs* args, const int2* items, int nitems, int nblocks,
                                 cudaStream_t s);
-cudaError_t launch_reduce_g(const PassArgs& a, float2* Gp, int j, int row0, int nrows, int col0,
-                            int ncols, cudaStream_t s);
+// G'_j of the chunk on the box [row0, row0 + nrows) x [col0, col0 + ncols) of the P grid,
+// written (or with accumulate added) to out[(Y - orow0) * opitch + (X - ocol0)].
+cudaError_t launch_reduce_g(const PassArgs& a, float2* out, int j, int row0, int nrows, int col0,
+                            int ncols, int opitch, int orow0, int ocol0, int accumulate,
+                            cudaStream_t s);
 cudaError_t launch_ref_residual(const float2* bref, const float* sqrt_dref, long long n2,
                                 float2* rref, double* part, int nblocks, int functional,
                                 cudaStream_t s);

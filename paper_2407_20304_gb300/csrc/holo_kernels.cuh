@@ -333,7 +333,7 @@ template <int P, bool SHIFT>
 __global__ void __launch_bounds__(RowCfg<P>::NT, RowCfg<P>::MINB)
 k_pass_a_multi(const PassArgs* __restrict__ args, const int2* __restrict__ items, int nitems) {
   extern __shared__ float2 smem[];
-  load_roots<P>(smem, args[0].twiddles);
+  load_roots<P>(smem, args[items[0].x].twiddles);  // every item has this P
   const TwRoots tw{smem};
   int jcur = -1;
   for (int it = blockIdx.x; it < nitems; it += gridDim.x) {
@@ -583,7 +583,7 @@ k_pass_b_multi(const PassArgs* __restrict__ args, const int2* __restrict__ items
   extern __shared__ float2 smem[];
   __shared__ double red[32];
   __shared__ uint64_t ybar;
-  load_roots<P>(smem, args[0].twiddles);
+  load_roots<P>(smem, args[items[0].x].twiddles);  // every item has this P
   const TwRoots tw{smem};
   if (threadIdx.x == 0) mbar_init(&ybar);
   __syncthreads();
@@ -819,38 +819,31 @@ __global__ void k_pass_b_tail(PassArgs a, int nblocks) {
 
 // ------------------------------------------------------------------ pass C
 
-// Pass C over block-steps of G lines: MULTI = false walks the lines of the single problem
-// `one` grid-stride; MULTI = true walks items {problem, base} of several problems (args in
-// device memory), one block-step per item.  The resident chirp table is identified by
-// problem * 16 + distance.
-template <int P, bool SHIFT, bool MULTI>
-__device__ __forceinline__ void pass_c_run(const PassArgs& one, const PassArgs* __restrict__ args,
-                                           const int2* __restrict__ items, int nitems) {
+// Pass C over items {problem, base} of several problems (args in device memory), one
+// block-step of G lines per item (MULTI = true; the single-problem kernel has its own loop).
+// The resident chirp table is identified by problem * 16 + distance.
+template <int P, bool SHIFT>
+__device__ __forceinline__ void pass_c_items(const PassArgs* __restrict__ args,
+                                             const int2* __restrict__ items, int nitems) {
   using F = Fft<P>;
   using R = RowCfg<P>;
   using H = SmemHead<P>;
   extern __shared__ float2 smem[];
-  load_roots<P>(smem, MULTI ? args[0].twiddles : one.twiddles);
+  load_roots<P>(smem, args[items[0].x].twiddles);  // every item has this P
   const TwRoots tw{smem};
   float2* chs = smem + H::ROOTS;
   const int g = threadIdx.x / F::T, t = threadIdx.x % F::T;
   float2* sm = smem + H::WORDS + g * R::LS;
   int jcur = -1;
-  const int nsteps = MULTI ? nitems : (one.nlines + R::G - 1) / R::G;
-  for (int it = blockIdx.x; it < nsteps; it += gridDim.x) {
-    int pkey = 0, base = it * R::G, next = -1;
-    if constexpr (MULTI) {
-      const int2 item = items[it];
-      pkey = item.x;
-      base = item.y;
-      if (it + (int)gridDim.x < nitems) {
-        const int2 ni = items[it + gridDim.x];
-        if (ni.x == item.x) next = ni.y;
-      }
-    } else {
-      next = base + gridDim.x * R::G;  // the prefetch checks it against nlines
+  for (int it = blockIdx.x; it < nitems; it += gridDim.x) {
+    const int2 item = items[it];
+    const int pkey = item.x, base = item.y;
+    int next = -1;
+    if (it + (int)gridDim.x < nitems) {
+      const int2 ni = items[it + gridDim.x];
+      if (ni.x == item.x) next = ni.y;
     }
-    const PassArgs& a = MULTI ? args[pkey] : one;
+    const PassArgs& a = args[pkey];
     const int n = a.n, lo = P / 2 - n / 2;
     const int p_lo = a.k0 * a.J;
     const int li = base + g;
@@ -935,10 +928,103 @@ __device__ __forceinline__ void pass_c_run(const PassArgs& one, const PassArgs* 
   }
 }
 
+// The single-problem pass C keeps its own grid-stride loop over the lines: built on the shared
+// body below it measured slower (more spills).
 template <int P, bool SHIFT>
-__global__ void __launch_bounds__(RowCfg<P>::NT, RowCfg<P>::MINB)
-k_pass_c(const __grid_constant__ PassArgs a) {
-  pass_c_run<P, SHIFT, false>(a, nullptr, nullptr, 0);
+__global__ void __launch_bounds__(RowCfg<P>::NT, RowCfg<P>::MINB) k_pass_c(PassArgs a) {
+  using F = Fft<P>;
+  using R = RowCfg<P>;
+  using H = SmemHead<P>;
+  extern __shared__ float2 smem[];
+  float2* roots = smem;
+  float2* chs = smem + H::ROOTS;
+  const int g = threadIdx.x / F::T, t = threadIdx.x % F::T;
+  float2* sm = smem + H::WORDS + g * R::LS;
+  load_roots<P>(roots, a.twiddles);
+  const TwRoots tw{roots};
+  const int n = a.n, lo = P / 2 - n / 2;
+  const int p_lo = a.k0 * a.J;
+  int jcur = -1;
+  for (int base = blockIdx.x * R::G; base < a.nlines; base += gridDim.x * R::G) {
+    const int li = base + g;
+    const bool valid = li < a.nlines;
+    const int line = a.line0 + (valid ? li : 0);
+    const int2 L = __ldg(a.lines + line);
+    const int gp = L.x, i = L.y;
+    const int lp = gp - p_lo, j = lp % a.J;
+    const int jb = (__ldg(a.lines + a.line0 + base).x - p_lo) % a.J;
+    float2* yrow = a.ybuf + (long long)lp * a.ystride + (long long)i * n;
+    float2 v[16];
+#pragma unroll
+    for (int c = 0; c < 16; ++c) {
+      const int rel = F::pos(t, c) - lo;
+      v[c] = (valid && (unsigned)rel < (unsigned)n) ? yrow[rel] : make_float2(0.f, 0.f);
+    }
+    // the next line of this thread group: its adjoint-field row, probe row and conj(w) v row go
+    // to L2 now (one bulk request each, issued by the line's first thread)
+    if (t == 0 && li + (int)gridDim.x * R::G < a.nlines) {
+      const int2 NL = __ldg(a.lines + a.line0 + li + gridDim.x * R::G);
+      const int nlp = NL.x - p_lo;
+      const PlaneDesc nd = a.planes[NL.x];
+      l2_prefetch_bulk(a.ybuf + (long long)nlp * a.ystride + (long long)NL.y * n,
+                       n * (uint32_t)sizeof(float2));
+      l2_prefetch_bulk(a.pj + ((long long)(nlp % a.J) * P + nd.by0 + NL.y) * P + nd.bx0,
+                       nd.bxs * (uint32_t)sizeof(float2));
+      l2_prefetch_bulk(a.gkbuf + (long long)nlp * a.gkstride + (long long)NL.y * nd.bxs,
+                       nd.bxs * (uint32_t)sizeof(float2));
+    }
+    ensure_chirp<P>(chs, a.chirp_zhat, R::G == 1 ? j : jb, jcur);
+    __syncthreads();
+    fft_fwd_with<P>(v, sm, tw, t, SyncBlock());
+    const bool own = R::G == 1 || j == jcur;
+    const float2* chg = a.chirp_zhat + (long long)j * P;
+    const float2* rmp = SHIFT ? a.ramp_x + (long long)gp * P : nullptr;
+#pragma unroll
+    for (int c = 0; c < 16; ++c) {
+      const int f = F::fpos(t, c);
+      v[c] = cmulc(v[c], own ? chirp_half<P>(chs, f) : __ldg(chg + f));
+      if (SHIFT) v[c] = cmulc(v[c], __ldg(rmp + f));
+    }
+    fft_inv_with<P>(v, sm, tw, t, SyncBlock());
+    // v holds the adjoint field on this P-grid row; the exchange buffer is free.
+    // The box holds w = R0(psi - ext) (R' psi in the SHIFT form) written by pass A; replace
+    // it by conj(w) v.
+    const PlaneDesc d = a.planes[gp];
+    const float2* prow = a.pj + ((long long)j * P + d.by0 + i) * P;
+    float2* gk = a.gkbuf + (long long)lp * a.gkstride + (long long)i * d.bxs;
+#pragma unroll
+    for (int c = 0; c < 16; ++c) {
+      const int X = F::pos(t, c), rel = X - d.bx0;
+      if (valid && (unsigned)rel < (unsigned)d.bxs) {
+        sm[rel] = cconjmul(__ldg(prow + X), v[c]);
+        gk[rel] = cconjmul(gk[rel], v[c]);
+      }
+    }
+    __syncthreads();
+    // x-transpose of the bilinear resample: h[ip] = w0 z[X0] + w1 z[X0 + 1] with the
+    // transposed taps of this plane (same FP64-built weights as the forward taps).
+    const AdjTap* xa = a.xadj + (long long)gp * n;
+#pragma unroll
+    for (int c = 0; c < 16; ++c) {
+      const int ip = F::pos(t, c);
+      if (!valid || ip >= n) continue;
+      const AdjTap at = xa[ip];
+      float2 h = make_float2(0.f, 0.f);
+      const int r0 = at.X0 - d.bx0;
+      if (at.w0 != 0.f) {
+        const float2 z = sm[r0];
+        h.x = at.w0 * z.x;
+        h.y = at.w0 * z.y;
+      }
+      if (at.w1 != 0.f) {
+        const float2 z = sm[r0 + 1];
+        h.x = fmaf(at.w1, z.x, h.x);
+        h.y = fmaf(at.w1, z.y, h.y);
+      }
+      yrow[ip] = h;
+    }
+    __syncthreads();
+  }
 }
 
 // Pass C of several problems of line length P in one persistent launch (items as
@@ -946,7 +1032,7 @@ k_pass_c(const __grid_constant__ PassArgs a) {
 template <int P, bool SHIFT>
 __global__ void __launch_bounds__(RowCfg<P>::NT, RowCfg<P>::MINB)
 k_pass_c_multi(const PassArgs* __restrict__ args, const int2* __restrict__ items, int nitems) {
-  pass_c_run<P, SHIFT, true>(args[0], args, items, nitems);
+  pass_c_items<P, SHIFT>(args, items, nitems);
 }
 
 // ------------------------------------------------------------------ launchers

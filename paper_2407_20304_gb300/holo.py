@@ -205,26 +205,40 @@ class Holo:
         return loss.value
 
     def gradient(self, psi, grad_psi=None, grad_q=None, k0=0, accumulate=False, loss_in=0.0,
-                 want_loss=True, accumulate_q=False):
+                 want_loss=True, accumulate_q=False, defer_q=False):
         """(F2, grad_psi, grad_q) over angles [k0, k0 + len(psi)) (Eq. gradpsi).
 
         accumulate: add to grad_psi, grad_q and loss_in; accumulate_q: add to grad_q and
-        loss_in only (the chunks of one problem own disjoint psi slices but share q)."""
+        loss_in only (the chunks of one problem own disjoint psi slices but share q);
+        defer_q: keep the probe-gradient sources for finish_q instead (grad_q is returned as
+        None)."""
         import torch
         nk = psi.shape[0]
         pp = _ptr(psi, torch.complex64, (nk, self.n, self.n), "psi")
         if grad_psi is None:
             grad_psi = torch.empty_like(psi)
-        if grad_q is None:
+        if grad_q is None and not defer_q:
             grad_q = torch.empty((self.P, self.P), dtype=torch.complex64, device=psi.device)
         pg = _ptr(grad_psi, torch.complex64, (nk, self.n, self.n), "grad_psi")
-        pq = _ptr(grad_q, torch.complex64, (self.P, self.P), "grad_q")
+        pq = ctypes.c_void_p(None) if defer_q else _ptr(grad_q, torch.complex64, (self.P, self.P),
+                                                        "grad_q")
         loss = ctypes.c_double(loss_in)
         lp = ctypes.byref(loss) if want_loss else None
-        flags = (_lib.ACCUMULATE if accumulate else 0) | (_lib.ACCUMULATE_Q if accumulate_q else 0)
+        flags = ((_lib.ACCUMULATE if accumulate else 0) | (_lib.ACCUMULATE_Q if accumulate_q else 0)
+                 | (_lib.DEFER_Q if defer_q else 0))
         st = self.lib.holo_gradient(self.ctx, k0, nk, pp, lp, pg, pq, flags)
         _check(self.lib, self.ctx, st, "holo_gradient")
-        return (loss.value if want_loss else None), grad_psi, grad_q
+        return (loss.value if want_loss else None), grad_psi, (None if defer_q else grad_q)
+
+    def finish_q(self, grad_q=None, accumulate=False):
+        """holo_finish_q: grad_q (written, or added to) from the deferred sources."""
+        import torch
+        if grad_q is None:
+            grad_q = torch.empty((self.P, self.P), dtype=torch.complex64, device=self.device)
+        pq = _ptr(grad_q, torch.complex64, (self.P, self.P), "grad_q")
+        st = self.lib.holo_finish_q(self.ctx, pq, _lib.ACCUMULATE_Q if accumulate else 0)
+        _check(self.lib, self.ctx, st, "holo_finish_q")
+        return grad_q
 
     def gradient_host(self, psi, sqrt_d=None, q=None, k0=0, grad_psi=None, grad_q=None):
         """holo_gradient_host: numpy in, numpy out (host buffers; copies inside the call)."""

@@ -399,3 +399,46 @@ def test_set_data_copies_the_amplitudes():
     again = h.gradient(psi)
     assert again[0] == ref[0]
     assert torch.equal(again[1], ref[1]) and torch.equal(again[2], ref[2])
+
+
+def test_deferred_probe_gradient_matches_oracle():
+    """Chunks with HOLO_DEFER_Q sum their probe-gradient sources (T and G'_j on the union
+    boxes) and holo_finish_q propagates them once: grad_q matches the oracle and the
+    per-chunk form to rounding, grad_psi and the loss are the per-chunk form's bit for bit; a
+    forward call between the chunks (a line search) leaves the pending sources intact."""
+    from paper_2407_20304_gb300 import HoloError
+    pr = make_problem(64, 128, 5, seed=31, point="object")
+    h = make_holo(pr, chunk=2)
+    psi = dev(pr["psi"], torch.complex64)
+    gp_a, gq_a = torch.empty_like(psi), torch.empty((128, 128), dtype=torch.complex64, device="cuda")
+    gp_b = torch.empty_like(psi)
+    loss_a = loss_b = 0.0
+    for i, k0 in enumerate(range(0, 5, 2)):
+        nk = min(2, 5 - k0)
+        loss_a, _, _ = h.gradient(psi[k0:k0 + nk], grad_psi=gp_a[k0:k0 + nk], grad_q=gq_a, k0=k0,
+                                  accumulate_q=i > 0, loss_in=loss_a)
+    with pytest.raises(HoloError, match="STATE"):
+        h.finish_q()
+    for i, k0 in enumerate(range(0, 5, 2)):
+        nk = min(2, 5 - k0)
+        loss_b, _, none = h.gradient(psi[k0:k0 + nk], grad_psi=gp_b[k0:k0 + nk], k0=k0,
+                                     accumulate_q=i > 0, loss_in=loss_b, defer_q=True)
+        assert none is None
+        h.forward(psi[0:2], k0=0)
+    gq_b = h.finish_q()
+    assert loss_b == loss_a and torch.equal(gp_b, gp_a)
+    assert rel(gq_b.cpu().numpy(), gq_a.cpu().numpy()) < 1e-6
+    F, gp_ref, gq_ref = oh.gradients(pr["psi"], pr["q"], pr["t"], pr["sqrt_d"], pr["sqrt_dref"],
+                                     pr["geo"])
+    assert abs(loss_b - F) / F < LOSS_TOL
+    assert rel(gq_b.cpu().numpy(), gq_ref) < GRAD_TOL
+    # finish_q adds with accumulate, and the sources are consumed
+    with pytest.raises(HoloError, match="STATE"):
+        h.finish_q()
+    # the host-buffer call does not defer (rejected before any other check)
+    from paper_2407_20304_gb300 import _lib
+    host = np.zeros((2, 64, 64), np.complex64)
+    out_q = np.zeros((128, 128), np.complex64)
+    st = h.lib.holo_gradient_host(h.ctx, 0, 2, host.ctypes.data, None, None, None,
+                                  host.ctypes.data, out_q.ctypes.data, _lib.DEFER_Q)
+    assert st == 1
