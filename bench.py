@@ -1121,7 +1121,7 @@ def run_batch(args):
                                + (f", {dropped} largest dropped for the memory budget" if dropped else ""),
                    "planes_per_step": planes,
                    "sizes": sorted({s["n"] for s in specs})},
-        "persistent": {"impl": "passes A-D of every round as persistent multi-problem launches "
+        "persistent": {"layout": b.layout, "impl": "passes A-D of every round as persistent multi-problem launches "
                                    "over device work lists (one per pass and line length), one "
                                    "captured CUDA graph, schedule autotuned per line length",
                        "ms_per_step": round(pers_ms, 3),

@@ -71,7 +71,8 @@ class HoloBatch:
         self.graph = None
         self.schedule = None
         self.tuning = {}
-        self._pb = None          # holo_batch handle of the persistent form
+        self._pbs = []           # holo_batch handles of the persistent form
+        self.layout = None
         self.pgraph = None
         self.ptuning = {}
 
@@ -176,29 +177,55 @@ class HoloBatch:
         if st != 0:
             raise _lib.HoloError(st, where, _lib.load().holo_last_error(self.inst[0].h.ctx).decode())
 
-    def prepare_persistent(self):
-        """Create (once) the library's batch over every instance, register the instances'
-        buffers and build the work lists (this sets pass_b_split = 0 on every context, so the
-        per-problem loop gives the same results)."""
-        lib = _lib.load()
-        if self._pb is None:
-            arr = (ctypes.c_void_p * len(self.inst))(*[it.h.ctx.value for it in self.inst])
-            out = ctypes.c_void_p()
-            self._check(lib.holo_batch_create(arr, len(self.inst), ctypes.byref(out)),
-                        "holo_batch_create")
-            self._pb = out
+    def _groups(self, layout):
+        """Instance indices per library batch: all in one ('one') or one batch per line length
+        ('per_length', each issued on its own graph branch)."""
+        if layout == "one":
+            return [list(range(len(self.inst)))]
+        by = {}
         for i, it in enumerate(self.inst):
-            self._check(lib.holo_batch_set_problem(
-                self._pb, i, ctypes.c_void_p(it.psi.data_ptr()), ctypes.c_void_p(it.q.data_ptr()),
-                ctypes.c_void_p(it.grad_psi.data_ptr()), ctypes.c_void_p(it.grad_q.data_ptr())),
-                "holo_batch_set_problem")
-        self._check(lib.holo_batch_prepare(self._pb), "holo_batch_prepare")
+            by.setdefault(it.h.P, []).append(i)
+        return [by[P] for P in sorted(by, reverse=True)]
+
+    def prepare_persistent(self, layout="one"):
+        """Build the library's batch(es) over the instances (holo_batch_*), register their
+        buffers and build the work lists (this sets pass_b_split = 0 on every context, so the
+        per-problem loop gives the same results).  layout: 'one' batch for all, or
+        'per_length' (one batch per line length, concurrent graph branches)."""
+        lib = _lib.load()
+        self.close()
+        self._pbs = []
+        for members in self._groups(layout):
+            arr = (ctypes.c_void_p * len(members))(*[self.inst[i].h.ctx.value for i in members])
+            out = ctypes.c_void_p()
+            self._check(lib.holo_batch_create(arr, len(members), ctypes.byref(out)),
+                        "holo_batch_create")
+            for slot, i in enumerate(members):
+                it = self.inst[i]
+                self._check(lib.holo_batch_set_problem(
+                    out, slot, ctypes.c_void_p(it.psi.data_ptr()), ctypes.c_void_p(it.q.data_ptr()),
+                    ctypes.c_void_p(it.grad_psi.data_ptr()), ctypes.c_void_p(it.grad_q.data_ptr())),
+                    "holo_batch_set_problem")
+            self._check(lib.holo_batch_prepare(out), "holo_batch_prepare")
+            self._pbs.append(out)
+        self.layout = layout
 
     def issue_persistent(self):
-        """Issue one persistent-form evaluation of the whole batch on the current stream."""
-        st = _lib.load().holo_batch_gradient(
-            self._pb, ctypes.c_void_p(torch.cuda.current_stream().cuda_stream))
-        self._check(st, "holo_batch_gradient")
+        """Issue one persistent-form evaluation of the whole batch: each library batch on its
+        own branch stream, joined back into the current stream."""
+        lib = _lib.load()
+        cur = torch.cuda.current_stream()
+        if len(self._pbs) == 1:
+            self._check(lib.holo_batch_gradient(self._pbs[0], ctypes.c_void_p(cur.cuda_stream)),
+                        "holo_batch_gradient")
+            return
+        streams = self._streams(len(self._pbs))
+        for s, pb in zip(streams, self._pbs):
+            s.wait_stream(cur)
+            self._check(lib.holo_batch_gradient(pb, ctypes.c_void_p(s.cuda_stream)),
+                        "holo_batch_gradient")
+        for s in streams:
+            cur.wait_stream(s)
 
     def capture_persistent(self):
         torch.cuda.synchronize()
@@ -215,36 +242,43 @@ class HoloBatch:
     def line_lengths(self):
         return sorted({it.h.P for it in self.inst}, reverse=True)
 
-    def autotune_persistent(self, candidates=((0, -1), (2, -1), (0, 0), (2, 0)), reps=2):
-        """Per line length, the (row blocks per SM, pass-B stage) schedule whose captured
-        persistent graph evaluates the whole batch fastest, by coordinate descent from the
-        first candidate (line lengths in decreasing order).  Returns (ms, {P: schedule})."""
+    def autotune_persistent(self, candidates=((0, -1), (2, -1), (0, 0), (2, 0)),
+                            layouts=("one", "per_length"), reps=2):
+        """The layout, then per line length the (row blocks per SM, pass-B stage) schedule,
+        whose captured persistent graph evaluates the whole batch fastest: coordinate descent
+        from the first candidate (layouts first, then line lengths in decreasing order), every
+        trial timed by graph replays.  Returns (ms, {P: schedule}); self.layout holds the
+        layout."""
         chosen = {P: candidates[0] for P in self.line_lengths()}
 
-        def apply(sched):
+        def apply(sched, layout):
             for it in self.inst:
                 rb, stage = sched[it.h.P]
                 it.h.set_schedule(rb, stage, 0)
-            self.prepare_persistent()
+            self.prepare_persistent(layout)
             self.capture_persistent()
             self.replay_persistent()
             return self._time(self.replay_persistent, reps)
 
-        best = apply(chosen)
-        self.ptuning = {"start": best}
+        best, best_layout = None, layouts[0]
+        self.ptuning = {}
+        for layout in layouts:
+            ms = apply(chosen, layout)
+            self.ptuning[f"layout {layout}"] = ms
+            if best is None or ms < best:
+                best, best_layout = ms, layout
         for P in self.line_lengths():
             for cand in candidates[1:]:
                 trial = dict(chosen)
                 trial[P] = cand
-                ms = apply(trial)
-                self.ptuning[f"P={P} {cand}"] = ms
+                ms = apply(trial, best_layout)
+                self.ptuning[f"{best_layout} P={P} {cand}"] = ms
                 if ms < best:
                     best, chosen = ms, trial
-        apply(chosen)
+        apply(chosen, best_layout)
         return best, chosen
 
     def close(self):
-        if self._pb is not None:
-            _lib.load().holo_batch_destroy(self._pb)
-            self._pb = None
-
+        for pb in getattr(self, "_pbs", []) or []:
+            _lib.load().holo_batch_destroy(pb)
+        self._pbs = []
