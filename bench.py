@@ -48,7 +48,7 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
     ap.add_argument("--workload", default="large",
-                    choices=("large", "autograd", "medium", "batch", "recon", "hier"))
+                    choices=("large", "autograd", "medium", "batch", "recon", "hier", "oracle"))
     ap.add_argument("--recon-iters", type=int, default=200,
                     help="CG iterations of --workload recon (convergence run)")
     ap.add_argument("--functional", choices=("amplitude", "intensity"), default="amplitude",
@@ -854,6 +854,55 @@ def precision_report(w):
     return out
 
 
+def run_oracle_timing(args):
+    """The FP64 oracle's own timings on the host cores (no GPU): the tiny workload's
+    reconstruction in full (psi 128^2 on 256^2, 8 angles x 4 distances, noiseless data, 10
+    joint CG iterations from psi = 1 and the perturbed probe), and plane-gradients/s at n =
+    512, 1024 and 2048 (a 4-angle x 4-distance subset at 512 and 1024, one angle x 4
+    distances at 2048) with the library FFT on every host core and on one core."""
+    from oracle import cg as ocg
+    from oracle import holo as oh
+    g = hs.WORKLOAD_GEOMETRY
+    out = {"metric": "FP64 oracle timings on the host cores", "cores": os.cpu_count(),
+           "impl": "oracle", "data": "synthetic"}
+    tw = hs.workloads()["tiny"]
+    rng = hs.rng_for(tw.seed, 201)
+    geo = oh.Geometry(g["wavelength"], g["pixel"], g["Z"], tuple(g["z"][:tw.n_dist]), tw.n, tw.P)
+    psi_true = hs.object_stack(tw, range(tw.n_angles), rng)
+    q_true = hs.striped_probe(tw.P, tw.probe_sigma, rng)
+    t = hs.sample_shifts(tw.n_angles, tw.n_dist, rng)
+    d = np.abs(oh.forward(psi_true, q_true, t, geo))
+    dr = np.abs(oh.reference_field(q_true, geo))
+    t0 = time.perf_counter()
+    r = ocg.reconstruct(np.ones((tw.n_angles, tw.n, tw.n), np.complex128),
+                        hs.perturbed_probe(q_true, rng), t, d, dr, geo, 10)
+    out["tiny_reconstruction"] = {"seconds": round(time.perf_counter() - t0, 2), "iterations": 10,
+                                  "F_first_last": [r["hist"]["F"][0], r["hist"]["F"][-1]]}
+    rates = {}
+    for n, K in ((512, 4), (1024, 4), (2048, 1)):
+        P = 2 * n
+        geo = oh.Geometry(g["wavelength"], g["pixel"], g["Z"], tuple(g["z"]), n, P)
+        wl = hs.Workload("o", n, P, K, 4, "layers", 40.0 * n / 128, 0.0, K, 0)
+        rng = hs.rng_for(hs.SEED_BASE + 202, n)
+        psi = hs.object_stack(wl, range(K), rng)
+        q = hs.striped_probe(P, 40.0 * n / 128, rng)
+        t = hs.sample_shifts(K, 4, rng)
+        d = np.abs(oh.forward(psi, q, t, geo)) * 1.01
+        entry = {"planes": K * 4}
+        for label, workers in (("all_cores", -1), ("one_core", 1)):
+            oh.FFT_WORKERS = workers
+            t0 = time.perf_counter()
+            for k in range(K):
+                for j in range(4):
+                    oh.plane_gradient(np.ones((n, n), np.complex128), q, t[k][j], d[k, j], geo, j)
+            entry[label] = round(K * 4 / (time.perf_counter() - t0), 4)
+        oh.FFT_WORKERS = -1
+        rates[str(n)] = entry
+    out["plane_gradients_per_s"] = rates
+    out["unit"] = UNIT
+    return out
+
+
 def run_reference(args, w):
     """The reference arm: the oracle timed as it stands, one plane-gradient per step."""
     inputs = oracle_setup(w)
@@ -1147,6 +1196,9 @@ def main():
         return
     if args.workload == "hier":
         print(json.dumps(run_hier(args)), flush=True)
+        return
+    if args.workload == "oracle":
+        print(json.dumps(run_oracle_timing(args)), flush=True)
         return
     w = hs.workloads()[args.workload]
     if args.chunk:

@@ -40,6 +40,10 @@ from dataclasses import dataclass, field
 import numpy as np
 import scipy.fft as sfft  # library FFT primitive (multi-threaded), as one step of D_z
 
+# Threads of the library FFT (-1: every host core).  Only the timing of the oracle depends
+# on it (a single-core timing run sets 1); the arithmetic does not.
+FFT_WORKERS = -1
+
 
 @dataclass(frozen=True)
 class Geometry:
@@ -100,7 +104,7 @@ def propagate(x, z, wavelength, dx):
     assert x.shape[-2] == P
     f = spatial_freq(P, dx)
     H = np.exp(-1j * np.pi * wavelength * z * (f[:, None] ** 2 + f[None, :] ** 2))
-    return sfft.ifft2(sfft.fft2(x, workers=-1) * H, workers=-1)
+    return sfft.ifft2(sfft.fft2(x, workers=FFT_WORKERS) * H, workers=FFT_WORKERS)
 
 
 def crop(x, n):
@@ -130,7 +134,7 @@ def shift(x, s):
     k[k >= P // 2] -= P
     ramp_y = np.exp(-2j * np.pi * k * s[0] / P)
     ramp_x = np.exp(-2j * np.pi * k * s[1] / P)
-    return sfft.ifft2(sfft.fft2(x, workers=-1) * np.outer(ramp_y, ramp_x), workers=-1)
+    return sfft.ifft2(sfft.fft2(x, workers=FFT_WORKERS) * np.outer(ramp_y, ramp_x), workers=FFT_WORKERS)
 
 
 def moved_object_shift(t, mt, s):
