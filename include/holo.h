@@ -300,9 +300,11 @@ holo_status holo_set_stream(holo_ctx* ctx, void* stream);
  *   row_blocks_per_sm  resident blocks per SM of the row passes A and C (0: as many as fit);
  *   pass_b_stage       pass B's TMA staging of its input tiles: -1 where it fits (default),
  *                      0 off (plain loads), 1 same as -1;
- *   pass_b_split       pass B's plane-split form for small problems: -1 automatic (default),
- *                      0 never (whole column groups per block), 1 whenever the last round of
- *                      column groups is partial.
+ *   pass_b_split       pass B's last, partial round of column groups: -1 automatic (default:
+ *                      split by planes with the plane-split kernel when there are fewer than
+ *                      three full rounds), 0 never split (whole column groups per block), 1
+ *                      split by the plane-split kernel (no TMA stage), 2 split inside the
+ *                      staged kernel, whenever the last round is partial.
  * HOLO_ERR_ARG for values outside these ranges. */
 holo_status holo_set_schedule(holo_ctx* ctx, int row_blocks_per_sm, int pass_b_stage,
                               int pass_b_split);

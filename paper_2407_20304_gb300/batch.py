@@ -178,20 +178,25 @@ class HoloBatch:
             raise _lib.HoloError(st, where, _lib.load().holo_last_error(self.inst[0].h.ctx).decode())
 
     def _groups(self, layout):
-        """Instance indices per library batch: all in one ('one') or one batch per line length
-        ('per_length', each issued on its own graph branch)."""
+        """Instance indices per library batch: all in one ('one'), one batch per line length
+        ('per_length'), or two per line length with the problems dealt alternately
+        ('per_length_x2'); every batch but 'one' is issued on its own graph branch."""
         if layout == "one":
             return [list(range(len(self.inst)))]
         by = {}
         for i, it in enumerate(self.inst):
             by.setdefault(it.h.P, []).append(i)
-        return [by[P] for P in sorted(by, reverse=True)]
+        groups = [by[P] for P in sorted(by, reverse=True)]
+        if layout == "per_length_x2":
+            groups = [half for g in groups for half in (g[0::2], g[1::2]) if half]
+        return groups
 
     def prepare_persistent(self, layout="one"):
         """Build the library's batch(es) over the instances (holo_batch_*), register their
         buffers and build the work lists (this sets pass_b_split = 0 on every context, so the
-        per-problem loop gives the same results).  layout: 'one' batch for all, or
-        'per_length' (one batch per line length, concurrent graph branches)."""
+        per-problem loop gives the same results).  layout: 'one' batch for all, 'per_length'
+        (one batch per line length) or 'per_length_x2' (two per line length), the batches of the
+        last two on concurrent graph branches."""
         lib = _lib.load()
         self.close()
         self._pbs = []
@@ -243,7 +248,7 @@ class HoloBatch:
         return sorted({it.h.P for it in self.inst}, reverse=True)
 
     def autotune_persistent(self, candidates=((0, -1), (2, -1), (0, 0), (2, 0)),
-                            layouts=("one", "per_length"), reps=2):
+                            layouts=("one", "per_length", "per_length_x2"), reps=2):
         """The layout, then per line length the (row blocks per SM, pass-B stage) schedule,
         whose captured persistent graph evaluates the whole batch fastest: coordinate descent
         from the first candidate (layouts first, then line lengths in decreasing order), every

@@ -553,22 +553,27 @@ PassArgs pass_args(holo_ctx* c, int k0, int nk, const void* psi) {
 //                d_red[0] and the call / running totals (k_loss_total); pass B writes or adds
 //                T = ext sum_kj r_kj (+ w_ref r_ref on the first part);
 //   eval_qgrad:  grad_q of the whole chunk from T and the per-plane conj(w) v.
-// Pass B's grid.  Whole column groups go to the blocks in rounds; when that leaves a partial
-// last round and fewer than three full ones (small n), the plane-split form spreads the
-// last round's (group, plane) items over all blocks, and its partial residual sums need
-// tslots slots of [n][C] per block.
+// Pass B's grid.  Whole column groups go to the blocks in rounds.  When that leaves a partial
+// last round, the (group, plane) items of that round can be spread over all blocks: by the
+// plane-split kernel (pb_split 1, no Y stage; the default when there are fewer than three full
+// rounds, i.e. small n) or by the staged kernel itself (pb_split 2).  The partial residual sums
+// of a split need tslots slots of [n][C] per block.
 holo_status pass_b_grid(holo_ctx* c, PassArgs& a, bool gradient, int* nblocks) {
   const int groups = a.pass_b_items;
   const int full = c->ops->pass_b_blocks(1 << 30, c->n, a.ymap ? a.max_box_rows : 0);
-  a.pb_split = c->sched_split < 0 ? (groups % full != 0 && groups / full < 3)
-                                  : (c->sched_split > 0 && groups % full != 0);
+  const bool partial = groups % full != 0;
+  if (c->sched_split < 0)
+    a.pb_split = partial && groups / full < 3 ? 1 : 0;
+  else
+    a.pb_split = partial ? c->sched_split : 0;
   a.tslots = 0;
   if (!a.pb_split) {
     *nblocks = std::min(full, groups);
     return HOLO_OK;
   }
   const long long per = (long long)a.J * a.nk;
-  const int nbx = c->ops->pass_b_blocks_split((long long)groups * per, c->n);
+  const int nbx = a.pb_split == 2 ? full
+                                  : c->ops->pass_b_blocks_split((long long)groups * per, c->n);
   const long long rounds = groups / nbx, tail = groups - rounds * nbx, titems = tail * per;
   const long long range = (titems + nbx - 1) / nbx;
   a.tslots = titems > 0 ? (int)((range + per - 1) / per + 1) : 0;
@@ -623,8 +628,11 @@ holo_status eval_planes(holo_ctx* c, PassArgs& a, bool gradient, bool first, int
     PassArgs ab = a;
     if (c->probe_shift) ab.ext = 0.f;
     HOLO_LAUNCH(c, c->ops->pass_b(ab, gradient ? 1 : 0, nbx, c->stream));
-    // the last round's combine kernel of the plane-split form
-    if (gradient && a.pb_split && a.pass_b_items % nbx) c->launches++;
+    // the last round's combine kernel of a split form (the staged split is compiled for the
+    // form without probe shifts only; with them pb_split 2 runs whole groups)
+    if (gradient && (a.pb_split == 1 || (a.pb_split == 2 && !c->probe_shift)) &&
+        a.pass_b_items % nbx)
+      c->launches++;
   }
   {
     PassTimer tm_red(c, HOLO_T_REDUCE);
@@ -1483,8 +1491,8 @@ holo_status holo_set_functional(holo_ctx* c, int functional) {
 holo_status holo_set_schedule(holo_ctx* c, int row_blocks_per_sm, int pass_b_stage,
                               int pass_b_split) {
   if (!c || row_blocks_per_sm < 0 || pass_b_stage < -1 || pass_b_stage > 1 || pass_b_split < -1 ||
-      pass_b_split > 1)
-    return fail(c, HOLO_ERR_ARG, "schedule: blocks per SM >= 0, stage and split in {-1, 0, 1}");
+      pass_b_split > 2)
+    return fail(c, HOLO_ERR_ARG, "schedule: blocks per SM >= 0, stage in {-1, 0, 1}, split in {-1 .. 2}");
   c->sched_row_per_sm = row_blocks_per_sm;
   c->sched_stage = pass_b_stage;
   c->sched_split = pass_b_split;

@@ -389,8 +389,10 @@ __device__ __forceinline__ void stage_y(const PassArgs& a, float2* stg, uint64_t
 // bid, bid + nblk, ...; its FP64 loss partial goes to a.loss_part[bid].  The caller has loaded
 // the twiddle roots at the head of shared memory and, for a staged problem, initialised the
 // Y-stage barrier.  The resident chirp table is identified by pkey * 16 + distance.  Returns
-// false when a bounded Y-stage wait gave up (the problem's error word is then set).
-template <int P, bool ADJ, bool SHIFT>
+// false when a bounded Y-stage wait gave up (the problem's error word is then set).  TSPLIT
+// compiles in the split of a partial last round (a.pb_split == 2); without it the block's
+// work is whole groups only and the segment bookkeeping folds away.
+template <int P, bool ADJ, bool SHIFT, bool TSPLIT = false>
 __device__ __forceinline__ bool pass_b_run(const PassArgs& a, int bid, int nblk, float2* smem,
                                            const TwRoots& tw, double* red, uint64_t* ybarp,
                                            uint32_t& yphase, int pkey, int& jcur) {
@@ -410,8 +412,37 @@ __device__ __forceinline__ bool pass_b_run(const PassArgs& a, int bid, int nblk,
   const bool staged = a.ymap != nullptr;
   float2* stg = reinterpret_cast<float2*>((reinterpret_cast<uintptr_t>(sS + n * C) + 127) &
                                           ~static_cast<uintptr_t>(127));
-  if (staged && threadIdx.x == 0 && bid < ngroups) stage_y<P>(a, stg, ybarp, bid, 0, 0);
-  for (int cg = bid; cg < ngroups; cg += nblk) {
+  // The block's work as segments {column group cg, planes [p0, p1)} with the planes in
+  // (distance, angle) order p = j * nk + kl: whole groups bid, bid + nblk, ...; with the last
+  // round split (a.pb_split == 2), the full rounds' whole groups and then the block's even share
+  // of the last round's (group, plane) items, whose residual sums go to the block's slots.
+  const int per = a.J * a.nk;
+  const bool tsplit = TSPLIT && a.pb_split == 2 && ngroups % nblk != 0;
+  const int rounds = tsplit ? ngroups / nblk : (ngroups - bid + nblk - 1) / nblk;
+  const long long titems = tsplit ? (long long)(ngroups - rounds * nblk) * per : 0;
+  const long long ti0 = titems * bid / nblk, ti1 = titems * (bid + 1) / nblk;
+  auto segment = [&](int sg, int& gcg, int& q0, int& q1) -> bool {
+    if (sg < rounds) {
+      gcg = bid + sg * nblk;
+      q0 = 0;
+      q1 = per;
+      return true;
+    }
+    if (!TSPLIT) return false;
+    const long long tg = ti0 / per + (sg - rounds), g0 = tg * per;
+    if (ti0 >= ti1 || g0 >= ti1) return false;
+    gcg = rounds * nblk + (int)tg;
+    q0 = (int)(ti0 > g0 ? ti0 - g0 : 0);
+    q1 = (int)(ti1 - g0 < per ? ti1 - g0 : per);
+    return true;
+  };
+  {
+    int c0, q0, q1;
+    if (staged && threadIdx.x == 0 && segment(0, c0, q0, q1))
+      stage_y<P>(a, stg, ybarp, c0, q0 / a.nk, q0 % a.nk);
+  }
+  int cg, p0, p1;
+  for (int sg = 0; segment(sg, cg, p0, p1); ++sg) {
     const int col = cg * C + g;
     const bool valid = col < n;
 #pragma unroll
@@ -423,9 +454,10 @@ __device__ __forceinline__ bool pass_b_run(const PassArgs& a, int bid, int nblk,
         if (ADJ) sS[rr * C + g] = make_float2(0.f, 0.f);
       }
     }
-    for (int j = 0; j < a.J; ++j) {
+    for (int pp = p0; pp < p1; ++pp) {
+      const int j = pp / a.nk, kl = pp - j * a.nk;
       ensure_chirp_key<P>(chs, a.chirp_zhat, j, pkey * 16 + j, jcur);
-      for (int kl = 0; kl < a.nk; ++kl) {
+      {
         const int lp = kl * a.J + j;
         const long long gplane = (long long)(a.k0 + kl) * a.J + j;
         const PlaneDesc d = a.planes[gplane];
@@ -446,15 +478,13 @@ __device__ __forceinline__ bool pass_b_run(const PassArgs& a, int bid, int nblk,
             return false;
           }
           if (threadIdx.x == 0) {
-            int nkl = kl + 1, nj = j, ncg = cg;
-            if (nkl == a.nk) {
-              nkl = 0;
-              if (++nj == a.J) {
-                nj = 0;
-                ncg += nblk;
-              }
+            int ncg = cg, np = pp + 1, n0, n1;
+            bool more = np < p1;
+            if (!more && segment(sg + 1, ncg, n0, n1)) {
+              np = n0;
+              more = true;
             }
-            if (ncg < ngroups) stage_y<P>(a, stg, ybarp, ncg, nj, nkl);
+            if (more) stage_y<P>(a, stg, ybarp, ncg, np / a.nk, np % a.nk);
           }
         } else {
 #pragma unroll
@@ -534,19 +564,30 @@ __device__ __forceinline__ bool pass_b_run(const PassArgs& a, int bid, int nblk,
       }
     }
     if constexpr (ADJ) {
+      if (!TSPLIT || sg < rounds) {
 #pragma unroll
-      for (int c = 0; c < 16; ++c) {
-        const int rr = F::pos(t, c) - lo;
-        if (valid && (unsigned)rr < (unsigned)n) {
-          const long long e = (long long)rr * n + col;
-          float2 acc = cscale(sS[rr * C + g], a.ext);
-          if (a.tq_accumulate) acc = cadd(acc, a.tq[e]);
-          if (a.rref) {
-            const float2 q = __ldg(a.rref + e);
-            acc.x = fmaf(a.wref, q.x, acc.x);
-            acc.y = fmaf(a.wref, q.y, acc.y);
+        for (int c = 0; c < 16; ++c) {
+          const int rr = F::pos(t, c) - lo;
+          if (valid && (unsigned)rr < (unsigned)n) {
+            const long long e = (long long)rr * n + col;
+            float2 acc = cscale(sS[rr * C + g], a.ext);
+            if (a.tq_accumulate) acc = cadd(acc, a.tq[e]);
+            if (a.rref) {
+              const float2 q = __ldg(a.rref + e);
+              acc.x = fmaf(a.wref, q.x, acc.x);
+              acc.y = fmaf(a.wref, q.y, acc.y);
+            }
+            a.tq[e] = acc;
           }
-          a.tq[e] = acc;
+        }
+      } else if constexpr (TSPLIT) {
+        // part of a last-round group: its partial residual sum goes to the block's slot
+        // sg - rounds; k_pass_b_tail adds the slots of the group in block order into T
+        float2* dst = a.tpart + ((long long)bid * a.tslots + (sg - rounds)) * n * C;
+#pragma unroll
+        for (int c = 0; c < 16; ++c) {
+          const int rr = F::pos(t, c) - lo;
+          if ((unsigned)rr < (unsigned)n) dst[rr * C + g] = sS[rr * C + g];
         }
       }
     }
@@ -556,7 +597,7 @@ __device__ __forceinline__ bool pass_b_run(const PassArgs& a, int bid, int nblk,
   return true;
 }
 
-template <int P, bool ADJ, bool SHIFT>
+template <int P, bool ADJ, bool SHIFT, bool TSPLIT = false>
 __global__ void __launch_bounds__(ColCfg<P>::NT) k_pass_b(const __grid_constant__ PassArgs a) {
   extern __shared__ float2 smem[];
   __shared__ double red[32];
@@ -569,7 +610,8 @@ __global__ void __launch_bounds__(ColCfg<P>::NT) k_pass_b(const __grid_constant_
   }
   uint32_t yphase = 0;
   int jcur = -1;
-  pass_b_run<P, ADJ, SHIFT>(a, blockIdx.x, gridDim.x, smem, tw, red, &ybar, yphase, 0, jcur);
+  pass_b_run<P, ADJ, SHIFT, TSPLIT>(a, blockIdx.x, gridDim.x, smem, tw, red, &ybar, yphase, 0,
+                                    jcur);
 }
 
 // Pass B of several problems of line length P in one persistent launch: items {problem, b},
@@ -1196,20 +1238,38 @@ cudaError_t launch_pass_b_split(const PassArgs& a, int nblocks, size_t sm, cudaS
   return cudaGetLastError();
 }
 
+template <int P, bool ADJ, bool SHIFT, bool TSPLIT>
+cudaError_t launch_pass_b_staged(const PassArgs& a, int nblocks, cudaStream_t s) {
+  using Cc = ColCfg<P>;
+  const size_t sm = pass_b_smem<P>(a.n, a.ymap ? a.max_box_rows : 0);
+  cudaError_t e = cudaFuncSetAttribute(k_pass_b<P, ADJ, SHIFT, TSPLIT>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  if (e != cudaSuccess) return e;
+  k_pass_b<P, ADJ, SHIFT, TSPLIT><<<nblocks, Cc::NT, sm, s>>>(a);
+  const int ngroups = (a.n + Cc::C - 1) / Cc::C, tail = ngroups - (ngroups / nblocks) * nblocks;
+  if (TSPLIT && tail > 0) {
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    k_pass_b_tail<P><<<tail, 256, 0, s>>>(a, nblocks);
+  }
+  return cudaGetLastError();
+}
+
+// pb_split: 0 whole column groups per block; 1 the plane-split kernel (no Y stage); 2 the
+// staged kernel with its last round split by planes, then the combine kernel.  The staged
+// split is compiled for the gradient without probe shifts; the other forms run pb_split 2 as
+// whole groups on the same grid.
 template <int P, bool ADJ, bool SHIFT>
 cudaError_t launch_pass_b_form(const PassArgs& a, int nblocks, cudaStream_t s) {
-  using Cc = ColCfg<P>;
-  if (a.pb_split) {
+  if (a.pb_split == 1) {
     PassArgs b = a;
     b.ymap = nullptr;
     return launch_pass_b_split<P, ADJ, SHIFT>(b, nblocks, pass_b_smem<P>(a.n), s);
   }
-  const size_t sm = pass_b_smem<P>(a.n, a.ymap ? a.max_box_rows : 0);
-  cudaError_t e = cudaFuncSetAttribute(k_pass_b<P, ADJ, SHIFT>,
-                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-  if (e != cudaSuccess) return e;
-  k_pass_b<P, ADJ, SHIFT><<<nblocks, Cc::NT, sm, s>>>(a);
-  return cudaGetLastError();
+  if constexpr (ADJ && !SHIFT) {
+    if (a.pb_split == 2) return launch_pass_b_staged<P, true, false, true>(a, nblocks, s);
+  }
+  return launch_pass_b_staged<P, ADJ, SHIFT, false>(a, nblocks, s);
 }
 
 // The SHIFT form (probe shifts) runs without the Y stage: its box is the whole grid.

@@ -375,7 +375,8 @@ class Holo:
 
     def set_schedule(self, row_blocks_per_sm=0, pass_b_stage=-1, pass_b_split=-1):
         """holo_set_schedule: resident row-pass blocks per SM (0: as many as fit), pass B's
-        TMA stage (-1 auto, 0 off) and plane-split form (-1 auto, 0 never, 1 when partial)."""
+        TMA stage (-1 auto, 0 off) and the split of its partial last round of column groups
+        (-1 auto, 0 never, 1 plane-split kernel, 2 inside the staged kernel)."""
         st = self.lib.holo_set_schedule(self.ctx, row_blocks_per_sm, pass_b_stage, pass_b_split)
         _check(self.lib, self.ctx, st, "holo_set_schedule")
         self.schedule = (row_blocks_per_sm, pass_b_stage, pass_b_split)

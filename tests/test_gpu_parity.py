@@ -169,6 +169,36 @@ def test_gradient_away_from_start_matches_oracle(n, P, K, J, point):
     assert e[0] < LOSS_TOL and e[1] < GRAD_TOL and e[2] < GRAD_TOL
 
 
+# Pass B's forms of a partial last round of column groups (holo_set_schedule's pass_b_split):
+# 0 whole groups per block, 1 the plane-split kernel, 2 the split inside the staged kernel
+# (with the Y stage from P = 1024 up), each against the oracle, forward loss included.
+SPLITS = [(64, 128, 2, 4, 0), (64, 128, 2, 4, 2), (100, 256, 2, 4, 1), (384, 768, 2, 4, 2),
+          (1024, 2048, 1, 4, 0), (1024, 2048, 1, 4, 1), (1024, 2048, 1, 4, 2),
+          (1826, 2048, 2, 2, 2), (1536, 3072, 1, 2, 2), (2048, 4096, 1, 2, 2),
+          (2048, 4096, 2, 2, 1)]
+
+
+@pytest.mark.parametrize("n,P,K,J,split", SPLITS)
+def test_pass_b_split_forms_match_oracle(n, P, K, J, split):
+    pr = make_problem(n, P, K, J=J, seed=5 * n + J + split, point="object")
+    h = make_holo(pr)
+    h.set_schedule(0, -1, split)
+    psi = dev(pr["psi"], torch.complex64)
+    loss_f = h.forward(psi)
+    loss, gp, gq = h.gradient(psi)
+    F, gp_ref, gq_ref = oh.gradients(pr["psi"], pr["q"], pr["t"], pr["sqrt_d"], pr["sqrt_dref"],
+                                     pr["geo"])
+    e = (abs(loss - F) / F, rel(gp.cpu().numpy(), gp_ref), rel(gq.cpu().numpy(), gq_ref))
+    print(f"n={n} P={P} split {split}: loss {e[0]:.2e}, grad_psi {e[1]:.2e}, grad_q {e[2]:.2e}")
+    assert abs(loss_f - F) / F < LOSS_TOL
+    assert e[0] < LOSS_TOL and e[1] < GRAD_TOL and e[2] < GRAD_TOL
+    # a second evaluation reuses the slots: the same results bit for bit
+    loss2, gp2, gq2 = h.gradient(psi)
+    assert loss2 == loss and torch.equal(gp2, gp) and torch.equal(gq2, gq)
+    with pytest.raises(RuntimeError):
+        h.set_schedule(0, -1, 3)
+
+
 @pytest.mark.parametrize("n,P,K,point", [(64, 128, 2, "iterated"), (96, 192, 2, "iterated"),
                                          (1024, 2048, 1, "object")])
 def test_forward_fields_away_from_start(n, P, K, point):
