@@ -110,6 +110,37 @@ __device__ __forceinline__ float2 chirp_half(const float2* __restrict__ tab, int
   return tab[Fft<P>::HW ? spad(i) : i];
 }
 
+// chirp_half at the frequencies fpos(t, c) held by thread t after the forward transform.
+// For P = 2^k these are b + T c (b the thread's base, below T): entry b + T c for c < 8 and
+// entry (T - b) + T (15 - c) for c >= 8 (the P/2 entry included), and at P = 4096 the padded
+// index spad of either is linear in c with step T + T/16 (T = 256).  So two per-thread offsets
+// make every lookup one shared-memory load at a constant offset.  P = 3 * 2^k keeps
+// chirp_half.
+template <int P, bool R3 = Fft<P>::R3>
+struct ChirpAt {
+  const float2* tab;
+  int t;
+  __device__ __forceinline__ ChirpAt(const float2* tb, int tt) : tab(tb), t(tt) {}
+  __device__ __forceinline__ float2 operator()(int c) const {
+    return chirp_half<P>(tab, Fft<P>::fpos(t, c));
+  }
+};
+template <int P>
+struct ChirpAt<P, false> {
+  using F = Fft<P>;
+  static constexpr int K = F::HW ? F::T + F::T / 16 : F::T;
+  const float2* tab;
+  int lo, hi;
+  __device__ __forceinline__ ChirpAt(const float2* tb, int t) : tab(tb) {
+    const int b = F::fpos(t, 0);
+    lo = F::HW ? spad(b) : b;
+    hi = F::HW ? spad(F::T - b) : F::T - b;
+  }
+  __device__ __forceinline__ float2 operator()(int c) const {
+    return c < 8 ? tab[lo + K * c] : tab[hi + K * (15 - c)];
+  }
+};
+
 // Copy the half chirp table of distance j into shared memory (block-wide).
 template <int P>
 __device__ __forceinline__ void load_chirp_half(float2* dst, const float2* __restrict__ src) {
@@ -135,6 +166,7 @@ k_line_dstep(LineArgs a, const float2* __restrict__ gtw) {
   load_roots<P>(roots, gtw);
   load_chirp_half<P>(chs, a.chirp);
   const TwRoots tw{roots};
+  const ChirpAt<P> cat(chs, t);
   for (int base = blockIdx.x * G; base < a.nlines; base += gridDim.x * G) {
     const int line = base + g;
     const bool valid = line < a.nlines;
@@ -150,7 +182,7 @@ k_line_dstep(LineArgs a, const float2* __restrict__ gtw) {
     fft_fwd_with<P>(v, sm, tw, t, SyncBlock());
 #pragma unroll
     for (int c = 0; c < 16; ++c) {
-      const float2 ch = chirp_half<P>(chs, F::fpos(t, c));
+      const float2 ch = cat(c);
       v[c] = a.conj_chirp ? cmulc(v[c], ch) : cmul(v[c], ch);
     }
     fft_inv_with<P>(v, sm, tw, t, SyncBlock());
@@ -297,11 +329,12 @@ __device__ __forceinline__ void pass_a_step(const Args& a, int base, int next, f
     fft_fwd_with<P>(v, sm, tw, t, SyncBlock());
     const bool own = R::G == 1 || pkey * 16 + j == jcur;
     const float2* chg = a.chirp_zhat + (long long)j * P;
+    const ChirpAt<P> cat(chs, t);
     const float2* rmp = SHIFT ? a.ramp_x + (long long)gp * P : nullptr;
 #pragma unroll
     for (int c = 0; c < 16; ++c) {
       const int f = F::fpos(t, c);
-      v[c] = cmul(v[c], own ? chirp_half<P>(chs, f) : __ldg(chg + f));
+      v[c] = cmul(v[c], own ? cat(c) : __ldg(chg + f));
       if (SHIFT) v[c] = cmul(v[c], __ldg(rmp + f));
     }
     fft_inv_with<P>(v, sm, tw, t, SyncBlock());
@@ -402,6 +435,7 @@ __device__ __forceinline__ bool pass_b_run(const PassArgs& a, int bid, int nblk,
   constexpr int C = Cc::C;
   float2* chs = smem + H::ROOTS;
   const int g = threadIdx.x % C, t = threadIdx.x / C;
+  const ChirpAt<P> cat(chs, t);
   float2* sm = smem + H::WORDS + g * Cc::LS;
   const int n = a.n, lo = P / 2 - n / 2;
   float2* sb = smem + H::WORDS + C * Cc::LS;
@@ -508,7 +542,7 @@ __device__ __forceinline__ bool pass_b_run(const PassArgs& a, int bid, int nblk,
         const float2* rmp = SHIFT ? a.ramp_y + gplane * P : nullptr;
 #pragma unroll
         for (int c = 0; c < 16; ++c) {
-          v[c] = cmul(v[c], chirp_half<P>(chs, F::fpos(t, c)));
+          v[c] = cmul(v[c], cat(c));
           if (SHIFT) v[c] = cmul(v[c], __ldg(rmp + F::fpos(t, c)));
         }
         fft_inv_with<P>(v, sm, tw, t, SyncBlock());
@@ -535,7 +569,7 @@ __device__ __forceinline__ bool pass_b_run(const PassArgs& a, int bid, int nblk,
             } else {
               const float mag = sqrtf(i2);
               diff = mag - dat;
-              s = mag > 0.f ? 1.f - dat / mag : 0.f;
+              s = mag > 0.f ? 1.f - __fdividef(dat, mag) : 0.f;
             }
             lsum = fmaf(diff, diff, lsum);
             if (uo) uo[e] = u;
@@ -551,7 +585,7 @@ __device__ __forceinline__ bool pass_b_run(const PassArgs& a, int bid, int nblk,
           fft_fwd_with<P>(v, sm, tw, t, SyncBlock());
 #pragma unroll
           for (int c = 0; c < 16; ++c) {
-            v[c] = cmulc(v[c], chirp_half<P>(chs, F::fpos(t, c)));
+            v[c] = cmulc(v[c], cat(c));
             if (SHIFT) v[c] = cmulc(v[c], __ldg(rmp + F::fpos(t, c)));
           }
           fft_inv_with<P>(v, sm, tw, t, SyncBlock());
@@ -659,6 +693,7 @@ __global__ void __launch_bounds__(ColCfg<P>::NT) k_pass_b_split(PassArgs a) {
   float2* roots = smem;
   float2* chs = smem + H::ROOTS;
   const int g = threadIdx.x % C, t = threadIdx.x / C;
+  const ChirpAt<P> cat(chs, t);
   float2* sm = smem + H::WORDS + g * Cc::LS;
   const int n = a.n, lo = P / 2 - n / 2;
   float2* sb = smem + H::WORDS + C * Cc::LS;
@@ -710,7 +745,7 @@ __global__ void __launch_bounds__(ColCfg<P>::NT) k_pass_b_split(PassArgs a) {
     const float2* rmp = SHIFT ? a.ramp_y + gplane * P : nullptr;
 #pragma unroll
     for (int c = 0; c < 16; ++c) {
-      v[c] = cmul(v[c], chirp_half<P>(chs, F::fpos(t, c)));
+      v[c] = cmul(v[c], cat(c));
       if (SHIFT) v[c] = cmul(v[c], __ldg(rmp + F::fpos(t, c)));
     }
     fft_inv_with<P>(v, sm, tw, t, SyncBlock());
@@ -735,7 +770,7 @@ __global__ void __launch_bounds__(ColCfg<P>::NT) k_pass_b_split(PassArgs a) {
         } else {
           const float mag = sqrtf(i2);
           diff = mag - dat;
-          s = mag > 0.f ? 1.f - dat / mag : 0.f;
+          s = mag > 0.f ? 1.f - __fdividef(dat, mag) : 0.f;
         }
         lsum = fmaf(diff, diff, lsum);
         if (uo) uo[e] = u;
@@ -751,7 +786,7 @@ __global__ void __launch_bounds__(ColCfg<P>::NT) k_pass_b_split(PassArgs a) {
       fft_fwd_with<P>(v, sm, tw, t, SyncBlock());
 #pragma unroll
       for (int c = 0; c < 16; ++c) {
-        v[c] = cmulc(v[c], chirp_half<P>(chs, F::fpos(t, c)));
+        v[c] = cmulc(v[c], cat(c));
         if (SHIFT) v[c] = cmulc(v[c], __ldg(rmp + F::fpos(t, c)));
       }
       fft_inv_with<P>(v, sm, tw, t, SyncBlock());
@@ -921,11 +956,12 @@ __device__ __forceinline__ void pass_c_items(const PassArgs* __restrict__ args,
     fft_fwd_with<P>(v, sm, tw, t, SyncBlock());
     const bool own = R::G == 1 || pkey * 16 + j == jcur;
     const float2* chg = a.chirp_zhat + (long long)j * P;
+    const ChirpAt<P> cat(chs, t);
     const float2* rmp = SHIFT ? a.ramp_x + (long long)gp * P : nullptr;
 #pragma unroll
     for (int c = 0; c < 16; ++c) {
       const int f = F::fpos(t, c);
-      v[c] = cmulc(v[c], own ? chirp_half<P>(chs, f) : __ldg(chg + f));
+      v[c] = cmulc(v[c], own ? cat(c) : __ldg(chg + f));
       if (SHIFT) v[c] = cmulc(v[c], __ldg(rmp + f));
     }
     fft_inv_with<P>(v, sm, tw, t, SyncBlock());
@@ -1020,11 +1056,12 @@ __global__ void __launch_bounds__(RowCfg<P>::NT, RowCfg<P>::MINB) k_pass_c(PassA
     fft_fwd_with<P>(v, sm, tw, t, SyncBlock());
     const bool own = R::G == 1 || j == jcur;
     const float2* chg = a.chirp_zhat + (long long)j * P;
+    const ChirpAt<P> cat(chs, t);
     const float2* rmp = SHIFT ? a.ramp_x + (long long)gp * P : nullptr;
 #pragma unroll
     for (int c = 0; c < 16; ++c) {
       const int f = F::fpos(t, c);
-      v[c] = cmulc(v[c], own ? chirp_half<P>(chs, f) : __ldg(chg + f));
+      v[c] = cmulc(v[c], own ? cat(c) : __ldg(chg + f));
       if (SHIFT) v[c] = cmulc(v[c], __ldg(rmp + f));
     }
     fft_inv_with<P>(v, sm, tw, t, SyncBlock());
