@@ -284,8 +284,8 @@ holo_status holo_get_timing(holo_ctx* ctx, double* ms, long long* launches);
  * partial sums live in a fixed 512 KiB device array inside the library (held on every GPU
  * that loads it until the process exits), so n_c64 may be at most 268435456 (2^28);
  * longer inputs return HOLO_ERR_UNSUPPORTED before any device work.  The first call on a
- * device looks up that array's device address (with the device current); make it before
- * any stream capture.  All calls share the array: calls that overlap on the GPU race.
+ * device looks up that array's device address (with the device current).  All calls share
+ * the array: calls that overlap on the GPU race.
  * There is no context to hold error text: HOLO_ERR_CUDA comes without details. */
 holo_status holo_dot_noalloc(const void* a, const void* b, long long n_c64, double* re_out,
                              void* stream);
