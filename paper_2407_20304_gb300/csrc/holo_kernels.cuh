@@ -230,7 +230,7 @@ __device__ __forceinline__ void ensure_chirp_key(float2* chs, const float2* __re
 // the block's next step in the same problem (its lines are prefetched into L2), or -1.  The
 // resident chirp table is identified by pkey * 16 + distance (pkey: the problem's index in a
 // batch, 0 for a single problem).
-template <int P, bool SHIFT, class Args>
+template <int P, bool SHIFT, bool HALF = false, class Args>
 __device__ __forceinline__ void pass_a_step(const Args& a, int base, int next, float2* smem,
                                             const TwRoots& tw, int pkey, int& jcur) {
   using F = Fft<P>;
@@ -342,12 +342,13 @@ __device__ __forceinline__ void pass_a_step(const Args& a, int base, int next, f
 #pragma unroll
     for (int c = 0; c < 16; ++c) {
       const int rel = F::pos(t, c) - lo;
-      if (valid && (unsigned)rel < (unsigned)n) yrow[rel] = v[c];
+      // HALF (n = P/2, P = 2^k >= 1024): the crop columns are those of registers 4 .. 11
+      if (valid && (HALF ? (c >= 4 && c < 12) : (unsigned)rel < (unsigned)n)) yrow[rel] = v[c];
     }
   }
 }
 
-template <int P, bool SHIFT>
+template <int P, bool SHIFT, bool HALF = false>
 __global__ void __launch_bounds__(RowCfg<P>::NT, RowCfg<P>::MINB)
 k_pass_a(const __grid_constant__ PassArgs a) {
   extern __shared__ float2 smem[];
@@ -356,7 +357,8 @@ k_pass_a(const __grid_constant__ PassArgs a) {
   int jcur = -1;
   const int step = gridDim.x * RowCfg<P>::G;
   for (int base = blockIdx.x * RowCfg<P>::G; base < a.nlines; base += step)
-    pass_a_step<P, SHIFT>(a, base, base + step < a.nlines ? base + step : -1, smem, tw, 0, jcur);
+    pass_a_step<P, SHIFT, HALF>(a, base, base + step < a.nlines ? base + step : -1, smem, tw, 0,
+                                jcur);
 }
 
 // Pass A of several problems of line length P in one persistent launch: items {problem,
@@ -425,7 +427,7 @@ __device__ __forceinline__ void stage_y(const PassArgs& a, float2* stg, uint64_t
 // false when a bounded Y-stage wait gave up (the problem's error word is then set).  TSPLIT
 // compiles in the split of a partial last round (a.pb_split == 2); without it the block's
 // work is whole groups only and the segment bookkeeping folds away.
-template <int P, bool ADJ, bool SHIFT, bool TSPLIT = false>
+template <int P, bool ADJ, bool SHIFT, bool TSPLIT = false, bool HALF = false>
 __device__ __forceinline__ bool pass_b_run(const PassArgs& a, int bid, int nblk, float2* smem,
                                            const TwRoots& tw, double* red, uint64_t* ybarp,
                                            uint32_t& yphase, int pkey, int& jcur) {
@@ -438,6 +440,14 @@ __device__ __forceinline__ bool pass_b_run(const PassArgs& a, int bid, int nblk,
   const ChirpAt<P> cat(chs, t);
   float2* sm = smem + H::WORDS + g * Cc::LS;
   const int n = a.n, lo = P / 2 - n / 2;
+  // HALF: n = P/2 with P = 2^k >= 1024, so the crop rows P/4 .. 3P/4 held by register c are
+  // those of c = 4 .. 11 exactly and C divides n (every column of a group is in the crop); the
+  // compiler then drops the checks, the zero inputs of the adjoint transform and the unused
+  // outputs of the forward one
+  static_assert(!HALF || (!F::R3 && P >= 1024), "the HALF form needs P = 2^k >= 1024");
+  auto in_crop = [&](int c, int rr) {
+    return HALF ? (c >= 4 && c < 12) : (unsigned)rr < (unsigned)n;
+  };
   float2* sb = smem + H::WORDS + C * Cc::LS;
   float2* sS = sb + n * C;
   const int ngroups = (n + C - 1) / C;
@@ -478,11 +488,11 @@ __device__ __forceinline__ bool pass_b_run(const PassArgs& a, int bid, int nblk,
   int cg, p0, p1;
   for (int sg = 0; segment(sg, cg, p0, p1); ++sg) {
     const int col = cg * C + g;
-    const bool valid = col < n;
+    const bool valid = HALF || col < n;
 #pragma unroll
     for (int c = 0; c < 16; ++c) {
       const int rr = F::pos(t, c) - lo;
-      if ((unsigned)rr < (unsigned)n) {
+      if (in_crop(c, rr)) {
         sb[rr * C + g] = (valid && a.ext != 0.f) ? __ldg(a.bref + (long long)rr * n + col)
                                                  : make_float2(0.f, 0.f);
         if (ADJ) sS[rr * C + g] = make_float2(0.f, 0.f);
@@ -537,7 +547,7 @@ __device__ __forceinline__ bool pass_b_run(const PassArgs& a, int bid, int nblk,
 #pragma unroll
         for (int c = 0; c < 16; ++c) {
           const int rr = F::pos(t, c) - lo;
-          dats[c] = (valid && (unsigned)rr < (unsigned)n) ? __ldg(ad + rr * C + g) : 0.f;
+          dats[c] = (valid && in_crop(c, rr)) ? __ldg(ad + rr * C + g) : 0.f;
         }
         const float2* rmp = SHIFT ? a.ramp_y + gplane * P : nullptr;
 #pragma unroll
@@ -552,7 +562,7 @@ __device__ __forceinline__ bool pass_b_run(const PassArgs& a, int bid, int nblk,
         for (int c = 0; c < 16; ++c) {
           const int rr = F::pos(t, c) - lo;
           float2 r = make_float2(0.f, 0.f);
-          if (valid && (unsigned)rr < (unsigned)n) {
+          if (valid && in_crop(c, rr)) {
             const long long e = (long long)rr * n + col;
             float2 u = v[c];
             const float2 b = sb[rr * C + g];
@@ -602,7 +612,7 @@ __device__ __forceinline__ bool pass_b_run(const PassArgs& a, int bid, int nblk,
 #pragma unroll
         for (int c = 0; c < 16; ++c) {
           const int rr = F::pos(t, c) - lo;
-          if (valid && (unsigned)rr < (unsigned)n) {
+          if (valid && in_crop(c, rr)) {
             const long long e = (long long)rr * n + col;
             float2 acc = cscale(sS[rr * C + g], a.ext);
             if (a.tq_accumulate) acc = cadd(acc, a.tq[e]);
@@ -621,7 +631,7 @@ __device__ __forceinline__ bool pass_b_run(const PassArgs& a, int bid, int nblk,
 #pragma unroll
         for (int c = 0; c < 16; ++c) {
           const int rr = F::pos(t, c) - lo;
-          if ((unsigned)rr < (unsigned)n) dst[rr * C + g] = sS[rr * C + g];
+          if (in_crop(c, rr)) dst[rr * C + g] = sS[rr * C + g];
         }
       }
     }
@@ -631,7 +641,7 @@ __device__ __forceinline__ bool pass_b_run(const PassArgs& a, int bid, int nblk,
   return true;
 }
 
-template <int P, bool ADJ, bool SHIFT, bool TSPLIT = false>
+template <int P, bool ADJ, bool SHIFT, bool TSPLIT = false, bool HALF = false>
 __global__ void __launch_bounds__(ColCfg<P>::NT) k_pass_b(const __grid_constant__ PassArgs a) {
   extern __shared__ float2 smem[];
   __shared__ double red[32];
@@ -644,8 +654,8 @@ __global__ void __launch_bounds__(ColCfg<P>::NT) k_pass_b(const __grid_constant_
   }
   uint32_t yphase = 0;
   int jcur = -1;
-  pass_b_run<P, ADJ, SHIFT, TSPLIT>(a, blockIdx.x, gridDim.x, smem, tw, red, &ybar, yphase, 0,
-                                    jcur);
+  pass_b_run<P, ADJ, SHIFT, TSPLIT, HALF>(a, blockIdx.x, gridDim.x, smem, tw, red, &ybar, yphase,
+                                          0, jcur);
 }
 
 // Pass B of several problems of line length P in one persistent launch: items {problem, b},
@@ -1008,7 +1018,7 @@ __device__ __forceinline__ void pass_c_items(const PassArgs* __restrict__ args,
 
 // The single-problem pass C keeps its own grid-stride loop over the lines: built on the shared
 // body below it measured slower (more spills).
-template <int P, bool SHIFT>
+template <int P, bool SHIFT, bool HALF = false>
 __global__ void __launch_bounds__(RowCfg<P>::NT, RowCfg<P>::MINB) k_pass_c(PassArgs a) {
   using F = Fft<P>;
   using R = RowCfg<P>;
@@ -1036,7 +1046,9 @@ __global__ void __launch_bounds__(RowCfg<P>::NT, RowCfg<P>::MINB) k_pass_c(PassA
 #pragma unroll
     for (int c = 0; c < 16; ++c) {
       const int rel = F::pos(t, c) - lo;
-      v[c] = (valid && (unsigned)rel < (unsigned)n) ? yrow[rel] : make_float2(0.f, 0.f);
+      // HALF (n = P/2, P = 2^k >= 1024): the crop columns are those of registers 4 .. 11
+      const bool in = HALF ? (c >= 4 && c < 12) : (unsigned)rel < (unsigned)n;
+      v[c] = (valid && in) ? yrow[rel] : make_float2(0.f, 0.f);
     }
     // the next line of this thread group: its adjoint-field row, probe row and conj(w) v row go
     // to L2 now (one bulk request each, issued by the line's first thread)
@@ -1086,7 +1098,7 @@ __global__ void __launch_bounds__(RowCfg<P>::NT, RowCfg<P>::MINB) k_pass_c(PassA
 #pragma unroll
     for (int c = 0; c < 16; ++c) {
       const int ip = F::pos(t, c);
-      if (!valid || ip >= n) continue;
+      if (!valid || (HALF ? c >= 8 : ip >= n)) continue;
       const AdjTap at = xa[ip];
       float2 h = make_float2(0.f, 0.f);
       const int r0 = at.X0 - d.bx0;
@@ -1184,23 +1196,33 @@ size_t pass_a_smem(int n) {
   return RowCfg<P>::SMEM_BYTES + (size_t)RowCfg<P>::G * n * sizeof(float2);
 }
 
-template <int P, bool SHIFT>
+template <int P, bool SHIFT, bool HALF = false>
 cudaError_t launch_pass_a_form(const PassArgs& a, cudaStream_t s) {
   using R = RowCfg<P>;
   if (a.nlines <= 0) return cudaSuccess;
   const size_t sm = pass_a_smem<P>(a.n);
-  cudaError_t e = cudaFuncSetAttribute(k_pass_a<P, SHIFT>,
+  cudaError_t e = cudaFuncSetAttribute(k_pass_a<P, SHIFT, HALF>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
   if (e != cudaSuccess) return e;
-  const int nb = multi_blocks(k_pass_a<P, SHIFT>, R::NT, sm, (a.nlines + R::G - 1) / R::G,
+  const int nb = multi_blocks(k_pass_a<P, SHIFT, HALF>, R::NT, sm, (a.nlines + R::G - 1) / R::G,
                               a.row_per_sm);
-  k_pass_a<P, SHIFT><<<nb, R::NT, sm, s>>>(a);
+  k_pass_a<P, SHIFT, HALF><<<nb, R::NT, sm, s>>>(a);
   return cudaGetLastError();
+}
+
+// Lines with n = P/2 (P = 2^k >= 1024, no probe shifts) run the row passes' HALF forms, whose
+// crop columns are fixed at compile time.
+template <int P>
+constexpr bool half_form_ok() {
+  return !Fft<P>::R3 && P >= 1024;
 }
 
 template <int P>
 cudaError_t launch_pass_a(const PassArgs& a, cudaStream_t s) {
-  return a.ramp_x ? launch_pass_a_form<P, true>(a, s) : launch_pass_a_form<P, false>(a, s);
+  if (a.ramp_x) return launch_pass_a_form<P, true>(a, s);
+  if constexpr (half_form_ok<P>())
+    if (2 * a.n == P) return launch_pass_a_form<P, false, true>(a, s);
+  return launch_pass_a_form<P, false>(a, s);
 }
 
 template <int P>
@@ -1275,14 +1297,14 @@ cudaError_t launch_pass_b_split(const PassArgs& a, int nblocks, size_t sm, cudaS
   return cudaGetLastError();
 }
 
-template <int P, bool ADJ, bool SHIFT, bool TSPLIT>
+template <int P, bool ADJ, bool SHIFT, bool TSPLIT, bool HALF = false>
 cudaError_t launch_pass_b_staged(const PassArgs& a, int nblocks, cudaStream_t s) {
   using Cc = ColCfg<P>;
   const size_t sm = pass_b_smem<P>(a.n, a.ymap ? a.max_box_rows : 0);
-  cudaError_t e = cudaFuncSetAttribute(k_pass_b<P, ADJ, SHIFT, TSPLIT>,
+  cudaError_t e = cudaFuncSetAttribute(k_pass_b<P, ADJ, SHIFT, TSPLIT, HALF>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
   if (e != cudaSuccess) return e;
-  k_pass_b<P, ADJ, SHIFT, TSPLIT><<<nblocks, Cc::NT, sm, s>>>(a);
+  k_pass_b<P, ADJ, SHIFT, TSPLIT, HALF><<<nblocks, Cc::NT, sm, s>>>(a);
   const int ngroups = (a.n + Cc::C - 1) / Cc::C, tail = ngroups - (ngroups / nblocks) * nblocks;
   if (TSPLIT && tail > 0) {
     e = cudaGetLastError();
@@ -1295,7 +1317,8 @@ cudaError_t launch_pass_b_staged(const PassArgs& a, int nblocks, cudaStream_t s)
 // pb_split: 0 whole column groups per block; 1 the plane-split kernel (no Y stage); 2 the
 // staged kernel with its last round split by planes, then the combine kernel.  The staged
 // split is compiled for the gradient without probe shifts; the other forms run pb_split 2 as
-// whole groups on the same grid.
+// whole groups on the same grid.  Whole groups with n = P/2 (P = 2^k >= 1024, no probe
+// shifts) run the HALF form, whose crop rows are fixed at compile time.
 template <int P, bool ADJ, bool SHIFT>
 cudaError_t launch_pass_b_form(const PassArgs& a, int nblocks, cudaStream_t s) {
   if (a.pb_split == 1) {
@@ -1305,6 +1328,9 @@ cudaError_t launch_pass_b_form(const PassArgs& a, int nblocks, cudaStream_t s) {
   }
   if constexpr (ADJ && !SHIFT) {
     if (a.pb_split == 2) return launch_pass_b_staged<P, true, false, true>(a, nblocks, s);
+  }
+  if constexpr (!SHIFT && half_form_ok<P>()) {
+    if (2 * a.n == P) return launch_pass_b_staged<P, ADJ, false, false, true>(a, nblocks, s);
   }
   return launch_pass_b_staged<P, ADJ, SHIFT, false>(a, nblocks, s);
 }
@@ -1322,23 +1348,26 @@ cudaError_t launch_pass_b(const PassArgs& a, int adj, int nblocks, cudaStream_t 
              : launch_pass_b_form<P, false, false>(a, nblocks, s);
 }
 
-template <int P, bool SHIFT>
+template <int P, bool SHIFT, bool HALF = false>
 cudaError_t launch_pass_c_form(const PassArgs& a, cudaStream_t s) {
   using R = RowCfg<P>;
   if (a.nlines <= 0) return cudaSuccess;
-  cudaError_t e = cudaFuncSetAttribute(k_pass_c<P, SHIFT>,
+  cudaError_t e = cudaFuncSetAttribute(k_pass_c<P, SHIFT, HALF>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)R::SMEM_BYTES);
   if (e != cudaSuccess) return e;
-  const int nb = multi_blocks(k_pass_c<P, SHIFT>, R::NT, R::SMEM_BYTES,
+  const int nb = multi_blocks(k_pass_c<P, SHIFT, HALF>, R::NT, R::SMEM_BYTES,
                               (a.nlines + R::G - 1) / R::G, a.row_per_sm);
-  k_pass_c<P, SHIFT><<<nb, R::NT, R::SMEM_BYTES, s>>>(a);
+  k_pass_c<P, SHIFT, HALF><<<nb, R::NT, R::SMEM_BYTES, s>>>(a);
   return cudaGetLastError();
 }
 
 template <int P>
 cudaError_t launch_pass_c(const PassArgs& a, cudaStream_t s) {
-  return a.ramp_x ? launch_pass_c_form<P, true>(a, s) : launch_pass_c_form<P, false>(a, s);
+  if (a.ramp_x) return launch_pass_c_form<P, true>(a, s);
+  if constexpr (half_form_ok<P>())
+    if (2 * a.n == P) return launch_pass_c_form<P, false, true>(a, s);
+  return launch_pass_c_form<P, false>(a, s);
 }
 
 template <int P, bool SHIFT>
