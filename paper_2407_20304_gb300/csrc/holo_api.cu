@@ -135,7 +135,9 @@ struct holo_ctx {
   size_t ws_bytes_planes = 0;
   // evaluation scratch
   float2* d_scratch = nullptr;  // P*P
-  float2* d_Gp = nullptr;       // P*P
+  // row stages of the probe-gradient sources, [sum of their rows][P] (eval_qfinish)
+  float2* d_qscr = nullptr;
+  size_t qscr_bytes = 0;
   float2* d_T = nullptr;        // n*n
   // deferred probe gradient (HOLO_DEFER_Q): per distance the union box {row0, rows, col0, cols}
   // of every plane's box, and G'_j accumulated on it (offset gacc_off[j] in d_gacc)
@@ -655,32 +657,6 @@ holo_status eval_planes(holo_ctx* c, PassArgs& a, bool gradient, bool first, int
 // grad_q = 2 [ D_{-zeta_0}( C* T ) + sum_j D_{-omega_j}(G'_j) ] with T = ext sum_kj r_kj +
 // w_ref r_ref written by pass B (zhat_j + omega_j = zeta_0 merges the ext-part of every
 // plane into one propagation).  `a` spans the whole chunk; its gkbuf holds every plane.
-holo_status eval_qgrad(holo_ctx* c, const PassArgs& a, float2* grad_q, int acc) {
-  PassTimer tm_q(c, HOLO_T_QGRAD);
-  const int P = c->P, n = c->n, lo = P / 2 - n / 2;
-  holo_status st = dstep2d(c, c->d_T, lo, n, lo, n, grad_q, 0, P, 0, P, c->d_chirp_zeta0, 1, 2.f,
-                           acc);
-  if (st != HOLO_OK) return st;
-  for (int j = 0; j < c->J; ++j) {
-    int r0 = P, r1 = 0, c0 = P, c1 = 0;
-    for (int k = a.k0; k < a.k0 + a.nk; ++k) {
-      const PlaneDesc& d = c->planes[(size_t)k * c->J + j];
-      if (d.bys <= 0 || d.bxs <= 0) continue;
-      r0 = std::min(r0, d.by0);
-      r1 = std::max(r1, d.by0 + d.bys);
-      c0 = std::min(c0, d.bx0);
-      c1 = std::max(c1, d.bx0 + d.bxs);
-    }
-    if (r1 <= r0 || c1 <= c0) continue;
-    HOLO_LAUNCH(c, holo::launch_reduce_g(a, c->d_Gp, j, r0, r1 - r0, c0, c1 - c0, c1 - c0, r0, c0,
-                                         0, c->stream));
-    st = dstep2d(c, c->d_Gp, r0, r1 - r0, c0, c1 - c0, grad_q, 0, P, 0, P,
-                 c->d_chirp_omega + (size_t)j * P, 1, 2.f, 1);
-    if (st != HOLO_OK) return st;
-  }
-  return HOLO_OK;
-}
-
 // Deferred probe gradient: the chunk's G'_j added (acc) or written into the accumulators on
 // the union boxes; T was written or accumulated by pass B (a.tq_accumulate).
 holo_status eval_qsources(holo_ctx* c, const PassArgs& a, int acc) {
@@ -711,21 +687,86 @@ holo_status eval_qsources(holo_ctx* c, const PassArgs& a, int acc) {
 }
 
 // grad_q (= or +=) 2 [ D_{-zeta_0}(C* T) + sum_j D_{-omega_j}(G'_j) ] from the accumulators.
+// The row stage of every source runs into its own scratch rows; the column stage of all of
+// them is one k_cols_sum launch (one inverse transform per column for the sum).  Where the
+// sources' chirps do not fit its shared memory, each source runs its own column stage.
 holo_status eval_qfinish(holo_ctx* c, float2* grad_q, int acc) {
   PassTimer tm_q(c, HOLO_T_QGRAD);
   const int P = c->P, n = c->n, lo = P / 2 - n / 2;
-  holo_status st = dstep2d(c, c->d_T, lo, n, lo, n, grad_q, 0, P, 0, P, c->d_chirp_zeta0, 1, 2.f,
-                           acc);
-  if (st != HOLO_OK) return st;
+  struct Src {
+    const float2* in;
+    int r_lo, rows, c_lo, w;
+    const float2* chirp;
+  };
+  Src src[holo::kMaxSumSources];
+  int S = 0;
+  src[S++] = {c->d_T, lo, n, lo, n, c->d_chirp_zeta0};
   for (int j = 0; j < c->J; ++j) {
     const int* qb = c->qbox[j];
     if (qb[1] <= 0 || qb[3] <= 0) continue;
-    st = dstep2d(c, c->d_gacc + c->gacc_off[j], qb[0], qb[1], qb[2], qb[3], grad_q, 0, P, 0, P,
-                 c->d_chirp_omega + (size_t)j * P, 1, 2.f, 1);
-    if (st != HOLO_OK) return st;
+    src[S++] = {c->d_gacc + c->gacc_off[j], qb[0], qb[1], qb[2], qb[3],
+                c->d_chirp_omega + (size_t)j * P};
   }
+  if (S > c->ops->cols_sum_max()) {
+    for (int s = 0; s < S; ++s) {
+      holo_status st = dstep2d(c, src[s].in, src[s].r_lo, src[s].rows, src[s].c_lo, src[s].w,
+                               grad_q, 0, P, 0, P, src[s].chirp, 1, 2.f, s == 0 ? acc : 1);
+      if (st != HOLO_OK) return st;
+    }
+    c->q_pending = false;
+    return HOLO_OK;
+  }
+  size_t rows = 0;
+  for (int s = 0; s < S; ++s) rows += (size_t)src[s].rows;
+  const size_t need = sizeof(float2) * rows * P;
+  if (need > c->qscr_bytes) {
+    dfree(c, c->d_qscr, c->qscr_bytes);
+    c->d_qscr = nullptr;
+    c->qscr_bytes = 0;
+    holo_status st = dalloc(c, (void**)&c->d_qscr, need);
+    if (st) return st;
+    c->qscr_bytes = need;
+  }
+  holo::SumArgs sa;
+  std::memset(&sa, 0, sizeof(sa));
+  size_t off = 0;
+  for (int s = 0; s < S; ++s) {
+    LineArgs a = line_args();
+    a.in = src[s].in;
+    a.in_line_stride = src[s].w;
+    a.in_step = 1;
+    a.in_lo = src[s].c_lo;
+    a.in_len = src[s].w;
+    a.out = c->d_qscr + off;  // [rows][P]
+    a.out_line_stride = P;
+    a.out_step = 1;
+    a.out_lo = 0;
+    a.out_len = P;
+    a.nlines = src[s].rows;
+    a.chirp = src[s].chirp;
+    a.conj_chirp = 1;
+    HOLO_LAUNCH(c, c->ops->rows(a, c->d_tw, c->stream));
+    sa.in[s] = c->d_qscr + off;
+    sa.r_lo[s] = src[s].r_lo;
+    sa.rows[s] = src[s].rows;
+    sa.chirp[s] = src[s].chirp;
+    off += (size_t)src[s].rows * P;
+  }
+  sa.S = S;
+  sa.conj_chirp = 1;
+  sa.alpha = 2.f;
+  sa.accumulate = acc;
+  sa.out = grad_q;
+  HOLO_LAUNCH(c, c->ops->cols_sum(sa, c->d_tw, c->stream));
   c->q_pending = false;
   return HOLO_OK;
+}
+
+// grad_q of one chunk: its sources on the union boxes, then the propagation.
+holo_status eval_qgrad(holo_ctx* c, const PassArgs& a, float2* grad_q, int acc) {
+  holo_status st = eval_qsources(c, a, 0);
+  if (st != HOLO_OK) return st;
+  return eval_qfinish(c, grad_q, acc);
 }
 
 // The whole evaluation of one chunk in one pass over its planes.
@@ -872,7 +913,6 @@ holo_status holo_create(const holo_geometry* geo, void* stream, holo_ctx** out) 
       (st = dalloc(c, (void**)&c->d_pj, cP * P * J)) ||
       (st = dalloc(c, (void**)&c->d_b, sizeof(float2) * (size_t)n * n)) ||
       (st = dalloc(c, (void**)&c->d_scratch, cP * P)) ||
-      (st = dalloc(c, (void**)&c->d_Gp, cP * P)) ||
       (st = dalloc(c, (void**)&c->d_T, sizeof(float2) * (size_t)n * n)) ||
       (st = dalloc(c, (void**)&c->d_rref, sizeof(float2) * (size_t)n * n)) ||
       (st = dalloc(c, (void**)&c->d_red, kRed * sizeof(double))) ||
@@ -907,7 +947,7 @@ holo_status holo_destroy(holo_ctx* c) {
   void* ptrs[] = {c->d_tw,    c->d_chirp_zhat, c->d_chirp_omega, c->d_chirp_zeta0,
                   c->d_chirp_tmp, c->d_planes, c->d_pj,          c->d_b,
                   c->ybuf,    c->gkbuf,        c->d_scratch,
-                  c->d_Gp,    c->d_T,          c->d_rref,        c->d_part,
+                  c->d_qscr,  c->d_T,          c->d_rref,        c->d_part,
                   c->d_red,   c->d_dot3,       c->d_tpart,       c->s_psi,         c->s_gpsi,
                   c->s_data,       c->s_dblk,       c->d_dblk,        c->d_gacc,
                   c->s_q,     c->s_gq,         c->d_xtap,        c->d_ytap,

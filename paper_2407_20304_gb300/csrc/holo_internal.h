@@ -4,6 +4,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include "holo.h"
+
 namespace holo {
 
 // One (angle k, distance j) plane: resample parameters and the bounding box of the
@@ -49,6 +51,22 @@ struct LineArgs {
   int conj_chirp;                        // 1: multiply by conj(chirp) (distance -z)
   float alpha;
   int accumulate;                        // 1: out += alpha * D(...)
+};
+
+// The column stage of sum_s D_s(x_s) over several sources whose row stage already ran: per
+// column of the P x P grid, the transforms of the sources' columns times their chirps are
+// summed and transformed back once (see k_cols_sum).
+constexpr int kMaxSumSources = 1 + HOLO_MAX_DIST;
+struct SumArgs {
+  int S;                                     // sources, 1 .. kMaxSumSources
+  const float2* in[kMaxSumSources];          // source s: rows [r_lo, r_lo + rows) of the grid,
+  int r_lo[kMaxSumSources];                  //   stored [rows][P]
+  int rows[kMaxSumSources];
+  const float2* chirp[kMaxSumSources];       // P entries, exp(-i pi lambda z_s f^2) / P
+  int conj_chirp;                            // 1: conj(chirp) (distance -z_s)
+  float alpha;
+  int accumulate;                            // 1: out += alpha * sum, else out = alpha * sum
+  float2* out;                               // [P][P]
 };
 
 // Parameters of the per-plane passes of one forward / gradient evaluation.
@@ -138,6 +156,10 @@ struct Ops {
   cudaError_t (*pass_b_multi)(const PassArgs* args, const int2* items, int nitems, int nprob,
                               int adj, int shift, int max_n, int max_rows, int per_sm,
                               cudaStream_t);
+  // the summed column stage (k_cols_sum) and the most sources whose chirps fit its shared
+  // memory on the current device
+  cudaError_t (*cols_sum)(const SumArgs&, const float2* tw, cudaStream_t);
+  int (*cols_sum_max)();
 };
 
 const Ops* ops_for(int P);

@@ -200,6 +200,63 @@ k_line_dstep(LineArgs a, const float2* __restrict__ gtw) {
   }
 }
 
+// The column stage of sum_s D_s(x_s): the rows of every source were propagated already (row
+// FFT, chirp, inverse), so D_s = IFFT_y chirp_s FFT_y on columns and the sum needs one inverse
+// per column: acc = sum_s chirp_s FFT_y(col_s), out (+)= alpha IFFT_y(acc).  Blocks own C
+// columns at a time, as k_line_dstep's column form; the half chirp tables of all sources stay
+// in shared memory after the twiddle roots.
+template <int P>
+__global__ void __launch_bounds__(ColCfg<P>::NT)
+k_cols_sum(const __grid_constant__ SumArgs a, const float2* __restrict__ gtw) {
+  using F = Fft<P>;
+  using H = SmemHead<P>;
+  constexpr int G = ColCfg<P>::C, LS = ColCfg<P>::LS;
+  extern __shared__ float2 smem[];
+  const int g = threadIdx.x % G, t = threadIdx.x / G;
+  float2* chs = smem + H::ROOTS;
+  float2* sm = smem + H::ROOTS + a.S * H::CHIRP + g * LS;
+  load_roots<P>(smem, gtw);
+  for (int s = 0; s < a.S; ++s) load_chirp_half<P>(chs + s * H::CHIRP, a.chirp[s]);
+  const TwRoots tw{smem};
+  for (int base = blockIdx.x * G; base < P; base += gridDim.x * G) {
+    const int col = base + g;
+    const bool valid = col < P;
+    float2 acc[16];
+#pragma unroll
+    for (int c = 0; c < 16; ++c) acc[c] = make_float2(0.f, 0.f);
+    for (int s = 0; s < a.S; ++s) {
+      const float2* in = a.in[s] + col;
+      const int r_lo = a.r_lo[s], rows = a.rows[s];
+      float2 v[16];
+#pragma unroll
+      for (int c = 0; c < 16; ++c) {
+        const int rel = F::pos(t, c) - r_lo;
+        v[c] = (valid && (unsigned)rel < (unsigned)rows) ? in[(long long)rel * P]
+                                                         : make_float2(0.f, 0.f);
+      }
+      // the exchange buffer is free once every thread finished the previous transform
+      __syncthreads();
+      fft_fwd_with<P>(v, sm, tw, t, SyncBlock());
+      const ChirpAt<P> cat(chs + s * H::CHIRP, t);
+#pragma unroll
+      for (int c = 0; c < 16; ++c)
+        acc[c] = cadd(acc[c], a.conj_chirp ? cmulc(v[c], cat(c)) : cmul(v[c], cat(c)));
+    }
+    __syncthreads();
+    fft_inv_with<P>(acc, sm, tw, t, SyncBlock());
+    if (valid) {
+#pragma unroll
+      for (int c = 0; c < 16; ++c) {
+        float2* o = a.out + (long long)F::pos(t, c) * P + col;
+        float2 r = cscale(acc[c], a.alpha);
+        if (a.accumulate) r = cadd(r, *o);
+        *o = r;
+      }
+    }
+    __syncthreads();
+  }
+}
+
 // Load the half chirp of distance j unless it is already resident (block-uniform j).
 template <int P>
 __device__ __forceinline__ void ensure_chirp(float2* chs, const float2* __restrict__ tables, int j,
@@ -1190,6 +1247,7 @@ cudaError_t launch_cols(const LineArgs& a, const float2* tw, cudaStream_t s) {
   return launch_lines<P, true>(a, tw, s);
 }
 
+
 // Pass A's shared memory: the row pass layout plus one mixed object row [n] per line.
 template <int P>
 size_t pass_a_smem(int n) {
@@ -1239,6 +1297,34 @@ inline int max_dynamic_smem() {
     if (v <= 0) v = 48 * 1024;
   }
   return v;
+}
+
+template <int P>
+size_t cols_sum_smem(int S) {
+  return (size_t)(SmemHead<P>::ROOTS + S * SmemHead<P>::CHIRP + ColCfg<P>::C * ColCfg<P>::LS) *
+         sizeof(float2);
+}
+
+template <int P>
+int cols_sum_max() {
+  const size_t cap = (size_t)max_dynamic_smem();
+  int S = 0;
+  while (S < kMaxSumSources && cols_sum_smem<P>(S + 1) <= cap) ++S;
+  return S;
+}
+
+// cudaErrorNotSupported (nothing launched) when the sources' chirps do not fit.
+template <int P>
+cudaError_t launch_cols_sum(const SumArgs& a, const float2* tw, cudaStream_t s) {
+  using Cc = ColCfg<P>;
+  if (a.S < 1 || a.S > cols_sum_max<P>()) return cudaErrorNotSupported;
+  const size_t sm = cols_sum_smem<P>(a.S);
+  cudaError_t e = cudaFuncSetAttribute(k_cols_sum<P>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)sm);
+  if (e != cudaSuccess) return e;
+  const int nb = persistent_blocks(k_cols_sum<P>, Cc::NT, sm, (P + Cc::C - 1) / Cc::C);
+  k_cols_sum<P><<<nb, Cc::NT, sm, s>>>(a, tw);
+  return cudaGetLastError();
 }
 
 // rows: box rows of the Y stage (0: plain loads)
@@ -1433,7 +1519,9 @@ const Ops* make_ops() {
                           ColCfg<P>::C,
                           RowCfg<P>::G,
                           launch_rows_multi<P>,
-                          launch_pass_b_multi<P>};
+                          launch_pass_b_multi<P>,
+                          launch_cols_sum<P>,
+                          cols_sum_max<P>};
   return &ops;
 }
 
