@@ -298,22 +298,27 @@ def run_ours(args, w, rank, world, local_rank):
     eta_psi, eta_q = torch.zeros_like(psi), torch.zeros_like(q)
     state = {"cur": 0, "first": True, "gam": None}
 
+    def dy_beta(num, d_new, d_old):
+        den = d_new - d_old
+        return num / den if den > 0 else 0.0
+
     def step():
         cur = state["cur"]
         h.set_probe(q)
+        # the object part's DY products (Eq. DaiYuan2) are formed by pass D (Re <g, g>,
+        # Re <g, eta>) and by the previous direction step (Re <g_prev, eta>)
+        h.set_dy_direction(None if state["first"] else eta_psi)
         loss, gp, gqc = h.gradient(psi, grad_psi=gpsi[cur], grad_q=gq[cur])
         if state["gam"] is None:
             # fixed small steps (relative 1e-3 of each block) for the benchmark's updates
             state["gam"] = (1e-3 * (K * n * n) ** 0.5 / max(np.sqrt(h.dot(gp, gp)), 1e-30),
                             1e-3 * np.sqrt(h.dot(q, q)) / max(np.sqrt(h.dot(gqc, gqc)), 1e-30))
-        for gcur, gprev, eta, x, gam in ((gp, gpsi[1 - cur], eta_psi, psi, state["gam"][0]),
-                                         (gqc, gq[1 - cur], eta_q, q, state["gam"][1])):
-            beta = 0.0
-            if not state["first"]:
-                num, d_new, d_old = h.dy_dots(gcur, gprev, eta)
-                den = d_new - d_old
-                beta = num / den if den > 0 else 0.0
-            h.direction_step(x, eta, gcur, beta, gam)
+        beta_psi = beta_q = 0.0
+        if not state["first"]:
+            beta_psi = dy_beta(*h.read_dy())
+            beta_q = dy_beta(*h.dy_dots(gqc, gq[1 - cur], eta_q))
+        h.direction_step(psi, eta_psi, gp, beta_psi, state["gam"][0], dy=True)
+        h.direction_step(q, eta_q, gqc, beta_q, state["gam"][1])
         state["first"] = False
         state["cur"] = 1 - cur
         return loss
@@ -417,7 +422,9 @@ def run_ours(args, w, rank, world, local_rank):
                    "functional": "F1 (Eq. min2, intensities)" if f1 else "F2 (Eq. min1, amplitudes)",
                    "probe_shifts": ("U(-2, 2) px per axis and plane, full-grid shift form"
                                     if args.probe_shifts else "none"),
-                   "step": "set_probe + gradient (F, grad_psi, grad_q) + DY inner products + fused direction/step"},
+                   "step": "set_probe + gradient (F, grad_psi, grad_q) + DY inner products (the "
+                           "object's formed in pass D and the direction step) + fused "
+                           "direction/step"},
         "roofline": roof, "clocks": clocks, "gpu_launches": launches, "per_pass": per_pass,
         "final_loss": loss,
     }

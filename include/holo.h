@@ -255,6 +255,27 @@ holo_status holo_dy_dots(holo_ctx* ctx, const void* g, const void* g_prev, const
 holo_status holo_direction_step(holo_ctx* ctx, void* x, void* eta, const void* g, double beta,
                                 double gamma, long long n_c64);
 
+/* The Dai-Yuan inner products (Eq. DaiYuan2) of the object part formed where the vectors
+ * already stream through the GPU, so that a CG step needs no separate pass over them:
+ * holo_set_dy_direction(ctx, eta): eta = dev complex64 laid out as the grad_psi of the
+ *   following holo_gradient calls ([nk][n][n], 16-byte aligned; HOLO_ERR_ARG otherwise), or
+ *   NULL to stop.  While it is set, every holo_gradient also forms Re <g, g> and Re <g, eta>
+ *   of the grad_psi g it writes (after the HOLO_ACCUMULATE addition): FP32 over the
+ *   elements of a psi row that one warp of 32 threads writes (n / 8 at most), then FP64
+ *   across warps and rows.  The caller keeps
+ *   eta alive while it is set; holo_gradient_host does not form the products.
+ * holo_direction_step_dy: holo_direction_step that also forms Re <g, eta_new> with its new
+ *   direction (accumulated like holo_dot).
+ * holo_read_dy(ctx, out): synchronises the stream; out[0] = Re <g, g> and out[1] =
+ *   Re <g, eta> of the last holo_gradient with a direction set, out[2] = Re <g, eta> of the
+ *   last holo_direction_step_dy.  With eta_k set during the evaluation of g_{k+1}, and out[2]
+ *   from the step that made eta_k from g_k, beta_DY = out[0] / (out[1] - out[2]): the three
+ *   holo_dy_dots products without a pass of their own. */
+holo_status holo_set_dy_direction(holo_ctx* ctx, const void* eta);
+holo_status holo_direction_step_dy(holo_ctx* ctx, void* x, void* eta, const void* g,
+                                   double beta, double gamma, long long n_c64);
+holo_status holo_read_dy(holo_ctx* ctx, double* out);
+
 /* Per-pass device timing (CUDA events recorded on the context's stream around each
  * launch group).  Pass ids: */
 #define HOLO_T_PROBE 0   /* holo_set_probe: p_j = D_{omega_j} q and C D_{zeta_0} q */

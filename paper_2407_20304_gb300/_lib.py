@@ -30,7 +30,8 @@ EXPORTS = ("holo_create", "holo_destroy", "holo_set_shifts", "holo_set_probe_shi
            "holo_set_stream", "holo_read_loss", "holo_set_device_error",
            "holo_workspace_bytes", "holo_launch_count", "holo_status_string", "holo_last_error",
            "holo_set_schedule", "holo_finish_q", "holo_batch_create", "holo_batch_set_problem",
-           "holo_batch_prepare", "holo_batch_gradient", "holo_batch_destroy")
+           "holo_batch_prepare", "holo_batch_gradient", "holo_batch_destroy",
+           "holo_set_dy_direction", "holo_direction_step_dy", "holo_read_dy")
 
 # Pass ids of holo_get_timing (HOLO_T_* in include/holo.h).
 TIMERS = ("probe", "pass_a", "pass_b", "pass_c", "pass_d", "qgrad", "reduce", "vector")
@@ -79,6 +80,9 @@ def _signatures():
         "holo_bin_amplitudes": [P, LL, ctypes.c_int, ctypes.c_int, P, P],
         "holo_upsample2": [P, LL, ctypes.c_int, P, P],
         "holo_direction_step": [P, P, P, P, D, D, LL],
+        "holo_set_dy_direction": [P, P],
+        "holo_direction_step_dy": [P, P, P, P, D, D, LL],
+        "holo_read_dy": [P, ctypes.POINTER(D)],
         "holo_dot_noalloc": [P, P, LL, ctypes.POINTER(D), P],
         "holo_set_stream": [P, P],
         "holo_read_loss": [P, ctypes.POINTER(D)],

@@ -69,7 +69,10 @@ constexpr int kHostMinPart = 2;
 constexpr int kHostWeights[kHostParts] = {1, 2, 3, 3, 3, 3, 3, 2};
 
 // d_red: kRed doubles; word kErrWord holds the device-wait error flag (as 64-bit integer).
-constexpr int kRed = 10;
+constexpr int kRed = 13;
+// d_red[10 .. 12]: the Dai-Yuan inner products formed inside holo_gradient (pass D) and
+// holo_direction_step_dy, read by holo_read_dy
+constexpr int kDyWord = 10;
 constexpr int kErrWord = 8;
 
 struct holo_ctx {
@@ -135,6 +138,11 @@ struct holo_ctx {
   size_t ws_bytes_planes = 0;
   // evaluation scratch
   float2* d_scratch = nullptr;  // P*P
+  // holo_set_dy_direction: the direction eta whose Dai-Yuan products pass D forms, and the
+  // FP64 partials of those products (pass D rows, direction-step blocks)
+  const float2* dy_eta = nullptr;
+  double* d_dypart = nullptr;
+  size_t dypart_bytes = 0;
   // row stages of the probe-gradient sources, [sum of their rows][P] (eval_qfinish)
   float2* d_qscr = nullptr;
   size_t qscr_bytes = 0;
@@ -805,6 +813,20 @@ holo_status read_loss(holo_ctx* c, double* loss, unsigned flags) {
   return HOLO_OK;
 }
 
+// FP64 partials of the Dai-Yuan products: count entries, at least one per block of a
+// direction step (grid_for caps those at 16 per SM of 152)
+holo_status ensure_dypart(holo_ctx* c, long long count) {
+  const size_t need = sizeof(double) * (size_t)std::max(count, 152LL * 16);
+  if (need <= c->dypart_bytes) return HOLO_OK;
+  dfree(c, c->d_dypart, c->dypart_bytes);
+  c->d_dypart = nullptr;
+  c->dypart_bytes = 0;
+  holo_status st = dalloc(c, (void**)&c->d_dypart, need);
+  if (st) return st;
+  c->dypart_bytes = need;
+  return HOLO_OK;
+}
+
 }  // namespace
 
 extern "C" {
@@ -947,7 +969,7 @@ holo_status holo_destroy(holo_ctx* c) {
   void* ptrs[] = {c->d_tw,    c->d_chirp_zhat, c->d_chirp_omega, c->d_chirp_zeta0,
                   c->d_chirp_tmp, c->d_planes, c->d_pj,          c->d_b,
                   c->ybuf,    c->gkbuf,        c->d_scratch,
-                  c->d_qscr,  c->d_T,          c->d_rref,        c->d_part,
+                  c->d_qscr,  c->d_T,          c->d_rref,        c->d_part,       c->d_dypart,
                   c->d_red,   c->d_dot3,       c->d_tpart,       c->s_psi,         c->s_gpsi,
                   c->s_data,       c->s_dblk,       c->d_dblk,        c->d_gacc,
                   c->s_q,     c->s_gq,         c->d_xtap,        c->d_ytap,
@@ -1239,7 +1261,19 @@ holo_status holo_gradient(holo_ctx* c, int k0, int nk, const void* psi, double* 
   PassArgs a = pass_args(c, k0, nk, psi);
   a.grad_psi = (float2*)grad_psi;
   a.accumulate = (flags & HOLO_ACCUMULATE) ? 1 : 0;
+  if (c->dy_eta) {
+    if ((st = ensure_dypart(c, 2LL * nk * c->n))) return st;
+    a.dy_eta = c->dy_eta;
+    a.dy_part = c->d_dypart;
+  }
   if ((st = run_eval(c, a, true, (float2*)grad_q, flags))) return st;
+  if (a.dy_eta) {
+    PassTimer tm(c, HOLO_T_REDUCE);
+    const int rows = nk * c->n;
+    HOLO_LAUNCH(c, holo::launch_sum_f64(c->d_dypart, rows, c->d_red + kDyWord, 0, c->stream));
+    HOLO_LAUNCH(c, holo::launch_sum_f64(c->d_dypart + rows, rows, c->d_red + kDyWord + 1, 0,
+                                        c->stream));
+  }
   if (!loss) return HOLO_OK;
   return read_loss(c, loss, flags);
 }
@@ -1479,6 +1513,38 @@ holo_status holo_direction_step(holo_ctx* c, void* x, void* eta, const void* g, 
   PassTimer tm(c, HOLO_T_VECTOR);
   HOLO_LAUNCH(c, holo::launch_direction_step((float2*)x, (float2*)eta, (const float2*)g,
                                              (float)beta, (float)gamma, n, c->stream));
+  return HOLO_OK;
+}
+
+holo_status holo_set_dy_direction(holo_ctx* c, const void* eta) {
+  if (!c) return HOLO_ERR_ARG;
+  if (eta && (reinterpret_cast<uintptr_t>(eta) & 15))
+    return fail(c, HOLO_ERR_ARG, "dy direction: 16-byte aligned device memory expected");
+  c->dy_eta = static_cast<const float2*>(eta);
+  return HOLO_OK;
+}
+
+holo_status holo_direction_step_dy(holo_ctx* c, void* x, void* eta, const void* g, double beta,
+                                   double gamma, long long n) {
+  if (!c || !x || !eta || !g || n < 0 || !std::isfinite(beta) || !std::isfinite(gamma))
+    return fail(c, HOLO_ERR_ARG, "bad argument");
+  holo_status st = ensure_dypart(c, 0);
+  if (st) return st;
+  PassTimer tm(c, HOLO_T_VECTOR);
+  int nb = 0;
+  HOLO_LAUNCH(c, holo::launch_direction_step_dot((float2*)x, (float2*)eta, (const float2*)g,
+                                                 (float)beta, (float)gamma, n, c->d_dypart, &nb,
+                                                 c->stream));
+  HOLO_LAUNCH(c, holo::launch_sum_f64(c->d_dypart, nb, c->d_red + kDyWord + 2, 0, c->stream));
+  return HOLO_OK;
+}
+
+holo_status holo_read_dy(holo_ctx* c, double* out) {
+  if (!c || !out) return fail(c, HOLO_ERR_ARG, "null argument");
+  HOLO_CK(c, cudaMemcpyAsync(c->h_red + kDyWord, c->d_red + kDyWord, 3 * sizeof(double),
+                             cudaMemcpyDeviceToHost, c->stream));
+  HOLO_CK(c, cudaStreamSynchronize(c->stream));
+  for (int i = 0; i < 3; ++i) out[i] = c->h_red[kDyWord + i];
   return HOLO_OK;
 }
 

@@ -36,6 +36,8 @@ __device__ __forceinline__ void pass_d_row(const PassArgs& a, int i, int kl) {
   __syncthreads();
   const int half = n / 2;
   float2* out = a.grad_psi + ((long long)kl * n + i) * n;
+  const float2* eta = a.dy_eta ? a.dy_eta + ((long long)kl * n + i) * n : nullptr;
+  float gg = 0.f, ge = 0.f;
   for (int p = threadIdx.x; p < half; p += blockDim.x) {
     float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
 #pragma unroll
@@ -65,6 +67,37 @@ __device__ __forceinline__ void pass_d_row(const PassArgs& a, int i, int kl) {
     }
     out[2 * p] = r0;
     out[2 * p + 1] = r1;
+    if (a.dy_eta) {
+      const float4 e = __ldg(reinterpret_cast<const float4*>(eta) + p);
+      gg = fmaf(r0.x, r0.x, fmaf(r0.y, r0.y, fmaf(r1.x, r1.x, fmaf(r1.y, r1.y, gg))));
+      ge = fmaf(r0.x, e.x, fmaf(r0.y, e.y, fmaf(r1.x, e.z, fmaf(r1.y, e.w, ge))));
+    }
+  }
+  if (a.dy_eta) {
+    // FP32 over the row's elements of a warp, FP64 across the warps (FP64 arithmetic is
+    // scarce on this part: a block-wide FP64 reduction per row cost more than the loads)
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      gg += __shfl_down_sync(0xffffffffu, gg, o);
+      ge += __shfl_down_sync(0xffffffffu, ge, o);
+    }
+    __shared__ float wsum[2][32];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+    if (lane == 0) {
+      wsum[0][w] = gg;
+      wsum[1][w] = ge;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      double sgg = 0.0, sge = 0.0;
+      for (int k = 0; k < nw; ++k) {
+        sgg += (double)wsum[0][k];
+        sge += (double)wsum[1][k];
+      }
+      const long long row = (long long)kl * n + i;
+      a.dy_part[row] = sgg;
+      a.dy_part[(long long)a.nk * n + row] = sge;
+    }
   }
 }
 
@@ -333,6 +366,30 @@ __global__ void k_direction_step(float2* __restrict__ x, float2* __restrict__ et
   }
 }
 
+// k_direction_step with Re <g, eta_new> accumulated as holo_dot accumulates (FP32 over 16
+// elements of a thread, then FP64), one partial per block.
+__global__ void k_direction_step_dot(float2* __restrict__ x, float2* __restrict__ eta,
+                                     const float2* __restrict__ g, float beta, float gamma,
+                                     long long n, double* __restrict__ part) {
+  __shared__ double red[32];
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  double acc = 0.0;
+  while (e < n) {
+    float s = 0.f;
+    for (int r = 0; r < 16 && e < n; ++r, e += stride) {
+      const float2 a = eta[e], d = g[e], xo = x[e];
+      const float2 en = make_float2(fmaf(beta, a.x, -d.x), fmaf(beta, a.y, -d.y));
+      eta[e] = en;
+      x[e] = make_float2(fmaf(gamma, en.x, xo.x), fmaf(gamma, en.y, xo.y));
+      s = fmaf(d.x, en.x, fmaf(d.y, en.y, s));
+    }
+    acc += (double)s;
+  }
+  const double t = block_sum_f64(acc, red);
+  if (threadIdx.x == 0) part[blockIdx.x] = t;
+}
+
 __global__ void k_axpy(float2* __restrict__ x, const float2* __restrict__ eta, float gamma,
                        long long n) {
   for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n;
@@ -464,6 +521,14 @@ cudaError_t launch_dot(const float2* a, const float2* b, long long n, double* pa
 cudaError_t launch_dot3(const float2* g, const float2* gp, const float2* eta, long long n,
                         double* part, int nblocks, cudaStream_t s) {
   k_dot3<<<nblocks, kThreads, 0, s>>>(g, gp, eta, n, part);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_direction_step_dot(float2* x, float2* eta, const float2* g, float beta,
+                                      float gamma, long long n, double* part, int* nblocks,
+                                      cudaStream_t s) {
+  *nblocks = grid_for(n);
+  k_direction_step_dot<<<*nblocks, kThreads, 0, s>>>(x, eta, g, beta, gamma, n, part);
   return cudaGetLastError();
 }
 

@@ -100,6 +100,11 @@ struct PassArgs {
   float2* u_out;               // optional [nk][J][n][n]
   double* loss_part;           // per block of pass B
   float2* grad_psi;            // [nk][n][n]
+  // Dai-Yuan inner products formed by pass D (null: none): Re <g, g> and Re <g, dy_eta> of
+  // the grad_psi it writes, one FP64 partial per psi row, at dy_part[kl n + i] and
+  // dy_part[nk n + kl n + i]
+  const float2* dy_eta;        // [nk][n][n]
+  double* dy_part;
   int accumulate;
   const float2* twiddles;      // device twiddle table for this P
   int max_box_rows;            // largest box height of the chunk
@@ -166,6 +171,11 @@ const Ops* ops_for(int P);
 
 // Line-length independent kernels (holo_common.cu).
 cudaError_t launch_pass_d(const PassArgs& a, cudaStream_t s);
+// eta = -g + beta eta, x += gamma eta (as launch_direction_step) with Re <g, eta> of the new
+// eta: FP64 partials, one per block, at part[0 .. *nblocks)
+cudaError_t launch_direction_step_dot(float2* x, float2* eta, const float2* g, float beta,
+                                      float gamma, long long n, double* part, int* nblocks,
+                                      cudaStream_t s);
 cudaError_t launch_pass_d_multi(const PassArgs* args, const int2* items, int nitems, int nblocks,
                                 cudaStream_t s);
 // G'_j of the chunk on the box [row0, row0 + nrows) x [col0, col0 + ncols) of the P grid,

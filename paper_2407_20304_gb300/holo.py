@@ -337,16 +337,36 @@ class Holo:
         _check(self.lib, self.ctx, st, "holo_dy_dots")
         return out[0], out[1], out[2]
 
-    def direction_step(self, x, eta, g, beta, gamma):
-        """eta = -g + beta * eta, then x += gamma * eta, in one pass."""
+    def direction_step(self, x, eta, g, beta, gamma, dy=False):
+        """eta = -g + beta * eta, then x += gamma * eta, in one pass.  dy: also form
+        Re <g, eta_new> (holo_direction_step_dy; read_dy()[2])."""
         import torch
         if not (x.shape == eta.shape == g.shape):
             raise ValueError("shape mismatch")
-        st = self.lib.holo_direction_step(self.ctx, _ptr(x, torch.complex64, None, "x"),
-                                          _ptr(eta, torch.complex64, None, "eta"),
-                                          _ptr(g, torch.complex64, None, "g"), float(beta),
-                                          float(gamma), x.numel())
-        _check(self.lib, self.ctx, st, "holo_direction_step")
+        fn = self.lib.holo_direction_step_dy if dy else self.lib.holo_direction_step
+        st = fn(self.ctx, _ptr(x, torch.complex64, None, "x"),
+                _ptr(eta, torch.complex64, None, "eta"), _ptr(g, torch.complex64, None, "g"),
+                float(beta), float(gamma), x.numel())
+        _check(self.lib, self.ctx, st, "holo_direction_step_dy" if dy else "holo_direction_step")
+
+    def set_dy_direction(self, eta):
+        """holo_set_dy_direction: while set (a complex64 CUDA tensor laid out as grad_psi of
+        the following gradient calls; None clears it), gradient() also forms Re <g, g> and
+        Re <g, eta> of the grad_psi it writes (read_dy()[0:2])."""
+        import torch
+        p = ctypes.c_void_p(None)
+        if eta is not None:
+            p = _ptr(eta, torch.complex64, None, "eta")
+        _check(self.lib, self.ctx, self.lib.holo_set_dy_direction(self.ctx, p),
+               "holo_set_dy_direction")
+        self._keep["dy"] = eta
+
+    def read_dy(self):
+        """holo_read_dy: (Re <g, g>, Re <g, eta>) of the last gradient with a direction set and
+        Re <g, eta_new> of the last direction_step(..., dy=True); beta_DY = a / (b - c)."""
+        out = (ctypes.c_double * 3)()
+        _check(self.lib, self.ctx, self.lib.holo_read_dy(self.ctx, out), "holo_read_dy")
+        return out[0], out[1], out[2]
 
     def set_stream(self, stream):
         """Issue later work on `stream` (a torch.cuda.Stream)."""

@@ -400,6 +400,46 @@ def test_dy_dots_and_fused_direction_step():
         assert torch.equal(x1, x2) and torch.equal(e1, e2)
 
 
+@pytest.mark.parametrize("n,P,K,accumulate", [(64, 128, 3, False), (256, 512, 2, True),
+                                                (2048, 4096, 1, False)])
+def test_dy_products_formed_in_the_gradient_and_the_step(n, P, K, accumulate):
+    """holo_set_dy_direction / holo_direction_step_dy / holo_read_dy: the Dai-Yuan products
+    formed inside pass D and the direction step against FP64 NumPy of the same vectors, and
+    against holo_dy_dots; the step's x and eta equal holo_direction_step's bit for bit."""
+    pr = make_problem(n, P, K, J=2, seed=7 * n + K, point="object")
+    h = make_holo(pr)
+    psi = dev(pr["psi"], torch.complex64)
+    rng = np.random.default_rng(n)
+    c64 = lambda a: dev(a.astype(np.complex64), torch.complex64)
+    eta = c64(rng.standard_normal((K, n, n)) + 1j * rng.standard_normal((K, n, n)))
+    g_prev = c64(rng.standard_normal((K, n, n)) + 1j * rng.standard_normal((K, n, n)))
+    g = torch.zeros_like(psi) if not accumulate else c64(0.1 * rng.standard_normal((K, n, n)))
+    h.set_dy_direction(eta)
+    gq = torch.zeros((P, P), dtype=torch.complex64, device="cuda")
+    h.gradient(psi, grad_psi=g, grad_q=gq, accumulate=accumulate)
+    gg, ge, _ = h.read_dy()
+    c = lambda t: t.cpu().numpy().astype(np.complex128)
+    ref_gg, ref_ge = np.real(np.vdot(c(g), c(g))), np.real(np.vdot(c(g), c(eta)))
+    assert abs(gg - ref_gg) <= 1e-6 * ref_gg
+    assert abs(ge - ref_ge) <= 1e-6 * np.sqrt(ref_gg * np.real(np.vdot(c(eta), c(eta))))
+    d = h.dy_dots(g, g_prev, eta)
+    assert abs(gg - d[0]) <= 1e-6 * d[0]
+    # the step: x and eta as holo_direction_step, and Re <g, eta_new>
+    x1, e1 = psi.clone(), eta.clone()
+    h.direction_step(x1, e1, g, 0.37, -0.05)
+    x2, e2 = psi.clone(), eta.clone()
+    h.direction_step(x2, e2, g, 0.37, -0.05, dy=True)
+    assert torch.equal(x1, x2) and torch.equal(e1, e2)
+    _, _, gn = h.read_dy()
+    ref_gn = np.real(np.vdot(c(g), c(e2)))
+    assert abs(gn - ref_gn) <= 1e-6 * np.sqrt(ref_gg * np.real(np.vdot(c(e2), c(e2))))
+    # cleared: a later gradient leaves the products of the last one
+    h.set_dy_direction(None)
+    h.gradient(psi, grad_psi=torch.empty_like(psi))
+    assert h.read_dy()[0] == gg
+    h.close()
+
+
 def test_state_and_argument_errors():
     from paper_2407_20304_gb300 import Holo, HoloError
     h = Holo(32, 2, 2, G["wavelength"], G["pixel"], G["Z"], G["z"][:2], pad=64)
