@@ -46,6 +46,11 @@
  *     return early and set a device error word; the next call that reads a loss (any call
  *     returning a loss, holo_read_loss) returns HOLO_ERR_TIMEOUT, clears the word, and the
  *     results of the evaluations since the previous loss read are invalid.
+ *   - A library built with HOLO_BOUNDS_CHECK defined (paper_2407_20304_gb300/build.py,
+ *     bounds_check=True: _build_bc/libholo.so) also checks its table-driven device indices
+ *     (line-table entries, plane boxes against the workspace strides, transposed taps); a
+ *     failed check skips the access and sets bit 2 of the same word, and the next loss read
+ *     returns HOLO_ERR_BOUNDS (before HOLO_ERR_TIMEOUT when both are set).  Nothing traps.
  */
 #ifndef HOLO_H
 #define HOLO_H
@@ -64,7 +69,8 @@ typedef enum {
   HOLO_ERR_TIMEOUT = 4,     /* a bounded device wait gave up */
   HOLO_ERR_STATE = 5,       /* call order: shifts / data / probe not set yet */
   HOLO_ERR_NUMERIC = 6,     /* non-finite loss */
-  HOLO_ERR_UNSUPPORTED = 7  /* valid but unsupported size (e.g. P = 80 or P > 4096) */
+  HOLO_ERR_UNSUPPORTED = 7, /* valid but unsupported size (e.g. P = 80 or P > 4096) */
+  HOLO_ERR_BOUNDS = 8       /* a device bounds check failed (HOLO_BOUNDS_CHECK builds only) */
 } holo_status;
 
 #define HOLO_MAX_DIST 8
@@ -374,8 +380,9 @@ holo_status holo_read_loss(holo_ctx* ctx, double* loss);
 /* Fault injection for tests (no counterpart in the paper; nothing faults on the GPU).
  * holo_set_device_error writes `word` into the context's device error word, the word a
  * bounded device wait sets when it gives up (see the conventions above), as if such a wait
- * had expired: the next call that reads a loss returns HOLO_ERR_TIMEOUT and clears it
- * (word 0 clears it now).  Synchronises the context's stream.
+ * had expired: the next call that reads a loss returns HOLO_ERR_TIMEOUT (HOLO_ERR_BOUNDS if
+ * bit 2 is set, as a failed bounds check sets it) and clears it (word 0 clears it now).
+ * Synchronises the context's stream.
  * The environment variable HOLO_FAULT (a comma-separated list, read at every check)
  * injects host-side failures: "alloc" fails every workspace allocation (HOLO_ERR_OOM, before
  * cudaMalloc), "arg" rejects every forward / gradient call (HOLO_ERR_ARG, before device

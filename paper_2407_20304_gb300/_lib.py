@@ -8,7 +8,10 @@ import ctypes
 import os
 
 HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(HERE, "_build", "libholo.so")
+# HOLO_BOUNDS_CHECK=1 selects the build whose device code checks its table-driven indices
+# (build.build(bounds_check=True)); results are the same, a failed check is HOLO_ERR_BOUNDS
+BOUNDS_CHECK = os.environ.get("HOLO_BOUNDS_CHECK") == "1"
+LIB_PATH = os.path.join(HERE, "_build_bc" if BOUNDS_CHECK else "_build", "libholo.so")
 MAX_DIST = 8
 F2_AMPLITUDE, F1_INTENSITY = 0, 1   # holo_set_functional
 ACCUMULATE = 1
@@ -18,7 +21,7 @@ NOALLOC_MAX_ELEMENTS = 1 << 28   # holo_dot_noalloc: capacity of its static part
 
 STATUS = {0: "HOLO_OK", 1: "HOLO_ERR_ARG", 2: "HOLO_ERR_CUDA", 3: "HOLO_ERR_OOM",
           4: "HOLO_ERR_TIMEOUT", 5: "HOLO_ERR_STATE", 6: "HOLO_ERR_NUMERIC",
-          7: "HOLO_ERR_UNSUPPORTED"}
+          7: "HOLO_ERR_UNSUPPORTED", 8: "HOLO_ERR_BOUNDS"}
 
 # Every symbol declared in include/holo.h.
 EXPORTS = ("holo_create", "holo_destroy", "holo_set_shifts", "holo_set_probe_shifts",
@@ -107,8 +110,10 @@ def load():
     if _lib is not None:
         return _lib
     if not os.path.exists(LIB_PATH):
-        raise RuntimeError(f"{LIB_PATH} is missing: build it with "
-                           "`python -c 'import __graft_entry__ as g; g.build()'`")
+        how = ("`python -c 'from paper_2407_20304_gb300 import build; "
+               "build.build(bounds_check=True)'`" if BOUNDS_CHECK else
+               "`python -c 'import __graft_entry__ as g; g.build()'`")
+        raise RuntimeError(f"{LIB_PATH} is missing: build it with {how}")
     lib = ctypes.CDLL(LIB_PATH)
     sigs = _signatures()
     for name, args in sigs.items():

@@ -2,7 +2,10 @@
 
 Each translation unit under csrc/ is compiled by its own nvcc process (in parallel), then
 linked into paper_2407_20304_gb300/_build/libholo.so.  No CMake, no torch extension
-machinery: the library exposes only the C ABI declared in include/holo.h.
+machinery: the library exposes only the C ABI declared in include/holo.h.  bounds_check=True
+builds the variant with HOLO_BOUNDS_CHECK defined (device checks of table-driven indices that
+report HOLO_ERR_BOUNDS instead of faulting) into _build_bc/, which the binding loads when the
+environment has HOLO_BOUNDS_CHECK=1.
 """
 
 import os
@@ -15,6 +18,7 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT, "libholo.so")
+OUT_BC = os.path.join(HERE, "_build_bc")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 
@@ -34,8 +38,8 @@ def headers():
     return hs + [os.path.join(ROOT, "include", "holo.h")]
 
 
-def _compile(src, extra, force=False):
-    obj = os.path.join(OUT, os.path.basename(src)[:-3] + ".o")
+def _compile(src, extra, force=False, out=OUT):
+    obj = os.path.join(out, os.path.basename(src)[:-3] + ".o")
     dep_mtime = max(os.path.getmtime(p) for p in headers() + [src, __file__])
     if not force and os.path.exists(obj) and os.path.getmtime(obj) >= dep_mtime:
         return obj, None
@@ -47,13 +51,20 @@ def _compile(src, extra, force=False):
     return obj, (r.stdout + r.stderr) if "-Xptxas=-v" in extra else None
 
 
-def build(verbose=False, ptxas_info=False, force=False):
+def compile_flags(bounds_check=False, ptxas_info=False):
+    """Extra nvcc flags of a build variant."""
+    return (["-DHOLO_BOUNDS_CHECK"] if bounds_check else []) + (["-Xptxas=-v"] if ptxas_info else [])
+
+
+def build(verbose=False, ptxas_info=False, force=False, bounds_check=False):
     """Compile and link libholo.so if any source changed; returns the library path."""
-    os.makedirs(OUT, exist_ok=True)
-    extra = ["-Xptxas=-v"] if ptxas_info else []
+    out = OUT_BC if bounds_check else OUT
+    lib = os.path.join(out, "libholo.so")
+    os.makedirs(out, exist_ok=True)
+    extra = compile_flags(bounds_check, ptxas_info)
     srcs = sources()
     with ThreadPoolExecutor(max_workers=min(len(srcs), os.cpu_count() or 4)) as ex:
-        results = list(ex.map(lambda s: _compile(s, extra, force), srcs))
+        results = list(ex.map(lambda s: _compile(s, extra, force, out), srcs))
     errs = [e for _, e in results if e and "error" in e.lower()]
     if errs:
         raise RuntimeError("nvcc failed:\n" + "\n".join(errs))
@@ -62,13 +73,14 @@ def build(verbose=False, ptxas_info=False, force=False):
             if e:
                 print(e)
     objs = [o for o, _ in results]
-    if force or not os.path.exists(LIB) or os.path.getmtime(LIB) < max(os.path.getmtime(o) for o in objs):
-        cmd = [nvcc(), "-shared", "-o", LIB, *objs, *ARCH]
+    if force or not os.path.exists(lib) or os.path.getmtime(lib) < max(os.path.getmtime(o) for o in objs):
+        cmd = [nvcc(), "-shared", "-o", lib, *objs, *ARCH]
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
             raise RuntimeError("link failed:\n$ " + " ".join(cmd) + "\n" + r.stdout + r.stderr)
-    return LIB
+    return lib
 
 
 if __name__ == "__main__":
-    print(build(verbose=True, ptxas_info="-v" in sys.argv, force="--force" in sys.argv))
+    print(build(verbose=True, ptxas_info="-v" in sys.argv, force="--force" in sys.argv,
+                bounds_check="--bounds-check" in sys.argv))

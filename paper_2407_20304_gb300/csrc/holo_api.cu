@@ -2,6 +2,7 @@
 //
 // Host side: argument validation, FP64 geometry and tables, per-plane resample boxes,
 // workspace management, and the launch sequence of one forward / gradient evaluation.
+#include <nvtx3/nvToolsExt.h>
 #include <algorithm>
 #include <cmath>
 #include <cstdio>
@@ -295,12 +296,20 @@ holo_status encode_ystage(holo_ctx* c, int maxbys) {
 }
 
 // Scoped event pair around a group of launches of one pass (no-op unless timing is on).
+// NVTX range names of the pass ids (HOLO_T_*), seen by nsys / ncu --nvtx
+constexpr const char* kPassRange[HOLO_NUM_TIMERS] = {
+    "holo:probe", "holo:pass_a", "holo:pass_b", "holo:pass_c",
+    "holo:pass_d", "holo:qgrad",  "holo:reduce", "holo:vector"};
+
+// Per-pass scope: an NVTX range around the pass's launches (always; the calls cost a pointer
+// test when no tool is attached) and, while timing is on, CUDA events on the context's stream.
 struct PassTimer {
   holo_ctx* c;
   int id;
   long long l0;
   cudaEvent_t a = nullptr;
   PassTimer(holo_ctx* ctx, int pass) : c(ctx), id(pass), l0(ctx->launches) {
+    nvtxRangePushA(kPassRange[pass]);
     if (!c->timing) return;
     a = take();
     if (a) cudaEventRecord(a, c->stream);
@@ -319,6 +328,7 @@ struct PassTimer {
     return e;
   }
   ~PassTimer() {
+    nvtxRangePop();
     if (!c->timing || !a) return;
     cudaEvent_t b = take();
     if (!b) return;
@@ -799,6 +809,9 @@ holo_status check_err_word(holo_ctx* c) {
   std::memcpy(&w, c->h_red + kErrWord, sizeof(w));
   if (!w) return HOLO_OK;
   HOLO_CK(c, cudaMemsetAsync(c->d_red + kErrWord, 0, sizeof(double), c->stream));
+  if (w & 2)
+    return fail(c, HOLO_ERR_BOUNDS,
+                "a device bounds check failed; results of the evaluations since the last loss read are invalid");
   return fail(c, HOLO_ERR_TIMEOUT, "pass B: Y-tile wait gave up; results of the call are invalid");
 }
 
@@ -873,6 +886,7 @@ const char* holo_status_string(holo_status s) {
     case HOLO_ERR_STATE: return "call order (shifts, data or probe not set)";
     case HOLO_ERR_NUMERIC: return "non-finite result";
     case HOLO_ERR_UNSUPPORTED: return "unsupported size";
+    case HOLO_ERR_BOUNDS: return "device bounds check failed";
   }
   return "unknown status";
 }

@@ -29,9 +29,21 @@ __device__ __forceinline__ void pass_d_row(const PassArgs& a, int i, int kl) {
     const PlaneDesc d = a.planes[gp];
     const float2* h = a.ybuf + (long long)(kl * a.J + j) * a.ystride;
     // rows X0 and X0 + 1 of the box; a zero weight marks a tap outside it (never read)
-    row[j] = reinterpret_cast<const float4*>(h + (long long)(at.X0 - d.by0) * n);
-    w0s[j] = at.w0;
-    w1s[j] = at.w1;
+    int r = at.X0 - d.by0;
+    float w0 = at.w0, w1 = at.w1;
+    if constexpr (kBoundsCheck) {
+      const bool ok = (w0 == 0.f || (r >= 0 && r < d.bys)) &&
+                      (w1 == 0.f || (r + 1 >= 0 && r + 1 < d.bys)) &&
+                      (long long)d.bys * n <= a.ystride;
+      if (!ok) {
+        flag_bounds(a.err);
+        r = 0;
+        w0 = w1 = 0.f;
+      }
+    }
+    row[j] = reinterpret_cast<const float4*>(h + (long long)r * n);
+    w0s[j] = w0;
+    w1s[j] = w1;
   }
   __syncthreads();
   const int half = n / 2;

@@ -102,6 +102,32 @@ __device__ __forceinline__ double block_sum_f64(double v, double* red) {
   return s;
 }
 
+// Builds with HOLO_BOUNDS_CHECK check their table-driven indices on the device: a bad entry
+// sets bit 2 of the problem's error word (HOLO_ERR_BOUNDS at the next loss read) and the access
+// is skipped; nothing traps.  Other builds compile the checks away.
+#if defined(HOLO_BOUNDS_CHECK)
+constexpr bool kBoundsCheck = true;
+#else
+constexpr bool kBoundsCheck = false;
+#endif
+
+__device__ __forceinline__ void flag_bounds(unsigned long long* err) { atomicOr(err, 2ull); }
+
+// A plane's box inside the P x P grid and inside the workspace strides of its problem.
+__device__ __forceinline__ bool plane_box_ok(const PassArgs& a, const PlaneDesc& d, int P) {
+  return d.by0 >= 0 && d.bys >= 0 && d.by0 + d.bys <= P && d.bx0 >= 0 && d.bxs >= 0 &&
+         d.bx0 + d.bxs <= P && d.bys <= a.tap_stride && d.bxs <= a.tap_stride &&
+         (long long)d.bys * a.n <= a.ystride && (long long)d.bys * d.bxs <= a.gkstride;
+}
+
+// A row-pass line (plane gp, box row i): the plane among the chunk's, the row inside its box.
+__device__ __forceinline__ bool line_ok(const PassArgs& a, int gp, int i, int P) {
+  const int p_lo = a.k0 * a.J;
+  if (gp < p_lo || gp >= p_lo + a.nk * a.J) return false;
+  const PlaneDesc d = a.planes[gp];
+  return i >= 0 && i < d.bys && plane_box_ok(a, d, P);
+}
+
 // Chirp exp(-i pi lambda z f^2)/P is even in the signed frequency, so a table of the
 // P/2 + 1 non-negative frequencies suffices: entry f for f <= P/2, entry P - f above.
 template <int P>
@@ -301,10 +327,18 @@ __device__ __forceinline__ void pass_a_step(const Args& a, int base, int next, f
   const int p_lo = a.k0 * a.J;
   {
     const int li = base + g;
-    const bool valid = li < a.nlines;
+    bool valid = li < a.nlines;
     const int line = a.line0 + (valid ? li : 0);
     const int2 L = __ldg(a.lines + line);
-    const int gp = L.x, i = L.y;
+    int gp = L.x, i = L.y;
+    if constexpr (kBoundsCheck) {
+      if (!line_ok(a, gp, i, P)) {
+        if (valid) flag_bounds(a.err);
+        valid = false;
+        gp = p_lo;
+        i = 0;
+      }
+    }
     const int lp = gp - p_lo, kl = lp / a.J, j = lp % a.J;
     const PlaneDesc d = a.planes[gp];
     const Tap yt = a.ytap[(long long)gp * a.tap_stride + i];
@@ -315,7 +349,8 @@ __device__ __forceinline__ void pass_a_step(const Args& a, int base, int next, f
     // lines of one block may belong to different distances only when G > 1; the chirp
     // table then follows the distance of the block's first line (block-uniform) and the
     // other lines read the chirp from global memory.
-    const int jb = (__ldg(a.lines + a.line0 + base).x - p_lo) % a.J;
+    int jb = (__ldg(a.lines + a.line0 + base).x - p_lo) % a.J;
+    if (kBoundsCheck && (jb < 0 || jb >= a.J)) jb = 0;
     // the line's two object rows mixed with its row tap, into shared memory:
     //   r[ix] = (1 - fy) (psi[iy0][ix] - ext) + fy (psi[iy0 + 1][ix] - ext)
     // (rows outside psi dropped); the x-interpolation below reads r, so each object pixel
@@ -369,6 +404,8 @@ __device__ __forceinline__ void pass_a_step(const Args& a, int base, int next, f
     // (one bulk request each, issued by the line's first thread)
     if (t == 0 && next >= 0 && next + g < a.nlines) {
       const int2 NL = __ldg(a.lines + a.line0 + next + g);
+      // (a bad entry is flagged when its own line runs)
+      if (!kBoundsCheck || line_ok(a, NL.x, NL.y, P)) {
       const int nlp = NL.x - p_lo;
       const PlaneDesc nd = a.planes[NL.x];
       const Tap nyt = a.ytap[(long long)NL.x * a.tap_stride + NL.y];
@@ -379,6 +416,7 @@ __device__ __forceinline__ void pass_a_step(const Args& a, int base, int next, f
         l2_prefetch_bulk(npsi + (long long)nyt.i0 * n, n * (uint32_t)sizeof(float2));
       if ((unsigned)(nyt.i0 + 1) < (unsigned)n)
         l2_prefetch_bulk(npsi + (long long)(nyt.i0 + 1) * n, n * (uint32_t)sizeof(float2));
+      }
     }
     ensure_chirp_key<P>(chs, a.chirp_zhat, R::G == 1 ? j : jb, pkey * 16 + (R::G == 1 ? j : jb),
                         jcur);
@@ -561,7 +599,13 @@ __device__ __forceinline__ bool pass_b_run(const PassArgs& a, int bid, int nblk,
       {
         const int lp = kl * a.J + j;
         const long long gplane = (long long)(a.k0 + kl) * a.J + j;
-        const PlaneDesc d = a.planes[gplane];
+        PlaneDesc d = a.planes[gplane];
+        if constexpr (kBoundsCheck) {
+          if (!plane_box_ok(a, d, P)) {
+            if (threadIdx.x == 0) flag_bounds(a.err);
+            d.bys = 0;  // the plane's box rows are skipped
+          }
+        }
         float2* yb = a.ybuf + (long long)lp * a.ystride;
         float2 v[16];
         if (staged) {
@@ -789,7 +833,13 @@ __global__ void __launch_bounds__(ColCfg<P>::NT) k_pass_b_split(PassArgs a) {
     const bool valid = col < n;
     const int lp = kl * a.J + j;
     const long long gplane = (long long)(a.k0 + kl) * a.J + j;
-    const PlaneDesc d = a.planes[gplane];
+    PlaneDesc d = a.planes[gplane];
+    if constexpr (kBoundsCheck) {
+      if (!plane_box_ok(a, d, P)) {
+        if (threadIdx.x == 0) flag_bounds(a.err);
+        d.bys = 0;  // the plane's box rows are skipped
+      }
+    }
     float2* yb = a.ybuf + (long long)lp * a.ystride;
     float2 v[16];
 #pragma unroll
@@ -991,12 +1041,21 @@ __device__ __forceinline__ void pass_c_items(const PassArgs* __restrict__ args,
     const int n = a.n, lo = P / 2 - n / 2;
     const int p_lo = a.k0 * a.J;
     const int li = base + g;
-    const bool valid = li < a.nlines;
+    bool valid = li < a.nlines;
     const int line = a.line0 + (valid ? li : 0);
     const int2 L = __ldg(a.lines + line);
-    const int gp = L.x, i = L.y;
+    int gp = L.x, i = L.y;
+    if constexpr (kBoundsCheck) {
+      if (!line_ok(a, gp, i, P)) {
+        if (valid) flag_bounds(a.err);
+        valid = false;
+        gp = p_lo;
+        i = 0;
+      }
+    }
     const int lp = gp - p_lo, j = lp % a.J;
-    const int jb = (__ldg(a.lines + a.line0 + base).x - p_lo) % a.J;
+    int jb = (__ldg(a.lines + a.line0 + base).x - p_lo) % a.J;
+    if (kBoundsCheck && (jb < 0 || jb >= a.J)) jb = 0;
     float2* yrow = a.ybuf + (long long)lp * a.ystride + (long long)i * n;
     float2 v[16];
 #pragma unroll
@@ -1008,6 +1067,8 @@ __device__ __forceinline__ void pass_c_items(const PassArgs* __restrict__ args,
     // to L2 now (one bulk request each, issued by the line's first thread)
     if (t == 0 && next >= 0 && next + g < a.nlines) {
       const int2 NL = __ldg(a.lines + a.line0 + next + g);
+      // (a bad entry is flagged when its own line runs)
+      if (!kBoundsCheck || line_ok(a, NL.x, NL.y, P)) {
       const int nlp = NL.x - p_lo;
       const PlaneDesc nd = a.planes[NL.x];
       l2_prefetch_bulk(a.ybuf + (long long)nlp * a.ystride + (long long)NL.y * n,
@@ -1016,6 +1077,7 @@ __device__ __forceinline__ void pass_c_items(const PassArgs* __restrict__ args,
                        nd.bxs * (uint32_t)sizeof(float2));
       l2_prefetch_bulk(a.gkbuf + (long long)nlp * a.gkstride + (long long)NL.y * nd.bxs,
                        nd.bxs * (uint32_t)sizeof(float2));
+      }
     }
     ensure_chirp_key<P>(chs, a.chirp_zhat, R::G == 1 ? j : jb, pkey * 16 + (R::G == 1 ? j : jb),
                         jcur);
@@ -1092,12 +1154,21 @@ __global__ void __launch_bounds__(RowCfg<P>::NT, RowCfg<P>::MINB) k_pass_c(PassA
   int jcur = -1;
   for (int base = blockIdx.x * R::G; base < a.nlines; base += gridDim.x * R::G) {
     const int li = base + g;
-    const bool valid = li < a.nlines;
+    bool valid = li < a.nlines;
     const int line = a.line0 + (valid ? li : 0);
     const int2 L = __ldg(a.lines + line);
-    const int gp = L.x, i = L.y;
+    int gp = L.x, i = L.y;
+    if constexpr (kBoundsCheck) {
+      if (!line_ok(a, gp, i, P)) {
+        if (valid) flag_bounds(a.err);
+        valid = false;
+        gp = p_lo;
+        i = 0;
+      }
+    }
     const int lp = gp - p_lo, j = lp % a.J;
-    const int jb = (__ldg(a.lines + a.line0 + base).x - p_lo) % a.J;
+    int jb = (__ldg(a.lines + a.line0 + base).x - p_lo) % a.J;
+    if (kBoundsCheck && (jb < 0 || jb >= a.J)) jb = 0;
     float2* yrow = a.ybuf + (long long)lp * a.ystride + (long long)i * n;
     float2 v[16];
 #pragma unroll
@@ -1111,14 +1182,17 @@ __global__ void __launch_bounds__(RowCfg<P>::NT, RowCfg<P>::MINB) k_pass_c(PassA
     // to L2 now (one bulk request each, issued by the line's first thread)
     if (t == 0 && li + (int)gridDim.x * R::G < a.nlines) {
       const int2 NL = __ldg(a.lines + a.line0 + li + gridDim.x * R::G);
-      const int nlp = NL.x - p_lo;
-      const PlaneDesc nd = a.planes[NL.x];
-      l2_prefetch_bulk(a.ybuf + (long long)nlp * a.ystride + (long long)NL.y * n,
-                       n * (uint32_t)sizeof(float2));
-      l2_prefetch_bulk(a.pj + ((long long)(nlp % a.J) * P + nd.by0 + NL.y) * P + nd.bx0,
-                       nd.bxs * (uint32_t)sizeof(float2));
-      l2_prefetch_bulk(a.gkbuf + (long long)nlp * a.gkstride + (long long)NL.y * nd.bxs,
-                       nd.bxs * (uint32_t)sizeof(float2));
+      // (a bad entry is flagged when its own line runs)
+      if (!kBoundsCheck || line_ok(a, NL.x, NL.y, P)) {
+        const int nlp = NL.x - p_lo;
+        const PlaneDesc nd = a.planes[NL.x];
+        l2_prefetch_bulk(a.ybuf + (long long)nlp * a.ystride + (long long)NL.y * n,
+                         n * (uint32_t)sizeof(float2));
+        l2_prefetch_bulk(a.pj + ((long long)(nlp % a.J) * P + nd.by0 + NL.y) * P + nd.bx0,
+                         nd.bxs * (uint32_t)sizeof(float2));
+        l2_prefetch_bulk(a.gkbuf + (long long)nlp * a.gkstride + (long long)NL.y * nd.bxs,
+                         nd.bxs * (uint32_t)sizeof(float2));
+      }
     }
     ensure_chirp<P>(chs, a.chirp_zhat, R::G == 1 ? j : jb, jcur);
     __syncthreads();

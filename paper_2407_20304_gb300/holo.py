@@ -403,7 +403,8 @@ class Holo:
 
     def set_device_error(self, word=1):
         """Test hook (holo_set_device_error): set the device error word as if a bounded
-        device wait had given up; the next loss read raises HOLO_ERR_TIMEOUT and clears it."""
+        device wait had given up (word 1; the next loss read raises HOLO_ERR_TIMEOUT) or a
+        device bounds check had failed (bit 2: HOLO_ERR_BOUNDS); the read clears it."""
         st = self.lib.holo_set_device_error(self.ctx, ctypes.c_ulonglong(word))
         _check(self.lib, self.ctx, st, "holo_set_device_error")
 

@@ -34,9 +34,34 @@ def test_every_declared_symbol_is_exported(lib):
 
 
 def test_status_strings(lib):
-    for s in range(8):
+    from paper_2407_20304_gb300 import _lib
+    for s in range(9):
         assert lib.holo_status_string(s)
+    assert lib.holo_status_string(8) == b"device bounds check failed"
     assert lib.holo_last_error(None) == b""
+    # every status of the header's enum has a name in the binding
+    src = open(os.path.join(ROOT, "include", "holo.h")).read()
+    enum = {int(v): k for k, v in re.findall(r"\b(HOLO_(?:OK|ERR_[A-Z]+))\s*=\s*(\d+)", src)}
+    assert enum == {k: v for k, v in _lib.STATUS.items()} | {0: "HOLO_OK"}
+
+
+def test_bounds_check_build_variant():
+    """The HOLO_BOUNDS_CHECK variant: its own flag and output directory, selected by the
+    environment (nothing is compiled here; the -m gpu tests build and run it)."""
+    import subprocess
+    import sys
+    from paper_2407_20304_gb300 import build as b
+    assert "-DHOLO_BOUNDS_CHECK" in b.compile_flags(bounds_check=True)
+    assert "-DHOLO_BOUNDS_CHECK" not in b.compile_flags()
+    code = "from paper_2407_20304_gb300 import _lib; print(_lib.LIB_PATH)"
+    env = dict(os.environ, HOLO_BOUNDS_CHECK="1")
+    out = subprocess.run([sys.executable, "-c", code], cwd=ROOT, env=env, capture_output=True,
+                         text=True, check=True).stdout.strip()
+    assert out.endswith(os.path.join("_build_bc", "libholo.so"))
+    env["HOLO_BOUNDS_CHECK"] = "0"
+    out = subprocess.run([sys.executable, "-c", code], cwd=ROOT, env=env, capture_output=True,
+                         text=True, check=True).stdout.strip()
+    assert out.endswith(os.path.join("_build", "libholo.so"))
 
 
 def _geo(**kw):

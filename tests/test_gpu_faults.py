@@ -56,12 +56,19 @@ def test_device_error_word_reports_timeout_once(setup):
     assert again[0] == clean[0]
     assert torch.equal(again[1], clean[1]) and torch.equal(again[2], clean[2])
     # a forward call reads the word too; clearing it by hand leaves nothing to report
-    h.set_device_error(7)
+    h.set_device_error(5)
     with pytest.raises(HoloError, match="TIMEOUT"):
         h.forward(psi)
     h.set_device_error(5)
     h.set_device_error(0)
     assert h.forward(psi) == h.forward(psi)
+    # bit 2 is a failed device bounds check, reported before a wait that gave up
+    for word in (2, 3):
+        h.set_device_error(word)
+        with pytest.raises(HoloError, match="BOUNDS") as e:
+            h.gradient(psi)
+        assert e.value.status == 8
+    assert h.gradient(psi)[0] == clean[0]
     h.close()
 
 
