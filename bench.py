@@ -1122,7 +1122,7 @@ def run_batch(args):
     import __graft_entry__
     __graft_entry__.build()
     g = hs.WORKLOAD_GEOMETRY
-    specs, dropped = batch_specs(hs.SEED_BASE + 3000)
+    specs, dropped = batch_specs(hs.config("batch")["seed"])
     insts = []
     for sp in specs:
         n, P, J, K, chunk = sp["n"], sp["P"], sp["J"], sp["K"], sp["chunk"]

@@ -13,19 +13,26 @@ vertical stripes of a few pixels' period (the multilayer-mirror features of Fig.
 Fig. 3), random sub-pixel sample shifts, and Poisson noise.
 """
 
+import json
+import os
 from dataclasses import dataclass
 
 import numpy as np
 
 SEED_BASE = 240720304
 
+# The synthetic configurations 0 .. 4 (tiny, medium, autograd, batch, large), their geometry
+# and flags, as data: configs.json next to this file.
+CONFIG_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "configs.json")
+_CONFIGS = json.load(open(CONFIG_PATH))
+
 # Geometry of the synthetic workloads: lambda = 3.72e-11 m, 10 nm object-plane pixel,
 # focus-to-sample distances z_j and focus-to-detector distance Z of Table 1.
 WORKLOAD_GEOMETRY = {
-    "wavelength": 3.72e-11,
-    "pixel": 1.0e-8,
-    "Z": 1.208,
-    "z": (4.6e-4, 5.1e-4, 6.2e-4, 8.3e-4),
+    "wavelength": _CONFIGS["geometry"]["wavelength"],
+    "pixel": _CONFIGS["geometry"]["pixel"],
+    "Z": _CONFIGS["geometry"]["Z"],
+    "z": tuple(_CONFIGS["geometry"]["z"]),
 }
 
 # The paper's instrument (Table 1): 17.05 keV, Z = 1.208 m, z_j in mm.
@@ -53,17 +60,40 @@ class Workload:
     seed: int
 
 
+def config(which):
+    """Configuration `which` (index 0 .. 4 or name) of configs.json, as a dict; its seed is
+    SEED_BASE + seed_offset."""
+    for c in _CONFIGS["configs"]:
+        if which in (c["index"], c["name"]):
+            return dict(c, seed=SEED_BASE + c["seed_offset"])
+    raise KeyError(which)
+
+
+def holo_geometry(which, chunk=None):
+    """The fields of the library's holo_geometry for a single-problem configuration (n, pad,
+    n_angles, n_dist, chunk, wavelength, pixel, Z, z, w_ref, ext)."""
+    c = config(which)
+    if isinstance(c["pad"], str):
+        raise ValueError(f"configuration {c['name']} has no single geometry")
+    g = _CONFIGS["geometry"]
+    f = _CONFIGS["flags"]
+    return {"n": c["n"], "pad": c["pad"], "n_angles": c["n_angles"], "n_dist": c["n_dist"],
+            "chunk": c["chunk"] if chunk is None else chunk, "wavelength": g["wavelength"],
+            "pixel": g["pixel"], "Z": g["Z"], "z": list(g["z"][:c["n_dist"]]),
+            "w_ref": f["w_ref"], "ext": f["ext"]}
+
+
 def workloads():
-    """The five synthetic workloads: tiny, medium, autograd-sized, batch, large."""
-    return {
-        "tiny": Workload("tiny", 128, 256, 8, 4, "ellipses", 40.0, 0.0, 8, SEED_BASE + 0),
-        "medium": Workload("medium", 512, 1024, 180, 4, "layers", 160.0, 1e4, 180,
-                           SEED_BASE + 1000),
-        "autograd": Workload("autograd", 1024, 2048, 90, 4, "layers", 320.0, 1e4, 90,
-                             SEED_BASE + 2000),
-        "large": Workload("large", 2048, 4096, 900, 4, "layers", 640.0, 1e4, 60,
-                          SEED_BASE + 4000),
-    }
+    """The single-problem synthetic workloads of configs.json: tiny, medium, autograd-sized,
+    large (the batch, configuration 3, is a list of problems drawn from its ranges)."""
+    out = {}
+    for c in _CONFIGS["configs"]:
+        if isinstance(c["pad"], str):
+            continue
+        out[c["name"]] = Workload(c["name"], c["n"], c["pad"], c["n_angles"], c["n_dist"],
+                                  c["phantom"], c["probe_sigma"], c["counts"], c["chunk"],
+                                  SEED_BASE + c["seed_offset"])
+    return out
 
 
 def rng_for(seed, stream=0):

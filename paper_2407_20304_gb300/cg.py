@@ -43,7 +43,11 @@ class Reconstruction:
     ARMIJO_C = 1e-4
 
     def __init__(self, holo, psi, q, gamma0=1.0, max_halvings=20, update_q=True,
-                 rule="dai-yuan", line_search="backtracking", group=None):
+                 rule="dai-yuan", line_search="backtracking", group=None, log_path=None,
+                 truth=None):
+        """log_path: append one JSON line per iteration (iter, F, both steps and betas, the
+        gradient norms, and with `truth` (psi's ground truth, laid out as psi) the relative
+        error ||psi - truth|| / ||truth||); with a process group rank 0 writes it."""
         if rule not in self.RULES or line_search not in self.SEARCHES:
             raise ValueError(f"rule in {self.RULES}, line_search in {self.SEARCHES}")
         self.group = group
@@ -63,6 +67,9 @@ class Reconstruction:
         self.F = None
         self.history = {"F": [], "gamma_psi": [], "gamma_q": [], "beta_psi": [], "beta_q": [],
                         "F_after_psi": []}
+        self.log_path = log_path
+        self.truth = truth
+        self._truth_sq = None
 
     # ------------------------------------------------------------------ reductions over ranks
     def _allreduce(self, vals):
@@ -181,7 +188,29 @@ class Reconstruction:
             for key, val in (("F", self.F), ("gamma_psi", gam_psi), ("gamma_q", gam_q),
                              ("beta_psi", betas[0]), ("beta_q", betas[1])):
                 self.history[key].append(val)
+            if self.log_path is not None:
+                self._log(gam_psi, gam_q, betas)
         return self.history
+
+    def _log(self, gam_psi, gam_q, betas):
+        rec = {"iter": len(self.history["F"]) - 1, "F": self.F, "gamma_psi": gam_psi,
+               "gamma_q": gam_q, "beta_psi": betas[0], "beta_q": betas[1],
+               "gnorm_psi": float(np.sqrt(max(self.gg[0], 0.0))),
+               "gnorm_q": float(np.sqrt(max(self.gg[1], 0.0)))}
+        if self.truth is not None:
+            # ||psi - truth||^2 from FP64 inner products (no psi-sized temporary)
+            if self._truth_sq is None:
+                self._truth_sq = self._dots(0, (self.truth, self.truth))[0]
+            pp, pt = self._dots(0, (self.psi, self.psi), (self.psi, self.truth))
+            rec["rel_err_psi"] = float(np.sqrt(max(pp - 2.0 * pt + self._truth_sq, 0.0) /
+                                               self._truth_sq))
+        rank = 0
+        if self.group is not None:
+            import torch.distributed as dist
+            rank = dist.get_rank()
+        if rank == 0:
+            with open(self.log_path, "a") as f:
+                f.write(json.dumps(rec) + "\n")
 
     # ------------------------------------------------------------------ checkpoint / resume
     def save(self, path):

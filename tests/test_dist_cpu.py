@@ -216,3 +216,25 @@ def test_checkpoint_resume_is_bit_exact(tmp_path):
     with pytest.raises(ValueError):
         Reconstruction(_OracleHolo(geo, t, sqrt_d, sqrt_dref), torch.from_numpy(psi.copy()),
                        torch.from_numpy(q.copy()), rule="polak-ribiere").load(path)
+
+
+def test_driver_iteration_log(tmp_path):
+    """The driver's JSONL log: one line per iteration, equal to its history, with the
+    gradient norms and the relative error against a ground truth (oracle stand-in, CPU)."""
+    import json
+    from paper_2407_20304_gb300.cg import Reconstruction
+    geo, psi, q, t, _, sqrt_d, sqrt_dref = _problem(False)
+    path = tmp_path / "log.jsonl"
+    truth = torch.from_numpy((0.9 + 0.05j) * np.ones_like(psi))
+    r = Reconstruction(_OracleHolo(geo, t, sqrt_d, sqrt_dref), torch.from_numpy(psi.copy()),
+                       torch.from_numpy(q.copy()), log_path=str(path), truth=truth)
+    r.run(3)
+    recs = [json.loads(line) for line in open(path)]
+    assert [x["iter"] for x in recs] == [1, 2, 3]
+    assert [x["F"] for x in recs] == r.history["F"][1:]
+    assert [x["gamma_psi"] for x in recs] == r.history["gamma_psi"]
+    assert [x["beta_q"] for x in recs] == r.history["beta_q"]
+    assert all(x["gnorm_psi"] > 0 and x["gnorm_q"] > 0 for x in recs)
+    d = r.psi.numpy().astype(np.complex128) - truth.numpy().astype(np.complex128)
+    ref = np.linalg.norm(d) / np.linalg.norm(truth.numpy().astype(np.complex128))
+    assert abs(recs[-1]["rel_err_psi"] - ref) <= 1e-9 * ref
