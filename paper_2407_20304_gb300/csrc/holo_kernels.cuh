@@ -32,6 +32,8 @@
 
 #pragma once
 
+#include <type_traits>
+
 #include "holo_fft.cuh"
 #include "holo_internal.h"
 #include "holo_tma.cuh"
@@ -126,6 +128,27 @@ __device__ __forceinline__ bool line_ok(const PassArgs& a, int gp, int i, int P)
   if (gp < p_lo || gp >= p_lo + a.nk * a.J) return false;
   const PlaneDesc d = a.planes[gp];
   return i >= 0 && i < d.bys && plane_box_ok(a, d, P);
+}
+
+// Pass C's MID form: one line per block (block-uniform line) and P = 2^k, so that register c
+// of thread t holds column t + T c; when the line's plane box lies inside the middle half of
+// the grid, P/4 .. 3P/4, only the registers c = 4 .. 11 hold box columns, and the inverse row
+// transform's other outputs are unused.  (The same form of pass A, whose forward transform
+// would take known zeros, measured slower: 9.85 -> 10.13 ms against 9.66 -> 9.45 ms here.)
+template <int P, bool SHIFT>
+__host__ __device__ constexpr bool mid_form_ok() {
+  return !SHIFT && !Fft<P>::R3 && RowCfg<P>::G == 1;
+}
+
+// The box of line `li`'s plane inside the grid's middle half P/4 .. 3P/4 (false for lines past
+// the end and, in HOLO_BOUNDS_CHECK builds, for bad line-table entries).
+template <int P>
+__device__ __forceinline__ bool line_box_mid(const PassArgs& a, int li) {
+  if (li >= a.nlines) return false;
+  const int2 L = __ldg(a.lines + a.line0 + li);
+  if (kBoundsCheck && !line_ok(a, L.x, L.y, P)) return false;
+  const PlaneDesc d = a.planes[L.x];
+  return d.bx0 >= P / 4 && d.bx0 + d.bxs <= 3 * P / 4;
 }
 
 // Chirp exp(-i pi lambda z f^2)/P is even in the signed frequency, so a table of the
@@ -1153,99 +1176,112 @@ __global__ void __launch_bounds__(RowCfg<P>::NT, RowCfg<P>::MINB) k_pass_c(PassA
   const int p_lo = a.k0 * a.J;
   int jcur = -1;
   for (int base = blockIdx.x * R::G; base < a.nlines; base += gridDim.x * R::G) {
-    const int li = base + g;
-    bool valid = li < a.nlines;
-    const int line = a.line0 + (valid ? li : 0);
-    const int2 L = __ldg(a.lines + line);
-    int gp = L.x, i = L.y;
-    if constexpr (kBoundsCheck) {
-      if (!line_ok(a, gp, i, P)) {
-        if (valid) flag_bounds(a.err);
-        valid = false;
-        gp = p_lo;
-        i = 0;
+    // MID (see mid_form_ok): the box columns are those of registers 4 .. 11, so the inverse
+    // transform's other outputs are unused
+    auto line = [&](auto mid) {
+      constexpr bool MID = decltype(mid)::value;
+      const int li = base + g;
+      bool valid = li < a.nlines;
+      const int line = a.line0 + (valid ? li : 0);
+      const int2 L = __ldg(a.lines + line);
+      int gp = L.x, i = L.y;
+      if constexpr (kBoundsCheck) {
+        if (!line_ok(a, gp, i, P)) {
+          if (valid) flag_bounds(a.err);
+          valid = false;
+          gp = p_lo;
+          i = 0;
+        }
       }
-    }
-    const int lp = gp - p_lo, j = lp % a.J;
-    int jb = (__ldg(a.lines + a.line0 + base).x - p_lo) % a.J;
-    if (kBoundsCheck && (jb < 0 || jb >= a.J)) jb = 0;
-    float2* yrow = a.ybuf + (long long)lp * a.ystride + (long long)i * n;
-    float2 v[16];
-#pragma unroll
-    for (int c = 0; c < 16; ++c) {
-      const int rel = F::pos(t, c) - lo;
-      // HALF (n = P/2, P = 2^k >= 1024): the crop columns are those of registers 4 .. 11
-      const bool in = HALF ? (c >= 4 && c < 12) : (unsigned)rel < (unsigned)n;
-      v[c] = (valid && in) ? yrow[rel] : make_float2(0.f, 0.f);
-    }
-    // the next line of this thread group: its adjoint-field row, probe row and conj(w) v row go
-    // to L2 now (one bulk request each, issued by the line's first thread)
-    if (t == 0 && li + (int)gridDim.x * R::G < a.nlines) {
-      const int2 NL = __ldg(a.lines + a.line0 + li + gridDim.x * R::G);
-      // (a bad entry is flagged when its own line runs)
-      if (!kBoundsCheck || line_ok(a, NL.x, NL.y, P)) {
-        const int nlp = NL.x - p_lo;
-        const PlaneDesc nd = a.planes[NL.x];
-        l2_prefetch_bulk(a.ybuf + (long long)nlp * a.ystride + (long long)NL.y * n,
-                         n * (uint32_t)sizeof(float2));
-        l2_prefetch_bulk(a.pj + ((long long)(nlp % a.J) * P + nd.by0 + NL.y) * P + nd.bx0,
-                         nd.bxs * (uint32_t)sizeof(float2));
-        l2_prefetch_bulk(a.gkbuf + (long long)nlp * a.gkstride + (long long)NL.y * nd.bxs,
-                         nd.bxs * (uint32_t)sizeof(float2));
+      const int lp = gp - p_lo, j = lp % a.J;
+      int jb = (__ldg(a.lines + a.line0 + base).x - p_lo) % a.J;
+      if (kBoundsCheck && (jb < 0 || jb >= a.J)) jb = 0;
+      float2* yrow = a.ybuf + (long long)lp * a.ystride + (long long)i * n;
+      float2 v[16];
+  #pragma unroll
+      for (int c = 0; c < 16; ++c) {
+        const int rel = F::pos(t, c) - lo;
+        // HALF (n = P/2, P = 2^k >= 1024): the crop columns are those of registers 4 .. 11
+        const bool in = HALF ? (c >= 4 && c < 12) : (unsigned)rel < (unsigned)n;
+        v[c] = (valid && in) ? yrow[rel] : make_float2(0.f, 0.f);
       }
-    }
-    ensure_chirp<P>(chs, a.chirp_zhat, R::G == 1 ? j : jb, jcur);
-    __syncthreads();
-    fft_fwd_with<P>(v, sm, tw, t, SyncBlock());
-    const bool own = R::G == 1 || j == jcur;
-    const float2* chg = a.chirp_zhat + (long long)j * P;
-    const ChirpAt<P> cat(chs, t);
-    const float2* rmp = SHIFT ? a.ramp_x + (long long)gp * P : nullptr;
-#pragma unroll
-    for (int c = 0; c < 16; ++c) {
-      const int f = F::fpos(t, c);
-      v[c] = cmulc(v[c], own ? cat(c) : __ldg(chg + f));
-      if (SHIFT) v[c] = cmulc(v[c], __ldg(rmp + f));
-    }
-    fft_inv_with<P>(v, sm, tw, t, SyncBlock());
-    // v holds the adjoint field on this P-grid row; the exchange buffer is free.
-    // The box holds w = R0(psi - ext) (R' psi in the SHIFT form) written by pass A; replace
-    // it by conj(w) v.
-    const PlaneDesc d = a.planes[gp];
-    const float2* prow = a.pj + ((long long)j * P + d.by0 + i) * P;
-    float2* gk = a.gkbuf + (long long)lp * a.gkstride + (long long)i * d.bxs;
-#pragma unroll
-    for (int c = 0; c < 16; ++c) {
-      const int X = F::pos(t, c), rel = X - d.bx0;
-      if (valid && (unsigned)rel < (unsigned)d.bxs) {
-        sm[rel] = cconjmul(__ldg(prow + X), v[c]);
-        gk[rel] = cconjmul(gk[rel], v[c]);
+      // the next line of this thread group: its adjoint-field row, probe row and conj(w) v row go
+      // to L2 now (one bulk request each, issued by the line's first thread)
+      if (t == 0 && li + (int)gridDim.x * R::G < a.nlines) {
+        const int2 NL = __ldg(a.lines + a.line0 + li + gridDim.x * R::G);
+        // (a bad entry is flagged when its own line runs)
+        if (!kBoundsCheck || line_ok(a, NL.x, NL.y, P)) {
+          const int nlp = NL.x - p_lo;
+          const PlaneDesc nd = a.planes[NL.x];
+          l2_prefetch_bulk(a.ybuf + (long long)nlp * a.ystride + (long long)NL.y * n,
+                           n * (uint32_t)sizeof(float2));
+          l2_prefetch_bulk(a.pj + ((long long)(nlp % a.J) * P + nd.by0 + NL.y) * P + nd.bx0,
+                           nd.bxs * (uint32_t)sizeof(float2));
+          l2_prefetch_bulk(a.gkbuf + (long long)nlp * a.gkstride + (long long)NL.y * nd.bxs,
+                           nd.bxs * (uint32_t)sizeof(float2));
+        }
       }
-    }
-    __syncthreads();
-    // x-transpose of the bilinear resample: h[ip] = w0 z[X0] + w1 z[X0 + 1] with the
-    // transposed taps of this plane (same FP64-built weights as the forward taps).
-    const AdjTap* xa = a.xadj + (long long)gp * n;
-#pragma unroll
-    for (int c = 0; c < 16; ++c) {
-      const int ip = F::pos(t, c);
-      if (!valid || (HALF ? c >= 8 : ip >= n)) continue;
-      const AdjTap at = xa[ip];
-      float2 h = make_float2(0.f, 0.f);
-      const int r0 = at.X0 - d.bx0;
-      if (at.w0 != 0.f) {
-        const float2 z = sm[r0];
-        h.x = at.w0 * z.x;
-        h.y = at.w0 * z.y;
+      ensure_chirp<P>(chs, a.chirp_zhat, R::G == 1 ? j : jb, jcur);
+      __syncthreads();
+      fft_fwd_with<P>(v, sm, tw, t, SyncBlock());
+      const bool own = R::G == 1 || j == jcur;
+      const float2* chg = a.chirp_zhat + (long long)j * P;
+      const ChirpAt<P> cat(chs, t);
+      const float2* rmp = SHIFT ? a.ramp_x + (long long)gp * P : nullptr;
+  #pragma unroll
+      for (int c = 0; c < 16; ++c) {
+        const int f = F::fpos(t, c);
+        v[c] = cmulc(v[c], own ? cat(c) : __ldg(chg + f));
+        if (SHIFT) v[c] = cmulc(v[c], __ldg(rmp + f));
       }
-      if (at.w1 != 0.f) {
-        const float2 z = sm[r0 + 1];
-        h.x = fmaf(at.w1, z.x, h.x);
-        h.y = fmaf(at.w1, z.y, h.y);
+      fft_inv_with<P>(v, sm, tw, t, SyncBlock());
+      // v holds the adjoint field on this P-grid row; the exchange buffer is free.
+      // The box holds w = R0(psi - ext) (R' psi in the SHIFT form) written by pass A; replace
+      // it by conj(w) v.
+      const PlaneDesc d = a.planes[gp];
+      const float2* prow = a.pj + ((long long)j * P + d.by0 + i) * P;
+      float2* gk = a.gkbuf + (long long)lp * a.gkstride + (long long)i * d.bxs;
+  #pragma unroll
+      for (int c = 0; c < 16; ++c) {
+        const int X = F::pos(t, c), rel = X - d.bx0;
+        if ((!MID || (c >= 4 && c < 12)) && valid && (unsigned)rel < (unsigned)d.bxs) {
+          sm[rel] = cconjmul(__ldg(prow + X), v[c]);
+          gk[rel] = cconjmul(gk[rel], v[c]);
+        }
       }
-      yrow[ip] = h;
+      __syncthreads();
+      // x-transpose of the bilinear resample: h[ip] = w0 z[X0] + w1 z[X0 + 1] with the
+      // transposed taps of this plane (same FP64-built weights as the forward taps).
+      const AdjTap* xa = a.xadj + (long long)gp * n;
+  #pragma unroll
+      for (int c = 0; c < 16; ++c) {
+        const int ip = F::pos(t, c);
+        if (!valid || (HALF ? c >= 8 : ip >= n)) continue;
+        const AdjTap at = xa[ip];
+        float2 h = make_float2(0.f, 0.f);
+        const int r0 = at.X0 - d.bx0;
+        if (at.w0 != 0.f) {
+          const float2 z = sm[r0];
+          h.x = at.w0 * z.x;
+          h.y = at.w0 * z.y;
+        }
+        if (at.w1 != 0.f) {
+          const float2 z = sm[r0 + 1];
+          h.x = fmaf(at.w1, z.x, h.x);
+          h.y = fmaf(at.w1, z.y, h.y);
+        }
+        yrow[ip] = h;
+      }
+      __syncthreads();
+    };
+    if constexpr (mid_form_ok<P, SHIFT>()) {
+      if (line_box_mid<P>(a, base))
+        line(std::true_type{});
+      else
+        line(std::false_type{});
+    } else {
+      line(std::false_type{});
     }
-    __syncthreads();
   }
 }
 
