@@ -63,7 +63,7 @@ class Workload:
 def config(which):
     """Configuration `which` (index 0 .. 4 or name) of configs.json, as a dict; its seed is
     SEED_BASE + seed_offset."""
-    for c in _CONFIGS["configs"]:
+    for c in _CONFIGS["problems"]:
         if which in (c["index"], c["name"]):
             return dict(c, seed=SEED_BASE + c["seed_offset"])
     raise KeyError(which)
@@ -87,7 +87,7 @@ def workloads():
     """The single-problem synthetic workloads of configs.json: tiny, medium, autograd-sized,
     large (the batch, configuration 3, is a list of problems drawn from its ranges)."""
     out = {}
-    for c in _CONFIGS["configs"]:
+    for c in _CONFIGS["problems"]:
         if isinstance(c["pad"], str):
             continue
         out[c["name"]] = Workload(c["name"], c["n"], c["pad"], c["n_angles"], c["n_dist"],
