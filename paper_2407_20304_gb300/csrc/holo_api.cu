@@ -88,7 +88,7 @@ struct holo_ctx {
   cudaStream_t stream = nullptr;
   // holo_gradient_host in parts: copy streams and their events (created on first use)
   cudaStream_t cs_in = nullptr, cs_out = nullptr;
-  cudaEvent_t ev_start = nullptr, ev_out = nullptr;
+  cudaEvent_t ev_start = nullptr, ev_out = nullptr, ev_q = nullptr;
   cudaEvent_t ev_in[kHostParts] = {}, ev_done[kHostParts] = {};
   const holo::Ops* ops = nullptr;
   double mt[HOLO_MAX_DIST] = {}, omega[HOLO_MAX_DIST] = {}, zeta[HOLO_MAX_DIST] = {},
@@ -624,7 +624,9 @@ holo_status eval_begin(holo_ctx* c, PassArgs& a) {
     HOLO_LAUNCH(c, holo::launch_sum_f64(c->d_part + nbx, kRefBlocks, c->d_red + 1, 0, c->stream));
     a.rref = c->d_rref;
   } else {
-    HOLO_CK(c, cudaMemsetAsync(c->d_red + 1, 0, sizeof(double), c->stream));
+    // no reference term in this call: red[1] = 0 (a sum over nothing, by a kernel rather than a
+    // memset, which could wait behind a host-buffer call's copies)
+    HOLO_LAUNCH(c, holo::launch_sum_f64(c->d_part, 0, c->d_red + 1, 0, c->stream));
   }
   return HOLO_OK;
 }
@@ -994,7 +996,7 @@ holo_status holo_destroy(holo_ctx* c) {
   if (c->h_red) cudaFreeHost(c->h_red);
   for (cudaStream_t st : {c->cs_in, c->cs_out})
     if (st) cudaStreamDestroy(st);
-  for (cudaEvent_t e : {c->ev_start, c->ev_out})
+  for (cudaEvent_t e : {c->ev_start, c->ev_out, c->ev_q})
     if (e) cudaEventDestroy(e);
   for (int i = 0; i < kHostParts; ++i) {
     if (c->ev_in[i]) cudaEventDestroy(c->ev_in[i]);
@@ -1240,7 +1242,11 @@ holo_status holo_set_probe(holo_ctx* c, const void* q) {
   const int P = c->P, n = c->n, lo = P / 2 - n / 2;
   const size_t plane = sizeof(float2) * (size_t)P * P;
   PassTimer tm(c, HOLO_T_PROBE);
-  HOLO_CK(c, cudaMemcpyAsync(c->d_pj, q, plane, cudaMemcpyDeviceToDevice, c->stream));
+  // p_0 = q (omega_0 = 0), copied by a kernel: a copy engine may still be busy with the
+  // host->device copies of a host-buffer call
+  (void)plane;
+  HOLO_LAUNCH(c, holo::launch_scale_add(c->d_pj, (const float2*)q, 1.f, (long long)P * P, 0,
+                                        c->stream));
   holo_status st;
   for (int j = 1; j < c->J; ++j) {
     // p_j = D_{omega_j}(q)  (Eq. fwd_model_cone3)
@@ -1309,6 +1315,7 @@ static holo_status gradient_host_parts(holo_ctx* c, int k0, int nk, int parts, c
     if (cudaStreamCreateWithFlags(&c->cs_in, cudaStreamNonBlocking) != cudaSuccess ||
         cudaStreamCreateWithFlags(&c->cs_out, cudaStreamNonBlocking) != cudaSuccess ||
         cudaEventCreateWithFlags(&c->ev_start, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&c->ev_q, cudaEventDisableTiming) != cudaSuccess ||
         cudaEventCreateWithFlags(&c->ev_out, cudaEventDisableTiming) != cudaSuccess)
       return fail(c, HOLO_ERR_CUDA, std::string("copy streams: ") + cudaGetErrorString(cudaGetLastError()));
     for (int i = 0; i < kHostParts; ++i)
@@ -1321,6 +1328,14 @@ static holo_status gradient_host_parts(holo_ctx* c, int k0, int nk, int parts, c
   HOLO_CK(c, cudaEventRecord(c->ev_start, c->stream));
   HOLO_CK(c, cudaStreamWaitEvent(c->cs_in, c->ev_start, 0));
   HOLO_CK(c, cudaStreamWaitEvent(c->cs_out, c->ev_start, 0));
+  // the probe first: every kernel of the call waits for it, and host->device copies run in
+  // the order they were issued, so a probe copied after the parts' psi and data would hold
+  // the whole call back by their copy time
+  if (q_host) {
+    HOLO_CK(c, cudaMemcpyAsync(c->s_q, q_host, sizeof(float2) * (size_t)P * P,
+                               cudaMemcpyHostToDevice, c->cs_in));
+    HOLO_CK(c, cudaEventRecord(c->ev_q, c->cs_in));
+  }
   int wsum = 0;
   for (int p = 0; p < parts; ++p) wsum += kHostWeights[p];
   // part p covers [bound(p), bound(p + 1)) (rounded weight prefix sums); with nk >= 2 parts
@@ -1340,8 +1355,7 @@ static holo_status gradient_host_parts(holo_ctx* c, int k0, int nk, int parts, c
     HOLO_CK(c, cudaEventRecord(c->ev_in[p], c->cs_in));
   }
   if (q_host) {
-    HOLO_CK(c, cudaMemcpyAsync(c->s_q, q_host, sizeof(float2) * (size_t)P * P,
-                               cudaMemcpyHostToDevice, c->stream));
+    HOLO_CK(c, cudaStreamWaitEvent(c->stream, c->ev_q, 0));
     if ((st = holo_set_probe(c, c->s_q))) return st;
   }
   PassArgs whole = pass_args(c, k0, nk, c->s_psi);
