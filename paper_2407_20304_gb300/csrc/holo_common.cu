@@ -184,23 +184,27 @@ __global__ void __launch_bounds__(256) k_reduce_g(PassArgs a, float2* Gp, int j,
 // row.  A block moves a tile of 32 rows x W columns (W a multiple of C) of one image through
 // shared memory: the rows are read and the groups' runs of 32 x C values written contiguously.
 constexpr int kBlkRows = 32;
-__global__ void __launch_bounds__(256) k_block_data(const float* __restrict__ in, int n, int C,
-                                                    int W, float* __restrict__ out) {
-  extern __shared__ float tile[];  // [kBlkRows][W + 1]
+template <int C>
+__global__ void __launch_bounds__(256) k_block_data(const float* __restrict__ in, int n,
+                                                    float* __restrict__ out) {
+  // W = max(64, C) columns of kBlkRows rows per block; C a power of two, so the index
+  // arithmetic is shifts and masks
+  constexpr int W = C >= 64 ? C : 64;
+  __shared__ float tile[kBlkRows][W + 1];
   const long long p = blockIdx.z;
   const int r0 = blockIdx.x * kBlkRows, c0 = blockIdx.y * W;
   const int groups = (n + C - 1) / C;
   const float* src = in + p * n * (long long)n;
   for (int e = threadIdx.x; e < kBlkRows * W; e += blockDim.x) {
     const int rr = e / W, cc = e % W, r = r0 + rr, col = c0 + cc;
-    tile[rr * (W + 1) + cc] = (r < n && col < n) ? __ldg(src + (long long)r * n + col) : 0.f;
+    tile[rr][cc] = (r < n && col < n) ? __ldg(src + (long long)r * n + col) : 0.f;
   }
   __syncthreads();
   const int g0 = c0 / C, ng = min(W / C, groups - g0), rows = min(kBlkRows, n - r0);
   float* dst = out + (p * groups + g0) * (long long)n * C;
-  for (int e = threadIdx.x; e < ng * rows * C; e += blockDim.x) {
-    const int gl = e / (rows * C), rem = e % (rows * C), rr = rem / C, cc = rem % C;
-    dst[((long long)gl * n + r0 + rr) * C + cc] = tile[rr * (W + 1) + gl * C + cc];
+  for (int e = threadIdx.x; e < kBlkRows * W; e += blockDim.x) {
+    const int gl = e / (kBlkRows * C), rr = (e / C) % kBlkRows, cc = e % C;
+    if (gl < ng && rr < rows) dst[((long long)gl * n + r0 + rr) * C + cc] = tile[rr][gl * C + cc];
   }
 }
 
@@ -484,16 +488,20 @@ cudaError_t launch_embed_edge(const float* a, int n, int P, float2* q, cudaStrea
 cudaError_t launch_block_data(const float* in, long long planes, int n, int C, float* out,
                               cudaStream_t s) {
   if (planes <= 0) return cudaSuccess;
-  const int W = C >= 64 ? C : 64;  // a multiple of C (C is 2^k or a power of two below 64)
+  const int W = C >= 64 ? C : 64;  // a multiple of C (C is a power of two, 2 .. 256)
   const int groups = (n + C - 1) / C;
   const dim3 grid((n + kBlkRows - 1) / kBlkRows, (groups * C + W - 1) / W, (unsigned)planes);
-  const size_t sm = (size_t)kBlkRows * (W + 1) * sizeof(float);
-  if (sm > 48 * 1024) {
-    cudaError_t e = cudaFuncSetAttribute(k_block_data, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)sm);
-    if (e != cudaSuccess) return e;
+  switch (C) {
+    case 2: k_block_data<2><<<grid, kThreads, 0, s>>>(in, n, out); break;
+    case 4: k_block_data<4><<<grid, kThreads, 0, s>>>(in, n, out); break;
+    case 8: k_block_data<8><<<grid, kThreads, 0, s>>>(in, n, out); break;
+    case 16: k_block_data<16><<<grid, kThreads, 0, s>>>(in, n, out); break;
+    case 32: k_block_data<32><<<grid, kThreads, 0, s>>>(in, n, out); break;
+    case 64: k_block_data<64><<<grid, kThreads, 0, s>>>(in, n, out); break;
+    case 128: k_block_data<128><<<grid, kThreads, 0, s>>>(in, n, out); break;
+    case 256: k_block_data<256><<<grid, kThreads, 0, s>>>(in, n, out); break;
+    default: return cudaErrorInvalidValue;
   }
-  k_block_data<<<grid, kThreads, sm, s>>>(in, n, C, W, out);
   return cudaGetLastError();
 }
 
