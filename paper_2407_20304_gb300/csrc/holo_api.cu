@@ -1349,9 +1349,15 @@ static holo_status gradient_host_parts(holo_ctx* c, int k0, int nk, int parts, c
     const int b0 = bound(p), m = bound(p + 1) - b0;
     HOLO_CK(c, cudaMemcpyAsync(c->s_psi + b0 * n2, static_cast<const float2*>(psi_host) + b0 * n2,
                                sizeof(float2) * m * n2, cudaMemcpyHostToDevice, c->cs_in));
-    if (sqrt_d_host)
+    if (sqrt_d_host) {
       HOLO_CK(c, cudaMemcpyAsync(c->s_data + (size_t)b0 * J * n2, sqrt_d_host + (size_t)b0 * J * n2,
                                  sizeof(float) * m * J * n2, cudaMemcpyHostToDevice, c->cs_in));
+      // the part's relayout runs on the copy stream as soon as its data arrive, beside the
+      // passes of the earlier parts (its blocks fit next to theirs on an SM)
+      HOLO_LAUNCH(c, holo::launch_block_data(c->s_data + (size_t)b0 * J * n2, (long long)m * J, n,
+                                             c->ops->pass_b_cols,
+                                             c->s_dblk + (size_t)b0 * J * dplane, c->cs_in));
+    }
     HOLO_CK(c, cudaEventRecord(c->ev_in[p], c->cs_in));
   }
   if (q_host) {
@@ -1366,10 +1372,7 @@ static holo_status gradient_host_parts(holo_ctx* c, int k0, int nk, int parts, c
     HOLO_CK(c, cudaStreamWaitEvent(c->stream, c->ev_in[p], 0));
     PassArgs a = pass_args(c, k0 + b0, m, c->s_psi + b0 * n2);
     if (sqrt_d_host) {
-      float* blk = c->s_dblk + (size_t)b0 * J * dplane;
-      HOLO_LAUNCH(c, holo::launch_block_data(c->s_data + (size_t)b0 * J * n2, (long long)m * J, n,
-                                             c->ops->pass_b_cols, blk, c->stream));
-      a.dblk = blk;
+      a.dblk = c->s_dblk + (size_t)b0 * J * dplane;
       a.data_k0 = k0 + b0;
     }
     a.grad_psi = c->s_gpsi + b0 * n2;
