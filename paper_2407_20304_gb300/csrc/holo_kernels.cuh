@@ -629,106 +629,127 @@ __device__ __forceinline__ bool pass_b_run(const PassArgs& a, int bid, int nblk,
             d.bys = 0;  // the plane's box rows are skipped
           }
         }
-        float2* yb = a.ybuf + (long long)lp * a.ystride;
-        float2 v[16];
-        if (staged) {
-          const bool ok = mbar_wait(ybarp, yphase);
-          yphase ^= 1;
-#pragma unroll
-          for (int c = 0; c < 16; ++c) {
-            const int rel = F::pos(t, c) - d.by0;
-            v[c] = (valid && (unsigned)rel < (unsigned)d.bys) ? stg[rel * C + g]
-                                                               : make_float2(0.f, 0.f);
-          }
-          // every thread has its tile entries: the stage is free for the next plane
-          if (__syncthreads_or(!ok)) {
-            if (threadIdx.x == 0) atomicOr(a.err, 1ull);
-            return false;
-          }
-          if (threadIdx.x == 0) {
-            int ncg = cg, np = pp + 1, n0, n1;
-            bool more = np < p1;
-            if (!more && segment(sg + 1, ncg, n0, n1)) {
-              np = n0;
-              more = true;
+        // MID (n = P/2 form only): the plane's box rows lie in P/4 .. 3P/4, i.e. in the
+        // registers c = 4 .. 11, so the forward column transform's other inputs are zero and the
+        // adjoint transform's other outputs unused (planes run distance-major, so each form runs
+        // in long stretches)
+        auto plane = [&](auto mid) -> bool {
+          constexpr bool MID = decltype(mid)::value;
+          float2* yb = a.ybuf + (long long)lp * a.ystride;
+          float2 v[16];
+          if (staged) {
+            const bool ok = mbar_wait(ybarp, yphase);
+            yphase ^= 1;
+  #pragma unroll
+            for (int c = 0; c < 16; ++c) {
+              const int rel = F::pos(t, c) - d.by0;
+              v[c] = ((!MID || (c >= 4 && c < 12)) && valid && (unsigned)rel < (unsigned)d.bys)
+                         ? stg[rel * C + g]
+                         : make_float2(0.f, 0.f);
             }
-            if (more) stage_y<P>(a, stg, ybarp, ncg, np / a.nk, np % a.nk);
-          }
-        } else {
-#pragma unroll
-          for (int c = 0; c < 16; ++c) {
-            const int rel = F::pos(t, c) - d.by0;
-            v[c] = (valid && (unsigned)rel < (unsigned)d.bys) ? yb[(long long)rel * n + col]
-                                                               : make_float2(0.f, 0.f);
-          }
-          __syncthreads();
-        }
-        fft_fwd_with<P>(v, sm, tw, t, SyncBlock());
-        // the data of the crop rows are fetched now, so the inverse transform hides their latency
-        const float* ad =
-            a.dblk + ((gplane - (long long)a.data_k0 * a.J) * a.dgroups + cg) * (long long)n * C;
-        float dats[16];
-#pragma unroll
-        for (int c = 0; c < 16; ++c) {
-          const int rr = F::pos(t, c) - lo;
-          dats[c] = (valid && in_crop(c, rr)) ? __ldg(ad + rr * C + g) : 0.f;
-        }
-        const float2* rmp = SHIFT ? a.ramp_y + gplane * P : nullptr;
-#pragma unroll
-        for (int c = 0; c < 16; ++c) {
-          v[c] = cmul(v[c], cat(c));
-          if (SHIFT) v[c] = cmul(v[c], __ldg(rmp + F::fpos(t, c)));
-        }
-        fft_inv_with<P>(v, sm, tw, t, SyncBlock());
-        float2* uo = a.u_out ? a.u_out + (long long)lp * n * n : nullptr;
-        float lsum = 0.f;
-#pragma unroll
-        for (int c = 0; c < 16; ++c) {
-          const int rr = F::pos(t, c) - lo;
-          float2 r = make_float2(0.f, 0.f);
-          if (valid && in_crop(c, rr)) {
-            const long long e = (long long)rr * n + col;
-            float2 u = v[c];
-            const float2 b = sb[rr * C + g];
-            u.x = fmaf(a.ext, b.x, u.x);
-            u.y = fmaf(a.ext, b.y, u.y);
-            const float dat = dats[c];
-            const float i2 = fmaf(u.x, u.x, u.y * u.y);
-            // F2: (|u| - a)^2, r = u - a u/|u| (u/|u| := 0 at |u| = 0);
-            // F1: (|u|^2 - d)^2, r = 2 (|u|^2 - d) u
-            float diff, s;
-            if (a.functional) {
-              diff = i2 - dat;
-              s = 2.f * diff;
-            } else {
-              const float mag = sqrtf(i2);
-              diff = mag - dat;
-              s = mag > 0.f ? 1.f - __fdividef(dat, mag) : 0.f;
+            // every thread has its tile entries: the stage is free for the next plane
+            if (__syncthreads_or(!ok)) {
+              if (threadIdx.x == 0) atomicOr(a.err, 1ull);
+              return false;  // (leaves the plane; the caller returns)
             }
-            lsum = fmaf(diff, diff, lsum);
-            if (uo) uo[e] = u;
-            if (ADJ) {
-              r = cscale(u, s);
-              sS[rr * C + g] = cadd(sS[rr * C + g], r);
+            if (threadIdx.x == 0) {
+              int ncg = cg, np = pp + 1, n0, n1;
+              bool more = np < p1;
+              if (!more && segment(sg + 1, ncg, n0, n1)) {
+                np = n0;
+                more = true;
+              }
+              if (more) stage_y<P>(a, stg, ybarp, ncg, np / a.nk, np % a.nk);
             }
+          } else {
+  #pragma unroll
+            for (int c = 0; c < 16; ++c) {
+              const int rel = F::pos(t, c) - d.by0;
+              v[c] = ((!MID || (c >= 4 && c < 12)) && valid && (unsigned)rel < (unsigned)d.bys)
+                         ? yb[(long long)rel * n + col]
+                         : make_float2(0.f, 0.f);
+            }
+            __syncthreads();
           }
-          v[c] = r;
-        }
-        dsum += (double)lsum;
-        if constexpr (ADJ) {
           fft_fwd_with<P>(v, sm, tw, t, SyncBlock());
-#pragma unroll
+          // the data of the crop rows are fetched now, so the inverse transform hides their latency
+          const float* ad =
+              a.dblk + ((gplane - (long long)a.data_k0 * a.J) * a.dgroups + cg) * (long long)n * C;
+          float dats[16];
+  #pragma unroll
           for (int c = 0; c < 16; ++c) {
-            v[c] = cmulc(v[c], cat(c));
-            if (SHIFT) v[c] = cmulc(v[c], __ldg(rmp + F::fpos(t, c)));
+            const int rr = F::pos(t, c) - lo;
+            dats[c] = (valid && in_crop(c, rr)) ? __ldg(ad + rr * C + g) : 0.f;
+          }
+          const float2* rmp = SHIFT ? a.ramp_y + gplane * P : nullptr;
+  #pragma unroll
+          for (int c = 0; c < 16; ++c) {
+            v[c] = cmul(v[c], cat(c));
+            if (SHIFT) v[c] = cmul(v[c], __ldg(rmp + F::fpos(t, c)));
           }
           fft_inv_with<P>(v, sm, tw, t, SyncBlock());
-#pragma unroll
+          float2* uo = a.u_out ? a.u_out + (long long)lp * n * n : nullptr;
+          float lsum = 0.f;
+  #pragma unroll
           for (int c = 0; c < 16; ++c) {
-            const int rel = F::pos(t, c) - d.by0;
-            if (valid && (unsigned)rel < (unsigned)d.bys) yb[(long long)rel * n + col] = v[c];
+            const int rr = F::pos(t, c) - lo;
+            float2 r = make_float2(0.f, 0.f);
+            if (valid && in_crop(c, rr)) {
+              const long long e = (long long)rr * n + col;
+              float2 u = v[c];
+              const float2 b = sb[rr * C + g];
+              u.x = fmaf(a.ext, b.x, u.x);
+              u.y = fmaf(a.ext, b.y, u.y);
+              const float dat = dats[c];
+              const float i2 = fmaf(u.x, u.x, u.y * u.y);
+              // F2: (|u| - a)^2, r = u - a u/|u| (u/|u| := 0 at |u| = 0);
+              // F1: (|u|^2 - d)^2, r = 2 (|u|^2 - d) u
+              float diff, s;
+              if (a.functional) {
+                diff = i2 - dat;
+                s = 2.f * diff;
+              } else {
+                const float mag = sqrtf(i2);
+                diff = mag - dat;
+                s = mag > 0.f ? 1.f - __fdividef(dat, mag) : 0.f;
+              }
+              lsum = fmaf(diff, diff, lsum);
+              if (uo) uo[e] = u;
+              if (ADJ) {
+                r = cscale(u, s);
+                sS[rr * C + g] = cadd(sS[rr * C + g], r);
+              }
+            }
+            v[c] = r;
           }
+          dsum += (double)lsum;
+          if constexpr (ADJ) {
+            fft_fwd_with<P>(v, sm, tw, t, SyncBlock());
+  #pragma unroll
+            for (int c = 0; c < 16; ++c) {
+              v[c] = cmulc(v[c], cat(c));
+              if (SHIFT) v[c] = cmulc(v[c], __ldg(rmp + F::fpos(t, c)));
+            }
+            fft_inv_with<P>(v, sm, tw, t, SyncBlock());
+  #pragma unroll
+            for (int c = 0; c < 16; ++c) {
+              const int rel = F::pos(t, c) - d.by0;
+              if ((!MID || (c >= 4 && c < 12)) && valid && (unsigned)rel < (unsigned)d.bys)
+                yb[(long long)rel * n + col] = v[c];
+            }
+          }
+          return true;
+        };
+        bool plane_ok;
+        if constexpr (HALF) {
+          if (d.by0 >= P / 4 && d.by0 + d.bys <= 3 * P / 4)
+            plane_ok = plane(std::true_type{});
+          else
+            plane_ok = plane(std::false_type{});
+        } else {
+          plane_ok = plane(std::false_type{});
         }
+        if (!plane_ok) return false;
       }
     }
     if constexpr (ADJ) {
