@@ -25,6 +25,8 @@ def main(src, dst):
     for p in json.loads(str(d["problems"])):
         key = p["key"]
         h = Holo(p["n"], p["K"], p["J"], p["wavelength"], p["pixel"], p["Z"], p["z"], pad=p["P"])
+        if key + "_s" in d:  # probe shifts first: the plane boxes follow from them
+            h.set_probe_shifts(d[key + "_s"].astype(np.float32))
         h.set_shifts(d[key + "_t"].astype(np.float32))
         h.set_data(torch.from_numpy(d[key + "_sqrt_d"].astype(np.float32)).cuda(),
                    torch.from_numpy(d[key + "_sqrt_dref"].astype(np.float32)).cuda())
