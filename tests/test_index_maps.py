@@ -123,3 +123,26 @@ def test_last_round_split_covers_every_item_once(ngroups, nblk, per):
             i0 = titems * bid // nblk
             slot = tg - i0 // per
             assert any(s[0] == rounds * nblk + tg and s[3] == slot for s in plan[bid])
+
+
+def test_host_call_parts_partition_every_chunk():
+    """holo_gradient_host's split of a chunk into parts (weights of the first `parts` entries,
+    rounded prefix sums): consecutive, non-empty parts covering [0, nk) for every nk up to
+    2000, with the constants read from the library source."""
+    import os
+    import re
+    src = open(os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))),
+                            "paper_2407_20304_gb300", "csrc", "holo_api.cu")).read()
+    n_parts = int(re.search(r"constexpr int kHostParts = (\d+);", src).group(1))
+    min_part = int(re.search(r"constexpr int kHostMinPart = (\d+);", src).group(1))
+    weights = [int(x) for x in re.search(r"kHostWeights\[kHostParts\] = \{([^}]*)\}", src)
+               .group(1).split(",")]
+    assert len(weights) == n_parts
+    for nk in range(1, 2001):
+        parts = min(n_parts, nk // min_part) if nk >= 2 * min_part else 1
+        if parts == 1:
+            continue
+        wsum = sum(weights[:parts])
+        bound = [(nk * sum(weights[:p]) + wsum // 2) // wsum for p in range(parts)] + [nk]
+        assert bound[0] == 0 and bound[-1] == nk
+        assert all(bound[p + 1] > bound[p] for p in range(parts)), nk
